@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the coined-walk spatial search hot path on one B300.
+
+Workload (default): 1024 x 1024 torus (2^20 vertices, 4 * 2^20 arcs), Grover
+coin with -I on one seeded marked vertex, flip-flop shift, uniform initial
+state over all arcs, 3000 walk steps with the marked-vertex probability
+recorded after every step, per-vertex probabilities (double sums) at the end.
+One bench "step" is that whole run.  The metric is walk-step arc updates per
+second: num_arcs * 3000 / (time of one run).  The headline runs in complex128;
+the complex64 mixed form (fp32 amplitudes, fp64 probability sums) is reported
+beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs its own replica of the workload (the
+walks are independent; there is no collective on the data path) and `value`
+is the total arc updates of all ranks over the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+L = 1024
+WALK_STEPS = 3000
+MARK_SEED = 2
+METRIC = "walk-step arc updates/s"
+UNIT = "arc-updates/s"
+
+# DRAM bytes per launch of the coin+shift kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
+# measured on; a changed kernel reports null until it is measured again.
+TRAFFIC = {}
+
+
+def workload():
+    n, eu, ev = synth.torus(L)
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    m = synth.seeded_vertex(MARK_SEED, n)
+    return n, eu, ev, row_ptr, col, m
+
+
+def coin_shift_bytes(n, arcs, esz):
+    """Algorithmic bytes of one coin+shift launch: read psi and rev, write psi, read row_ptr."""
+    return arcs * (2 * esz + 4) + 4 * (n + 1)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, f[2:6]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n, eu, ev, m, budget_s=12.0):
+    """The FP64 oracle, untuned, on the host cores: walk steps of the same search."""
+    import oracle
+    cores = oracle.threads()
+    ar = oracle.Arcs(n, eu, ev)
+    psi = synth.uniform_state(ar.num_arcs)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        psi = oracle.coined_evolve(ar, psi, 5, marked=[m])
+        done += 5
+    el = time.perf_counter() - t0
+    return {"value": ar.num_arcs * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d walk steps of the 1024x1024 torus search (complex128 oracle, OpenMP)" % done}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    n, eu, ev, _, _, m = workload()
+    cores = oracle.threads()
+    ar = oracle.Arcs(n, eu, ev)
+    psi = synth.uniform_state(ar.num_arcs)
+    per = 4   # walk steps per bench step (bounded sample of the 3000-step run)
+    for _ in range(args.warmup):
+        psi = oracle.coined_evolve(ar, psi, per, marked=[m])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        psi = oracle.coined_evolve(ar, psi, per, marked=[m])
+    el = time.perf_counter() - t0
+    value = ar.num_arcs * per * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "torus1024_search", "n": n, "arcs": ar.num_arcs,
+                       "walk_steps_per_step": per, "marked": m, "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d walk steps per bench step of the 1024x1024 torus search" % per},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2406_08186_b300 as hw
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, eu, ev, row_ptr, col, m = workload()
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    arcs = G.num_arcs
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def make(dt):
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        psi0 = torch.full((arcs,), 1.0 / math.sqrt(arcs), dtype=cdt, device="cuda")
+        return dict(dt=dt, psi0=psi0, out=torch.empty_like(psi0),
+                    rec=torch.empty(WALK_STEPS, dtype=torch.float64, device="cuda"),
+                    prob=torch.empty(n, dtype=torch.float64, device="cuda"),
+                    norm=torch.empty(1, dtype=torch.float64, device="cuda"))
+
+    launches_per_run = WALK_STEPS + 1 + 1 + 2   # steps, final record, probability, norm (2)
+
+    def run(b, ev_evolve=None):
+        if ev_evolve:
+            ev_evolve[0].record(stream)
+        hw.hw_coined_evolve(G, hw.HW_COIN_GROVER, [m], b["dt"], 1, WALK_STEPS, b["psi0"], b["out"],
+                            b["rec"], stream=stream)
+        if ev_evolve:
+            ev_evolve[1].record(stream)
+        hw.hw_probability(G, n, b["dt"], 1, b["out"], b["prob"], b["norm"], stream=stream)
+
+    def timed(b):
+        for _ in range(args.warmup):
+            run(b)
+        torch.cuda.synchronize()
+        barrier()
+        total = evolve = 0.0
+        pairs = []
+        for _ in range(args.steps):
+            flush.zero_()       # L2 flush outside the timed events
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            run(b, (e[1], e[2]))
+            e[3].record(stream)
+            pairs.append(e)
+        torch.cuda.synchronize()
+        barrier()
+        for e in pairs:
+            total += e[0].elapsed_time(e[3]) / 1e3
+            evolve += e[1].elapsed_time(e[2]) / 1e3
+        return total, evolve
+
+    peak, peak_src = measured_peaks()
+    b128 = make(hw.HW_C128)
+    with Clocks(local) as clk:
+        t128, ev128 = timed(b128)
+    clocks = clk.summary()
+    b64 = make(hw.HW_C64)
+    t64, ev64 = timed(b64)
+
+    # correctness guard on the measured buffers: unit norm, record consistent
+    norm128 = float(b128["norm"].item())
+    norm64 = float(b64["norm"].item())
+    if abs(norm128 - 1) > 1e-10 or abs(norm64 - 1) > 1e-3:
+        raise RuntimeError("norm check failed: %r %r" % (norm128, norm64))
+
+    # end to end through the C ABI from pinned host buffers
+    host_psi = b128["psi0"].cpu().pin_memory()
+    host_prob = torch.empty(n, dtype=torch.float64).pin_memory()
+    host_rec = torch.empty(WALK_STEPS, dtype=torch.float64).pin_memory()
+
+    def run_e2e():
+        b128["psi0"].copy_(host_psi, non_blocking=True)
+        run(b128)
+        host_prob.copy_(b128["prob"], non_blocking=True)
+        host_rec.copy_(b128["rec"], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        run_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t_e2e = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run_e2e()
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e += e0.elapsed_time(e1) / 1e3
+    barrier()
+
+    def allmax(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t128, t64, t_e2e = allmax(t128), allmax(t64), allmax(t_e2e)
+    work = arcs * WALK_STEPS * args.steps * world
+    value = work / t128
+    per_launch128 = ev128 / (args.steps * WALK_STEPS)
+    per_launch64 = ev64 / (args.steps * WALK_STEPS)
+    bytes128 = coin_shift_bytes(n, arcs, 16)
+    bytes64 = coin_shift_bytes(n, arcs, 8)
+    src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2406_08186_b300", "csrc", "coined.cu"),
+                                 "rb").read()).hexdigest()
+    ach128 = bytes128 / per_launch128 / 1e9
+    ach64 = bytes64 / per_launch64 / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t128 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "torus1024_search", "n": n, "arcs": arcs, "walk_steps": WALK_STEPS,
+                   "coin": "grover", "marked": m, "state": "complex128", "record": "p_m(t) every step",
+                   "l2": "256 MiB written between timed steps; working set 151 MB > L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "k_coined_step<double,grover>",
+                     "achieved": ach128, "peak": peak, "unit": "GB/s", "frac": ach128 / peak,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
+                     "bytes_per_launch": bytes128, "launch_us": per_launch128 * 1e6,
+                     "traffic": TRAFFIC.get(("c128", src_hash))},
+        "c64_mixed": {"value": work / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.steps,
+                      "dtype": "f32 (fp64 probability sums)",
+                      "roofline": {"bound": "hbm", "achieved": ach64, "peak": peak, "unit": "GB/s",
+                                   "frac": ach64 / peak, "bytes_per_launch": bytes64,
+                                   "launch_us": per_launch64 * 1e6,
+                                   "traffic": TRAFFIC.get(("c64", src_hash)),
+                                   "note": "working set 88 MB fits in L2"}},
+        "e2e": {"value": work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": arcs * 16,
+                "d2h_bytes_per_step": n * 8 + WALK_STEPS * 8},
+        "gpu_launches": launches_per_run * args.steps,
+        "clocks": clocks,
+        "norm_after": {"c128": norm128, "c64": norm64},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, eu, ev, m)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.free()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_profile(args):
+    """A few launches of one kernel on the bench workload, for ncu captures."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    n, eu, ev, row_ptr, col, m = workload()
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
+    cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+    psi0 = torch.full((G.num_arcs,), 1.0 / math.sqrt(G.num_arcs), dtype=cdt, device="cuda")
+    out = torch.empty_like(psi0)
+    rec = torch.empty(args.profile_steps, dtype=torch.float64, device="cuda")
+    hw.hw_coined_evolve(G, hw.HW_COIN_GROVER, [m], dt, 1, args.profile_steps, psi0, out, rec)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "steps": args.profile_steps,
+                      "p_m_last": float(rec[-1].item())}))
+    G.free()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["coined_c128", "coined_c64"],
+                    help="run a few coin+shift launches of the workload and exit (for ncu)")
+    ap.add_argument("--profile-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * hiperwalk_b300.h -- C ABI of the B300 quantum-walk evolution library.
+ *
+ * The operations follow Motta, Bezerra, Santos, Portugal, "Hiperwalk:
+ * Simulation of Quantum Walks with Heterogeneous High-Performance Computing"
+ * (arXiv 2406.08186):
+ *   Sec. 3.1  continuous-time walk: H = -gamma A - sum_{v in M} |v><v|,
+ *             U(t) = e^{-iHt}, |psi(t)> = U(t)|psi(0)>, probability |<v|psi(t)>|^2
+ *   Sec. 3.2  coined walk: U = S C, flip-flop shift S|v,w> = |w,v>, Grover coin
+ *             C|v,w> = sum_{v' in N(v)} (2/d(v) - delta_{w,v'}) |v,v'>,
+ *             |psi(t)> = U^t |psi(0)>, p_v(t) = sum_{w in N(v)} |<v,w|psi(t)>|^2;
+ *             the basis is the arc list sorted by tail, then by head.
+ *
+ * General conventions (every entry point):
+ *   - Every call returns an hw_status; on failure hw_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread).
+ *   - Arguments are validated on the host before anything is launched; a
+ *     call that fails validation launches nothing and writes nothing.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) of the CURRENT device, which
+ *     must be the device the graph was created on.  Host pointers are read
+ *     before the call returns; device buffers must stay alive until the
+ *     stream has executed the work.
+ *   - Device buffers (psi, U, record, prob) are allocated and owned by the
+ *     caller; the library never frees them.  Complex numbers are interleaved
+ *     (re, im): HW_C64 = 2 x float (8 bytes), HW_C128 = 2 x double (16 bytes).
+ *     Device buffers must be aligned to their element size (16 bytes for
+ *     HW_C128, 8 for HW_C64 and double).
+ *   - Batched buffers are batch-innermost: element (i, b) is at i*batch + b.
+ *   - No call waits without bound: device-side waits carry a time limit and
+ *     report HW_ETIMEDOUT.
+ */
+#ifndef HIPERWALK_B300_H
+#define HIPERWALK_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HW_OK = 0,
+    HW_EINVAL = -1,         /* invalid argument or graph */
+    HW_ENOMEM = -2,         /* device or host allocation failed */
+    HW_ECUDA = -3,          /* a CUDA runtime call or launch failed */
+    HW_ETIMEDOUT = -4,      /* a device-side wait ran out of time */
+    HW_EUNSUPPORTED = -5    /* valid request outside this build's limits */
+} hw_status;
+
+typedef enum { HW_C64 = 1, HW_C128 = 2 } hw_dtype;
+
+/* Grover (Sec. 3.2) or Fourier: C[j][k] = omega^(jk)/sqrt(d), omega = e^{2 pi i/d},
+ * j, k = positions of the vertex's arcs in basis order.  A marked vertex's coin
+ * block is -I for both (the search oracle). */
+typedef enum { HW_COIN_GROVER = 0, HW_COIN_FOURIER = 1 } hw_coin;
+
+typedef struct hw_graph hw_graph;   /* opaque; owns the device CSR and index tables */
+
+/* Optional knobs.  Pass NULL for defaults, or a struct set up by hw_opts_init. */
+typedef struct hw_opts {
+    int32_t record_stride;     /* coined/CTQW record: one entry every `stride` steps (>= 1, default 1) */
+    int32_t taylor_degree;     /* hw_ctqw_expm: Taylor degree m (0 = chosen for < 2^-60 truncation) */
+    int32_t taylor_squarings;  /* hw_ctqw_expm: squarings s (-1 = chosen so ||H dt||_1 / 2^s <= 1/2) */
+    int32_t gemm_slices;       /* hw_ctqw_expm, HW_C64: bf16 slices per fp32 operand (2 or 3; 0 = 3) */
+    int32_t tile;              /* batched coined kernel: rows per CTA (0 = autotuned) */
+    int32_t reserved[3];
+} hw_opts;
+
+/* Fill `opts` with the defaults. */
+void hw_opts_init(hw_opts *opts);
+
+/*
+ * hw_graph_csr -- build the arc basis of an undirected simple graph (Sec. 3.2).
+ *   n        number of vertices (>= 1)
+ *   row_ptr  HOST int64[n+1], row_ptr[0] = 0, non-decreasing
+ *   col_idx  HOST int32[row_ptr[n]], the adjacency matrix's column indices, any
+ *            order inside a row
+ * The matrix must be the adjacency matrix of a simple undirected graph:
+ * symmetric, 0/1, zero diagonal.  Degree-0 vertices are allowed (their arc
+ * block is empty).  The library sorts each row (arc (v, w) then sits at
+ * position row_ptr[v] + rank of w among v's neighbours), builds the
+ * arc-reversal table rev[a] (the flip-flop shift as an index map:
+ * S|v,w> = |w,v> sends arc a to arc rev[a]) and uploads both to the current
+ * device.  The call synchronises `stream` before returning.
+ *   *out     receives the graph handle, owned by the caller until hw_graph_free.
+ * Errors: HW_EINVAL (self-loop, repeated entry, asymmetric, index out of
+ * range, malformed row_ptr), HW_EUNSUPPORTED (2|E| >= 2^31), HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       void *stream, hw_graph **out);
+
+/*
+ * hw_graph_arcs_host -- the same arc basis as hw_graph_csr, computed on the
+ * host only (no device is touched).  Same input rules and errors.
+ *   row_ptr_out  HOST int32[n+1]           (may be NULL)
+ *   head_out     HOST int32[row_ptr[n]]    heads, sorted inside each row (may be NULL)
+ *   rev_out      HOST int32[row_ptr[n]]    reversal table (may be NULL)
+ * Buffers are caller-owned.
+ */
+hw_status hw_graph_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                             int32_t *row_ptr_out, int32_t *head_out, int32_t *rev_out);
+
+/* Release the graph's device and host memory.  NULL is accepted.  The caller
+ * must make sure no enqueued work still uses the graph. */
+hw_status hw_graph_free(hw_graph *g);
+
+/*
+ * Read-only views of the graph (any output pointer may be NULL):
+ *   n, num_arcs         vertex and arc counts
+ *   d_row_ptr           DEVICE int32[n+1], first arc of each vertex
+ *   d_head              DEVICE int32[num_arcs], head of each arc (sorted inside rows)
+ *   d_rev               DEVICE int32[num_arcs], index of the reversed arc
+ * The views live as long as the graph.
+ */
+hw_status hw_graph_info(const hw_graph *g, int64_t *n, int64_t *num_arcs,
+                        const int32_t **d_row_ptr, const int32_t **d_head,
+                        const int32_t **d_rev);
+
+/*
+ * hw_coined_evolve -- |psi(t)> = (S C)^steps |psi(0)> (Sec. 3.2), coin first,
+ * then the flip-flop shift, in every step.
+ *   coin, marked     coin kind; HOST int32[n_marked] marked vertex ids (any order,
+ *                    no repeats; n_marked = 0 allowed): their coin block is -I
+ *   dt               HW_C128 or HW_C64 (amplitudes and coin arithmetic in that
+ *                    precision; probabilities are always summed in double)
+ *   batch            number of independent states sharing the graph (>= 1)
+ *   psi_in           DEVICE [num_arcs][batch] initial states
+ *   psi_out          DEVICE [num_arcs][batch] final states; may equal psi_in
+ *                    (in place), must not overlap it otherwise
+ *   record           DEVICE double[steps / stride][batch] or NULL: entry
+ *                    (k-1, b) is the total probability on the marked vertices
+ *                    of state b after step k*stride.  Needs n_marked >= 1.
+ * Scratch: one state-sized buffer (and a small record buffer) is taken from
+ * the stream-ordered allocator and returned on the same stream.
+ * Errors: HW_EINVAL, HW_EUNSUPPORTED (Fourier coin on a vertex of degree > 4096),
+ * HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marked,
+                           int32_t n_marked, hw_dtype dt, int32_t batch, int64_t steps,
+                           const void *psi_in, void *psi_out, double *record,
+                           const hw_opts *opts, void *stream);
+
+/*
+ * hw_ctqw_expm -- U = e^{-i H time} with H = -gamma A - sum_{m in M} |m><m|
+ * (Sec. 3.1), dense, by a truncated Taylor series with scaling and squaring:
+ * U = (sum_{k<=m} (-i H time/2^s)^k / k!)^(2^s).
+ *   U_out    DEVICE [n][n] row-major complex (dt), caller-owned
+ *   dt       HW_C128: products in double precision;
+ *            HW_C64: products of the powers of H on the tensor cores from
+ *            split-bf16 operands with fp32 accumulation; Taylor sums and
+ *            squarings in double; U rounded to complex64 at the end.
+ * Scratch: a few n x n real buffers from the stream-ordered allocator.
+ * Errors: HW_EINVAL, HW_EUNSUPPORTED (n > 32768), HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t *marked,
+                       int32_t n_marked, double time, hw_dtype dt, void *U_out,
+                       const hw_opts *opts, void *stream);
+
+/*
+ * hw_ctqw_evolve -- psi_out = U^steps psi_in (Sec. 3.1: |psi(k dt)> = U(dt)^k |psi(0)>).
+ *   U        DEVICE [n][n] row-major complex (dt), e.g. from hw_ctqw_expm
+ *   psi_in   DEVICE [n][batch]; psi_out DEVICE [n][batch], may equal psi_in
+ *   marked   HOST int32[n_marked]; record as in hw_coined_evolve
+ *            (probability |<m|psi>|^2 summed over the marked vertices).
+ * Errors: HW_EINVAL, HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32_t batch, int64_t steps,
+                         const void *psi_in, void *psi_out, const int32_t *marked,
+                         int32_t n_marked, double *record, const hw_opts *opts, void *stream);
+
+/*
+ * hw_probability -- per-vertex probabilities, summed in double precision.
+ *   g != NULL: coined walk, p_v = sum_{w in N(v)} |<v,w|psi>|^2 (Sec. 3.2);
+ *              psi is DEVICE [num_arcs][batch]; n is ignored.
+ *   g == NULL: continuous-time walk, p_v = |<v|psi>|^2 (Sec. 3.1); psi is
+ *              DEVICE [n][batch].
+ *   prob_out  DEVICE double[n][batch] (may be NULL if only the norm is wanted)
+ *   norm_out  DEVICE double[batch] or NULL: sum_v p_v per state
+ * Errors: HW_EINVAL, HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_probability(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batch,
+                         const void *psi, double *prob_out, double *norm_out, void *stream);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *hw_last_error(void);
+
+/* Library version string. */
+const char *hw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIPERWALK_B300_H */

@@ -1,0 +1,240 @@
+"""Python binding of libhiperwalk_b300 (B300 quantum-walk evolution library).
+
+Argument marshalling only: every function here forwards to the C ABI declared
+in include/hiperwalk_b300.h, whose kernels do all the work.  Device buffers are
+torch CUDA tensors (complex64 / complex128 / float64, contiguous); host inputs
+are numpy arrays.  There is no CPU fallback: if the compiled library is
+missing the first call raises ``ImportError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhiperwalk_b300.so")
+
+HW_OK, HW_EINVAL, HW_ENOMEM, HW_ECUDA, HW_ETIMEDOUT, HW_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+HW_C64, HW_C128 = 1, 2
+HW_COIN_GROVER, HW_COIN_FOURIER = 0, 1
+
+STATUS_NAMES = {0: "HW_OK", -1: "HW_EINVAL", -2: "HW_ENOMEM", -3: "HW_ECUDA",
+                -4: "HW_ETIMEDOUT", -5: "HW_EUNSUPPORTED"}
+
+# every entry point the header declares
+EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free", "hw_graph_info",
+           "hw_coined_evolve", "hw_ctqw_expm", "hw_ctqw_evolve", "hw_probability",
+           "hw_last_error", "hw_version")
+
+
+class HWError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+class hw_opts(ctypes.Structure):
+    _fields_ = [("record_stride", ctypes.c_int32), ("taylor_degree", ctypes.c_int32),
+                ("taylor_squarings", ctypes.c_int32), ("gemm_slices", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded shared library (loaded on first use)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libhiperwalk_b300.so is not built; run "
+                              "`python -m paper_2406_08186_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        st = ctypes.c_int
+        L.hw_opts_init.argtypes = [ctypes.POINTER(hw_opts)]
+        L.hw_opts_init.restype = None
+        L.hw_graph_csr.argtypes = [i64, P, P, P, ctypes.POINTER(P)]
+        L.hw_graph_csr.restype = st
+        L.hw_graph_arcs_host.argtypes = [i64, P, P, P, P, P]
+        L.hw_graph_arcs_host.restype = st
+        L.hw_graph_free.argtypes = [P]
+        L.hw_graph_free.restype = st
+        L.hw_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                    ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]
+        L.hw_graph_info.restype = st
+        L.hw_coined_evolve.argtypes = [P, st, P, i32, st, i32, i64, P, P, P, ctypes.POINTER(hw_opts), P]
+        L.hw_coined_evolve.restype = st
+        L.hw_ctqw_expm.argtypes = [P, d, P, i32, d, st, P, ctypes.POINTER(hw_opts), P]
+        L.hw_ctqw_expm.restype = st
+        L.hw_ctqw_evolve.argtypes = [P, i64, st, i32, i64, P, P, P, i32, P, ctypes.POINTER(hw_opts), P]
+        L.hw_ctqw_evolve.restype = st
+        L.hw_probability.argtypes = [P, i64, st, i32, P, P, P, P]
+        L.hw_probability.restype = st
+        L.hw_last_error.argtypes = []
+        L.hw_last_error.restype = ctypes.c_char_p
+        L.hw_version.argtypes = []
+        L.hw_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != HW_OK:
+        raise HWError(status, lib().hw_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+_CPLX = {HW_C64: "complex64", HW_C128: "complex128"}
+
+
+def _dev(t, kind=None):
+    """Device pointer of a contiguous CUDA tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if kind is not None and str(t.dtype).split(".")[-1] != kind:
+        raise ValueError("expected dtype %s, got %s" % (kind, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_i32(a):
+    if a is None:
+        return None, 0
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.size
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, hw_opts):
+        return ctypes.byref(opts)
+    o = hw_opts_init()
+    for k, v in dict(opts).items():
+        setattr(o, k, v)
+    return ctypes.byref(o)
+
+
+def hw_opts_init() -> hw_opts:
+    o = hw_opts()
+    lib().hw_opts_init(ctypes.byref(o))
+    return o
+
+
+def hw_last_error() -> str:
+    return lib().hw_last_error().decode()
+
+
+def hw_version() -> str:
+    return lib().hw_version().decode()
+
+
+class Graph:
+    """Owner of an ``hw_graph`` handle (freed by ``free()`` or garbage collection)."""
+
+    def __init__(self, handle, n, num_arcs):
+        self.handle = handle
+        self.n = n
+        self.num_arcs = num_arcs
+
+    def free(self):
+        if self.handle is not None and _lib is not None:
+            _lib.hw_graph_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if self.handle is None:
+            raise ValueError("graph already freed")
+        return self.handle
+
+
+def hw_graph_csr(n: int, row_ptr, col_idx, stream=None) -> Graph:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().hw_graph_csr(int(n), rp.ctypes.data_as(ctypes.c_void_p),
+                              ci.ctypes.data_as(ctypes.c_void_p), _stream(stream), ctypes.byref(h)))
+    g = Graph(h, int(n), 0)
+    g.num_arcs = hw_graph_info(g)["num_arcs"]
+    return g
+
+
+def hw_graph_arcs_host(n: int, row_ptr, col_idx):
+    """(row_ptr int32[n+1], head int32[2E], rev int32[2E]) computed by the library on the host."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    m = int(rp[-1]) if rp.size else 0
+    rp_out = np.zeros(int(n) + 1, dtype=np.int32)
+    head = np.zeros(max(m, 0), dtype=np.int32)
+    rev = np.zeros(max(m, 0), dtype=np.int32)
+    _check(lib().hw_graph_arcs_host(int(n), rp.ctypes.data_as(ctypes.c_void_p),
+                                    ci.ctypes.data_as(ctypes.c_void_p),
+                                    rp_out.ctypes.data_as(ctypes.c_void_p),
+                                    head.ctypes.data_as(ctypes.c_void_p),
+                                    rev.ctypes.data_as(ctypes.c_void_p)))
+    return rp_out, head, rev
+
+
+def hw_graph_free(g: Graph):
+    g.free()
+
+
+def hw_graph_info(g: Graph) -> dict:
+    n, m = ctypes.c_int64(), ctypes.c_int64()
+    rp, hd, rv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().hw_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(rp),
+                               ctypes.byref(hd), ctypes.byref(rv)))
+    return {"n": n.value, "num_arcs": m.value, "d_row_ptr": rp.value, "d_head": hd.value,
+            "d_rev": rv.value}
+
+
+def hw_coined_evolve(g: Graph, coin: int, marked, dt: int, batch: int, steps: int, psi_in, psi_out,
+                     record=None, opts=None, stream=None):
+    m, nm = _host_i32(marked)
+    _check(lib().hw_coined_evolve(g, int(coin), None if m is None else m.ctypes.data_as(ctypes.c_void_p),
+                                  nm, int(dt), int(batch), int(steps), _dev(psi_in, _CPLX[dt]),
+                                  _dev(psi_out, _CPLX[dt]), _dev(record, "float64"), _opts(opts),
+                                  _stream(stream)))
+
+
+def hw_ctqw_expm(g: Graph, gamma: float, marked, time: float, dt: int, U_out, opts=None, stream=None):
+    m, nm = _host_i32(marked)
+    _check(lib().hw_ctqw_expm(g, float(gamma), None if m is None else m.ctypes.data_as(ctypes.c_void_p),
+                              nm, float(time), int(dt), _dev(U_out, _CPLX[dt]), _opts(opts),
+                              _stream(stream)))
+
+
+def hw_ctqw_evolve(U, n: int, dt: int, batch: int, steps: int, psi_in, psi_out, marked=None,
+                   record=None, opts=None, stream=None):
+    m, nm = _host_i32(marked)
+    _check(lib().hw_ctqw_evolve(_dev(U, _CPLX[dt]), int(n), int(dt), int(batch), int(steps),
+                                _dev(psi_in, _CPLX[dt]), _dev(psi_out, _CPLX[dt]),
+                                None if m is None else m.ctypes.data_as(ctypes.c_void_p), nm,
+                                _dev(record, "float64"), _opts(opts), _stream(stream)))
+
+
+def hw_probability(g, n: int, dt: int, batch: int, psi, prob_out=None, norm_out=None, stream=None):
+    _check(lib().hw_probability(g, int(n), int(dt), int(batch), _dev(psi, _CPLX[dt]),
+                                _dev(prob_out, "float64"), _dev(norm_out, "float64"), _stream(stream)))

@@ -1,0 +1,232 @@
+// Entry points of the C ABI: validation, scratch management and dispatch to
+// the kernels.  Nothing here computes amplitudes; every step of a walk runs
+// in the CUDA kernels of coined.cu, prob.cu and ctqw.cu.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace {
+thread_local std::string t_err;
+}
+
+hw_status hw_fail(hw_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+hw_status hw_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return HW_OK;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation)
+        return hw_fail(HW_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return hw_fail(HW_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void hw_clear_error() { t_err.clear(); }
+
+extern "C" const char *hw_last_error(void) { return t_err.c_str(); }
+
+extern "C" const char *hw_version(void) { return "hiperwalk_b300 0.1 (sm_103a)"; }
+
+extern "C" void hw_opts_init(hw_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->record_stride = 1;
+    o->taylor_degree = 0;
+    o->taylor_squarings = -1;
+    o->gemm_slices = 0;
+    o->tile = 0;
+}
+
+hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaStream_t st,
+                      MarkedList *out)
+{
+    std::memset(out, 0, sizeof *out);
+    if (n_marked == 0) return HW_OK;
+    std::vector<int32_t> m(marked, marked + n_marked);
+    std::sort(m.begin(), m.end());
+    for (int32_t i = 0; i < n_marked; ++i) {
+        if (m[i] < 0 || m[i] >= n) return hw_fail(HW_EINVAL, "marked vertex %d out of range", m[i]);
+        if (i && m[i] == m[i - 1]) return hw_fail(HW_EINVAL, "marked vertex %d repeated", m[i]);
+    }
+    out->n = n_marked;
+    if (n_marked <= kInlineMarked) {
+        std::copy(m.begin(), m.end(), out->inl);
+        return HW_OK;
+    }
+    int32_t *d = nullptr;
+    hw_status s = hw_cuda(cudaMallocAsync((void **)&d, sizeof(int32_t) * n_marked, st),
+                          "cudaMallocAsync(marked)");
+    if (s != HW_OK) return s;
+    // the host vector dies on return, so this copy must have completed by then
+    s = hw_cuda(cudaMemcpyAsync(d, m.data(), sizeof(int32_t) * n_marked, cudaMemcpyHostToDevice, st),
+                "upload marked");
+    if (s == HW_OK) s = hw_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (s != HW_OK) { cudaFreeAsync(d, st); return s; }
+    out->dev = d;
+    return HW_OK;
+}
+
+void free_marked(MarkedList &m, cudaStream_t st)
+{
+    if (m.dev) cudaFreeAsync(const_cast<int32_t *>(m.dev), st);
+    m.dev = nullptr;
+}
+
+static hw_status check_device(const hw_graph *g)
+{
+    int dev = -1;
+    hw_status s = hw_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != HW_OK) return s;
+    if (dev != g->device)
+        return hw_fail(HW_EINVAL, "graph lives on device %d, current device is %d", g->device, dev);
+    return HW_OK;
+}
+
+namespace {
+// Scratch taken from the stream-ordered allocator; returned on the stream.
+struct Scratch {
+    cudaStream_t st;
+    void *p = nullptr;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    hw_status get(size_t bytes, const char *what)
+    {
+        return hw_cuda(cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st), what);
+    }
+    ~Scratch() { if (p) cudaFreeAsync(p, st); }
+};
+}  // namespace
+
+extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marked,
+                                      int32_t n_marked, hw_dtype dt, int32_t batch, int64_t steps,
+                                      const void *psi_in, void *psi_out, double *record,
+                                      const hw_opts *opts, void *stream)
+{
+    hw_clear_error();
+    if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
+    if (coin != HW_COIN_GROVER && coin != HW_COIN_FOURIER) return hw_fail(HW_EINVAL, "unknown coin");
+    if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
+    if (steps < 0) return hw_fail(HW_EINVAL, "steps must be >= 0");
+    if (n_marked < 0 || (n_marked > 0 && !marked)) return hw_fail(HW_EINVAL, "bad marked list");
+    if (!psi_in || !psi_out) return hw_fail(HW_EINVAL, "psi_in/psi_out is NULL");
+    const size_t esz = cplx_bytes(dt);
+    if ((uintptr_t)psi_in % esz || (uintptr_t)psi_out % esz)
+        return hw_fail(HW_EINVAL, "state buffers must be aligned to %zu bytes", esz);
+    const int stride = opts ? opts->record_stride : 1;
+    if (stride < 1) return hw_fail(HW_EINVAL, "record_stride must be >= 1");
+    if (record && n_marked == 0) return hw_fail(HW_EINVAL, "record needs at least one marked vertex");
+    if (record && (uintptr_t)record % 8) return hw_fail(HW_EINVAL, "record must be 8-byte aligned");
+    if (coin == HW_COIN_FOURIER && g->max_degree > 4096)
+        return hw_fail(HW_EUNSUPPORTED, "Fourier coin limited to degree <= 4096 (max degree %d)",
+                       g->max_degree);
+    const size_t bytes = size_t(g->num_arcs) * batch * esz;
+    const char *ip = static_cast<const char *>(psi_in);
+    const char *op = static_cast<const char *>(psi_out);
+    if (ip != op && ip < op + bytes && op < ip + bytes)
+        return hw_fail(HW_EINVAL, "psi_in and psi_out overlap without being equal");
+    hw_status s = check_device(g);
+    if (s != HW_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    if (steps == 0 || g->num_arcs == 0) {
+        if (ip != op && bytes)
+            if ((s = hw_cuda(cudaMemcpyAsync(psi_out, psi_in, bytes, cudaMemcpyDeviceToDevice, st),
+                             "copy")) != HW_OK)
+                return s;
+        if (record && steps >= stride) {
+            // no arcs: every marked probability is zero
+            if ((s = hw_cuda(cudaMemsetAsync(record, 0, sizeof(double) * (steps / stride) * batch, st),
+                             "memset record")) != HW_OK)
+                return s;
+        }
+        return HW_OK;
+    }
+
+    MarkedList mk;
+    if ((s = make_marked(marked, n_marked, g->n, st, &mk)) != HW_OK) return s;
+    struct FreeMarked {
+        MarkedList &m; cudaStream_t st;
+        ~FreeMarked() { free_marked(m, st); }
+    } release_marked{mk, st};
+
+    const int64_t slots = record ? steps / stride : 0;
+    Scratch tmp(st), recbuf(st);
+    if ((s = tmp.get(bytes, "cudaMallocAsync(state scratch)")) != HW_OK) return s;
+    double *rec_part = nullptr;
+    if (slots) {
+        if (n_marked == 1) {
+            rec_part = record;  // one marked vertex: partials are the record itself
+        } else {
+            if ((s = recbuf.get(sizeof(double) * slots * n_marked * batch, "cudaMallocAsync(record)")) != HW_OK)
+                return s;
+            rec_part = static_cast<double *>(recbuf.p);
+        }
+    }
+
+    // Ping-pong so that the last step lands in psi_out: step k (1-based) writes
+    // psi_out when (steps - k) is even and the scratch otherwise.  In place
+    // with an odd step count, step 1 would read and write psi_out, so it reads
+    // a scratch copy of the input instead.
+    void *P = psi_out, *T = tmp.p;
+    const void *src = psi_in;
+    if (ip == op && steps % 2 == 1) {
+        if ((s = hw_cuda(cudaMemcpyAsync(T, psi_in, bytes, cudaMemcpyDeviceToDevice, st), "copy")) != HW_OK)
+            return s;
+        src = T;
+    }
+    for (int64_t k = 1; k <= steps; ++k) {
+        void *dst = ((steps - k) % 2 == 0) ? P : T;
+        CoinedStep cs;
+        cs.in = src;
+        cs.out = dst;
+        cs.marked = mk;
+        cs.rec_part = rec_part;
+        cs.rec_slot = (slots && (k - 1) >= stride && (k - 1) % stride == 0) ? (k - 1) / stride - 1 : -1;
+        s = (batch == 1) ? launch_coined_step(g, dt, coin, cs, st)
+                         : launch_coined_step_batched(g, dt, coin, batch, cs, opts ? opts->tile : 0, st);
+        if (s != HW_OK) return s;
+        src = dst;
+    }
+    if (slots && steps % stride == 0) {
+        s = launch_marked_prob(g->d_row_ptr, dt, batch, psi_out, mk,
+                               rec_part + (slots - 1) * n_marked * batch, st);
+        if (s != HW_OK) return s;
+    }
+    if (slots && n_marked > 1) {
+        if ((s = launch_record_finalize(rec_part, n_marked, slots, batch, record, st)) != HW_OK) return s;
+    }
+    return HW_OK;
+}
+
+extern "C" hw_status hw_probability(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batch,
+                                    const void *psi, double *prob_out, double *norm_out, void *stream)
+{
+    hw_clear_error();
+    if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
+    if (!psi) return hw_fail(HW_EINVAL, "psi is NULL");
+    if (!prob_out && !norm_out) return hw_fail(HW_EINVAL, "nothing to compute");
+    if ((uintptr_t)psi % cplx_bytes(dt)) return hw_fail(HW_EINVAL, "psi misaligned");
+    if (((uintptr_t)prob_out | (uintptr_t)norm_out) % 8) return hw_fail(HW_EINVAL, "outputs misaligned");
+    if (g) {
+        hw_status s = check_device(g);
+        if (s != HW_OK) return s;
+        n = g->n;
+    } else if (n < 1) {
+        return hw_fail(HW_EINVAL, "n must be >= 1");
+    }
+    return launch_probability(g, n, dt, batch, psi, prob_out, norm_out, static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,664 @@
+// Fused coin + flip-flop shift for the coined quantum walk (Sec. 3.2):
+//   psi'[rev[a]] = (C psi)[a],  C block-diagonal per vertex.
+// Grover:   (C psi)_a = 2 m_v - psi_a,  m_v = mean of psi over v's arcs
+// Fourier:  (C psi)_j = d^{-1/2} sum_k omega^{jk} psi_k, omega = e^{2 pi i/d}
+// Marked vertex: (C psi)_a = -psi_a.
+//
+// One read and one scattered write of the state per arc plus the 4-byte
+// reversal index: an HBM-bound stream.  A CTA owns a block of whole vertices
+// (at most kTileArcs arcs), stages their arcs in shared memory with coalesced
+// loads, forms the per-vertex coin in shared memory and scatters the results.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename R> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+
+template <typename V, typename R>
+__device__ __forceinline__ V mkv(R x, R y) { V r; r.x = x; r.y = y; return r; }
+
+// Fourier twiddles omega_d^r = (cos 2 pi r/d, sin 2 pi r/d) for d <= kTwMax,
+// at c_tw[d*(d-1)/2 + r] (filled once from the host); larger d use sincospi.
+constexpr int kTwMax = 32;
+__constant__ double2 c_tw[kTwMax * (kTwMax + 1) / 2];
+
+__device__ __forceinline__ void twiddle(int r, int d, double *s, double *c)
+{
+    if (d <= kTwMax) {
+        const double2 w = c_tw[d * (d - 1) / 2 + r];
+        *c = w.x;
+        *s = w.y;
+    } else {
+        sincospi(2.0 * double(r) / double(d), s, c);
+    }
+}
+__device__ __forceinline__ void twiddle(int r, int d, float *s, float *c)
+{
+    if (d <= kTwMax) {
+        const double2 w = c_tw[d * (d - 1) / 2 + r];
+        *c = float(w.x);
+        *s = float(w.y);
+    } else {
+        sincospif(2.0f * float(r) / float(d), s, c);
+    }
+}
+
+// index of v in the sorted marked list, or -1
+__device__ __forceinline__ int find_marked(const MarkedList &mk, int v)
+{
+    int lo = 0, hi = mk.n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int m = mk.dev ? __ldg(mk.dev + mid) : mk.inl[mid];
+        if (m == v) return mid;
+        if (m < v) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+// deterministic block sum (fixed shuffle tree, then fixed order over warps)
+template <typename T>
+__device__ __forceinline__ T block_sum(T x, T *red)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = x;
+    __syncthreads();
+    T t = 0;
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) t += red[i];
+    return t;
+}
+
+struct StepArgs {
+    const double *two_over_d;
+    const int32_t *row_ptr;
+    const int32_t *rev;
+    const int32_t *blk;
+    double *rec_part;
+    const void *in;
+    void *out;
+    int64_t rec_slot;
+    int32_t nblk;
+    MarkedList mk;
+};
+
+// A vertex with more arcs than a tile: one CTA, two passes over global memory.
+template <typename R, int COIN>
+__device__ void heavy_vertex(const StepArgs &a, int v, int a0, int d)
+{
+    using V = typename Cx<R>::T;
+    __shared__ R red_r[kThreads / 32];
+    __shared__ double red_d[kThreads / 32];
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+    const int mi = find_marked(a.mk, v);
+    if (mi >= 0 && a.rec_part && a.rec_slot >= 0) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const V p = in[a0 + i];
+            acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+        }
+        acc = block_sum(acc, red_d);
+        if (threadIdx.x == 0) a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+    }
+    if (mi >= 0) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const V p = in[a0 + i];
+            out[a.rev[a0 + i]] = mkv<V, R>(-p.x, -p.y);
+        }
+        return;
+    }
+    if (COIN == HW_COIN_GROVER) {
+        R sx = 0, sy = 0;
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const V p = in[a0 + i];
+            sx += p.x;
+            sy += p.y;
+        }
+        sx = block_sum(sx, red_r);
+        sy = block_sum(sy, red_r);
+        const R f = R(a.two_over_d[d]);
+        const R mx = sx * f, my = sy * f;
+        for (int i = threadIdx.x; i < d; i += blockDim.x) {
+            const V p = in[a0 + i];
+            out[a.rev[a0 + i]] = mkv<V, R>(mx - p.x, my - p.y);
+        }
+    } else {
+        const R scale = R(1) / sqrt(R(d));
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            R cx = 0, cy = 0;
+            for (int k = 0; k < d; ++k) {
+                R s, c;
+                twiddle(int((int64_t(j) * k) % d), d, &s, &c);
+                const V p = in[a0 + k];
+                cx += c * p.x - s * p.y;
+                cy += c * p.y + s * p.x;
+            }
+            out[a.rev[a0 + j]] = mkv<V, R>(cx * scale, cy * scale);
+        }
+    }
+}
+
+template <typename R, int COIN>
+__global__ void __launch_bounds__(kThreads) k_coined_step(StepArgs a)
+{
+    using V = typename Cx<R>::T;
+    constexpr int kPer = kTileArcs / kThreads;   // arcs per thread
+    __shared__ V s_psi[kTileArcs];
+    __shared__ V s_coef[kTileVerts];          // Grover: 2 m_v (0 if marked); Fourier: (marked, 0)
+    __shared__ int32_t s_rp[kTileVerts + 1];
+    __shared__ uint16_t s_tail[kTileArcs];
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+
+    for (int b = blockIdx.x; b < a.nblk; b += gridDim.x) {
+        const int v0 = a.blk[b], v1 = a.blk[b + 1];
+        const int nv = v1 - v0;
+        for (int i = threadIdx.x; i <= nv; i += blockDim.x) s_rp[i] = a.row_ptr[v0 + i];
+        __syncthreads();
+        const int a0 = s_rp[0];
+        const int na = s_rp[nv] - a0;
+        if (na > kTileArcs) {              // block-uniform branch: one heavy vertex
+            heavy_vertex<R, COIN>(a, v0, a0, na);
+            __syncthreads();
+            continue;
+        }
+        // all global loads of the tile first (state and reversal index)
+        V p[kPer];
+        int r[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * kThreads;
+            if (i < na) {
+                p[k] = in[a0 + i];
+                r[k] = a.rev[a0 + i];
+                s_psi[i] = p[k];
+            }
+        }
+        __syncthreads();
+        for (int lv = threadIdx.x; lv < nv; lv += blockDim.x) {
+            const int s = s_rp[lv] - a0, e = s_rp[lv + 1] - a0;
+            const int mi = find_marked(a.mk, v0 + lv);
+            for (int j = s; j < e; ++j) s_tail[j] = uint16_t(lv);
+            if (COIN == HW_COIN_GROVER) {
+                R sx = 0, sy = 0;
+                for (int j = s; j < e; ++j) { sx += s_psi[j].x; sy += s_psi[j].y; }
+                const R f = (mi < 0) ? R(a.two_over_d[e - s]) : R(0);
+                s_coef[lv] = mkv<V, R>(sx * f, sy * f);
+            } else {
+                s_coef[lv] = mkv<V, R>(mi >= 0 ? R(1) : R(0), R(0));
+            }
+            if (mi >= 0 && a.rec_part && a.rec_slot >= 0) {
+                double acc = 0.0;
+                for (int j = s; j < e; ++j)
+                    acc += double(s_psi[j].x) * double(s_psi[j].x) + double(s_psi[j].y) * double(s_psi[j].y);
+                a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * kThreads;
+            if (i >= na) break;
+            const int lv = s_tail[i];
+            V c;
+            if (COIN == HW_COIN_GROVER) {
+                const V m2 = s_coef[lv];
+                c = mkv<V, R>(m2.x - p[k].x, m2.y - p[k].y);
+            } else if (s_coef[lv].x != R(0)) {
+                c = mkv<V, R>(-p[k].x, -p[k].y);
+            } else {
+                const int s = s_rp[lv] - a0, d = s_rp[lv + 1] - s_rp[lv], j = i - s;
+                R cx = 0, cy = 0;
+                for (int q = 0; q < d; ++q) {
+                    R sn, cs;
+                    twiddle((j * q) % d, d, &sn, &cs);
+                    const V x = s_psi[s + q];
+                    cx += cs * x.x - sn * x.y;
+                    cy += cs * x.y + sn * x.x;
+                }
+                const R scale = R(1) / sqrt(R(d));
+                c = mkv<V, R>(cx * scale, cy * scale);
+            }
+            out[r[k]] = c;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- regular
+// Every vertex has the same degree D <= 8.  One thread owns one vertex and
+// its D consecutive arcs: D vector loads of psi and one vector load of rev,
+// the coin in registers, D scattered stores.  Thread-per-vertex keeps the
+// floating-point instruction count per arc minimal, which matters for
+// complex128: B300's FP64 pipe issues about one warp instruction every 16
+// cycles per SM, so per-lane butterfly sums would make the step FP64-bound.
+struct RegArgs {
+    const int32_t *rev;
+    double *rec_part;
+    const void *in;
+    void *out;
+    int64_t rec_slot;
+    int64_t n;
+    double two_over_d;
+    MarkedList mk;
+};
+
+template <int D>
+__device__ __forceinline__ void load_rev(const int32_t *__restrict__ rev, int64_t v, int *r)
+{
+    const int32_t *p = rev + v * D;
+    if (D == 4) {
+        const int4 q = __ldg(reinterpret_cast<const int4 *>(p));
+        r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+    } else if (D == 8) {
+        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p));
+        const int4 q1 = __ldg(reinterpret_cast<const int4 *>(p) + 1);
+        r[0] = q0.x; r[1] = q0.y; r[2] = q0.z; r[3] = q0.w;
+        r[4] = q1.x; r[5] = q1.y; r[6] = q1.z; r[7] = q1.w;
+    } else if (D == 2) {
+        const int2 q = __ldg(reinterpret_cast<const int2 *>(p));
+        r[0] = q.x; r[1] = q.y;
+    } else {
+#pragma unroll
+        for (int j = 0; j < D; ++j) r[j] = __ldg(p + j);
+    }
+}
+
+template <typename R, int D, int COIN>
+__global__ void __launch_bounds__(kThreads) k_coined_vertex(RegArgs a)
+{
+    using V = typename Cx<R>::T;
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= a.n) return;
+    V p[D];
+    int r[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) p[j] = in[v * D + j];
+    load_rev<D>(a.rev, v, r);
+    const int mi = find_marked(a.mk, int(v));
+    if (mi >= 0) {
+        if (a.rec_part && a.rec_slot >= 0) {
+            double acc = 0.0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc += double(p[j].x) * double(p[j].x) + double(p[j].y) * double(p[j].y);
+            a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(-p[j].x, -p[j].y);
+        return;
+    }
+    if (COIN == HW_COIN_GROVER) {
+        R sx = p[0].x, sy = p[0].y;
+#pragma unroll
+        for (int j = 1; j < D; ++j) { sx += p[j].x; sy += p[j].y; }
+        const R f = R(a.two_over_d);
+        // c_j = (2/d) sum - psi_j, one fused multiply-add per component
+#pragma unroll
+        for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
+    } else {
+        const R scale = R(1) / sqrt(R(D));
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            R cx = 0, cy = 0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const double2 w = c_tw[D * (D - 1) / 2 + (j * k) % D];
+                cx += R(w.x) * p[k].x - R(w.y) * p[k].y;
+                cy += R(w.x) * p[k].y + R(w.y) * p[k].x;
+            }
+            out[r[j]] = mkv<V, R>(cx * scale, cy * scale);
+        }
+    }
+}
+
+
+// Lane-group variant for complex64 (FP32 arithmetic is cheap; the limit is
+// memory requests): a group of G = 2^ceil(log2 d) consecutive lanes owns one
+// vertex, lane j < d holds arc d*v + j, so loads of psi and rev are fully
+// coalesced; the Grover sum runs as an xor-shuffle tree inside the group.
+template <typename R, int G, int COIN, int U>
+__global__ void __launch_bounds__(kThreads) k_coined_lanes(RegArgs a, int d)
+{
+    using V = typename Cx<R>::T;
+    constexpr int VPW = 32 / G;
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (G - 1);
+    const int base = lane & ~(G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t vbase = warp * (VPW * U) + lane / G;
+    const R f2 = R(a.two_over_d);
+
+    V p[U];
+    int r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t v = vbase + u * VPW;
+        if (v < a.n && j < d) {
+            const int64_t arc = v * d + j;
+            p[u] = in[arc];
+            r[u] = __ldg(a.rev + arc);
+        } else {
+            p[u] = mkv<V, R>(R(0), R(0));
+            r[u] = -1;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t v = vbase + u * VPW;
+        const int mi = (v < a.n) ? find_marked(a.mk, int(v)) : -1;   // uniform in the group
+        if (mi >= 0 && a.rec_part && a.rec_slot >= 0) {
+            double acc = double(p[u].x) * double(p[u].x) + double(p[u].y) * double(p[u].y);
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(gmask, acc, o);
+            if (j == 0) a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+        }
+        V c;
+        if (COIN == HW_COIN_GROVER) {
+            R sx = p[u].x, sy = p[u].y;
+#pragma unroll
+            for (int o = 1; o < G; o <<= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+            const R f = (mi >= 0) ? R(0) : f2;
+            c = mkv<V, R>(fma(f, sx, -p[u].x), fma(f, sy, -p[u].y));
+        } else {
+            R cx = 0, cy = 0;
+            for (int k = 0; k < d; ++k) {
+                const R qx = __shfl_sync(0xffffffffu, p[u].x, base + k);
+                const R qy = __shfl_sync(0xffffffffu, p[u].y, base + k);
+                R sn, cs;
+                twiddle((j * k) % d, d, &sn, &cs);
+                cx += cs * qx - sn * qy;
+                cy += cs * qy + sn * qx;
+            }
+            const R scale = R(1) / sqrt(R(d));
+            c = (mi >= 0) ? mkv<V, R>(-p[u].x, -p[u].y) : mkv<V, R>(cx * scale, cy * scale);
+        }
+        if (r[u] >= 0) out[r[u]] = c;
+    }
+}
+
+// ---------------------------------------------------------------- batched
+// States [num_arcs][batch] share the graph.  One warp per vertex: for each
+// column the warp sums the vertex's rows (coalesced across the batch), then
+// writes each coin output row to its reversed arc.
+struct BatchArgs {
+    const double *two_over_d;
+    const int32_t *row_ptr;
+    const int32_t *rev;
+    double *rec_part;
+    const void *in;
+    void *out;
+    int64_t rec_slot;
+    int32_t n;
+    int32_t batch;
+    int32_t verts_per_warp;
+    MarkedList mk;
+};
+
+template <typename R, int COIN>
+__global__ void __launch_bounds__(kThreads) k_coined_step_batched(BatchArgs a)
+{
+    using V = typename Cx<R>::T;
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int B = a.batch;
+    const int64_t vbeg = warp * a.verts_per_warp;
+    const int64_t vend = (vbeg + a.verts_per_warp < a.n) ? vbeg + a.verts_per_warp : int64_t(a.n);
+    for (int64_t v = vbeg; v < vend; ++v) {
+        const int s = a.row_ptr[v], e = a.row_ptr[v + 1], d = e - s;
+        if (d == 0) continue;
+        const int mi = find_marked(a.mk, int(v));
+        for (int c = lane; c < B; c += 32) {
+            if (mi >= 0) {
+                double acc = 0.0;
+                for (int j = s; j < e; ++j) {
+                    const V p = in[int64_t(j) * B + c];
+                    acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+                    out[int64_t(a.rev[j]) * B + c] = mkv<V, R>(-p.x, -p.y);
+                }
+                if (a.rec_part && a.rec_slot >= 0)
+                    a.rec_part[(a.rec_slot * a.mk.n + mi) * B + c] = acc;
+            } else if (COIN == HW_COIN_GROVER) {
+                R sx = 0, sy = 0;
+                for (int j = s; j < e; ++j) {
+                    const V p = in[int64_t(j) * B + c];
+                    sx += p.x;
+                    sy += p.y;
+                }
+                const R f = R(a.two_over_d[d]);
+                sx *= f;
+                sy *= f;
+                for (int j = s; j < e; ++j) {
+                    const V p = in[int64_t(j) * B + c];
+                    out[int64_t(a.rev[j]) * B + c] = mkv<V, R>(sx - p.x, sy - p.y);
+                }
+            } else {
+                const R scale = R(1) / sqrt(R(d));
+                for (int j = 0; j < d; ++j) {
+                    R cx = 0, cy = 0;
+                    for (int k = 0; k < d; ++k) {
+                        R sn, cs;
+                        twiddle(int((int64_t(j) * k) % d), d, &sn, &cs);
+                        const V q = in[int64_t(s + k) * B + c];
+                        cx += cs * q.x - sn * q.y;
+                        cy += cs * q.y + sn * q.x;
+                    }
+                    out[int64_t(a.rev[s + j]) * B + c] = mkv<V, R>(cx * scale, cy * scale);
+                }
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------- marked records
+// dst[mi*batch + b] = sum over the arcs of marked[mi] of |psi|^2 (row_ptr != NULL),
+// or |psi[marked[mi]]|^2 for a vertex-indexed state (row_ptr == NULL).
+template <typename R>
+__global__ void k_marked_prob(const int32_t *__restrict__ row_ptr, const void *psi_, MarkedList mk,
+                              int batch, double *__restrict__ dst)
+{
+    using V = typename Cx<R>::T;
+    const V *psi = static_cast<const V *>(psi_);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mk.n * batch) return;
+    const int mi = i / batch, b = i % batch;
+    const int v = mk.dev ? mk.dev[mi] : mk.inl[mi];
+    const int s = row_ptr ? row_ptr[v] : v;
+    const int e = row_ptr ? row_ptr[v + 1] : v + 1;
+    double acc = 0.0;
+    for (int j = s; j < e; ++j) {
+        const V p = psi[int64_t(j) * batch + b];
+        acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+    }
+    dst[i] = acc;
+}
+
+__global__ void k_record_finalize(const double *__restrict__ part, int n_marked, int64_t slots,
+                                  int batch, double *__restrict__ record)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= slots * batch) return;
+    const int64_t s = i / batch;
+    const int b = int(i % batch);
+    double acc = 0.0;
+    for (int m = 0; m < n_marked; ++m) acc += part[(s * n_marked + m) * batch + b];
+    record[i] = acc;
+}
+
+}  // namespace
+
+template <typename R, int COIN>
+static void launch_vertex(int d, const RegArgs &a, cudaStream_t st)
+{
+    const int64_t grid = (a.n + kThreads - 1) / kThreads;
+    switch (d) {
+    case 1: k_coined_vertex<R, 1, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    case 2: k_coined_vertex<R, 2, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    case 3: k_coined_vertex<R, 3, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    case 4: k_coined_vertex<R, 4, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    case 5: k_coined_vertex<R, 5, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    case 6: k_coined_vertex<R, 6, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    case 7: k_coined_vertex<R, 7, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    default: k_coined_vertex<R, 8, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    }
+}
+
+template <typename R, int G, int COIN>
+static void launch_lanes_g(const RegArgs &a, int d, cudaStream_t st)
+{
+    constexpr int U = 4;
+    constexpr int VPW = 32 / G;
+    const int64_t warps = (a.n + VPW * U - 1) / (VPW * U);
+    const int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
+    k_coined_lanes<R, G, COIN, U><<<grid, kThreads, 0, st>>>(a, d);
+}
+
+template <typename R, int COIN>
+static void launch_lanes(int d, const RegArgs &a, cudaStream_t st)
+{
+    if (d <= 1) launch_lanes_g<R, 1, COIN>(a, d, st);
+    else if (d <= 2) launch_lanes_g<R, 2, COIN>(a, d, st);
+    else if (d <= 4) launch_lanes_g<R, 4, COIN>(a, d, st);
+    else if (d <= 8) launch_lanes_g<R, 8, COIN>(a, d, st);
+    else if (d <= 16) launch_lanes_g<R, 16, COIN>(a, d, st);
+    else launch_lanes_g<R, 32, COIN>(a, d, st);
+}
+
+static hw_status upload_twiddles()
+{
+    static bool done = false;   // per process; the table is the same for every device
+    static int dev_done = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (done && dev == dev_done) return HW_OK;
+    std::vector<double2> tw(kTwMax * (kTwMax + 1) / 2);
+    for (int d = 1; d <= kTwMax; ++d)
+        for (int r = 0; r < d; ++r) {
+            const double ang = 2.0 * 3.14159265358979323846 * double(r) / double(d);
+            tw[d * (d - 1) / 2 + r] = make_double2(std::cos(ang), std::sin(ang));
+        }
+    hw_status s = hw_cuda(cudaMemcpyToSymbol(c_tw, tw.data(), sizeof(double2) * tw.size()),
+                          "cudaMemcpyToSymbol(twiddles)");
+    if (s == HW_OK) { done = true; dev_done = dev; }
+    return s;
+}
+
+hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const CoinedStep &s,
+                             cudaStream_t st)
+{
+    if (coin == HW_COIN_FOURIER) {
+        hw_status ts = upload_twiddles();
+        if (ts != HW_OK) return ts;
+    }
+    const bool regular = g->min_degree == g->max_degree && g->max_degree >= 1;
+    if (regular && ((dt == HW_C128 && g->max_degree <= 8) || (dt == HW_C64 && g->max_degree <= 32))) {
+        const int d = g->max_degree;
+        RegArgs r;
+        r.rev = g->d_rev;
+        r.rec_part = s.rec_part;
+        r.in = s.in;
+        r.out = s.out;
+        r.rec_slot = s.rec_slot;
+        r.n = g->n;
+        r.two_over_d = 2.0 / double(d);
+        r.mk = s.marked;
+        if (dt == HW_C128) {
+            if (coin == HW_COIN_GROVER) launch_vertex<double, HW_COIN_GROVER>(d, r, st);
+            else launch_vertex<double, HW_COIN_FOURIER>(d, r, st);
+        } else {
+            if (coin == HW_COIN_GROVER) launch_lanes<float, HW_COIN_GROVER>(d, r, st);
+            else launch_lanes<float, HW_COIN_FOURIER>(d, r, st);
+        }
+        return hw_cuda(cudaGetLastError(), "k_coined_vertex/k_coined_lanes launch");
+    }
+    StepArgs a;
+    a.two_over_d = g->d_two_over_d;
+    a.row_ptr = g->d_row_ptr;
+    a.rev = g->d_rev;
+    a.blk = g->d_blk;
+    a.nblk = g->nblk;
+    a.mk = s.marked;
+    a.rec_part = s.rec_part;
+    a.rec_slot = s.rec_slot;
+    a.in = s.in;
+    a.out = s.out;
+    const int grid = g->nblk;
+    if (dt == HW_C128) {
+        if (coin == HW_COIN_GROVER) k_coined_step<double, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
+        else k_coined_step<double, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+    } else {
+        if (coin == HW_COIN_GROVER) k_coined_step<float, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
+        else k_coined_step<float, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+    }
+    return hw_cuda(cudaGetLastError(), "k_coined_step launch");
+}
+
+hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coin, int batch,
+                                     const CoinedStep &s, int tile, cudaStream_t st)
+{
+    if (coin == HW_COIN_FOURIER) {
+        hw_status ts = upload_twiddles();
+        if (ts != HW_OK) return ts;
+    }
+    BatchArgs a;
+    a.two_over_d = g->d_two_over_d;
+    a.row_ptr = g->d_row_ptr;
+    a.rev = g->d_rev;
+    a.mk = s.marked;
+    a.rec_part = s.rec_part;
+    a.rec_slot = s.rec_slot;
+    a.in = s.in;
+    a.out = s.out;
+    a.n = int32_t(g->n);
+    a.batch = batch;
+    a.verts_per_warp = tile > 0 ? tile : 4;
+    const int64_t warps = (g->n + a.verts_per_warp - 1) / a.verts_per_warp;
+    const int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
+    if (dt == HW_C128) {
+        if (coin == HW_COIN_GROVER) k_coined_step_batched<double, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
+        else k_coined_step_batched<double, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+    } else {
+        if (coin == HW_COIN_GROVER) k_coined_step_batched<float, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
+        else k_coined_step_batched<float, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+    }
+    return hw_cuda(cudaGetLastError(), "k_coined_step_batched launch");
+}
+
+hw_status launch_marked_prob(const int32_t *row_ptr, hw_dtype dt, int batch, const void *psi,
+                             const MarkedList &mk, double *dst, cudaStream_t st)
+{
+    const int total = mk.n * batch;
+    const int grid = (total + 127) / 128;
+    if (dt == HW_C128) k_marked_prob<double><<<grid, 128, 0, st>>>(row_ptr, psi, mk, batch, dst);
+    else k_marked_prob<float><<<grid, 128, 0, st>>>(row_ptr, psi, mk, batch, dst);
+    return hw_cuda(cudaGetLastError(), "k_marked_prob launch");
+}
+
+hw_status launch_record_finalize(const double *rec_part, int32_t n_marked, int64_t slots, int batch,
+                                 double *record, cudaStream_t st)
+{
+    const int64_t total = slots * batch;
+    const int64_t grid = (total + 255) / 256;
+    k_record_finalize<<<grid, 256, 0, st>>>(rec_part, n_marked, slots, batch, record);
+    return hw_cuda(cudaGetLastError(), "k_record_finalize launch");
+}

@@ -1,0 +1,164 @@
+// Graph -> arc basis (Sec. 3.2): arcs sorted by tail then head, the flip-flop
+// shift as a reversal table, and the vertex-block partition used by the
+// fused coin+shift kernel.  Host code; the result is uploaded once per graph.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+hw_status hw_build_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                             std::vector<int32_t> &rp, std::vector<int32_t> &head,
+                             std::vector<int32_t> &rev)
+{
+    if (n < 1) return hw_fail(HW_EINVAL, "n must be >= 1 (got %lld)", (long long)n);
+    if (n >= (int64_t(1) << 31) - 1) return hw_fail(HW_EUNSUPPORTED, "n >= 2^31 - 1");
+    if (!row_ptr) return hw_fail(HW_EINVAL, "row_ptr is NULL");
+    if (row_ptr[0] != 0) return hw_fail(HW_EINVAL, "row_ptr[0] must be 0");
+    for (int64_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return hw_fail(HW_EINVAL, "row_ptr decreases at %lld", (long long)v);
+    const int64_t m = row_ptr[n];
+    if (m >= (int64_t(1) << 31)) return hw_fail(HW_EUNSUPPORTED, "2|E| = %lld >= 2^31 arcs", (long long)m);
+    if (m > 0 && !col_idx) return hw_fail(HW_EINVAL, "col_idx is NULL");
+
+    rp.resize(n + 1);
+    for (int64_t v = 0; v <= n; ++v) rp[v] = int32_t(row_ptr[v]);
+    head.assign(col_idx, col_idx + m);
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t *b = head.data() + rp[v], *e = head.data() + rp[v + 1];
+        std::sort(b, e);
+        for (int32_t *p = b; p < e; ++p) {
+            if (*p < 0 || *p >= n)
+                return hw_fail(HW_EINVAL, "column %d out of range in row %lld", *p, (long long)v);
+            if (*p == v) return hw_fail(HW_EINVAL, "self-loop at vertex %lld", (long long)v);
+            if (p > b && p[-1] == *p)
+                return hw_fail(HW_EINVAL, "repeated entry (%lld, %d)", (long long)v, *p);
+        }
+    }
+    rev.resize(m);
+    for (int64_t v = 0; v < n; ++v) {
+        for (int32_t a = rp[v]; a < rp[v + 1]; ++a) {
+            const int32_t w = head[a];
+            const int32_t *b = head.data() + rp[w], *e = head.data() + rp[w + 1];
+            const int32_t *p = std::lower_bound(b, e, int32_t(v));
+            if (p == e || *p != v)
+                return hw_fail(HW_EINVAL, "not symmetric: (%lld, %d) has no (%d, %lld)",
+                               (long long)v, w, w, (long long)v);
+            rev[a] = int32_t(p - head.data());
+        }
+    }
+    return HW_OK;
+}
+
+void hw_partition_blocks(const std::vector<int32_t> &rp, int tile_arcs, int tile_verts,
+                         std::vector<int32_t> &blk)
+{
+    const int64_t n = int64_t(rp.size()) - 1;
+    blk.clear();
+    blk.push_back(0);
+    int64_t v0 = 0;
+    while (v0 < n) {
+        int64_t v = v0;
+        // a vertex too large for a tile gets a block of its own
+        if (rp[v + 1] - rp[v] > tile_arcs) {
+            v = v0 + 1;
+        } else {
+            while (v < n && v - v0 < tile_verts && rp[v + 1] - rp[v0] <= tile_arcs) ++v;
+        }
+        blk.push_back(int32_t(v));
+        v0 = v;
+    }
+}
+
+extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                  void *stream, hw_graph **out)
+{
+    hw_clear_error();
+    if (!out) return hw_fail(HW_EINVAL, "out is NULL");
+    *out = nullptr;
+    hw_graph *g = new (std::nothrow) hw_graph;
+    if (!g) return hw_fail(HW_ENOMEM, "host allocation failed");
+    std::vector<int32_t> head, rev;
+    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, g->h_row_ptr, head, rev);
+    if (s != HW_OK) { delete g; return s; }
+    g->n = n;
+    g->num_arcs = g->h_row_ptr[n];
+    g->max_degree = 0;
+    g->min_degree = INT32_MAX;
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t d = g->h_row_ptr[v + 1] - g->h_row_ptr[v];
+        g->max_degree = std::max(g->max_degree, d);
+        g->min_degree = std::min(g->min_degree, d);
+    }
+    hw_partition_blocks(g->h_row_ptr, kTileArcs, kTileVerts, g->h_blk);
+    g->nblk = int32_t(g->h_blk.size() - 1);
+
+    std::vector<double> w(g->max_degree + 1, 0.0);
+    for (int32_t d = 1; d <= g->max_degree; ++d) w[d] = 2.0 / double(d);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto fail = [&](hw_status e) { hw_graph_free(g); return e; };
+    if ((s = hw_cuda(cudaGetDevice(&g->device), "cudaGetDevice")) != HW_OK) return fail(s);
+    const size_t arcs_b = sizeof(int32_t) * std::max<int64_t>(g->num_arcs, 1);
+    if (cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&g->d_head, arcs_b) != cudaSuccess ||
+        cudaMalloc(&g->d_rev, arcs_b) != cudaSuccess ||
+        cudaMalloc(&g->d_blk, sizeof(int32_t) * g->h_blk.size()) != cudaSuccess ||
+        cudaMalloc(&g->d_two_over_d, sizeof(double) * (g->max_degree + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(hw_fail(HW_ENOMEM, "device allocation of the graph failed"));
+    }
+    if ((s = hw_cuda(cudaMemcpyAsync(g->d_row_ptr, g->h_row_ptr.data(), sizeof(int32_t) * (n + 1),
+                                     cudaMemcpyHostToDevice, st), "upload row_ptr")) != HW_OK ||
+        (s = hw_cuda(cudaMemcpyAsync(g->d_head, head.data(), sizeof(int32_t) * g->num_arcs,
+                                     cudaMemcpyHostToDevice, st), "upload head")) != HW_OK ||
+        (s = hw_cuda(cudaMemcpyAsync(g->d_rev, rev.data(), sizeof(int32_t) * g->num_arcs,
+                                     cudaMemcpyHostToDevice, st), "upload rev")) != HW_OK ||
+        (s = hw_cuda(cudaMemcpyAsync(g->d_blk, g->h_blk.data(), sizeof(int32_t) * g->h_blk.size(),
+                                     cudaMemcpyHostToDevice, st), "upload blocks")) != HW_OK ||
+        (s = hw_cuda(cudaMemcpyAsync(g->d_two_over_d, w.data(), sizeof(double) * w.size(),
+                                     cudaMemcpyHostToDevice, st), "upload weights")) != HW_OK ||
+        (s = hw_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HW_OK)
+        return fail(s);
+    *out = g;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_graph_free(hw_graph *g)
+{
+    hw_clear_error();
+    if (!g) return HW_OK;
+    cudaFree(g->d_row_ptr);
+    cudaFree(g->d_head);
+    cudaFree(g->d_rev);
+    cudaFree(g->d_blk);
+    cudaFree(g->d_two_over_d);
+    cudaGetLastError();
+    delete g;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_graph_info(const hw_graph *g, int64_t *n, int64_t *num_arcs,
+                                   const int32_t **d_row_ptr, const int32_t **d_head,
+                                   const int32_t **d_rev)
+{
+    hw_clear_error();
+    if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
+    if (n) *n = g->n;
+    if (num_arcs) *num_arcs = g->num_arcs;
+    if (d_row_ptr) *d_row_ptr = g->d_row_ptr;
+    if (d_head) *d_head = g->d_head;
+    if (d_rev) *d_rev = g->d_rev;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_graph_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                        int32_t *row_ptr_out, int32_t *head_out, int32_t *rev_out)
+{
+    hw_clear_error();
+    std::vector<int32_t> rp, head, rev;
+    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, rp, head, rev);
+    if (s != HW_OK) return s;
+    if (row_ptr_out) std::memcpy(row_ptr_out, rp.data(), sizeof(int32_t) * rp.size());
+    if (head_out) std::memcpy(head_out, head.data(), sizeof(int32_t) * head.size());
+    if (rev_out) std::memcpy(rev_out, rev.data(), sizeof(int32_t) * rev.size());
+    return HW_OK;
+}

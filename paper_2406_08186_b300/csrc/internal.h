@@ -1,0 +1,79 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "hiperwalk_b300.h"
+
+// Arc tile of the fused coin+shift kernel: a CTA owns whole vertices whose
+// arcs fit in one tile; a vertex with more arcs than a tile gets a CTA alone.
+constexpr int kTileArcs = 1024;
+constexpr int kTileVerts = 1024;
+
+struct hw_graph {
+    int device = -1;
+    int64_t n = 0;
+    int64_t num_arcs = 0;
+    int32_t max_degree = 0;
+    int32_t min_degree = 0;
+    int32_t nblk = 0;                // vertex blocks of the coin+shift kernel
+    int32_t *d_row_ptr = nullptr;    // [n+1]
+    int32_t *d_head = nullptr;       // [num_arcs]
+    int32_t *d_rev = nullptr;        // [num_arcs]
+    int32_t *d_blk = nullptr;        // [nblk+1] first vertex of each block
+    double *d_two_over_d = nullptr;  // [max_degree+1], 2/d (0 for d = 0): the Grover weight
+    std::vector<int32_t> h_row_ptr;  // host copy for launch decisions
+    std::vector<int32_t> h_blk;
+};
+
+// ---- errors (api.cpp)
+hw_status hw_fail(hw_status s, const char *fmt, ...);
+hw_status hw_cuda(cudaError_t e, const char *what);
+void hw_clear_error();
+
+// ---- host graph construction (graph.cpp)
+// Sorted rows, reversal table and block partition, all on the host.
+hw_status hw_build_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                             std::vector<int32_t> &rp, std::vector<int32_t> &head,
+                             std::vector<int32_t> &rev);
+void hw_partition_blocks(const std::vector<int32_t> &rp, int tile_arcs, int tile_verts,
+                         std::vector<int32_t> &blk);
+
+// ---- device launchers (coined.cu, prob.cu, ctqw.cu)
+// Marked lists up to this length travel inside the kernel parameters (no
+// upload, no host synchronisation); longer lists are uploaded once per call.
+constexpr int kInlineMarked = 16;
+struct MarkedList {
+    const int32_t *dev;          // device array (sorted) when n > kInlineMarked, else nullptr
+    int32_t n;
+    int32_t inl[kInlineMarked];  // sorted ids when n <= kInlineMarked
+};
+
+struct CoinedStep {
+    const void *in;
+    void *out;
+    MarkedList marked;
+    double *rec_part;        // [slots][n_marked] or nullptr
+    int64_t rec_slot;        // slot receiving the marked probability of `in`, or -1
+};
+hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const CoinedStep &s,
+                             cudaStream_t st);
+hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coin, int batch,
+                                     const CoinedStep &s, int tile, cudaStream_t st);
+hw_status launch_marked_prob(const int32_t *row_ptr, hw_dtype dt, int batch, const void *psi,
+                             const MarkedList &marked, double *dst, cudaStream_t st);
+hw_status launch_record_finalize(const double *rec_part, int32_t n_marked, int64_t slots,
+                                 int batch, double *record, cudaStream_t st);
+hw_status launch_probability(const hw_graph *g, int64_t n, hw_dtype dt, int batch,
+                             const void *psi, double *prob, double *norm, cudaStream_t st);
+
+// Validated, sorted marked list; long lists get a device copy (stream-ordered
+// allocation, released by free_marked on the same stream).
+hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaStream_t st,
+                      MarkedList *out);
+void free_marked(MarkedList &m, cudaStream_t st);
+
+inline size_t cplx_bytes(hw_dtype dt) { return dt == HW_C128 ? 16 : 8; }

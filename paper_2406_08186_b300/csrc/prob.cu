@@ -1,0 +1,161 @@
+// Per-vertex probabilities and norms, accumulated in double precision.
+//   coined (Sec. 3.2):  p_v = sum_{w in N(v)} |<v,w|psi>|^2
+//   CTQW   (Sec. 3.1):  p_v = |<v|psi>|^2
+// norm_b = sum over rows of |psi[row][b]|^2 by a fixed two-level reduction
+// (per-CTA partials in scratch, then one pass over the partials), so that the
+// result does not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace {
+
+template <typename R> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+
+// coined: thread per (vertex, column), sequential over the vertex's arcs
+template <typename R>
+__global__ void k_prob_coined(const int32_t *__restrict__ row_ptr, int64_t n, int batch,
+                              const void *psi_, double *__restrict__ prob)
+{
+    using V = typename Cx<R>::T;
+    const V *__restrict__ psi = static_cast<const V *>(psi_);
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n * batch) return;
+    const int64_t v = i / batch;
+    const int b = int(i % batch);
+    double acc = 0.0;
+    for (int a = row_ptr[v]; a < row_ptr[v + 1]; ++a) {
+        const V p = psi[int64_t(a) * batch + b];
+        acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+    }
+    prob[i] = acc;
+}
+
+// CTQW: elementwise
+template <typename R>
+__global__ void k_prob_vertex(int64_t total, const void *psi_, double *__restrict__ prob)
+{
+    using V = typename Cx<R>::T;
+    const V *__restrict__ psi = static_cast<const V *>(psi_);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const V p = psi[i];
+        prob[i] = double(p.x) * double(p.x) + double(p.y) * double(p.y);
+    }
+}
+
+constexpr int kNormThreads = 256;
+
+// partial[blk*batch + b] = sum over rows [blk*chunk, (blk+1)*chunk) of |psi[row][b]|^2.
+// Threads are laid out as (row lane r, column b) with batch <= 256 columns
+// per pass; the per-column reduction over r runs in a fixed order.
+template <typename R>
+__global__ void __launch_bounds__(kNormThreads)
+k_norm_partial(const void *psi_, int64_t rows, int batch, int64_t chunk, double *__restrict__ partial)
+{
+    using V = typename Cx<R>::T;
+    __shared__ double red[kNormThreads];
+    const V *__restrict__ psi = static_cast<const V *>(psi_);
+    const int64_t r0 = int64_t(blockIdx.x) * chunk;
+    const int64_t r1 = min(r0 + chunk, rows);
+    for (int c0 = 0; c0 < batch; c0 += kNormThreads) {
+        const int cols = min(kNormThreads, batch - c0);
+        const int lanes = kNormThreads / cols;            // rows processed side by side
+        const int t = threadIdx.x;
+        const int r = t / cols, b = c0 + t % cols;
+        double acc = 0.0;
+        if (r < lanes) {
+#pragma unroll 4
+            for (int64_t row = r0 + r; row < r1; row += lanes) {
+                const V p = psi[row * batch + b];
+                acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+            }
+        }
+        red[t] = (r < lanes) ? acc : 0.0;
+        __syncthreads();
+        if (t < cols) {
+            double s = 0.0;
+            for (int k = 0; k < lanes; ++k) s += red[k * cols + t];
+            partial[int64_t(blockIdx.x) * batch + c0 + t] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// one CTA per column: strided partial sums, then a fixed tree
+__global__ void __launch_bounds__(kNormThreads)
+k_norm_final(const double *__restrict__ partial, int nparts, int batch, double *__restrict__ norm)
+{
+    __shared__ double red[kNormThreads];
+    const int b = blockIdx.x;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += kNormThreads) s += partial[int64_t(k) * batch + b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kNormThreads / 2; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) norm[b] = red[0];
+}
+
+}  // namespace
+
+// Partial count used by the norm reduction for `rows` rows.
+static int norm_parts(int64_t rows)
+{
+    return int(std::max<int64_t>(1, std::min<int64_t>(1184, (rows + 4095) / 4096)));
+}
+
+hw_status launch_norm(hw_dtype dt, int batch, const void *psi, int64_t rows, double *partial,
+                      double *norm, cudaStream_t st)
+{
+    const int parts = norm_parts(rows);
+    const int64_t chunk = (rows + parts - 1) / parts;
+    if (dt == HW_C128) k_norm_partial<double><<<parts, kNormThreads, 0, st>>>(psi, rows, batch, chunk, partial);
+    else k_norm_partial<float><<<parts, kNormThreads, 0, st>>>(psi, rows, batch, chunk, partial);
+    hw_status s = hw_cuda(cudaGetLastError(), "k_norm_partial launch");
+    if (s != HW_OK) return s;
+    k_norm_final<<<batch, kNormThreads, 0, st>>>(partial, parts, batch, norm);
+    return hw_cuda(cudaGetLastError(), "k_norm_final launch");
+}
+
+size_t norm_scratch_bytes(int64_t rows, int batch)
+{
+    return sizeof(double) * size_t(norm_parts(rows)) * size_t(batch);
+}
+
+hw_status launch_probability(const hw_graph *g, int64_t n, hw_dtype dt, int batch, const void *psi,
+                             double *prob, double *norm, cudaStream_t st)
+{
+    hw_status s = HW_OK;
+    if (prob) {
+        if (g) {
+            const int64_t total = g->n * batch;
+            const int64_t grid = std::max<int64_t>(1, (total + 255) / 256);
+            if (dt == HW_C128) k_prob_coined<double><<<grid, 256, 0, st>>>(g->d_row_ptr, g->n, batch, psi, prob);
+            else k_prob_coined<float><<<grid, 256, 0, st>>>(g->d_row_ptr, g->n, batch, psi, prob);
+        } else {
+            const int64_t total = n * batch;
+            const int64_t grid = std::min<int64_t>(148 * 16, std::max<int64_t>(1, (total + 255) / 256));
+            if (dt == HW_C128) k_prob_vertex<double><<<grid, 256, 0, st>>>(total, psi, prob);
+            else k_prob_vertex<float><<<grid, 256, 0, st>>>(total, psi, prob);
+        }
+        if ((s = hw_cuda(cudaGetLastError(), "probability launch")) != HW_OK) return s;
+    }
+    if (norm) {
+        const int64_t rows = g ? g->num_arcs : n;
+        if (rows == 0) return hw_cuda(cudaMemsetAsync(norm, 0, sizeof(double) * batch, st), "memset norm");
+        void *partial = nullptr;
+        if ((s = hw_cuda(cudaMallocAsync(&partial, norm_scratch_bytes(rows, batch), st),
+                         "cudaMallocAsync(norm partials)")) != HW_OK)
+            return s;
+        s = launch_norm(dt, batch, psi, rows, static_cast<double *>(partial), norm, st);
+        cudaFreeAsync(partial, st);
+    }
+    return s;
+}
