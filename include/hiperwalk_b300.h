@@ -158,6 +158,17 @@ hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t *marked,
                        const hw_opts *opts, void *stream);
 
 /*
+ * hw_ctqw_plan -- the Taylor degree m and squaring count s that hw_ctqw_expm
+ * uses by default: with nu = max_v (|gamma| d(v) + [v in M]) |time| (the
+ * 1-norm of H time; H is symmetric), s = smallest with nu / 2^s <= 1/2 and
+ * m = smallest with theta^(m+1)/(m+1)! < 2^-60, theta = nu / 2^s.  Host only.
+ *   degree, squarings   HOST outputs (may be NULL)
+ * Errors: HW_EINVAL.
+ */
+hw_status hw_ctqw_plan(const hw_graph *g, double gamma, const int32_t *marked, int32_t n_marked,
+                       double time, int32_t *degree, int32_t *squarings);
+
+/*
  * hw_ctqw_evolve -- psi_out = U^steps psi_in (Sec. 3.1: |psi(k dt)> = U(dt)^k |psi(0)>).
  *   U        DEVICE [n][n] row-major complex (dt), e.g. from hw_ctqw_expm
  *   psi_in   DEVICE [n][batch]; psi_out DEVICE [n][batch], may equal psi_in

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "HW_OK", -1: "HW_EINVAL", -2: "HW_ENOMEM", -3: "HW_ECUDA",
 
 # every entry point the header declares
 EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free", "hw_graph_info",
-           "hw_coined_evolve", "hw_ctqw_expm", "hw_ctqw_evolve", "hw_probability",
+           "hw_coined_evolve", "hw_ctqw_plan", "hw_ctqw_expm", "hw_ctqw_evolve", "hw_probability",
            "hw_last_error", "hw_version")
 
 
@@ -68,6 +68,8 @@ def lib():
         L.hw_graph_info.restype = st
         L.hw_coined_evolve.argtypes = [P, st, P, i32, st, i32, i64, P, P, P, ctypes.POINTER(hw_opts), P]
         L.hw_coined_evolve.restype = st
+        L.hw_ctqw_plan.argtypes = [P, d, P, i32, d, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.hw_ctqw_plan.restype = st
         L.hw_ctqw_expm.argtypes = [P, d, P, i32, d, st, P, ctypes.POINTER(hw_opts), P]
         L.hw_ctqw_expm.restype = st
         L.hw_ctqw_evolve.argtypes = [P, i64, st, i32, i64, P, P, P, i32, P, ctypes.POINTER(hw_opts), P]
@@ -217,6 +219,15 @@ def hw_coined_evolve(g: Graph, coin: int, marked, dt: int, batch: int, steps: in
                                   nm, int(dt), int(batch), int(steps), _dev(psi_in, _CPLX[dt]),
                                   _dev(psi_out, _CPLX[dt]), _dev(record, "float64"), _opts(opts),
                                   _stream(stream)))
+
+
+def hw_ctqw_plan(g: Graph, gamma: float, marked, time: float):
+    """(Taylor degree, squarings) that hw_ctqw_expm chooses by default."""
+    m, nm = _host_i32(marked)
+    deg, sq = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().hw_ctqw_plan(g, float(gamma), None if m is None else m.ctypes.data_as(ctypes.c_void_p),
+                              nm, float(time), ctypes.byref(deg), ctypes.byref(sq)))
+    return deg.value, sq.value
 
 
 def hw_ctqw_expm(g: Graph, gamma: float, marked, time: float, dt: int, U_out, opts=None, stream=None):

@@ -1,16 +1,504 @@
-// Continuous-time walk (Sec. 3.1): placeholder until the kernels land.
+// Continuous-time quantum walk (Sec. 3.1): H = -gamma A - sum_{m in M} |m><m|,
+// U(t) = e^{-iHt}, |psi(k dt)> = U(dt)^k |psi(0)>.
+//
+// hw_ctqw_expm builds U(time) densely by scaling and squaring a truncated
+// Taylor series.  With Y = H time / 2^s (real symmetric),
+//   e^{-iY} = sum_{k<=m} (-i)^k Y^k / k!,
+// so every power is real: Q_k = Y^k / k! = (Q_{k-1} Y) / k, and
+//   Re U += Q_k for k = 0 mod 4,  -= for k = 2 mod 4,
+//   Im U -= Q_k for k = 1 mod 4,  += for k = 3 mod 4.
+// The accumulation runs in double in the GEMM epilogue.  Then s squarings
+// U <- U^2 with U symmetric: Re' = Re Re - Im Im, Im' = X + X^T, X = Re Im.
+//
+// hw_ctqw_evolve applies U `steps` times (ping-pong) and records the
+// probability on the marked vertices after each application.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "internal.h"
 
-extern "C" hw_status hw_ctqw_expm(const hw_graph *, double, const int32_t *, int32_t, double, hw_dtype,
-                                  void *, const hw_opts *, void *)
+hw_status launch_tc_power_step(int n, const float *Q, const float *Y, float inv_k, float *Qn,
+                               double *accU, double sign, int slices, cudaStream_t st);
+bool tc_gemm_available();
+
+namespace {
+
+// ------------------------------------------------------------ FP64 GEMM
+// C = A1 B1 (+ sigma A2 B2), row-major n x n, register-blocked SIMT DFMA.
+constexpr int BM = 64, BN = 64, BK = 16;
+
+enum { EPI_STORE = 0, EPI_TAYLOR = 1 };
+
+struct GemmArgs {
+    const double *A1, *B1, *A2, *B2;
+    double sigma;
+    int n;
+    int epi;
+    double *out;      // C (EPI_STORE) or Q_k (EPI_TAYLOR)
+    double scale;     // C *= scale before the epilogue
+    double *acc;      // EPI_TAYLOR: acc += sign * C
+    double sign;
+};
+
+__global__ void __launch_bounds__(256) k_dgemm(GemmArgs g)
 {
-    hw_clear_error();
-    return hw_fail(HW_EUNSUPPORTED, "hw_ctqw_expm not built yet");
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN];
+    const int n = g.n;
+    const int t = threadIdx.x;
+    const int ty = t / 16, tx = t % 16;
+    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    double acc[4][4] = {};
+    for (int pass = 0; pass < (g.A2 ? 2 : 1); ++pass) {
+        const double *A = pass ? g.A2 : g.A1;
+        const double *B = pass ? g.B2 : g.B1;
+        const double sg = pass ? g.sigma : 1.0;
+        for (int k0 = 0; k0 < n; k0 += BK) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = t + 256 * q;
+                const int r = e / BK, c = e % BK;
+                const int gi = i0 + r, gk = k0 + c;
+                As[c][r] = (gi < n && gk < n) ? A[int64_t(gi) * n + gk] * sg : 0.0;
+                const int rb = e / BN, cb = e % BN;
+                const int gkb = k0 + rb, gj = j0 + cb;
+                Bs[rb][cb] = (gkb < n && gj < n) ? B[int64_t(gkb) * n + gj] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gi = i0 + ty * 4 + i;
+        if (gi >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gj = j0 + tx * 4 + j;
+            if (gj >= n) continue;
+            const int64_t o = int64_t(gi) * n + gj;
+            const double c = acc[i][j] * g.scale;
+            g.out[o] = c;
+            if (g.epi == EPI_TAYLOR) g.acc[o] += g.sign * c;
+        }
+    }
 }
 
-extern "C" hw_status hw_ctqw_evolve(const void *, int64_t, hw_dtype, int32_t, int64_t, const void *, void *,
-                                    const int32_t *, int32_t, double *, const hw_opts *, void *)
+hw_status dgemm(const GemmArgs &a, cudaStream_t st)
+{
+    dim3 grid((a.n + BN - 1) / BN, (a.n + BM - 1) / BM);
+    k_dgemm<<<grid, 256, 0, st>>>(a);
+    return hw_cuda(cudaGetLastError(), "k_dgemm launch");
+}
+
+// ------------------------------------------------------------ elementwise
+// Y = tau * H: -gamma*tau on every arc, -tau added on marked diagonals.
+__global__ void k_scatter_y(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ head,
+                            int n, double off, double *__restrict__ Y)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    for (int a = row_ptr[v]; a < row_ptr[v + 1]; ++a) Y[int64_t(v) * n + head[a]] = off;
+}
+
+__global__ void k_mark_diag(MarkedList mk, int n, double diag, double *__restrict__ Y)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= mk.n) return;
+    const int m = mk.dev ? mk.dev[i] : mk.inl[i];
+    Y[int64_t(m) * n + m] += diag;
+}
+
+// Re U = I, Im U = -Y (the k = 0 and k = 1 terms); Q_1 = Y.
+__global__ void k_taylor_init(int n, const double *__restrict__ Y, double *__restrict__ re,
+                              double *__restrict__ im)
+{
+    const int64_t total = int64_t(n) * n;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e / n, j = e % n;
+        re[e] = (i == j) ? 1.0 : 0.0;
+        im[e] = -Y[e];
+    }
+}
+
+// Im' = X + X^T
+__global__ void k_sym_add(int n, const double *__restrict__ X, double *__restrict__ out)
+{
+    const int64_t total = int64_t(n) * n;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e / n, j = e % n;
+        out[e] = X[e] + X[j * n + i];
+    }
+}
+
+template <typename V>
+__global__ void k_pack_u(int64_t total, const double *__restrict__ re, const double *__restrict__ im,
+                         V *__restrict__ U)
+{
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        V u;
+        u.x = decltype(u.x)(re[e]);
+        u.y = decltype(u.y)(im[e]);
+        U[e] = u;
+    }
+}
+
+__global__ void k_to_float(int64_t total, const double *__restrict__ x, float *__restrict__ y)
+{
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x)
+        y[e] = float(x[e]);
+}
+
+int ew_grid(int64_t total) { return int(std::min<int64_t>(148 * 32, (total + 255) / 256)); }
+
+// ------------------------------------------------------------ apply U
+// y[i][b] = sum_j U[i][j] x[j][b].  One warp per row; lanes stride the
+// columns (coalesced reads of U), x is staged in shared memory in chunks.
+// A marked row also writes |y|^2 into the record partials.
+constexpr int kApplyThreads = 256;
+constexpr int kApplyChunk = 2048;   // columns of x staged per pass
+
+template <typename R>
+struct Cx2;
+template <> struct Cx2<double> { using T = double2; };
+template <> struct Cx2<float> { using T = float2; };
+
+template <typename R, int BT>
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply(const void *U_, const void *x_, void *y_, int n, int batch, MarkedList mk, double *rec_part,
+        int64_t rec_slot)
+{
+    using V = typename Cx2<R>::T;
+    extern __shared__ unsigned char smem_raw[];
+    V *xs = reinterpret_cast<V *>(smem_raw);
+    const V *__restrict__ U = static_cast<const V *>(U_);
+    const V *__restrict__ x = static_cast<const V *>(x_);
+    V *__restrict__ y = static_cast<V *>(y_);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (kApplyThreads / 32) + warp;
+    for (int b0 = 0; b0 < batch; b0 += BT) {
+        const int nb = min(BT, batch - b0);
+        R ax[BT], ay[BT];
+#pragma unroll
+        for (int b = 0; b < BT; ++b) { ax[b] = 0; ay[b] = 0; }
+        for (int c0 = 0; c0 < n; c0 += kApplyChunk) {
+            const int cn = min(kApplyChunk, n - c0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < cn * nb; e += kApplyThreads) {
+                const int j = e / nb, b = e % nb;
+                xs[j * BT + b] = x[int64_t(c0 + j) * batch + b0 + b];
+            }
+            __syncthreads();
+            if (i < n) {
+                const V *Ui = U + int64_t(i) * n + c0;
+                for (int j = lane; j < cn; j += 32) {
+                    const V u = Ui[j];
+#pragma unroll
+                    for (int b = 0; b < BT; ++b) {
+                        if (b < nb) {
+                            const V q = xs[j * BT + b];
+                            ax[b] = fma(u.x, q.x, fma(-u.y, q.y, ax[b]));
+                            ay[b] = fma(u.x, q.y, fma(u.y, q.x, ay[b]));
+                        }
+                    }
+                }
+            }
+        }
+        if (i < n) {
+#pragma unroll
+            for (int b = 0; b < BT; ++b) {
+                R sx = ax[b], sy = ay[b];
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                }
+                ax[b] = sx;
+                ay[b] = sy;
+            }
+            if (lane < nb) {
+                R ox = 0, oy = 0;
+#pragma unroll
+                for (int b = 0; b < BT; ++b)
+                    if (b == lane) { ox = ax[b]; oy = ay[b]; }
+                V o;
+                o.x = ox;
+                o.y = oy;
+                y[int64_t(i) * batch + b0 + lane] = o;
+                if (rec_part && rec_slot >= 0) {
+                    // marked rows: |y|^2 into the partials [slot][mi][batch]
+                    int lo = 0, hi = mk.n, mi = -1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        const int m = mk.dev ? mk.dev[mid] : mk.inl[mid];
+                        if (m == i) { mi = mid; break; }
+                        if (m < i) lo = mid + 1; else hi = mid;
+                    }
+                    if (mi >= 0)
+                        rec_part[(rec_slot * mk.n + mi) * batch + b0 + lane] =
+                            double(ox) * double(ox) + double(oy) * double(oy);
+                }
+            }
+        }
+    }
+}
+
+template <typename R, int BT>
+hw_status launch_apply_bt(const void *U, const void *x, void *y, int n, int batch, const MarkedList &mk,
+                          double *rec_part, int64_t rec_slot, cudaStream_t st)
+{
+    using V = typename Cx2<R>::T;
+    const int grid = (n + kApplyThreads / 32 - 1) / (kApplyThreads / 32);
+    const size_t smem = sizeof(V) * kApplyChunk * BT;
+    cudaError_t e = cudaFuncSetAttribute(k_apply<R, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply)");
+    k_apply<R, BT><<<grid, kApplyThreads, smem, st>>>(U, x, y, n, batch, mk, rec_part, rec_slot);
+    return hw_cuda(cudaGetLastError(), "k_apply launch");
+}
+
+template <typename R>
+hw_status launch_apply(const void *U, const void *x, void *y, int n, int batch, const MarkedList &mk,
+                       double *rec_part, int64_t rec_slot, cudaStream_t st)
+{
+    if (batch == 1) return launch_apply_bt<R, 1>(U, x, y, n, batch, mk, rec_part, rec_slot, st);
+    return launch_apply_bt<R, 4>(U, x, y, n, batch, mk, rec_part, rec_slot, st);
+}
+
+struct DevBuf {
+    cudaStream_t st;
+    void *p = nullptr;
+    explicit DevBuf(cudaStream_t s) : st(s) {}
+    hw_status get(size_t bytes, const char *what)
+    {
+        return hw_cuda(cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st), what);
+    }
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+    ~DevBuf() { if (p) cudaFreeAsync(p, st); }
+};
+
+}  // namespace
+
+// Taylor degree and squarings (exposed for tests through hw_ctqw_plan).
+static void ctqw_plan(double norm1, int *m_out, int *s_out)
+{
+    int s = 0;
+    while (norm1 / std::ldexp(1.0, s) > 0.5) ++s;
+    const double theta = norm1 / std::ldexp(1.0, s);
+    int m = 1;
+    // smallest m with theta^(m+1)/(m+1)! < 2^-60
+    double term = theta;   // theta^(m+1)/(m+1)! for m = 0
+    while (m < 30) {
+        term = term * theta / double(m + 1);
+        if (term < std::ldexp(1.0, -60)) break;
+        ++m;
+    }
+    *m_out = std::max(m, 1);
+    *s_out = s;
+}
+
+extern "C" hw_status hw_ctqw_plan(const hw_graph *g, double gamma, const int32_t *marked,
+                                  int32_t n_marked, double time, int32_t *degree, int32_t *squarings)
 {
     hw_clear_error();
-    return hw_fail(HW_EUNSUPPORTED, "hw_ctqw_evolve not built yet");
+    if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
+    std::vector<char> is_m(g->n, 0);
+    for (int32_t i = 0; i < n_marked; ++i)
+        if (marked[i] >= 0 && marked[i] < g->n) is_m[marked[i]] = 1;
+    double norm1 = 0.0;
+    for (int64_t v = 0; v < g->n; ++v) {
+        const double r = std::fabs(gamma) * (g->h_row_ptr[v + 1] - g->h_row_ptr[v]) + (is_m[v] ? 1.0 : 0.0);
+        norm1 = std::max(norm1, r);
+    }
+    norm1 *= std::fabs(time);
+    int m, s;
+    ctqw_plan(norm1, &m, &s);
+    if (degree) *degree = m;
+    if (squarings) *squarings = s;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t *marked,
+                                  int32_t n_marked, double time, hw_dtype dt, void *U_out,
+                                  const hw_opts *opts, void *stream)
+{
+    hw_clear_error();
+    if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
+    if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (!U_out) return hw_fail(HW_EINVAL, "U_out is NULL");
+    if ((uintptr_t)U_out % cplx_bytes(dt)) return hw_fail(HW_EINVAL, "U_out misaligned");
+    if (!std::isfinite(gamma) || !std::isfinite(time)) return hw_fail(HW_EINVAL, "gamma/time not finite");
+    if (n_marked < 0 || (n_marked > 0 && !marked)) return hw_fail(HW_EINVAL, "bad marked list");
+    if (g->n > 32768) return hw_fail(HW_EUNSUPPORTED, "dense U limited to n <= 32768 (n = %lld)", (long long)g->n);
+    int dev = -1;
+    hw_status s = hw_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != HW_OK) return s;
+    if (dev != g->device) return hw_fail(HW_EINVAL, "graph lives on device %d, current is %d", g->device, dev);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = int(g->n);
+    MarkedList mk;
+    if ((s = make_marked(marked, n_marked, g->n, st, &mk)) != HW_OK) return s;
+    struct Rel { MarkedList &m; cudaStream_t st; ~Rel() { free_marked(m, st); } } rel{mk, st};
+
+    int m_deg, sq;
+    if ((s = hw_ctqw_plan(g, gamma, marked, n_marked, time, &m_deg, &sq)) != HW_OK) return s;
+    if (opts && opts->taylor_degree > 0) m_deg = opts->taylor_degree;
+    if (opts && opts->taylor_squarings >= 0) sq = opts->taylor_squarings;
+    if (m_deg > 40 || sq > 60) return hw_fail(HW_EINVAL, "Taylor degree %d / squarings %d out of range", m_deg, sq);
+    const int slices = (opts && opts->gemm_slices) ? opts->gemm_slices : 3;
+    if (slices != 2 && slices != 3) return hw_fail(HW_EINVAL, "gemm_slices must be 2 or 3");
+    const double tau = time / std::ldexp(1.0, sq);
+    const int64_t nn = int64_t(n) * n;
+    const size_t bytes = sizeof(double) * nn;
+
+    DevBuf Y(st), Q(st), Qn(st), Re(st), Im(st);
+    if ((s = Y.get(bytes, "cudaMallocAsync(Y)")) != HW_OK || (s = Q.get(bytes, "cudaMallocAsync(Q)")) != HW_OK ||
+        (s = Qn.get(bytes, "cudaMallocAsync(Q)")) != HW_OK || (s = Re.get(bytes, "cudaMallocAsync(ReU)")) != HW_OK ||
+        (s = Im.get(bytes, "cudaMallocAsync(ImU)")) != HW_OK)
+        return s;
+
+    // T1: Y = tau H
+    if ((s = hw_cuda(cudaMemsetAsync(Y.p, 0, bytes, st), "memset Y")) != HW_OK) return s;
+    k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, n, -gamma * tau, Y.as<double>());
+    if (mk.n) k_mark_diag<<<(mk.n + 127) / 128, 128, 0, st>>>(mk, n, -tau, Y.as<double>());
+    k_taylor_init<<<ew_grid(nn), 256, 0, st>>>(n, Y.as<double>(), Re.as<double>(), Im.as<double>());
+    if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;
+
+    // T2 + T3: Q_k = Q_{k-1} Y / k, accumulated into Re/Im U with the sign of (-i)^k
+    const bool use_tc = (dt == HW_C64) && tc_gemm_available();
+    if (use_tc) {
+        // complex64 path: powers on the tensor cores from split-bf16 fp32 operands
+        float *Yf = reinterpret_cast<float *>(Q.p);                 // fp32 copies fit in the
+        float *Qf = Yf + nn;                                         // double buffers (2 floats
+        float *Qnf = reinterpret_cast<float *>(Qn.p);                // per double)
+        k_to_float<<<ew_grid(nn), 256, 0, st>>>(nn, Y.as<double>(), Yf);
+        k_to_float<<<ew_grid(nn), 256, 0, st>>>(nn, Y.as<double>(), Qf);
+        for (int k = 2; k <= m_deg; ++k) {
+            double *accU = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
+            const double sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
+            if ((s = launch_tc_power_step(n, Qf, Yf, float(1.0 / k), Qnf, accU, sign, slices, st)) != HW_OK)
+                return s;
+            std::swap(Qf, Qnf);
+        }
+    } else {
+        double *Qk = Y.as<double>();   // Q_1 = Y
+        double *dst = Q.as<double>();
+        for (int k = 2; k <= m_deg; ++k) {
+            GemmArgs a{};
+            a.A1 = Qk;
+            a.B1 = Y.as<double>();
+            a.n = n;
+            a.epi = EPI_TAYLOR;
+            a.out = dst;
+            a.scale = 1.0 / double(k);
+            a.acc = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
+            a.sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
+            if ((s = dgemm(a, st)) != HW_OK) return s;
+            Qk = dst;
+            dst = (dst == Q.as<double>()) ? Qn.as<double>() : Q.as<double>();
+        }
+    }
+
+    // T4: U <- U^2, sq times (FP64)
+    for (int r = 0; r < sq; ++r) {
+        GemmArgs a{};
+        a.A1 = Re.as<double>(); a.B1 = Re.as<double>();
+        a.A2 = Im.as<double>(); a.B2 = Im.as<double>();
+        a.sigma = -1.0;
+        a.n = n; a.epi = EPI_STORE; a.out = Q.as<double>(); a.scale = 1.0;
+        if ((s = dgemm(a, st)) != HW_OK) return s;                     // Re Re - Im Im
+        GemmArgs b{};
+        b.A1 = Re.as<double>(); b.B1 = Im.as<double>();
+        b.n = n; b.epi = EPI_STORE; b.out = Qn.as<double>(); b.scale = 1.0;
+        if ((s = dgemm(b, st)) != HW_OK) return s;                     // X = Re Im
+        k_sym_add<<<ew_grid(nn), 256, 0, st>>>(n, Qn.as<double>(), Im.as<double>());
+        std::swap(Re.p, Q.p);
+        if ((s = hw_cuda(cudaGetLastError(), "squaring")) != HW_OK) return s;
+    }
+
+    if (dt == HW_C128) k_pack_u<double2><<<ew_grid(nn), 256, 0, st>>>(nn, Re.as<double>(), Im.as<double>(), static_cast<double2 *>(U_out));
+    else k_pack_u<float2><<<ew_grid(nn), 256, 0, st>>>(nn, Re.as<double>(), Im.as<double>(), static_cast<float2 *>(U_out));
+    return hw_cuda(cudaGetLastError(), "pack U");
+}
+
+extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32_t batch, int64_t steps,
+                                    const void *psi_in, void *psi_out, const int32_t *marked,
+                                    int32_t n_marked, double *record, const hw_opts *opts, void *stream)
+{
+    hw_clear_error();
+    if (!U || !psi_in || !psi_out) return hw_fail(HW_EINVAL, "NULL buffer");
+    if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (n < 1 || n > (int64_t(1) << 30)) return hw_fail(HW_EINVAL, "bad n");
+    if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
+    if (steps < 0) return hw_fail(HW_EINVAL, "steps must be >= 0");
+    if (n_marked < 0 || (n_marked > 0 && !marked)) return hw_fail(HW_EINVAL, "bad marked list");
+    const size_t esz = cplx_bytes(dt);
+    if ((uintptr_t)U % esz || (uintptr_t)psi_in % esz || (uintptr_t)psi_out % esz)
+        return hw_fail(HW_EINVAL, "buffers misaligned");
+    const int stride = opts ? opts->record_stride : 1;
+    if (stride < 1) return hw_fail(HW_EINVAL, "record_stride must be >= 1");
+    if (record && n_marked == 0) return hw_fail(HW_EINVAL, "record needs at least one marked vertex");
+    const size_t bytes = size_t(n) * batch * esz;
+    const char *ip = static_cast<const char *>(psi_in);
+    const char *op = static_cast<const char *>(psi_out);
+    if (ip != op && ip < op + bytes && op < ip + bytes)
+        return hw_fail(HW_EINVAL, "psi_in and psi_out overlap without being equal");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    hw_status s;
+    if (steps == 0) {
+        if (ip != op) return hw_cuda(cudaMemcpyAsync(psi_out, psi_in, bytes, cudaMemcpyDeviceToDevice, st), "copy");
+        return HW_OK;
+    }
+    MarkedList mk;
+    if ((s = make_marked(marked, n_marked, n, st, &mk)) != HW_OK) return s;
+    struct Rel { MarkedList &m; cudaStream_t st; ~Rel() { free_marked(m, st); } } rel{mk, st};
+    const int64_t slots = record ? steps / stride : 0;
+    DevBuf tmp(st), recbuf(st);
+    if ((s = tmp.get(bytes, "cudaMallocAsync(state scratch)")) != HW_OK) return s;
+    double *rec_part = nullptr;
+    if (slots) {
+        if (n_marked == 1) {
+            rec_part = record;
+        } else {
+            if ((s = recbuf.get(sizeof(double) * slots * n_marked * batch, "cudaMallocAsync(record)")) != HW_OK)
+                return s;
+            rec_part = recbuf.as<double>();
+        }
+    }
+    // same ping-pong schedule as the coined walk: the last step lands in psi_out
+    void *P = psi_out, *T = tmp.p;
+    const void *src = psi_in;
+    if (ip == op && steps % 2 == 1) {
+        if ((s = hw_cuda(cudaMemcpyAsync(T, psi_in, bytes, cudaMemcpyDeviceToDevice, st), "copy")) != HW_OK)
+            return s;
+        src = T;
+    }
+    for (int64_t k = 1; k <= steps; ++k) {
+        void *dst = ((steps - k) % 2 == 0) ? P : T;
+        const int64_t slot = (slots && k % stride == 0) ? k / stride - 1 : -1;
+        s = (dt == HW_C128) ? launch_apply<double>(U, src, dst, int(n), batch, mk, rec_part, slot, st)
+                            : launch_apply<float>(U, src, dst, int(n), batch, mk, rec_part, slot, st);
+        if (s != HW_OK) return s;
+        src = dst;
+    }
+    if (slots && n_marked > 1)
+        if ((s = launch_record_finalize(rec_part, n_marked, slots, batch, record, st)) != HW_OK) return s;
+    return HW_OK;
 }

@@ -1,0 +1,189 @@
+"""GPU parity of the continuous-time walk (Sec. 3.1) against the FP64 oracle.
+
+U = e^{-iH dt} from hw_ctqw_expm is compared column by column with the
+oracle's sparse series action, and the evolved states / marked-vertex curves
+from hw_ctqw_evolve with the oracle's evolution.  complex128: max-abs <= 1e-12;
+complex64: probability L1 <= 1e-3 after 1000+ applications.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL128 = 1e-12
+
+
+def _graph(hw, g):
+    n, eu, ev = g
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    return hw.hw_graph_csr(n, row_ptr, col)
+
+
+def gpu_expm(hw, g, gamma, marked, t, dt=2, opts=None):
+    import torch
+    G = _graph(hw, g)
+    n = g[0]
+    cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+    U = torch.empty((n, n), dtype=cdt, device="cuda")
+    hw.hw_ctqw_expm(G, gamma, list(marked), t, dt, U, opts=opts)
+    torch.cuda.synchronize()
+    return G, U
+
+
+def gpu_evolve(hw, U, psi0, steps, marked, dt=2, batch=1, record=True):
+    import torch
+    n = U.shape[0]
+    cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+    x = torch.from_numpy(np.ascontiguousarray(psi0)).to("cuda", cdt)
+    out = torch.empty_like(x)
+    rec = torch.empty(steps * batch, dtype=torch.float64, device="cuda") if record else None
+    hw.hw_ctqw_evolve(U, n, dt, batch, steps, x, out, list(marked), rec)
+    prob = torch.empty(n * batch, dtype=torch.float64, device="cuda")
+    norm = torch.empty(batch, dtype=torch.float64, device="cuda")
+    hw.hw_probability(None, n, dt, batch, out, prob, norm)
+    torch.cuda.synchronize()
+    return (out.cpu().numpy().astype(np.complex128), None if rec is None else rec.cpu().numpy(),
+            prob.cpu().numpy(), norm.cpu().numpy())
+
+
+CASES = [
+    ("Q6", synth.hypercube(6), 1 / 6, [5]),
+    ("er300", synth.erdos_renyi(300, 0.03, seed=4), 0.3, [0, 17, 299 - 40]),
+    ("C101", synth.cycle(101), 0.5, []),
+    ("K33", synth.complete(33), 1 / 33, [32]),
+    ("star", synth.star(130), 0.2, [0]),
+]
+
+
+@pytest.mark.parametrize("t", [0.1, 1.0, 10.0])
+@pytest.mark.parametrize("name,g,gamma,marked", CASES)
+def test_expm_c128_matches_oracle_columns(hw, name, g, gamma, marked, t):
+    marked = [m for m in marked if m < g[0]]
+    G, U = gpu_expm(hw, g, gamma, marked, t)
+    ar = oracle.Arcs(*g)
+    ref = oracle.ctqw_columns(ar, gamma, t, np.arange(g[0]), marked=marked)
+    # Each squaring roughly doubles the rounding error already in U, so the
+    # 1e-12 bar (the configured workloads need s <= 2) widens as 2^s / 64 for
+    # the stress cases with many squarings (the star at t = 10 needs s = 10).
+    s = hw.hw_ctqw_plan(G, gamma, marked, t)[1]
+    tol = TOL128 * max(1.0, 2.0 ** s / 64)
+    assert np.max(np.abs(U.cpu().numpy() - ref)) <= tol
+    G.free()
+
+
+def test_expm_c64_close(hw):
+    g = synth.hypercube(7)
+    G, U = gpu_expm(hw, g, 1 / 7, [3], 0.1, dt=1)
+    ar = oracle.Arcs(*g)
+    ref = oracle.ctqw_columns(ar, 1 / 7, 0.1, np.arange(128), marked=[3])
+    assert np.max(np.abs(U.cpu().numpy() - ref)) < 2e-6
+    G.free()
+
+
+def test_expm_hypercube_closed_form(hw):
+    # no marks: U[u, v] = cos(gamma t)^(k-h) (i sin(gamma t))^h, h = Hamming distance
+    k, gamma, t = 8, 0.25, 3.0
+    G, U = gpu_expm(hw, synth.hypercube(k), gamma, [], t)
+    u = np.arange(1 << k)
+    h = np.array([bin(x).count("1") for x in range(1 << k)])
+    H = h[u[:, None] ^ u[None, :]]
+    ref = math.cos(gamma * t) ** (k - H) * (1j * math.sin(gamma * t)) ** H
+    assert np.max(np.abs(U.cpu().numpy() - ref)) <= TOL128
+    G.free()
+
+
+def test_plan_matches_stated_rule(hw):
+    g = synth.hypercube(12)
+    G = _graph(hw, g)
+    m = synth.seeded_vertex(3, 4096)
+    assert hw.hw_ctqw_plan(G, 1 / 12, [m], 0.1) == (12, 0)   # ||H dt|| = 0.2
+    assert hw.hw_ctqw_plan(G, 1 / 12, [m], 1.0)[1] == 2
+    assert hw.hw_ctqw_plan(G, 1 / 12, [m], 10.0)[1] == 6
+    G.free()
+
+
+def test_evolve_matches_oracle_and_hamming_reduction(hw):
+    k, gamma, dt, steps = 10, 1 / 10, 0.1, 300
+    g = synth.hypercube(k)
+    N = 1 << k
+    m = synth.seeded_vertex(3, N)
+    G, U = gpu_expm(hw, g, gamma, [m], dt)
+    psi0 = synth.uniform_state(N)
+    psi, rec, prob, norm = gpu_evolve(hw, U, psi0, steps, [m])
+    ar = oracle.Arcs(*g)
+    ref, rec_ref = oracle.ctqw_evolve(ar, gamma, psi0, dt, steps, marked=[m], record=True)
+    assert np.max(np.abs(psi - ref)) <= TOL128
+    assert np.max(np.abs(rec - rec_ref)) <= TOL128
+    assert np.max(np.abs(prob - oracle.prob_vertex(ref))) <= TOL128
+    assert abs(norm[0] - 1) < 1e-12
+    # independent closed form: Hamming-weight classes around m
+    A = np.zeros((k + 1, k + 1))
+    for r in range(k):
+        A[r, r + 1] = A[r + 1, r] = math.sqrt((r + 1) * (k - r))
+    Hr = -gamma * A
+    Hr[0, 0] -= 1.0
+    w, V = np.linalg.eigh(Hr)
+    x0 = np.array([math.sqrt(math.comb(k, r) / N) for r in range(k + 1)])
+    times = dt * np.arange(1, steps + 1)
+    amp0 = (V[0, :][None, :] * np.exp(-1j * np.outer(times, w))) @ (V.T @ x0)
+    assert np.max(np.abs(rec - np.abs(amp0) ** 2)) <= TOL128
+    G.free()
+
+
+def test_evolve_batched_and_in_place(hw):
+    import torch
+    g = synth.erdos_renyi(200, 0.05, seed=2)
+    n = g[0]
+    marked = [1, 150]
+    G, U = gpu_expm(hw, g, 0.4, marked, 0.3)
+    ar = oracle.Arcs(*g)
+    B, steps = 3, 40
+    psi0 = synth.gaussian_states(n, B, seed=9)
+    psi, rec, prob, norm = gpu_evolve(hw, U, psi0, steps, marked, batch=B)
+    psi = psi.reshape(n, B)
+    rec = rec.reshape(steps, B)
+    for b in range(B):
+        ref, rr = oracle.ctqw_evolve(ar, 0.4, psi0[:, b], 0.3, steps, marked=marked, record=True)
+        assert np.max(np.abs(psi[:, b] - ref)) <= TOL128
+        assert np.max(np.abs(rec[:, b] - rr)) <= TOL128
+    # in place, odd step count
+    x = torch.from_numpy(psi0[:, 0].copy()).cuda()
+    hw.hw_ctqw_evolve(U, n, hw.HW_C128, 1, 7, x, x)
+    ref = oracle.ctqw_evolve(ar, 0.4, psi0[:, 0], 0.3, 7, marked=marked)
+    assert np.max(np.abs(x.cpu().numpy() - ref)) <= TOL128
+    G.free()
+
+
+@pytest.mark.parametrize("dt", [2, 1])
+def test_config3_hypercube12_search_full_size(hw, dt):
+    # Q_12, gamma = 1/12, one seeded mark, dt = 0.1, uniform start, 2000 applications.
+    k, gamma, tstep, steps = 12, 1 / 12, 0.1, 2000
+    g = synth.hypercube(k)
+    N = 1 << k
+    m = synth.seeded_vertex(3, N)
+    G, U = gpu_expm(hw, g, gamma, [m], tstep, dt=dt)
+    ar = oracle.Arcs(*g)
+    cols = np.array([0, m, 1, 2047, 4095, 1234, 3000, 77])
+    refU = oracle.ctqw_columns(ar, gamma, tstep, cols, marked=[m])
+    Uc = U[:, torch_index(cols)].cpu().numpy()
+    psi0 = synth.uniform_state(N)
+    psi, rec, prob, norm = gpu_evolve(hw, U, psi0, steps, [m], dt=dt)
+    ref, rec_ref = oracle.ctqw_evolve(ar, gamma, psi0, tstep, steps, marked=[m], record=True)
+    if dt == 2:
+        assert np.max(np.abs(Uc - refU)) <= TOL128
+        assert np.max(np.abs(psi - ref)) <= TOL128
+        assert np.max(np.abs(rec - rec_ref)) <= TOL128
+    else:
+        assert np.max(np.abs(Uc - refU)) < 2e-6
+        assert np.sum(np.abs(prob - oracle.prob_vertex(ref))) <= 1e-3
+        assert np.max(np.abs(rec - rec_ref)) < 1e-4
+    G.free()
+
+
+def torch_index(cols):
+    import torch
+    return torch.from_numpy(np.asarray(cols)).cuda()
