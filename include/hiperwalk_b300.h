@@ -151,7 +151,10 @@ hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marke
  *            split-bf16 operands with fp32 accumulation; Taylor sums and
  *            squarings in double; U rounded to complex64 at the end.
  * Scratch: a few n x n real buffers from the stream-ordered allocator.
- * Errors: HW_EINVAL, HW_EUNSUPPORTED (n > 32768), HW_ENOMEM, HW_ECUDA.
+ * With HW_C64 the call synchronises `stream` before returning, to report a
+ * device-side pipeline timeout of the tensor-core kernel as HW_ETIMEDOUT.
+ * Errors: HW_EINVAL, HW_EUNSUPPORTED (n > 32768), HW_ENOMEM, HW_ECUDA,
+ * HW_ETIMEDOUT.
  */
 hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t *marked,
                        int32_t n_marked, double time, hw_dtype dt, void *U_out,
@@ -192,6 +195,24 @@ hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32_t batch, i
  */
 hw_status hw_probability(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batch,
                          const void *psi, double *prob_out, double *norm_out, void *stream);
+
+/*
+ * hw_gemm_tc -- C = A B^T on the tensor cores (tcgen05, bf16 inputs, fp32
+ * accumulation) with each fp32 operand split into `slices` bf16 terms
+ * (1: plain bf16; 2: ~2^-16 relative error, 3 products; 3: ~2^-24, 6 products).
+ * This is the contraction behind the complex64 Taylor series of
+ * hw_ctqw_expm (there A = Y^(k-1)/(k-1)!, B = Y, symmetric), exposed for tests
+ * and measurement.
+ *   A  DEVICE float[m][k] row-major;  B  DEVICE float[n][k] row-major
+ *   C  DEVICE float[m][n] row-major, caller-owned
+ * Scratch (bf16 slices, 3(m+n)k x 2 bytes) comes from the stream-ordered
+ * allocator.  The call synchronises `stream` before returning, to report a
+ * device-side pipeline timeout as HW_ETIMEDOUT.
+ * Errors: HW_EINVAL, HW_EUNSUPPORTED (not an sm_103 device), HW_ENOMEM,
+ * HW_ECUDA, HW_ETIMEDOUT.
+ */
+hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A, const float *B, float *C,
+                     int32_t slices, void *stream);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *hw_last_error(void);

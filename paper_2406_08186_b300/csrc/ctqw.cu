@@ -20,10 +20,6 @@
 
 #include "internal.h"
 
-hw_status launch_tc_power_step(int n, const float *Q, const float *Y, float inv_k, float *Qn,
-                               double *accU, double sign, int slices, cudaStream_t st);
-bool tc_gemm_available();
-
 namespace {
 
 // ------------------------------------------------------------ FP64 GEMM
@@ -159,13 +155,6 @@ __global__ void k_pack_u(int64_t total, const double *__restrict__ re, const dou
         u.y = decltype(u.y)(im[e]);
         U[e] = u;
     }
-}
-
-__global__ void k_to_float(int64_t total, const double *__restrict__ x, float *__restrict__ y)
-{
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x)
-        y[e] = float(x[e]);
 }
 
 int ew_grid(int64_t total) { return int(std::min<int64_t>(148 * 32, (total + 255) / 256)); }
@@ -384,19 +373,17 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     // T2 + T3: Q_k = Q_{k-1} Y / k, accumulated into Re/Im U with the sign of (-i)^k
     const bool use_tc = (dt == HW_C64) && tc_gemm_available();
     if (use_tc) {
-        // complex64 path: powers on the tensor cores from split-bf16 fp32 operands
-        float *Yf = reinterpret_cast<float *>(Q.p);                 // fp32 copies fit in the
-        float *Qf = Yf + nn;                                         // double buffers (2 floats
-        float *Qnf = reinterpret_cast<float *>(Qn.p);                // per double)
-        k_to_float<<<ew_grid(nn), 256, 0, st>>>(nn, Y.as<double>(), Yf);
-        k_to_float<<<ew_grid(nn), 256, 0, st>>>(nn, Y.as<double>(), Qf);
-        for (int k = 2; k <= m_deg; ++k) {
+        // complex64 path: powers on the tensor cores from split-bf16 operands
+        TcPower *tp = nullptr;
+        if ((s = tc_power_begin(n, Y.as<double>(), slices, st, &tp)) != HW_OK) return s;
+        for (int k = 2; k <= m_deg && s == HW_OK; ++k) {
             double *accU = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
             const double sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
-            if ((s = launch_tc_power_step(n, Qf, Yf, float(1.0 / k), Qnf, accU, sign, slices, st)) != HW_OK)
-                return s;
-            std::swap(Qf, Qnf);
+            s = tc_power_step(tp, k, accU, sign, st);
         }
+        hw_status e = tc_power_end(tp, st, s == HW_OK);
+        if (s == HW_OK) s = e;
+        if (s != HW_OK) return s;
     } else {
         double *Qk = Y.as<double>();   // Q_1 = Y
         double *dst = Q.as<double>();

@@ -76,4 +76,12 @@ hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaSt
                       MarkedList *out);
 void free_marked(MarkedList &m, cudaStream_t st);
 
+// tensor-core Taylor powers (gemm_tc.cu): Q_k = Q_{k-1} Y / k on tcgen05 from
+// split-bf16 operands, accU += sign Q_k in double
+struct TcPower;
+bool tc_gemm_available();
+hw_status tc_power_begin(int n, const double *Y, int ns, cudaStream_t st, TcPower **out);
+hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream_t st);
+hw_status tc_power_end(TcPower *p, cudaStream_t st, bool check);
+
 inline size_t cplx_bytes(hw_dtype dt) { return dt == HW_C128 ? 16 : 8; }
