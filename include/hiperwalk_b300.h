@@ -197,6 +197,28 @@ hw_status hw_probability(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batc
                          const void *psi, double *prob_out, double *norm_out, void *stream);
 
 /*
+ * hw_probability_noalloc -- the same results as hw_probability, for callers
+ * that cannot allocate device memory during a call: programs running under a
+ * fixed, pre-reserved memory budget that must not meet out-of-memory halfway
+ * through a request, and platforms without the stream-ordered allocator
+ * (cudaDevAttrMemoryPoolsSupported == 0).  The paper has no counterpart; it
+ * is a deployment variant of hw_probability.
+ * It allocates nothing: the norm's partial sums use a static device array
+ * built into the library (1184 x 64 doubles, about 0.6 MB, held on every
+ * device that loads the library until the process exits).
+ *   Arguments, layouts and results as hw_probability.
+ *   Limit: batch <= 64 when norm_out != NULL (HW_EINVAL otherwise).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the one array, so
+ * calls whose work overlaps on the GPU (different streams, no ordering) race
+ * on it and must be serialised by the caller.
+ * Errors: HW_EINVAL, HW_EUNSUPPORTED (device index >= 64), HW_ECUDA.
+ */
+hw_status hw_probability_noalloc(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batch,
+                                 const void *psi, double *prob_out, double *norm_out, void *stream);
+
+/*
  * hw_gemm_tc -- C = A B^T on the tensor cores (tcgen05, bf16 inputs, fp32
  * accumulation) with each fp32 operand split into `slices` bf16 terms
  * (1: plain bf16; 2: ~2^-16 relative error, 3 products; 3: ~2^-24, 6 products).

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "HW_OK", -1: "HW_EINVAL", -2: "HW_ENOMEM", -3: "HW_ECUDA",
 # every entry point the header declares
 EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free", "hw_graph_info",
            "hw_coined_evolve", "hw_ctqw_plan", "hw_ctqw_expm", "hw_ctqw_evolve", "hw_probability",
-           "hw_gemm_tc", "hw_last_error", "hw_version")
+           "hw_probability_noalloc", "hw_gemm_tc", "hw_last_error", "hw_version")
 
 
 class HWError(RuntimeError):
@@ -76,6 +76,8 @@ def lib():
         L.hw_ctqw_evolve.restype = st
         L.hw_probability.argtypes = [P, i64, st, i32, P, P, P, P]
         L.hw_probability.restype = st
+        L.hw_probability_noalloc.argtypes = [P, i64, st, i32, P, P, P, P]
+        L.hw_probability_noalloc.restype = st
         L.hw_gemm_tc.argtypes = [i64, i64, i64, P, P, P, i32, P]
         L.hw_gemm_tc.restype = st
         L.hw_last_error.argtypes = []
@@ -251,6 +253,14 @@ def hw_ctqw_evolve(U, n: int, dt: int, batch: int, steps: int, psi_in, psi_out, 
 def hw_probability(g, n: int, dt: int, batch: int, psi, prob_out=None, norm_out=None, stream=None):
     _check(lib().hw_probability(g, int(n), int(dt), int(batch), _dev(psi, _CPLX[dt]),
                                 _dev(prob_out, "float64"), _dev(norm_out, "float64"), _stream(stream)))
+
+
+def hw_probability_noalloc(g, n: int, dt: int, batch: int, psi, prob_out=None, norm_out=None,
+                           stream=None):
+    """hw_probability without device allocation (norm partials in a built-in array; batch <= 64)."""
+    _check(lib().hw_probability_noalloc(g, int(n), int(dt), int(batch), _dev(psi, _CPLX[dt]),
+                                        _dev(prob_out, "float64"), _dev(norm_out, "float64"),
+                                        _stream(stream)))
 
 
 def hw_gemm_tc(A, B, C, slices: int = 3, stream=None):

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 
@@ -158,4 +159,88 @@ hw_status launch_probability(const hw_graph *g, int64_t n, hw_dtype dt, int batc
         cudaFreeAsync(partial, st);
     }
     return s;
+}
+
+// ---------------------------------------------------------------- no allocation
+// hw_probability for callers that cannot allocate device memory during a
+// call: programs that run under a fixed, pre-reserved memory budget (a
+// serving loop that must not hit out-of-memory halfway through a request),
+// and platforms where the stream-ordered allocator is unavailable
+// (cudaDevAttrMemoryPoolsSupported == 0, as under some virtualised or MPS
+// setups).  The norm's per-CTA partials live in this file-scope device
+// array instead of coming from cudaMallocAsync.  Every device that loads the
+// library holds the array until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxParts = 1184;    // norm_parts() never exceeds this
+constexpr int kNoAllocMaxBatch = 64;      // largest batch the array serves
+static __device__ __align__(256) double g_norm_scratch[kNoAllocMaxParts * kNoAllocMaxBatch];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[kMaxDevices] = {};   // device address of g_norm_scratch, per device
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is resolved
+// with cudaGetSymbolAddress, once per device, with that device current.
+hw_status scratch_on_current_device(double **out)
+{
+    int dev = -1;
+    hw_status s = hw_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != HW_OK) return s;
+    if (dev < 0 || dev >= kMaxDevices) return hw_fail(HW_EUNSUPPORTED, "device index %d >= %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if ((s = hw_cuda(cudaGetSymbolAddress(&p, g_norm_scratch), "cudaGetSymbolAddress(g_norm_scratch)")) != HW_OK)
+            return s;
+        g_scratch_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return HW_OK;
+}
+
+}  // namespace
+
+extern "C" hw_status hw_probability_noalloc(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batch,
+                                            const void *psi, double *prob_out, double *norm_out,
+                                            void *stream)
+{
+    hw_clear_error();
+    if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
+    if (!psi) return hw_fail(HW_EINVAL, "psi is NULL");
+    if (!prob_out && !norm_out) return hw_fail(HW_EINVAL, "nothing to compute");
+    if ((uintptr_t)psi % cplx_bytes(dt)) return hw_fail(HW_EINVAL, "psi misaligned");
+    if (((uintptr_t)prob_out | (uintptr_t)norm_out) % 8) return hw_fail(HW_EINVAL, "outputs misaligned");
+    if (norm_out && batch > kNoAllocMaxBatch)
+        return hw_fail(HW_EINVAL, "hw_probability_noalloc: batch %d exceeds the built-in scratch limit of %d "
+                       "states for the norm (use hw_probability)", batch, kNoAllocMaxBatch);
+    if (g) {
+        int dev = -1;
+        hw_status s = hw_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+        if (s != HW_OK) return s;
+        if (dev != g->device) return hw_fail(HW_EINVAL, "graph lives on device %d, current is %d", g->device, dev);
+        n = g->n;
+    } else if (n < 1) {
+        return hw_fail(HW_EINVAL, "n must be >= 1");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *scratch = nullptr;
+    if (norm_out) {
+        hw_status s = scratch_on_current_device(&scratch);
+        if (s != HW_OK) return s;
+    }
+    if (prob_out) {
+        hw_status s = launch_probability(g, n, dt, batch, psi, prob_out, nullptr, st);
+        if (s != HW_OK) return s;
+    }
+    if (norm_out) {
+        const int64_t rows = g ? g->num_arcs : n;
+        if (rows == 0) return hw_cuda(cudaMemsetAsync(norm_out, 0, sizeof(double) * batch, st), "memset norm");
+        // every partial the final pass reads is written by the first pass, so
+        // nothing left in the array by an earlier call needs clearing
+        return launch_norm(dt, batch, psi, rows, scratch, norm_out, st);
+    }
+    return HW_OK;
 }
