@@ -323,6 +323,136 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def run_workload_batched(args):
+    """Batched coined walks: ER graph n = 2^20, mean degree 8 (isolated vertices dropped),
+    64 unit complex64 states, Grover coin, 500 steps, one SpMM-shaped launch per step."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    n0 = 1 << 20
+    n, eu, ev = synth.erdos_renyi(n0, 8.0 / (n0 - 1), seed=5)
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    A2, B, steps = G.num_arcs, 64, 500
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    psi0 = torch.randn((A2, B), dtype=torch.complex64, device="cuda", generator=gen)
+    psi0 /= torch.linalg.vector_norm(psi0, dim=0, keepdim=True)
+    out = torch.empty_like(psi0)
+    norm = torch.empty(B, dtype=torch.float64, device="cuda")
+    prob = torch.empty(n * B, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, 2, psi0, out)   # autotunes the launch shape once
+    for _ in range(args.warmup):
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, steps, psi0, out)
+    torch.cuda.synchronize()
+    tot = ev_t = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e = _events(4)
+        e[0].record(stream)
+        e[1].record(stream)
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, steps, psi0, out)
+        e[2].record(stream)
+        hw.hw_probability(G, n, hw.HW_C64, B, out, prob, norm)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        tot += e[0].elapsed_time(e[3]) / 1e3
+        ev_t += e[1].elapsed_time(e[2]) / 1e3
+    peak, src = measured_peaks()
+    per_launch = ev_t / (args.steps * steps)
+    bytes_launch = A2 * (2 * B * 8 + 4) + 4 * (n + 1)
+    nm = norm.cpu().numpy()
+    print(json.dumps({"workload": "er_batched", "metric": METRIC, "unit": UNIT,
+                      "value": A2 * B * steps * args.steps / tot, "ms_per_step": 1e3 * tot / args.steps,
+                      "n": n, "arcs": A2, "batch": B, "walk_steps": steps, "dtype": "f32 (fp64 sums)",
+                      "roofline": {"bound": "hbm", "achieved": bytes_launch / per_launch / 1e9, "peak": peak,
+                                   "unit": "GB/s", "frac": bytes_launch / per_launch / 1e9 / peak,
+                                   "bytes_per_launch": bytes_launch, "launch_us": per_launch * 1e6,
+                                   "peak_source": src},
+                      "norm_minmax": [float(nm.min()), float(nm.max())]}), flush=True)
+
+
+def run_workload_ctqw(args):
+    """CTQW search on Q_12: U = exp(-iH 0.1) dense (Taylor, scaling and squaring), 2000 applications."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    g = synth.hypercube(12)
+    n = 4096
+    m = synth.seeded_vertex(3, n)
+    row_ptr, col = synth.adjacency_csr(*g)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    stream = torch.cuda.current_stream()
+    peak, src = measured_peaks()
+    res = {"workload": "hypercube12_ctqw", "n": n, "marked": m, "gamma": 1 / 12, "dt": 0.1,
+           "applications": 2000}
+    for dt, name in ((hw.HW_C128, "c128"), (hw.HW_C64, "c64")):
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        U = torch.empty((n, n), dtype=cdt, device="cuda")
+        x = torch.full((n,), 1 / 64, dtype=cdt, device="cuda")
+        y = torch.empty_like(x)
+        rec = torch.empty(2000, dtype=torch.float64, device="cuda")
+        for _ in range(max(1, args.warmup)):
+            hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+            hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec)
+        torch.cuda.synchronize()
+        t_exp = t_ev = 0.0
+        for _ in range(args.steps):
+            e = _events(3)
+            e[0].record(stream)
+            hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+            e[1].record(stream)
+            hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            t_exp += e[0].elapsed_time(e[1]) / 1e3
+            t_ev += e[1].elapsed_time(e[2]) / 1e3
+        t_exp /= args.steps
+        t_ev /= args.steps
+        deg, sq = hw.hw_ctqw_plan(G, 1 / 12, [m], 0.1)
+        gemm_flop = (deg - 1) * 2.0 * n ** 3
+        apply_bytes = n * n * (16 if dt == hw.HW_C128 else 8)
+        res[name] = {"expm_ms": t_exp * 1e3, "evolve_ms": t_ev * 1e3, "taylor_degree": deg, "squarings": sq,
+                     "gemm_tflops_useful": gemm_flop / t_exp / 1e12,
+                     "apply_us": t_ev / 2000 * 1e6, "apply_gbs": apply_bytes / (t_ev / 2000) / 1e9,
+                     "apply_frac_hbm": apply_bytes / (t_ev / 2000) / 1e9 / peak,
+                     "p_m_max": float(rec.max().item())}
+    res["peak_hbm"] = peak
+    print(json.dumps(res), flush=True)
+
+
+def run_workload_torus64(args):
+    """64 x 64 torus, Grover, no mark, start on the 4 arcs of (32, 32), 100 steps, complex128."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    n, eu, ev = synth.torus(64)
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    psi0 = torch.from_numpy(synth.state_on_vertex_arcs(synth.arc_offsets(n, eu, ev), 32 * 64 + 32)).cuda()
+    out = torch.empty_like(psi0)
+    prob = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
+        hw.hw_probability(G, n, hw.HW_C128, 1, out, prob)
+    torch.cuda.synchronize()
+    e = _events(2)
+    e[0].record(stream)
+    for _ in range(args.steps):
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
+        hw.hw_probability(G, n, hw.HW_C128, 1, out, prob)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    t = e[0].elapsed_time(e[1]) / 1e3 / args.steps
+    print(json.dumps({"workload": "torus64_center", "metric": METRIC, "unit": UNIT,
+                      "value": G.num_arcs * 100 / t, "us_per_run": t * 1e6, "us_per_walk_step": t / 100 * 1e6}),
+          flush=True)
+
+
 def run_profile(args):
     """A few launches of one kernel on the bench workload, for ncu captures."""
     import torch
@@ -351,9 +481,18 @@ def main():
     ap.add_argument("--profile", choices=["coined_c128", "coined_c64"],
                     help="run a few coin+shift launches of the workload and exit (for ncu)")
     ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--workload", default="torus1024_search",
+                    choices=["torus1024_search", "torus64_center", "hypercube12_ctqw", "er_batched"],
+                    help="the default is the benchmarked workload; the others print their own line")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.workload == "er_batched":
+        run_workload_batched(args)
+    elif args.workload == "hypercube12_ctqw":
+        run_workload_ctqw(args)
+    elif args.workload == "torus64_center":
+        run_workload_torus64(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -63,7 +63,11 @@ typedef struct hw_opts {
     int32_t taylor_degree;     /* hw_ctqw_expm: Taylor degree m (0 = chosen for < 2^-60 truncation) */
     int32_t taylor_squarings;  /* hw_ctqw_expm: squarings s (-1 = chosen so ||H dt||_1 / 2^s <= 1/2) */
     int32_t gemm_slices;       /* hw_ctqw_expm, HW_C64: bf16 slices per fp32 operand (2 or 3; 0 = 3) */
-    int32_t tile;              /* batched coined kernel: rows per CTA (0 = autotuned) */
+    int32_t tile;              /* batched Grover kernel launch shape: 0 = autotuned on the first
+                                  call per (graph, dtype, batch), which then synchronises the
+                                  stream once; 1..12 = (rows held in registers, threads per
+                                  CTA, vertices per warp) in {8,16} x {128,256} x {1,2,4},
+                                  row-major */
     int32_t reserved[3];
 } hw_opts;
 

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -470,6 +471,142 @@ __global__ void __launch_bounds__(kThreads) k_coined_step_batched(BatchArgs a)
     }
 }
 
+
+// Batched Grover step with rows held in registers.  The batch of a vertex's
+// arc is one contiguous row (batch x 8 or 16 bytes); a warp owns a vertex,
+// each lane a 16-byte (or 8-byte) slice of the row, so every row load and
+// every row store to the reversed arc is one coalesced line.  Up to DREG rows
+// stay in registers between the sum and the stores; larger vertices re-read.
+struct RowsArgs {
+    const double *two_over_d;
+    const int32_t *row_ptr;
+    const int32_t *rev;
+    double *rec_part;
+    const void *in;
+    void *out;
+    int64_t rec_slot;
+    int64_t n;
+    int32_t batch;
+    int32_t vpw;             // vertices per warp
+    MarkedList mk;
+};
+
+template <typename R, int CPL> struct RowVec;
+template <> struct RowVec<float, 2> {
+    using T = float4;
+    static __device__ __forceinline__ T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ float re(const T &v, int q) { return q ? v.z : v.x; }
+    static __device__ __forceinline__ float im(const T &v, int q) { return q ? v.w : v.y; }
+};
+template <> struct RowVec<float, 1> {
+    using T = float2;
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ float re(const T &v, int) { return v.x; }
+    static __device__ __forceinline__ float im(const T &v, int) { return v.y; }
+};
+template <> struct RowVec<double, 1> {
+    using T = double2;
+    static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
+    static __device__ __forceinline__ double re(const T &v, int) { return v.x; }
+    static __device__ __forceinline__ double im(const T &v, int) { return v.y; }
+};
+
+// c = f * sum - p, componentwise (Grover), or -p (marked: f = 0 handled by caller)
+__device__ __forceinline__ float4 grover_row(float f, const float4 &s, const float4 &p)
+{
+    return make_float4(fmaf(f, s.x, -p.x), fmaf(f, s.y, -p.y), fmaf(f, s.z, -p.z), fmaf(f, s.w, -p.w));
+}
+__device__ __forceinline__ float2 grover_row(float f, const float2 &s, const float2 &p)
+{
+    return make_float2(fmaf(f, s.x, -p.x), fmaf(f, s.y, -p.y));
+}
+__device__ __forceinline__ double2 grover_row(double f, const double2 &s, const double2 &p)
+{
+    return make_double2(fma(f, s.x, -p.x), fma(f, s.y, -p.y));
+}
+__device__ __forceinline__ void add_row(float4 &a, const float4 &b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+__device__ __forceinline__ void add_row(float2 &a, const float2 &b) { a.x += b.x; a.y += b.y; }
+__device__ __forceinline__ void add_row(double2 &a, const double2 &b) { a.x += b.x; a.y += b.y; }
+
+template <typename R, int CPL, int DREG>
+__global__ void __launch_bounds__(256) k_coined_rows(RowsArgs a)
+{
+    using RV = RowVec<R, CPL>;
+    using T = typename RV::T;
+    const T *__restrict__ in = static_cast<const T *>(a.in);
+    T *__restrict__ out = static_cast<T *>(a.out);
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int B = a.batch;
+    const int BV = B / CPL;                   // row length in vectors
+    const int64_t v0 = gw * a.vpw;
+    const int64_t v1 = (v0 + a.vpw < a.n) ? v0 + a.vpw : a.n;
+    for (int64_t v = v0; v < v1; ++v) {
+        const int s = a.row_ptr[v], e = a.row_ptr[v + 1], d = e - s;
+        if (d == 0) continue;
+        const int mi = find_marked(a.mk, int(v));
+        const int rv = (lane < d) ? __ldg(a.rev + s + lane) : 0;
+        const R f = (mi >= 0) ? R(0) : R(a.two_over_d[d]);
+        for (int c0 = 0; c0 < BV; c0 += 32) {
+            const int cv = c0 + lane;             // this lane's vector column
+            const bool act = cv < BV;
+            if (d <= DREG) {
+                T p[DREG];
+                T sum = RV::zero();
+#pragma unroll
+                for (int j = 0; j < DREG; ++j) {
+                    if (j < d) {
+                        p[j] = act ? in[int64_t(s + j) * BV + cv] : RV::zero();
+                        add_row(sum, p[j]);
+                    }
+                }
+                if (mi >= 0 && a.rec_part && a.rec_slot >= 0 && act) {
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        double acc = 0.0;
+#pragma unroll
+                        for (int j = 0; j < DREG; ++j)
+                            if (j < d) {
+                                const double x = RV::re(p[j], q), y = RV::im(p[j], q);
+                                acc += x * x + y * y;
+                            }
+                        a.rec_part[(a.rec_slot * a.mk.n + mi) * B + cv * CPL + q] = acc;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < DREG; ++j) {
+                    if (j < d) {
+                        const int r = __shfl_sync(0xffffffffu, rv, j);
+                        if (act) out[int64_t(r) * BV + cv] = grover_row(f, sum, p[j]);
+                    }
+                }
+            } else {
+                T sum = RV::zero();
+                double acc[CPL] = {};
+                for (int j = 0; j < d; ++j) {
+                    const T p = act ? in[int64_t(s + j) * BV + cv] : RV::zero();
+                    add_row(sum, p);
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        const double x = RV::re(p, q), y = RV::im(p, q);
+                        acc[q] += x * x + y * y;
+                    }
+                }
+                if (mi >= 0 && a.rec_part && a.rec_slot >= 0 && act)
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) a.rec_part[(a.rec_slot * a.mk.n + mi) * B + cv * CPL + q] = acc[q];
+                for (int j = 0; j < d; ++j) {
+                    const int r = (j < 32) ? __shfl_sync(0xffffffffu, rv, j) : __ldg(a.rev + s + j);
+                    if (act) {
+                        const T p = in[int64_t(s + j) * BV + cv];
+                        out[int64_t(r) * BV + cv] = grover_row(f, sum, p);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // -------------------------------------------------------- marked records
 // dst[mi*batch + b] = sum over the arcs of marked[mi] of |psi|^2 (row_ptr != NULL),
 // or |psi[marked[mi]]|^2 for a vertex-indexed state (row_ptr == NULL).
@@ -613,35 +750,116 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
     return hw_cuda(cudaGetLastError(), "k_coined_step launch");
 }
 
+// Launch shapes of the batched Grover kernel: (threads per CTA, vertices per
+// warp, rows kept in registers).
+constexpr int kNumRowShapes = 12;
+constexpr int kRowShapes[kNumRowShapes][3] = {
+    {128, 1, 8}, {128, 2, 8}, {128, 4, 8}, {256, 1, 8}, {256, 2, 8}, {256, 4, 8},
+    {128, 1, 16}, {128, 2, 16}, {128, 4, 16}, {256, 1, 16}, {256, 2, 16}, {256, 4, 16}};
+
+template <typename R, int CPL>
+static void launch_rows(const RowsArgs &a, int shape, cudaStream_t st)
+{
+    const int threads = kRowShapes[shape][0];
+    const int64_t warps = (a.n + a.vpw - 1) / a.vpw;
+    const int64_t grid = (warps * 32 + threads - 1) / threads;
+    if (kRowShapes[shape][2] == 8) k_coined_rows<R, CPL, 8><<<grid, threads, 0, st>>>(a);
+    else k_coined_rows<R, CPL, 16><<<grid, threads, 0, st>>>(a);
+}
+
+static void launch_rows_dt(hw_dtype dt, int batch, RowsArgs a, int shape, cudaStream_t st)
+{
+    a.vpw = kRowShapes[shape][1];
+    if (dt == HW_C128) launch_rows<double, 1>(a, shape, st);
+    else if (batch % 2 == 0) launch_rows<float, 2>(a, shape, st);
+    else launch_rows<float, 1>(a, shape, st);
+}
+
+// Pick the fastest launch shape for (graph, dtype, batch) by timing each
+// candidate on this call's own buffers (the outputs are rewritten by the
+// real launch afterwards); the choice is cached on the graph.  Synchronises
+// the stream once per new key.
+static hw_status tune_rows(const hw_graph *g, hw_dtype dt, int batch, const RowsArgs &base, cudaStream_t st,
+                           int *best)
+{
+    const long long key = (long long)batch * 4 + int(dt);
+    {
+        std::lock_guard<std::mutex> lock(g->tune_mu);
+        auto it = g->tune_rows.find(key);
+        if (it != g->tune_rows.end()) { *best = it->second; return HW_OK; }
+    }
+    RowsArgs a = base;
+    a.rec_part = nullptr;
+    cudaEvent_t e0, e1;
+    hw_status s = hw_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+    if (s != HW_OK) return s;
+    if ((s = hw_cuda(cudaEventCreate(&e1), "cudaEventCreate")) != HW_OK) { cudaEventDestroy(e0); return s; }
+    float best_ms = 1e30f;
+    int pick = 4;
+    for (int c = 0; c < kNumRowShapes && s == HW_OK; ++c) {
+        launch_rows_dt(dt, batch, a, c, st);   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch_rows_dt(dt, batch, a, c, st);
+        cudaEventRecord(e1, st);
+        s = hw_cuda(cudaEventSynchronize(e1), "autotune");
+        float ms = 0.f;
+        if (s == HW_OK) cudaEventElapsedTime(&ms, e0, e1);
+        if (s == HW_OK && ms < best_ms) { best_ms = ms; pick = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != HW_OK) return s;
+    {
+        std::lock_guard<std::mutex> lock(g->tune_mu);
+        g->tune_rows[key] = pick;
+    }
+    *best = pick;
+    return HW_OK;
+}
+
 hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coin, int batch,
                                      const CoinedStep &s, int tile, cudaStream_t st)
 {
     if (coin == HW_COIN_FOURIER) {
         hw_status ts = upload_twiddles();
         if (ts != HW_OK) return ts;
+        BatchArgs a;
+        a.two_over_d = g->d_two_over_d;
+        a.row_ptr = g->d_row_ptr;
+        a.rev = g->d_rev;
+        a.mk = s.marked;
+        a.rec_part = s.rec_part;
+        a.rec_slot = s.rec_slot;
+        a.in = s.in;
+        a.out = s.out;
+        a.n = int32_t(g->n);
+        a.batch = batch;
+        a.verts_per_warp = 4;
+        const int64_t warps = (g->n + a.verts_per_warp - 1) / a.verts_per_warp;
+        const int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
+        if (dt == HW_C128) k_coined_step_batched<double, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+        else k_coined_step_batched<float, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+        return hw_cuda(cudaGetLastError(), "k_coined_step_batched launch");
     }
-    BatchArgs a;
+    RowsArgs a;
     a.two_over_d = g->d_two_over_d;
     a.row_ptr = g->d_row_ptr;
     a.rev = g->d_rev;
-    a.mk = s.marked;
     a.rec_part = s.rec_part;
-    a.rec_slot = s.rec_slot;
     a.in = s.in;
     a.out = s.out;
-    a.n = int32_t(g->n);
+    a.rec_slot = s.rec_slot;
+    a.n = g->n;
     a.batch = batch;
-    a.verts_per_warp = tile > 0 ? tile : 4;
-    const int64_t warps = (g->n + a.verts_per_warp - 1) / a.verts_per_warp;
-    const int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
-    if (dt == HW_C128) {
-        if (coin == HW_COIN_GROVER) k_coined_step_batched<double, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
-        else k_coined_step_batched<double, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
-    } else {
-        if (coin == HW_COIN_GROVER) k_coined_step_batched<float, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
-        else k_coined_step_batched<float, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+    a.vpw = 1;
+    a.mk = s.marked;
+    int shape = tile - 1;
+    if (tile <= 0) {
+        hw_status ts = tune_rows(g, dt, batch, a, st, &shape);
+        if (ts != HW_OK) return ts;
     }
-    return hw_cuda(cudaGetLastError(), "k_coined_step_batched launch");
+    launch_rows_dt(dt, batch, a, shape, st);
+    return hw_cuda(cudaGetLastError(), "k_coined_rows launch");
 }
 
 hw_status launch_marked_prob(const int32_t *row_ptr, hw_dtype dt, int batch, const void *psi,

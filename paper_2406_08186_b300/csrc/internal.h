@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "hiperwalk_b300.h"
@@ -27,6 +29,9 @@ struct hw_graph {
     double *d_two_over_d = nullptr;  // [max_degree+1], 2/d (0 for d = 0): the Grover weight
     std::vector<int32_t> h_row_ptr;  // host copy for launch decisions
     std::vector<int32_t> h_blk;
+    // autotuned launch shape of the batched kernel per (batch, dtype)
+    mutable std::mutex tune_mu;
+    mutable std::map<long long, int> tune_rows;
 };
 
 // ---- errors (api.cpp)
