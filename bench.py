@@ -457,6 +457,21 @@ def run_profile(args):
     """A few launches of one kernel on the bench workload, for ncu captures."""
     import torch
     import paper_2406_08186_b300 as hw
+    if args.profile == "batched_c64":
+        # Erdos-Renyi n = 2^18, mean degree 8, 64 complex64 states (about 2 GB on the device)
+        n0 = 1 << 18
+        n, eu, ev = synth.erdos_renyi(n0, 8.0 / (n0 - 1), seed=5)
+        row_ptr, col = synth.adjacency_csr(n, eu, ev)
+        G = hw.hw_graph_csr(n, row_ptr, col)
+        gen = torch.Generator(device="cuda").manual_seed(4)
+        x = torch.randn((G.num_arcs, 64), dtype=torch.complex64, device="cuda", generator=gen)
+        out = torch.empty_like(x)
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C64, 64, args.profile_steps, x, out,
+                            opts={"tile": args.profile_tile})
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "steps": args.profile_steps, "tile": args.profile_tile}))
+        G.free()
+        return
     n, eu, ev, row_ptr, col, m = workload()
     G = hw.hw_graph_csr(n, row_ptr, col)
     dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
@@ -478,9 +493,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["coined_c128", "coined_c64"],
+    ap.add_argument("--profile", choices=["coined_c128", "coined_c64", "batched_c64"],
                     help="run a few coin+shift launches of the workload and exit (for ncu)")
     ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--profile-tile", type=int, default=10)
     ap.add_argument("--workload", default="torus1024_search",
                     choices=["torus1024_search", "torus64_center", "hypercube12_ctqw", "er_batched"],
                     help="the default is the benchmarked workload; the others print their own line")

@@ -65,9 +65,10 @@ typedef struct hw_opts {
     int32_t gemm_slices;       /* hw_ctqw_expm, HW_C64: bf16 slices per fp32 operand (2 or 3; 0 = 3) */
     int32_t tile;              /* batched Grover kernel launch shape: 0 = autotuned on the first
                                   call per (graph, dtype, batch), which then synchronises the
-                                  stream once; 1..12 = (rows held in registers, threads per
-                                  CTA, vertices per warp) in {8,16} x {128,256} x {1,2,4},
-                                  row-major */
+                                  stream once; 1..12 = register-row kernel with (rows held
+                                  in registers, threads per CTA, vertices per warp) in
+                                  {8,16} x {128,256} x {1,2,4}, row-major; 13, 14 = TMA-staged
+                                  ring kernel with 2 or 1 CTAs per SM */
     int32_t reserved[3];
 } hw_opts;
 
@@ -137,8 +138,10 @@ hw_status hw_graph_info(const hw_graph *g, int64_t *n, int64_t *num_arcs,
  *                    of state b after step k*stride.  Needs n_marked >= 1.
  * Scratch: one state-sized buffer (and a small record buffer) is taken from
  * the stream-ordered allocator and returned on the same stream.
+ * A device-side wait that runs out of time (the batched kernel's bounded
+ * mbarrier waits) is reported as HW_ETIMEDOUT by the next call on the graph.
  * Errors: HW_EINVAL, HW_EUNSUPPORTED (Fourier coin on a vertex of degree > 4096),
- * HW_ENOMEM, HW_ECUDA.
+ * HW_ENOMEM, HW_ECUDA, HW_ETIMEDOUT.
  */
 hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marked,
                            int32_t n_marked, hw_dtype dt, int32_t batch, int64_t steps,

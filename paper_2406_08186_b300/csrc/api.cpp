@@ -127,7 +127,7 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
         return hw_fail(HW_EINVAL, "state buffers must be aligned to %zu bytes", esz);
     const int stride = opts ? opts->record_stride : 1;
     if (stride < 1) return hw_fail(HW_EINVAL, "record_stride must be >= 1");
-    if (opts && (opts->tile < 0 || opts->tile > 12)) return hw_fail(HW_EINVAL, "tile must be 0..12");
+    if (opts && (opts->tile < 0 || opts->tile > 14)) return hw_fail(HW_EINVAL, "tile must be 0..14");
     if (record && n_marked == 0) return hw_fail(HW_EINVAL, "record needs at least one marked vertex");
     if (record && (uintptr_t)record % 8) return hw_fail(HW_EINVAL, "record must be 8-byte aligned");
     if (coin == HW_COIN_FOURIER && g->max_degree > 4096)
@@ -140,6 +140,10 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
         return hw_fail(HW_EINVAL, "psi_in and psi_out overlap without being equal");
     hw_status s = check_device(g);
     if (s != HW_OK) return s;
+    if (g->h_err && *reinterpret_cast<volatile int *>(g->h_err)) {
+        *g->h_err = 0;
+        return hw_fail(HW_ETIMEDOUT, "a device-side wait of an earlier call on this graph ran out of time");
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     if (steps == 0 || g->num_arcs == 0) {

@@ -10,6 +10,7 @@
 // loads, forms the per-vertex coin in shared memory and scatters the results.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -607,6 +608,183 @@ __global__ void __launch_bounds__(256) k_coined_rows(RowsArgs a)
     }
 }
 
+
+// Batched Grover step with TMA bulk staging.  A vertex's batch rows are one
+// contiguous block (d x rowbytes), so each warp streams its own consecutive
+// vertices through a ring of kRingSlots shared-memory slots with
+// cp.async.bulk (one mbarrier per slot), prefetching kRingSlots-1 vertices
+// ahead while it sums and scatters the current one.  In-flight data occupies
+// shared memory, not registers, so every SM keeps tens of KB of loads in
+// flight.  Vertices whose rows do not fit a slot are read directly.
+constexpr int kRingSlots = 3;
+constexpr int kSlotBytes = 8192;
+constexpr int kRingWarps = 4;
+constexpr uint64_t kRingWaitNs = 2000000000ull;
+
+struct RingArgs {
+    const double *two_over_d;
+    const int32_t *row_ptr;
+    const int32_t *rev;
+    double *rec_part;
+    const void *in;
+    void *out;
+    int *err;                // zero-copy host word: set on a wait timeout
+    int64_t rec_slot;
+    int64_t n;
+    int32_t batch;
+    int32_t rowbytes;
+    MarkedList mk;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 0) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kRingWaitNs) return false;
+        }
+    }
+}
+
+// issued by one lane: stage the rows of vertex v into a slot (or just arrive
+// when they do not fit, or v is past the warp's range)
+__device__ __forceinline__ void ring_issue(const RingArgs &a, int64_t v, int64_t vend, uint32_t slot, uint32_t bar)
+{
+    uint32_t bytes = 0;
+    const char *src = nullptr;
+    if (v < vend) {
+        const int s = a.row_ptr[v], e = a.row_ptr[v + 1];
+        const int64_t b = int64_t(e - s) * a.rowbytes;
+        if (b > 0 && b <= kSlotBytes) {
+            bytes = uint32_t(b);
+            src = static_cast<const char *>(a.in) + int64_t(s) * a.rowbytes;
+        }
+    }
+    if (bytes) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(slot), "l"(src), "r"(bytes), "r"(bar) : "memory");
+    } else {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    }
+}
+
+template <typename R, int CPL>
+__global__ void __launch_bounds__(kRingWarps * 32) k_coined_ring(RingArgs a)
+{
+    using RV = RowVec<R, CPL>;
+    using T = typename RV::T;
+    extern __shared__ __align__(128) uint8_t ring_raw[];
+    __shared__ __align__(8) uint64_t bars[kRingWarps][kRingSlots];
+    __shared__ int rev_s[kRingWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *ring = ring_raw + warp * (kRingSlots * kSlotBytes);
+    const uint32_t ring_s = smem_addr(ring);
+    if (lane == 0) {
+        for (int k = 0; k < kRingSlots; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bars[warp][k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t W = int64_t(gridDim.x) * kRingWarps;
+    const int64_t w = int64_t(blockIdx.x) * kRingWarps + warp;
+    const int64_t vbeg = a.n * w / W, vend = a.n * (w + 1) / W;
+    const T *__restrict__ in = static_cast<const T *>(a.in);
+    T *__restrict__ out = static_cast<T *>(a.out);
+    const int BV = a.rowbytes / int(sizeof(T));       // 16-byte (or 8-byte) vectors per row
+    const int B = a.batch;
+
+    if (lane == 0)
+        for (int k = 0; k < kRingSlots - 1; ++k)
+            ring_issue(a, vbeg + k, vend, ring_s + k * kSlotBytes, smem_addr(&bars[warp][k]));
+    bool ok = true;
+    int64_t waited = 0;     // slots consumed so far (phase bookkeeping for the drain)
+    for (int64_t v = vbeg; v < vend && ok; ++v) {
+        const int64_t k = v - vbeg;
+        const int slot = int(k % kRingSlots);
+        // keep kRingSlots-1 vertices in flight: refill the slot freed last iteration
+        if (lane == 0) {
+            const int nxt = int((k + kRingSlots - 1) % kRingSlots);
+            ring_issue(a, v + kRingSlots - 1, vend, ring_s + nxt * kSlotBytes, smem_addr(&bars[warp][nxt]));
+        }
+        const int s = a.row_ptr[v], e = a.row_ptr[v + 1], d = e - s;
+        if (lane < d) rev_s[warp][lane] = __ldg(a.rev + s + lane);
+        __syncwarp();
+        if (!ring_wait(smem_addr(&bars[warp][slot]), uint32_t((k / kRingSlots) & 1))) {
+            if (lane == 0) atomicExch(a.err, 1);
+            ok = false;
+            break;
+        }
+        waited = k + 1;
+        if (d > 0) {
+            const int mi = find_marked(a.mk, int(v));
+            const bool staged = int64_t(d) * a.rowbytes <= kSlotBytes;
+            const T *rows = staged ? reinterpret_cast<const T *>(ring + slot * kSlotBytes) : in + int64_t(s) * BV;
+            if (mi >= 0) {
+                // marked vertex (rare): -I coin, and its probability in double for the record.
+                // Kept apart from the Grover loop so no FP64 work is issued for other vertices.
+                for (int cv = lane; cv < BV; cv += 32) {
+                    if (a.rec_part && a.rec_slot >= 0) {
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) {
+                            double acc = 0.0;
+                            for (int j = 0; j < d; ++j) {
+                                const T p = rows[j * BV + cv];
+                                const double x = RV::re(p, q), y = RV::im(p, q);
+                                acc += x * x + y * y;
+                            }
+                            a.rec_part[(a.rec_slot * a.mk.n + mi) * B + cv * CPL + q] = acc;
+                        }
+                    }
+                    for (int j = 0; j < d; ++j) {
+                        const int r = (j < 32) ? rev_s[warp][j] : __ldg(a.rev + s + j);
+                        out[int64_t(r) * BV + cv] = grover_row(R(0), RV::zero(), rows[j * BV + cv]);
+                    }
+                }
+            } else {
+                const R f = R(a.two_over_d[d]);
+                for (int cv = lane; cv < BV; cv += 32) {
+                    T sum = RV::zero();
+                    for (int j = 0; j < d; ++j) add_row(sum, rows[j * BV + cv]);
+                    for (int j = 0; j < d; ++j) {
+                        const int r = (j < 32) ? rev_s[warp][j] : __ldg(a.rev + s + j);
+                        out[int64_t(r) * BV + cv] = grover_row(f, sum, rows[j * BV + cv]);
+                    }
+                }
+            }
+        }
+        // the slot is read; order those generic reads before the async refill
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    // drain: wait (bounded) for every issued slot not consumed yet, so no bulk
+    // copy is still writing this CTA's shared memory when it exits
+    const int64_t issued = (vend - vbeg) + kRingSlots - 1;
+    const int64_t last = ok ? issued : (waited + kRingSlots - 1 < issued ? waited + kRingSlots - 1 : issued);
+    for (int64_t k = waited; k < last; ++k)
+        if (!ring_wait(smem_addr(&bars[warp][int(k % kRingSlots)]), uint32_t((k / kRingSlots) & 1))) {
+            if (lane == 0) atomicExch(a.err, 1);
+            break;
+        }
+}
+
 // -------------------------------------------------------- marked records
 // dst[mi*batch + b] = sum over the arcs of marked[mi] of |psi|^2 (row_ptr != NULL),
 // or |psi[marked[mi]]|^2 for a vertex-indexed state (row_ptr == NULL).
@@ -767,12 +945,62 @@ static void launch_rows(const RowsArgs &a, int shape, cudaStream_t st)
     else k_coined_rows<R, CPL, 16><<<grid, threads, 0, st>>>(a);
 }
 
+constexpr int kNumShapes = kNumRowShapes + 2;   // + TMA ring with 2 or 1 CTAs per SM
+
+template <typename R, int CPL>
+static hw_status launch_ring(const RingArgs &a, int ctas_per_sm, cudaStream_t st)
+{
+    const int smem = kRingWarps * kRingSlots * kSlotBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_coined_ring<R, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_coined_ring)");
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t warps_needed = (a.n + 3) / 4;   // at least 4 vertices per warp
+    int64_t grid = int64_t(sms) * ctas_per_sm;
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, (warps_needed + kRingWarps - 1) / kRingWarps));
+    k_coined_ring<R, CPL><<<grid, kRingWarps * 32, smem, st>>>(a);
+    return HW_OK;
+}
+
 static void launch_rows_dt(hw_dtype dt, int batch, RowsArgs a, int shape, cudaStream_t st)
 {
     a.vpw = kRowShapes[shape][1];
     if (dt == HW_C128) launch_rows<double, 1>(a, shape, st);
     else if (batch % 2 == 0) launch_rows<float, 2>(a, shape, st);
     else launch_rows<float, 1>(a, shape, st);
+}
+
+// ring staging needs 16-byte aligned rows that fit a slot
+static bool ring_ok(hw_dtype dt, int batch, const void *in, const void *out)
+{
+    const int rowbytes = batch * int(cplx_bytes(dt));
+    return rowbytes % 16 == 0 && rowbytes <= kSlotBytes && (uintptr_t(in) % 16) == 0 && (uintptr_t(out) % 16) == 0;
+}
+
+static hw_status launch_shape(const hw_graph *g, hw_dtype dt, int batch, const RowsArgs &a, int shape,
+                              cudaStream_t st)
+{
+    if (shape < kNumRowShapes) {
+        launch_rows_dt(dt, batch, a, shape, st);
+        return HW_OK;
+    }
+    RingArgs r;
+    r.two_over_d = a.two_over_d;
+    r.row_ptr = a.row_ptr;
+    r.rev = a.rev;
+    r.rec_part = a.rec_part;
+    r.in = a.in;
+    r.out = a.out;
+    r.err = g->d_err;
+    r.rec_slot = a.rec_slot;
+    r.n = a.n;
+    r.batch = batch;
+    r.rowbytes = batch * int(cplx_bytes(dt));
+    r.mk = a.mk;
+    const int per_sm = (shape == kNumRowShapes) ? 2 : 1;
+    if (dt == HW_C128) return launch_ring<double, 1>(r, per_sm, st);
+    return launch_ring<float, 2>(r, per_sm, st);
 }
 
 // Pick the fastest launch shape for (graph, dtype, batch) by timing each
@@ -796,10 +1024,12 @@ static hw_status tune_rows(const hw_graph *g, hw_dtype dt, int batch, const Rows
     if ((s = hw_cuda(cudaEventCreate(&e1), "cudaEventCreate")) != HW_OK) { cudaEventDestroy(e0); return s; }
     float best_ms = 1e30f;
     int pick = 4;
-    for (int c = 0; c < kNumRowShapes && s == HW_OK; ++c) {
-        launch_rows_dt(dt, batch, a, c, st);   // warm-up
+    const int shapes = ring_ok(dt, batch, base.in, base.out) ? kNumShapes : kNumRowShapes;
+    for (int c = 0; c < shapes && s == HW_OK; ++c) {
+        s = launch_shape(g, dt, batch, a, c, st);   // warm-up
+        if (s != HW_OK) break;
         cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; ++r) launch_rows_dt(dt, batch, a, c, st);
+        for (int r = 0; r < 3; ++r) launch_shape(g, dt, batch, a, c, st);
         cudaEventRecord(e1, st);
         s = hw_cuda(cudaEventSynchronize(e1), "autotune");
         float ms = 0.f;
@@ -858,8 +1088,10 @@ hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coi
         hw_status ts = tune_rows(g, dt, batch, a, st, &shape);
         if (ts != HW_OK) return ts;
     }
-    launch_rows_dt(dt, batch, a, shape, st);
-    return hw_cuda(cudaGetLastError(), "k_coined_rows launch");
+    if (shape >= kNumRowShapes && !ring_ok(dt, batch, s.in, s.out)) shape = 9;
+    hw_status ls = launch_shape(g, dt, batch, a, shape, st);
+    if (ls != HW_OK) return ls;
+    return hw_cuda(cudaGetLastError(), "batched coined launch");
 }
 
 hw_status launch_marked_prob(const int32_t *row_ptr, hw_dtype dt, int batch, const void *psi,

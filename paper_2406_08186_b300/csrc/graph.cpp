@@ -102,7 +102,9 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
         cudaMalloc(&g->d_head, arcs_b) != cudaSuccess ||
         cudaMalloc(&g->d_rev, arcs_b) != cudaSuccess ||
         cudaMalloc(&g->d_blk, sizeof(int32_t) * g->h_blk.size()) != cudaSuccess ||
-        cudaMalloc(&g->d_two_over_d, sizeof(double) * (g->max_degree + 1)) != cudaSuccess) {
+        cudaMalloc(&g->d_two_over_d, sizeof(double) * (g->max_degree + 1)) != cudaSuccess ||
+        cudaHostAlloc(&g->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&g->d_err, g->h_err, 0) != cudaSuccess) {
         cudaGetLastError();
         return fail(hw_fail(HW_ENOMEM, "device allocation of the graph failed"));
     }
@@ -118,6 +120,7 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
                                      cudaMemcpyHostToDevice, st), "upload weights")) != HW_OK ||
         (s = hw_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HW_OK)
         return fail(s);
+    *g->h_err = 0;
     *out = g;
     return HW_OK;
 }
@@ -131,6 +134,7 @@ extern "C" hw_status hw_graph_free(hw_graph *g)
     cudaFree(g->d_rev);
     cudaFree(g->d_blk);
     cudaFree(g->d_two_over_d);
+    if (g->h_err) cudaFreeHost(g->h_err);
     cudaGetLastError();
     delete g;
     return HW_OK;

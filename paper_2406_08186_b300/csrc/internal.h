@@ -27,6 +27,8 @@ struct hw_graph {
     int32_t *d_rev = nullptr;        // [num_arcs]
     int32_t *d_blk = nullptr;        // [nblk+1] first vertex of each block
     double *d_two_over_d = nullptr;  // [max_degree+1], 2/d (0 for d = 0): the Grover weight
+    int *h_err = nullptr;            // zero-copy word: a kernel's bounded wait ran out of time
+    int *d_err = nullptr;            // its device alias
     std::vector<int32_t> h_row_ptr;  // host copy for launch decisions
     std::vector<int32_t> h_blk;
     // autotuned launch shape of the batched kernel per (batch, dtype)

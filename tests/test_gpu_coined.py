@@ -215,3 +215,32 @@ def test_invalid_calls_report_errors(hw):
         hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 4, x[:-1], x[1:])  # overlapping buffers
     assert e.value.status == hw.HW_EINVAL
     G.free()
+
+
+@pytest.mark.parametrize("tile", [1, 6, 7, 12, 13, 14])
+@pytest.mark.parametrize("dt,B", [(1, 8), (2, 4), (1, 64)])
+def test_batched_every_launch_shape(hw, tile, dt, B):
+    # every register-row shape and both TMA-ring shapes, with a record; degrees
+    # up to 20 exercise the rows that do not fit the register/ring capacity
+    import torch
+    g = synth.erdos_renyi(3000, 10 / 2999, seed=17)
+    ar = oracle.Arcs(*g)
+    n, steps = ar.n, 9
+    psi0 = synth.gaussian_states(ar.num_arcs, B, seed=5)
+    marked = [4, n - 2]
+    row_ptr, col = synth.adjacency_csr(*g)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    cdt = torch.complex128 if dt == 2 else torch.complex64
+    x = torch.from_numpy(psi0).to("cuda", cdt).reshape(-1)
+    out = torch.empty_like(x)
+    rec = torch.empty(steps * B, dtype=torch.float64, device="cuda")
+    hw.hw_coined_evolve(G, 0, marked, dt, B, steps, x, out, rec, opts={"tile": tile})
+    torch.cuda.synchronize()
+    psi = out.cpu().numpy().astype(np.complex128).reshape(-1, B)
+    recs = rec.cpu().numpy().reshape(steps, B)
+    for b in (0, B - 1):
+        ref, rr = oracle.coined_evolve(ar, psi0[:, b], steps, 0, marked, record=True)
+        tol = TOL128 if dt == 2 else 1e-5
+        assert np.max(np.abs(psi[:, b] - ref)) <= tol
+        assert np.max(np.abs(recs[:, b] - rr)) <= tol
+    G.free()

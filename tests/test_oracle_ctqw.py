@@ -102,3 +102,17 @@ def test_small_graphs_against_scipy_expm(seed):
     assert np.max(np.abs(got - np.linalg.matrix_power(U, 5) @ psi0)) < 1e-12
     p = oracle.prob_vertex(got)
     assert abs(p.sum() - 1.0) < 1e-13
+
+
+def test_single_vector_action_and_vertex_probability():
+    n, eu, ev = synth.erdos_renyi(12, 0.4, seed=6, drop_isolated=False)
+    ar = oracle.Arcs(n, eu, ev)
+    A = np.zeros((n, n))
+    A[eu, ev] = A[ev, eu] = 1.0
+    H = -0.9 * A
+    H[3, 3] -= 1.0
+    x = synth.random_state(n, seed=8)
+    ref = scipy.linalg.expm(-1j * H * 0.7) @ x
+    assert np.max(np.abs(oracle.ctqw_action(ar, 0.9, 0.7, x, marked=[3]) - ref)) < 1e-13
+    p = oracle.prob_vertex(np.array([3 + 4j, 1j, 0.0]))
+    assert np.array_equal(p, np.array([25.0, 1.0, 0.0]))
