@@ -253,8 +253,13 @@ struct RegArgs {
     int64_t rec_slot;
     int64_t n;
     double two_over_d;
+    float two_over_d_f;     // the same weight rounded once on the host (no per-thread conversion)
     MarkedList mk;
 };
+
+template <typename R> __device__ __forceinline__ R grover_weight(const RegArgs &a);
+template <> __device__ __forceinline__ double grover_weight<double>(const RegArgs &a) { return a.two_over_d; }
+template <> __device__ __forceinline__ float grover_weight<float>(const RegArgs &a) { return a.two_over_d_f; }
 
 template <int D>
 __device__ __forceinline__ void load_rev(const int32_t *__restrict__ rev, int64_t v, int *r)
@@ -277,55 +282,67 @@ __device__ __forceinline__ void load_rev(const int32_t *__restrict__ rev, int64_
     }
 }
 
-template <typename R, int D, int COIN>
+template <typename R, int D, int COIN, int VPT>
 __global__ void __launch_bounds__(kThreads) k_coined_vertex(RegArgs a)
 {
     using V = typename Cx<R>::T;
     const V *__restrict__ in = static_cast<const V *>(a.in);
     V *__restrict__ out = static_cast<V *>(a.out);
-    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (v >= a.n) return;
-    V p[D];
-    int r[D];
+    const int64_t base = int64_t(blockIdx.x) * blockDim.x * VPT + threadIdx.x;
+    V p[VPT][D];
+    int r[VPT][D];
+    // every load of this thread's vertices first, then the arithmetic
 #pragma unroll
-    for (int j = 0; j < D; ++j) p[j] = in[v * D + j];
-    load_rev<D>(a.rev, v, r);
-    const int mi = find_marked(a.mk, int(v));
-    if (mi >= 0) {
-        if (a.rec_part && a.rec_slot >= 0) {
-            double acc = 0.0;
+    for (int u = 0; u < VPT; ++u) {
+        const int64_t v = base + int64_t(u) * blockDim.x;
+        if (v < a.n) {
 #pragma unroll
-            for (int j = 0; j < D; ++j) acc += double(p[j].x) * double(p[j].x) + double(p[j].y) * double(p[j].y);
-            a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+            for (int j = 0; j < D; ++j) p[u][j] = in[v * D + j];
+            load_rev<D>(a.rev, v, r[u]);
         }
-#pragma unroll
-        for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(-p[j].x, -p[j].y);
-        return;
     }
-    if (COIN == HW_COIN_GROVER) {
-        R sx = p[0].x, sy = p[0].y;
 #pragma unroll
-        for (int j = 1; j < D; ++j) { sx += p[j].x; sy += p[j].y; }
-        const R f = R(a.two_over_d);
-        // c_j = (2/d) sum - psi_j, one fused multiply-add per component
+    for (int u = 0; u < VPT; ++u) {
+        const int64_t v = base + int64_t(u) * blockDim.x;
+        if (v >= a.n) continue;
+        const int mi = find_marked(a.mk, int(v));
+        if (mi >= 0) {
+            if (a.rec_part && a.rec_slot >= 0) {
+                double acc = 0.0;
 #pragma unroll
-        for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
-    } else {
-        const R scale = R(1) / sqrt(R(D));
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            R cx = 0, cy = 0;
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const double2 w = c_tw[D * (D - 1) / 2 + (j * k) % D];
-                cx += R(w.x) * p[k].x - R(w.y) * p[k].y;
-                cy += R(w.x) * p[k].y + R(w.y) * p[k].x;
+                for (int j = 0; j < D; ++j)
+                    acc += double(p[u][j].x) * double(p[u][j].x) + double(p[u][j].y) * double(p[u][j].y);
+                a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
             }
-            out[r[j]] = mkv<V, R>(cx * scale, cy * scale);
+#pragma unroll
+            for (int j = 0; j < D; ++j) out[r[u][j]] = mkv<V, R>(-p[u][j].x, -p[u][j].y);
+            continue;
+        }
+        if (COIN == HW_COIN_GROVER) {
+            R sx = p[u][0].x, sy = p[u][0].y;
+#pragma unroll
+            for (int j = 1; j < D; ++j) { sx += p[u][j].x; sy += p[u][j].y; }
+            const R f = grover_weight<R>(a);
+            // c_j = (2/d) sum - psi_j, one fused multiply-add per component
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+                out[r[u][j]] = mkv<V, R>(fma(f, sx, -p[u][j].x), fma(f, sy, -p[u][j].y));
+        } else {
+            const R scale = R(1) / sqrt(R(D));
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                R cx = 0, cy = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const double2 w = c_tw[D * (D - 1) / 2 + (j * k) % D];
+                    cx += R(w.x) * p[u][k].x - R(w.y) * p[u][k].y;
+                    cy += R(w.x) * p[u][k].y + R(w.y) * p[u][k].x;
+                }
+                out[r[u][j]] = mkv<V, R>(cx * scale, cy * scale);
+            }
         }
     }
 }
-
 
 // Lane-group variant for complex64 (FP32 arithmetic is cheap; the limit is
 // memory requests): a group of G = 2^ceil(log2 d) consecutive lanes owns one
@@ -344,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_lanes(RegArgs a, int d)
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
     const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t vbase = warp * (VPW * U) + lane / G;
-    const R f2 = R(a.two_over_d);
+    const R f2 = grover_weight<R>(a);
 
     V p[U];
     int r[U];
@@ -364,7 +381,8 @@ __global__ void __launch_bounds__(kThreads) k_coined_lanes(RegArgs a, int d)
     for (int u = 0; u < U; ++u) {
         const int64_t v = vbase + u * VPW;
         const int mi = (v < a.n) ? find_marked(a.mk, int(v)) : -1;   // uniform in the group
-        if (mi >= 0 && a.rec_part && a.rec_slot >= 0) {
+        // warp-uniform test first, so warps without a marked vertex issue no FP64 work
+        if (__any_sync(0xffffffffu, mi >= 0) && a.rec_part && a.rec_slot >= 0 && mi >= 0) {
             double acc = double(p[u].x) * double(p[u].x) + double(p[u].y) * double(p[u].y);
 #pragma unroll
             for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(gmask, acc, o);
@@ -825,16 +843,17 @@ __global__ void k_record_finalize(const double *__restrict__ part, int n_marked,
 template <typename R, int COIN>
 static void launch_vertex(int d, const RegArgs &a, cudaStream_t st)
 {
-    const int64_t grid = (a.n + kThreads - 1) / kThreads;
+    constexpr int VPT = 1;   // vertices per thread (2 doubles the registers; measured slower while FP64-bound)
+    const int64_t grid = (a.n + kThreads * VPT - 1) / (kThreads * VPT);
     switch (d) {
-    case 1: k_coined_vertex<R, 1, COIN><<<grid, kThreads, 0, st>>>(a); break;
-    case 2: k_coined_vertex<R, 2, COIN><<<grid, kThreads, 0, st>>>(a); break;
-    case 3: k_coined_vertex<R, 3, COIN><<<grid, kThreads, 0, st>>>(a); break;
-    case 4: k_coined_vertex<R, 4, COIN><<<grid, kThreads, 0, st>>>(a); break;
-    case 5: k_coined_vertex<R, 5, COIN><<<grid, kThreads, 0, st>>>(a); break;
-    case 6: k_coined_vertex<R, 6, COIN><<<grid, kThreads, 0, st>>>(a); break;
-    case 7: k_coined_vertex<R, 7, COIN><<<grid, kThreads, 0, st>>>(a); break;
-    default: k_coined_vertex<R, 8, COIN><<<grid, kThreads, 0, st>>>(a); break;
+    case 1: k_coined_vertex<R, 1, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    case 2: k_coined_vertex<R, 2, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    case 3: k_coined_vertex<R, 3, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    case 4: k_coined_vertex<R, 4, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    case 5: k_coined_vertex<R, 5, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    case 6: k_coined_vertex<R, 6, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    case 7: k_coined_vertex<R, 7, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    default: k_coined_vertex<R, 8, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
     }
 }
 
@@ -896,6 +915,7 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
         r.rec_slot = s.rec_slot;
         r.n = g->n;
         r.two_over_d = 2.0 / double(d);
+        r.two_over_d_f = float(2.0 / double(d));
         r.mk = s.marked;
         if (dt == HW_C128) {
             if (coin == HW_COIN_GROVER) launch_vertex<double, HW_COIN_GROVER>(d, r, st);
