@@ -243,6 +243,92 @@ hw_status hw_probability_noalloc(const hw_graph *g, int64_t n, hw_dtype dt, int3
 hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A, const float *B, float *C,
                      int32_t slices, void *stream);
 
+/*
+ * hw_ctqw_evolve_sparse -- psi_out = (e^{-iH time})^steps psi_in (Sec. 3.1)
+ * without forming U: each application sums the exponential series of
+ * H time/q on the CSR, q = 2^s parts, degree m, with (m, s) from
+ * hw_ctqw_plan (opts may override).  Suited to graphs too large for a dense
+ * U.  Arguments, layouts, record and errors as hw_ctqw_evolve, with the graph
+ * and (gamma, marked) of hw_ctqw_expm.  Scratch: four state-sized buffers.
+ */
+hw_status hw_ctqw_evolve_sparse(const hw_graph *g, double gamma, const int32_t *marked, int32_t n_marked,
+                                double time, hw_dtype dt, int32_t batch, int64_t steps,
+                                const void *psi_in, void *psi_out, double *record,
+                                const hw_opts *opts, void *stream);
+
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of walk jobs on one GPU (no counterpart in the paper,
+ * which evolves one walk per call).  Jobs wait in a queue until a slot and
+ * device memory in the server's arena are free; every admitted job keeps its
+ * states on the device, and each hw_server_run round advances every resident
+ * job by K sub-steps (a coined step, or one series term of e^{-iH dt}) with
+ * one multi-job kernel launch per sub-step, K launches replayed as one CUDA
+ * graph.  Each job starts from the uniform state over its basis (all arcs for
+ * a coined walk, all vertices for a CTQW) and returns its probabilities
+ * (Sec. 3.1 / 3.2, summed in double) and, with marked vertices, the total
+ * marked probability after every step.  A job's result does not depend on
+ * the other jobs in the mix.
+ */
+typedef enum { HW_JOB_COINED = 0, HW_JOB_CTQW = 1 } hw_job_kind;
+
+typedef struct hw_job {
+    const hw_graph *graph;   /* resident graph; coined jobs need a regular graph, degree 1..32 */
+    int32_t kind;            /* hw_job_kind; coined jobs use the Grover coin */
+    int32_t dt;              /* HW_C64 or HW_C128 */
+    int64_t steps;           /* walk steps / applications of e^{-iH time} (>= 1) */
+    const int32_t *marked;   /* HOST ids, copied at submit; 0..4 vertices */
+    int32_t n_marked;
+    int32_t reserved;
+    double gamma;            /* CTQW: H = -gamma A - sum_m |m><m| */
+    double time;             /* CTQW: time per application */
+} hw_job;
+
+typedef struct hw_server hw_server;
+
+/*
+ * hw_server_create -- reserve the device arena (arena_bytes, cudaMalloc once),
+ * a pinned host arena for results (host_bytes), a job table of max_jobs
+ * slots, and capture the K-launch graph (K = substeps_per_round).  The server
+ * runs on a stream of its own; `stream` is unused (pass NULL).
+ * Errors: HW_EINVAL, HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int32_t substeps_per_round,
+                           int64_t host_bytes, void *stream, hw_server **out);
+
+/* Queue a job; *job_id receives its id.  HW_ENOMEM if it could never fit the
+ * arenas; HW_EUNSUPPORTED for a coined job on an irregular graph. */
+hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *job_id);
+
+/*
+ * One scheduling round: retire jobs whose last sub-step has run (their
+ * results are produced and copied back asynchronously), release the memory
+ * of retired jobs whose copies have completed, admit queued jobs first come
+ * first served while a slot and arena memory are free, and launch K
+ * sub-steps of all resident jobs.  Does not wait for the GPU, except for the
+ * previous round's table upload.  *n_completed (may be NULL) receives the
+ * number of jobs that became collectable in this round.
+ */
+hw_status hw_server_run(hw_server *s, int32_t *n_completed);
+
+/* Ids of jobs that became collectable since the last poll (up to max_ids). */
+hw_status hw_server_poll(hw_server *s, int64_t *ids, int32_t max_ids, int32_t *n_ids);
+
+/*
+ * Copy a finished job's results to HOST buffers and forget the job:
+ *   prob      double[n] (n_prob must equal the graph's vertex count), or NULL
+ *   record    double[steps] (needs a marked vertex), or NULL
+ *   latency_s seconds from submit to the round that saw the results ready, or NULL
+ */
+hw_status hw_server_result(hw_server *s, int64_t job_id, double *prob, int64_t n_prob, double *record,
+                           int64_t n_record, double *latency_s);
+
+/* Occupancy counters (any output may be NULL). */
+hw_status hw_server_stats(const hw_server *s, int64_t *queued, int64_t *resident, int64_t *arena_used,
+                          int64_t *ticks);
+
+/* Wait for the server's stream and free everything it holds. */
+hw_status hw_server_destroy(hw_server *s);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *hw_last_error(void);
 

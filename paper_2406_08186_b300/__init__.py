@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhiperwalk_b300.so")
 HW_OK, HW_EINVAL, HW_ENOMEM, HW_ECUDA, HW_ETIMEDOUT, HW_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 HW_C64, HW_C128 = 1, 2
 HW_COIN_GROVER, HW_COIN_FOURIER = 0, 1
+HW_JOB_COINED, HW_JOB_CTQW = 0, 1
 
 STATUS_NAMES = {0: "HW_OK", -1: "HW_EINVAL", -2: "HW_ENOMEM", -3: "HW_ECUDA",
                 -4: "HW_ETIMEDOUT", -5: "HW_EUNSUPPORTED"}
@@ -26,7 +27,9 @@ STATUS_NAMES = {0: "HW_OK", -1: "HW_EINVAL", -2: "HW_ENOMEM", -3: "HW_ECUDA",
 # every entry point the header declares
 EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free", "hw_graph_info",
            "hw_coined_evolve", "hw_ctqw_plan", "hw_ctqw_expm", "hw_ctqw_evolve", "hw_probability",
-           "hw_probability_noalloc", "hw_gemm_tc", "hw_last_error", "hw_version")
+           "hw_probability_noalloc", "hw_gemm_tc", "hw_ctqw_evolve_sparse",
+           "hw_server_create", "hw_server_submit", "hw_server_run", "hw_server_poll",
+           "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_last_error", "hw_version")
 
 
 class HWError(RuntimeError):
@@ -40,6 +43,12 @@ class hw_opts(ctypes.Structure):
     _fields_ = [("record_stride", ctypes.c_int32), ("taylor_degree", ctypes.c_int32),
                 ("taylor_squarings", ctypes.c_int32), ("gemm_slices", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class hw_job(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("kind", ctypes.c_int32), ("dt", ctypes.c_int32),
+                ("steps", ctypes.c_int64), ("marked", ctypes.c_void_p), ("n_marked", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double), ("time", ctypes.c_double)]
 
 
 _lib = None
@@ -80,6 +89,23 @@ def lib():
         L.hw_probability_noalloc.restype = st
         L.hw_gemm_tc.argtypes = [i64, i64, i64, P, P, P, i32, P]
         L.hw_gemm_tc.restype = st
+        L.hw_ctqw_evolve_sparse.argtypes = [P, d, P, i32, d, st, i32, i64, P, P, P, ctypes.POINTER(hw_opts), P]
+        L.hw_ctqw_evolve_sparse.restype = st
+        L.hw_server_create.argtypes = [i64, i32, i32, i64, P, ctypes.POINTER(P)]
+        L.hw_server_create.restype = st
+        L.hw_server_submit.argtypes = [P, ctypes.POINTER(hw_job), ctypes.POINTER(i64)]
+        L.hw_server_submit.restype = st
+        L.hw_server_run.argtypes = [P, ctypes.POINTER(i32)]
+        L.hw_server_run.restype = st
+        L.hw_server_poll.argtypes = [P, P, i32, ctypes.POINTER(i32)]
+        L.hw_server_poll.restype = st
+        L.hw_server_result.argtypes = [P, i64, P, i64, P, i64, ctypes.POINTER(d)]
+        L.hw_server_result.restype = st
+        L.hw_server_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64)]
+        L.hw_server_stats.restype = st
+        L.hw_server_destroy.argtypes = [P]
+        L.hw_server_destroy.restype = st
         L.hw_last_error.argtypes = []
         L.hw_last_error.restype = ctypes.c_char_p
         L.hw_version.argtypes = []
@@ -269,3 +295,87 @@ def hw_gemm_tc(A, B, C, slices: int = 3, stream=None):
     n = B.shape[0]
     _check(lib().hw_gemm_tc(int(m), int(n), int(k), _dev(A, "float32"), _dev(B, "float32"),
                             _dev(C, "float32"), int(slices), _stream(stream)))
+
+
+def hw_ctqw_evolve_sparse(g: Graph, gamma: float, marked, time: float, dt: int, batch: int, steps: int,
+                          psi_in, psi_out, record=None, opts=None, stream=None):
+    m, nm = _host_i32(marked)
+    _check(lib().hw_ctqw_evolve_sparse(g, float(gamma), None if m is None else m.ctypes.data_as(ctypes.c_void_p),
+                                       nm, float(time), int(dt), int(batch), int(steps),
+                                       _dev(psi_in, _CPLX[dt]), _dev(psi_out, _CPLX[dt]),
+                                       _dev(record, "float64"), _opts(opts), _stream(stream)))
+
+
+class Server:
+    """Owner of an ``hw_server`` (continuous batching of walk jobs)."""
+
+    def __init__(self, arena_bytes: int, max_jobs: int = 256, substeps: int = 8, host_bytes: int = 1 << 30):
+        h = ctypes.c_void_p()
+        _check(lib().hw_server_create(int(arena_bytes), int(max_jobs), int(substeps), int(host_bytes), None,
+                                      ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+    def submit(self, graph: Graph, kind: int, dt: int, steps: int, marked=(), gamma: float = 0.0,
+               time: float = 0.0) -> int:
+        m = np.ascontiguousarray(list(marked), dtype=np.int32)
+        j = hw_job(graph.handle, int(kind), int(dt), int(steps),
+                   m.ctypes.data_as(ctypes.c_void_p) if m.size else None, int(m.size), 0, float(gamma),
+                   float(time))
+        jid = ctypes.c_int64()
+        _check(lib().hw_server_submit(self, ctypes.byref(j), ctypes.byref(jid)))
+        self._keep[jid.value] = (graph, int(steps), int(m.size))
+        return jid.value
+
+    def run(self) -> int:
+        n = ctypes.c_int32()
+        _check(lib().hw_server_run(self, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, max_ids: int = 4096):
+        ids = np.zeros(max_ids, dtype=np.int64)
+        n = ctypes.c_int32()
+        _check(lib().hw_server_poll(self, ids.ctypes.data_as(ctypes.c_void_p), int(max_ids), ctypes.byref(n)))
+        return [int(x) for x in ids[:n.value]]
+
+    def result(self, job_id: int):
+        graph, steps, nm = self._keep.pop(job_id)
+        prob = np.empty(graph.n, dtype=np.float64)
+        rec = np.empty(steps, dtype=np.float64) if nm else None
+        lat = ctypes.c_double()
+        _check(lib().hw_server_result(self, int(job_id), prob.ctypes.data_as(ctypes.c_void_p), prob.size,
+                                      None if rec is None else rec.ctypes.data_as(ctypes.c_void_p),
+                                      0 if rec is None else rec.size, ctypes.byref(lat)))
+        return prob, rec, lat.value
+
+    def stats(self):
+        q, r, a, t = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().hw_server_stats(self, ctypes.byref(q), ctypes.byref(r), ctypes.byref(a), ctypes.byref(t)))
+        return {"queued": q.value, "resident": r.value, "arena_used": a.value, "ticks": t.value}
+
+    def drain(self):
+        """Run rounds until every submitted job is collectable; returns their ids."""
+        done = []
+        while True:
+            self.run()
+            done += self.poll()
+            st = self.stats()
+            if st["queued"] == 0 and st["resident"] == 0:
+                self.run()
+                done += self.poll()
+                return done
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            _lib.hw_server_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

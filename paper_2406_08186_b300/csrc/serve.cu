@@ -1,0 +1,697 @@
+// Serving: continuous batching of walk jobs on one GPU.
+//
+// Jobs (a coined walk or a continuous-time walk on a resident graph, any
+// step count, complex64 or complex128, up to 4 marked vertices) are queued by
+// hw_server_submit and admitted as soon as a slot and device memory (a
+// first-fit arena reserved at creation) are free.  Every resident job's
+// buffers stay on the device; each scheduling round launches, as one CUDA
+// graph, K sub-steps of a single multi-job kernel that advances every
+// resident job by one sub-step (a coined walk step, or one Taylor term of
+// e^{-iH dt}), reading a device job table and tile list, so jobs that join or
+// leave between rounds never require re-capturing the graph.  Finished jobs
+// are retired: probabilities (double sums) and the marked-probability record
+// are produced on the device and copied to a pinned host arena; the caller
+// collects them with hw_server_result.
+//
+// Each job's arithmetic depends only on its own data and a fixed per-vertex
+// order, so its result is the same alone and in any mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int kServeThreads = 256;
+constexpr int kTileVertices = 1024;
+constexpr int kMaxServeMarked = 4;
+
+struct SJob {
+    const int32_t *row_ptr;
+    const int32_t *head;
+    const int32_t *rev;
+    void *X[2];              // state ping-pong
+    void *T[2];              // CTQW series terms
+    double *rec;             // [steps][n_marked] per-marked partials (nullptr if no marks)
+    int64_t n;
+    int64_t start_tick;
+    int64_t total_subs;
+    double two_over_d;
+    double gamma;
+    double tau;
+    int32_t kind;            // 0 coined, 1 CTQW
+    int32_t dt;              // HW_C64 / HW_C128
+    int32_t d;               // coined: the graph's (regular) degree
+    int32_t m;               // CTQW: series degree
+    int32_t q;               // CTQW: parts per application
+    int32_t n_marked;
+    int32_t marked[kMaxServeMarked];
+};
+
+struct Tile {
+    int32_t job, v0, v1, pad;
+};
+
+template <typename R> struct CxS;
+template <> struct CxS<double> { using T = double2; };
+template <> struct CxS<float> { using T = float2; };
+
+__device__ __forceinline__ int job_marked(const SJob &J, int v)
+{
+    for (int i = 0; i < J.n_marked; ++i)
+        if (J.marked[i] == v) return i;
+    return -1;
+}
+
+// one coined walk step for vertex v (regular degree d), step index w
+template <typename R>
+__device__ void serve_coined(const SJob &J, int64_t w, int v)
+{
+    using V = typename CxS<R>::T;
+    const V *__restrict__ in = static_cast<const V *>(J.X[w & 1]);
+    V *__restrict__ out = static_cast<V *>(J.X[(w + 1) & 1]);
+    const int d = J.d;
+    const int64_t s = int64_t(v) * d;
+    const int mi = job_marked(J, v);
+    if (mi >= 0) {
+        if (J.rec && w >= 1) {
+            double acc = 0.0;
+            for (int j = 0; j < d; ++j) {
+                const V p = in[s + j];
+                acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+            }
+            J.rec[(w - 1) * J.n_marked + mi] = acc;
+        }
+        for (int j = 0; j < d; ++j) {
+            const V p = in[s + j];
+            V c;
+            c.x = -p.x;
+            c.y = -p.y;
+            out[J.rev[s + j]] = c;
+        }
+        return;
+    }
+    R sx = 0, sy = 0;
+    for (int j = 0; j < d; ++j) {
+        const V p = in[s + j];
+        sx += p.x;
+        sy += p.y;
+    }
+    const R f = R(J.two_over_d);
+    for (int j = 0; j < d; ++j) {
+        const V p = in[s + j];
+        V c;
+        c.x = fma(f, sx, -p.x);
+        c.y = fma(f, sy, -p.y);
+        out[J.rev[s + j]] = c;
+    }
+}
+
+// one Taylor term of a CTQW job for vertex v, sub-step index ls
+template <typename R>
+__device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
+{
+    using V = typename CxS<R>::T;
+    const int64_t per = int64_t(J.q) * J.m;
+    const int64_t w = ls / per;
+    const int64_t rem = ls % per;
+    const int64_t r = rem / J.m;
+    const int k = int(rem % J.m) + 1;
+    const int cur = int((w * J.q + r) & 1);
+    const V *__restrict__ x = static_cast<const V *>(J.X[cur]);
+    const V *__restrict__ tin = (k == 1) ? x : static_cast<const V *>(J.T[(k - 1) & 1]);
+    V *__restrict__ tout = static_cast<V *>(J.T[k & 1]);
+    V *__restrict__ acc = static_cast<V *>(J.X[1 - cur]);
+    R sx = 0, sy = 0;
+    for (int a = J.row_ptr[v]; a < J.row_ptr[v + 1]; ++a) {
+        const V q = tin[J.head[a]];
+        sx += q.x;
+        sy += q.y;
+    }
+    R hx = R(-J.gamma) * sx, hy = R(-J.gamma) * sy;
+    const int mi = job_marked(J, v);
+    if (mi >= 0) {
+        hx -= tin[v].x;
+        hy -= tin[v].y;
+    }
+    const R c = R(J.tau / double(k));
+    V t;
+    t.x = c * hy;
+    t.y = -c * hx;
+    tout[v] = t;
+    const V base = (k == 1) ? x[v] : acc[v];
+    V o;
+    o.x = base.x + t.x;
+    o.y = base.y + t.y;
+    acc[v] = o;
+    if (mi >= 0 && J.rec && k == J.m && r == J.q - 1)
+        J.rec[w * J.n_marked + mi] = double(o.x) * double(o.x) + double(o.y) * double(o.y);
+}
+
+// One sub-step of every resident job.  Tiles are (job, vertex range); the
+// grid loops over them, so the launch shape never depends on the job mix.
+__global__ void __launch_bounds__(kServeThreads)
+k_serve_step(const SJob *__restrict__ jobs, const Tile *__restrict__ tiles, const int *__restrict__ ntiles,
+             const int64_t *__restrict__ tick)
+{
+    const int nt = *ntiles;
+    const int64_t now = *tick;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const SJob &J = jobs[tl.job];
+        const int64_t local = now - J.start_tick;
+        if (local < 0 || local >= J.total_subs) continue;
+        for (int v = tl.v0 + threadIdx.x; v < tl.v1; v += blockDim.x) {
+            if (J.kind == 0) {
+                if (J.dt == HW_C128) serve_coined<double>(J, local, v);
+                else serve_coined<float>(J, local, v);
+            } else {
+                if (J.dt == HW_C128) serve_ctqw<double>(J, local, v);
+                else serve_ctqw<float>(J, local, v);
+            }
+        }
+    }
+}
+
+__global__ void k_serve_tick(int64_t *tick) { *tick += 1; }
+
+template <typename V>
+__global__ void k_fill(V *x, int64_t count, double value)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
+        V v;
+        v.x = decltype(v.x)(value);
+        v.y = 0;
+        x[i] = v;
+    }
+}
+
+// record[w] = sum over marked of the partials, in marked order
+__global__ void k_serve_record(const double *part, int n_marked, int64_t steps, double *record)
+{
+    const int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (w >= steps) return;
+    double s = 0.0;
+    for (int i = 0; i < n_marked; ++i) s += part[w * n_marked + i];
+    record[w] = s;
+}
+
+// First-fit allocator over one reserved region (device or pinned host).
+class Arena {
+public:
+    void init(char *base, size_t size)
+    {
+        base_ = base;
+        size_ = size;
+        free_.clear();
+        free_[0] = size;
+        used_ = 0;
+    }
+    char *alloc(size_t bytes)
+    {
+        bytes = (bytes + 255) & ~size_t(255);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                const size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > bytes) free_[off + bytes] = len - bytes;
+                used_ += bytes;
+                live_[off] = bytes;
+                return base_ + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(char *p)
+    {
+        if (!p) return;
+        const size_t off = size_t(p - base_);
+        auto lv = live_.find(off);
+        if (lv == live_.end()) return;
+        size_t len = lv->second;
+        live_.erase(lv);
+        used_ -= len;
+        size_t start = off;
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && nx->first == off + len) {
+            len += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                start = pv->first;
+                len += pv->second;
+                free_.erase(pv);
+            }
+        }
+        free_[start] = len;
+    }
+    size_t used() const { return used_; }
+    size_t size() const { return size_; }
+
+private:
+    char *base_ = nullptr;
+    size_t size_ = 0, used_ = 0;
+    std::map<size_t, size_t> free_, live_;
+};
+
+enum JobState { QUEUED, RESIDENT, RETIRING, DONE };
+
+struct Job {
+    int64_t id;
+    hw_job spec;
+    std::vector<int32_t> marked;
+    JobState state = QUEUED;
+    int slot = -1;
+    char *dev = nullptr;        // arena block: states, terms, record partials, prob
+    char *host = nullptr;       // pinned result block: prob, record
+    int64_t n = 0, dim = 0;
+    int64_t total_subs = 0;
+    int64_t end_tick = 0;
+    int32_t m = 1, q = 1;
+    size_t dev_bytes = 0, host_bytes = 0;
+    cudaEvent_t done_ev = nullptr;
+    double t_submit = 0, t_done = 0;
+};
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct hw_server {
+    int device = -1;
+    cudaStream_t st = nullptr;
+    int max_jobs = 0;
+    int K = 8;
+    char *dev_base = nullptr;
+    char *host_base = nullptr;
+    Arena dev_arena, host_arena;
+    SJob *d_jobs = nullptr, *h_jobs = nullptr;       // device table + pinned mirror
+    Tile *d_tiles = nullptr, *h_tiles = nullptr;
+    int *d_ntiles = nullptr, *h_ntiles = nullptr;
+    int64_t *d_tick = nullptr;
+    int64_t tick = 0;
+    int max_tiles = 0;
+    bool table_dirty = true;
+    bool upload_pending = false;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int> free_slots;
+    std::map<int64_t, Job> jobs;
+    std::deque<int64_t> queue;
+    std::vector<int64_t> resident;
+    std::vector<int64_t> completed;   // not yet polled
+    int64_t next_id = 1;
+    cudaEvent_t upload_ev = nullptr;  // the pinned table mirror is free to rewrite after this
+};
+
+static hw_status server_capture(hw_server *s)
+{
+    cudaGraph_t g = nullptr;
+    hw_status st = hw_cuda(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (st != HW_OK) return st;
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    for (int k = 0; k < s->K; ++k) {
+        k_serve_step<<<sms * 8, kServeThreads, 0, s->st>>>(s->d_jobs, s->d_tiles, s->d_ntiles, s->d_tick);
+        k_serve_tick<<<1, 1, 0, s->st>>>(s->d_tick);
+    }
+    st = hw_cuda(cudaStreamEndCapture(s->st, &g), "end capture");
+    if (st != HW_OK) return st;
+    st = hw_cuda(cudaGraphInstantiate(&s->graph, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    return st;
+}
+
+extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int32_t substeps_per_round,
+                                      int64_t host_bytes, void *stream, hw_server **out)
+{
+    hw_clear_error();
+    if (!out) return hw_fail(HW_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (arena_bytes < (1 << 20) || max_jobs < 1 || max_jobs > 65536 || substeps_per_round < 1 ||
+        substeps_per_round > 1024 || host_bytes < (1 << 20))
+        return hw_fail(HW_EINVAL, "bad server limits");
+    (void)stream;
+    hw_server *s = new (std::nothrow) hw_server;
+    if (!s) return hw_fail(HW_ENOMEM, "host allocation failed");
+    s->max_jobs = max_jobs;
+    s->K = substeps_per_round;
+    s->max_tiles = max_jobs * 64;
+    auto fail = [&](hw_status e) { hw_server_destroy(s); return e; };
+    hw_status st;
+    if ((st = hw_cuda(cudaGetDevice(&s->device), "cudaGetDevice")) != HW_OK) return fail(st);
+    // the server runs on a stream of its own (graph capture needs a non-legacy stream)
+    if ((st = hw_cuda(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking), "cudaStreamCreate")) != HW_OK)
+        return fail(st);
+    s->own_stream = true;
+    if ((st = hw_cuda(cudaMalloc(&s->dev_base, size_t(arena_bytes)), "cudaMalloc(serving arena)")) != HW_OK ||
+        (st = hw_cuda(cudaHostAlloc(&s->host_base, size_t(host_bytes), cudaHostAllocDefault), "cudaHostAlloc(results)")) != HW_OK ||
+        (st = hw_cuda(cudaMalloc(&s->d_jobs, sizeof(SJob) * max_jobs), "cudaMalloc(job table)")) != HW_OK ||
+        (st = hw_cuda(cudaHostAlloc(&s->h_jobs, sizeof(SJob) * max_jobs, cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
+        (st = hw_cuda(cudaMalloc(&s->d_tiles, sizeof(Tile) * s->max_tiles), "cudaMalloc(tiles)")) != HW_OK ||
+        (st = hw_cuda(cudaHostAlloc(&s->h_tiles, sizeof(Tile) * s->max_tiles, cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
+        (st = hw_cuda(cudaMalloc(&s->d_ntiles, sizeof(int)), "cudaMalloc")) != HW_OK ||
+        (st = hw_cuda(cudaHostAlloc(&s->h_ntiles, sizeof(int), cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
+        (st = hw_cuda(cudaMalloc(&s->d_tick, sizeof(int64_t)), "cudaMalloc")) != HW_OK ||
+        (st = hw_cuda(cudaEventCreateWithFlags(&s->upload_ev, cudaEventDisableTiming), "event")) != HW_OK)
+        return fail(st);
+    s->dev_arena.init(s->dev_base, size_t(arena_bytes));
+    s->host_arena.init(s->host_base, size_t(host_bytes));
+    std::memset(s->h_jobs, 0, sizeof(SJob) * max_jobs);
+    *s->h_ntiles = 0;
+    for (int i = max_jobs - 1; i >= 0; --i) s->free_slots.push_back(i);
+    if ((st = hw_cuda(cudaMemsetAsync(s->d_tick, 0, sizeof(int64_t), s->st), "memset tick")) != HW_OK ||
+        (st = hw_cuda(cudaMemsetAsync(s->d_ntiles, 0, sizeof(int), s->st), "memset")) != HW_OK ||
+        (st = server_capture(s)) != HW_OK)
+        return fail(st);
+    *out = s;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_server_destroy(hw_server *s)
+{
+    hw_clear_error();
+    if (!s) return HW_OK;
+    if (s->st) cudaStreamSynchronize(s->st);
+    for (auto &kv : s->jobs)
+        if (kv.second.done_ev) cudaEventDestroy(kv.second.done_ev);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->upload_ev) cudaEventDestroy(s->upload_ev);
+    cudaFree(s->dev_base);
+    cudaFreeHost(s->host_base);
+    cudaFree(s->d_jobs);
+    cudaFreeHost(s->h_jobs);
+    cudaFree(s->d_tiles);
+    cudaFreeHost(s->h_tiles);
+    cudaFree(s->d_ntiles);
+    cudaFreeHost(s->h_ntiles);
+    cudaFree(s->d_tick);
+    if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+    cudaGetLastError();
+    delete s;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *job_id)
+{
+    hw_clear_error();
+    if (!s || !job || !job_id) return hw_fail(HW_EINVAL, "NULL argument");
+    const hw_graph *g = job->graph;
+    if (!g) return hw_fail(HW_EINVAL, "job has no graph");
+    if (g->device != s->device) return hw_fail(HW_EINVAL, "graph and server live on different devices");
+    if (job->kind != HW_JOB_COINED && job->kind != HW_JOB_CTQW) return hw_fail(HW_EINVAL, "unknown job kind");
+    if (job->dt != HW_C64 && job->dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (job->steps < 1) return hw_fail(HW_EINVAL, "steps must be >= 1");
+    if (job->n_marked < 0 || job->n_marked > kMaxServeMarked || (job->n_marked && !job->marked))
+        return hw_fail(HW_EINVAL, "0..%d marked vertices", kMaxServeMarked);
+    if (job->kind == HW_JOB_COINED && (g->min_degree != g->max_degree || g->max_degree < 1 || g->max_degree > 32))
+        return hw_fail(HW_EUNSUPPORTED, "served coined jobs need a regular graph of degree 1..32");
+    if (g->n >= (int64_t(1) << 30)) return hw_fail(HW_EUNSUPPORTED, "graph too large to serve");
+    Job J;
+    J.id = s->next_id++;
+    J.spec = *job;
+    J.marked.assign(job->marked, job->marked + job->n_marked);
+    std::sort(J.marked.begin(), J.marked.end());
+    for (int i = 0; i < job->n_marked; ++i) {
+        if (J.marked[i] < 0 || J.marked[i] >= g->n) return hw_fail(HW_EINVAL, "marked vertex out of range");
+        if (i && J.marked[i] == J.marked[i - 1]) return hw_fail(HW_EINVAL, "marked vertex repeated");
+    }
+    J.spec.marked = nullptr;
+    J.n = g->n;
+    const size_t esz = cplx_bytes(hw_dtype(job->dt));
+    if (job->kind == HW_JOB_COINED) {
+        J.dim = g->num_arcs;
+        J.total_subs = job->steps;
+    } else {
+        if (!std::isfinite(job->gamma) || !std::isfinite(job->time)) return hw_fail(HW_EINVAL, "gamma/time not finite");
+        int m, sq;
+        hw_status st = hw_ctqw_plan(g, job->gamma, J.marked.data(), job->n_marked, job->time, &m, &sq);
+        if (st != HW_OK) return st;
+        if (sq > 20) return hw_fail(HW_EUNSUPPORTED, "||H dt|| too large to serve");
+        J.m = m;
+        J.q = 1 << sq;
+        J.dim = g->n;
+        J.total_subs = job->steps * int64_t(J.q) * J.m;
+    }
+    const size_t state = (size_t(J.dim) * esz + 255) & ~size_t(255);
+    const size_t rec = job->n_marked ? ((size_t(job->steps) * job->n_marked * 8 + 255) & ~size_t(255)) : 0;
+    const size_t prob = (size_t(J.n) * 8 + 255) & ~size_t(255);
+    J.dev_bytes = (job->kind == HW_JOB_COINED ? 2 : 4) * state + rec + prob +
+                  ((size_t(job->steps) * 8 + 255) & ~size_t(255));
+    J.host_bytes = prob + ((size_t(job->steps) * 8 + 255) & ~size_t(255));
+    if (J.dev_bytes > s->dev_arena.size() || J.host_bytes > s->host_arena.size())
+        return hw_fail(HW_ENOMEM, "job needs %zu device bytes; the serving arena holds %zu", J.dev_bytes,
+                       s->dev_arena.size());
+    J.t_submit = now_s();
+    *job_id = J.id;
+    s->queue.push_back(J.id);
+    s->jobs.emplace(J.id, std::move(J));
+    return HW_OK;
+}
+
+static void rebuild_tiles(hw_server *s)
+{
+    int nt = 0;
+    for (int64_t id : s->resident) {
+        const Job &J = s->jobs[id];
+        for (int64_t v0 = 0; v0 < J.n && nt < s->max_tiles; v0 += kTileVertices) {
+            Tile t;
+            t.job = J.slot;
+            t.v0 = int32_t(v0);
+            t.v1 = int32_t(std::min<int64_t>(J.n, v0 + kTileVertices));
+            t.pad = 0;
+            s->h_tiles[nt++] = t;
+        }
+    }
+    *s->h_ntiles = nt;
+}
+
+static hw_status admit(hw_server *s, Job &J)
+{
+    const hw_graph *g = J.spec.graph;
+    const size_t esz = cplx_bytes(hw_dtype(J.spec.dt));
+    char *dev = s->dev_arena.alloc(J.dev_bytes);
+    if (!dev) return HW_ENOMEM;
+    char *host = s->host_arena.alloc(J.host_bytes);
+    if (!host) {
+        s->dev_arena.release(dev);
+        return HW_ENOMEM;
+    }
+    J.dev = dev;
+    J.host = host;
+    J.slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    const size_t state = (size_t(J.dim) * esz + 255) & ~size_t(255);
+    SJob &D = s->h_jobs[J.slot];
+    std::memset(&D, 0, sizeof D);
+    D.row_ptr = g->d_row_ptr;
+    D.head = g->d_head;
+    D.rev = g->d_rev;
+    D.X[0] = dev;
+    D.X[1] = dev + state;
+    const int nstates = (J.spec.kind == HW_JOB_COINED) ? 2 : 4;
+    if (nstates == 4) {
+        D.T[0] = dev + 2 * state;
+        D.T[1] = dev + 3 * state;
+    }
+    D.rec = J.spec.n_marked ? reinterpret_cast<double *>(dev + nstates * state) : nullptr;
+    D.n = J.n;
+    D.start_tick = s->tick;
+    D.total_subs = J.total_subs;
+    D.two_over_d = g->max_degree ? 2.0 / double(g->max_degree) : 0.0;
+    D.gamma = J.spec.gamma;
+    D.tau = J.spec.time / double(J.q);
+    D.kind = J.spec.kind;
+    D.dt = J.spec.dt;
+    D.d = g->max_degree;
+    D.m = J.m;
+    D.q = J.q;
+    D.n_marked = J.spec.n_marked;
+    for (int i = 0; i < J.spec.n_marked; ++i) D.marked[i] = J.marked[i];
+    // uniform start over the basis: arcs (coined) or vertices (CTQW)
+    const double amp = 1.0 / std::sqrt(double(J.dim));
+    const int grid = int(std::min<int64_t>(148 * 16, (J.dim + 255) / 256));
+    if (J.spec.dt == HW_C128) k_fill<double2><<<grid, 256, 0, s->st>>>(static_cast<double2 *>(D.X[0]), J.dim, amp);
+    else k_fill<float2><<<grid, 256, 0, s->st>>>(static_cast<float2 *>(D.X[0]), J.dim, amp);
+    J.end_tick = s->tick + J.total_subs;
+    J.state = RESIDENT;
+    s->resident.push_back(J.id);
+    s->table_dirty = true;
+    return hw_cuda(cudaGetLastError(), "k_fill launch");
+}
+
+static hw_status retire(hw_server *s, Job &J)
+{
+    const hw_graph *g = J.spec.graph;
+    const SJob &D = s->h_jobs[J.slot];
+    const hw_dtype dt = hw_dtype(J.spec.dt);
+    const size_t esz = cplx_bytes(dt);
+    const int nstates = (J.spec.kind == HW_JOB_COINED) ? 2 : 4;
+    const size_t state = (size_t(J.dim) * esz + 255) & ~size_t(255);
+    const size_t rec = J.spec.n_marked ? ((size_t(J.spec.steps) * J.spec.n_marked * 8 + 255) & ~size_t(255)) : 0;
+    double *d_prob = reinterpret_cast<double *>(J.dev + nstates * state + rec);
+    double *d_record = reinterpret_cast<double *>(J.dev + nstates * state + rec +
+                                                  ((size_t(J.n) * 8 + 255) & ~size_t(255)));
+    const int64_t final_parity = (J.spec.kind == HW_JOB_COINED) ? (J.spec.steps & 1)
+                                                                 : ((J.spec.steps * J.q) & 1);
+    const void *psi = D.X[final_parity];
+    hw_status st = launch_probability(J.spec.kind == HW_JOB_COINED ? g : nullptr, J.n, dt, 1, psi, d_prob, nullptr,
+                                      s->st);
+    if (st != HW_OK) return st;
+    if (J.spec.n_marked) {
+        if (J.spec.kind == HW_JOB_COINED) {
+            MarkedList mk;
+            std::memset(&mk, 0, sizeof mk);
+            mk.n = J.spec.n_marked;
+            for (int i = 0; i < mk.n; ++i) mk.inl[i] = J.marked[i];
+            st = launch_marked_prob(g->d_row_ptr, dt, 1, psi, mk, D.rec + (J.spec.steps - 1) * mk.n, s->st);
+            if (st != HW_OK) return st;
+        }
+        k_serve_record<<<int((J.spec.steps + 255) / 256), 256, 0, s->st>>>(D.rec, J.spec.n_marked, J.spec.steps,
+                                                                          d_record);
+        if ((st = hw_cuda(cudaGetLastError(), "k_serve_record")) != HW_OK) return st;
+    }
+    const size_t prob_b = (size_t(J.n) * 8 + 255) & ~size_t(255);
+    if ((st = hw_cuda(cudaMemcpyAsync(J.host, d_prob, size_t(J.n) * 8, cudaMemcpyDeviceToHost, s->st), "D2H prob")) != HW_OK)
+        return st;
+    if (J.spec.n_marked &&
+        (st = hw_cuda(cudaMemcpyAsync(J.host + prob_b, d_record, size_t(J.spec.steps) * 8, cudaMemcpyDeviceToHost, s->st),
+                      "D2H record")) != HW_OK)
+        return st;
+    if ((st = hw_cuda(cudaEventCreateWithFlags(&J.done_ev, cudaEventDisableTiming), "event")) != HW_OK) return st;
+    if ((st = hw_cuda(cudaEventRecord(J.done_ev, s->st), "event record")) != HW_OK) return st;
+    J.state = RETIRING;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_server_run(hw_server *s, int32_t *n_completed)
+{
+    hw_clear_error();
+    if (!s) return hw_fail(HW_EINVAL, "server is NULL");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != s->device) return hw_fail(HW_EINVAL, "server lives on device %d, current is %d", s->device, dev);
+    hw_status st;
+    int32_t done = 0;
+    // the pinned table mirror is rewritten below: the last upload must have read it
+    if (s->upload_pending) {
+        if ((st = hw_cuda(cudaEventSynchronize(s->upload_ev), "upload event")) != HW_OK) return st;
+        s->upload_pending = false;
+    }
+    // 1. retire jobs whose last sub-step has been launched
+    for (size_t i = 0; i < s->resident.size();) {
+        Job &J = s->jobs[s->resident[i]];
+        if (J.end_tick <= s->tick) {
+            if ((st = retire(s, J)) != HW_OK) return st;
+            s->free_slots.push_back(J.slot);
+            s->resident.erase(s->resident.begin() + i);
+            s->table_dirty = true;
+        } else {
+            ++i;
+        }
+    }
+    // 2. finished copies: release memory, report
+    for (auto &kv : s->jobs) {
+        Job &J = kv.second;
+        if (J.state != RETIRING) continue;
+        const cudaError_t q = cudaEventQuery(J.done_ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return hw_cuda(q, "job completion");
+        cudaEventDestroy(J.done_ev);
+        J.done_ev = nullptr;
+        s->dev_arena.release(J.dev);
+        J.dev = nullptr;
+        J.state = DONE;
+        J.t_done = now_s();
+        s->completed.push_back(J.id);
+        ++done;
+    }
+    // 3. admit queued jobs while a slot and memory are free (first come, first served)
+    while (!s->queue.empty() && !s->free_slots.empty()) {
+        Job &J = s->jobs[s->queue.front()];
+        st = admit(s, J);
+        if (st == HW_ENOMEM) break;
+        if (st != HW_OK) return st;
+        s->queue.pop_front();
+    }
+    // 4. launch K sub-steps of every resident job
+    if (!s->resident.empty()) {
+        if (s->table_dirty) {
+            rebuild_tiles(s);
+            if ((st = hw_cuda(cudaMemcpyAsync(s->d_jobs, s->h_jobs, sizeof(SJob) * s->max_jobs, cudaMemcpyHostToDevice,
+                                              s->st), "upload jobs")) != HW_OK ||
+                (st = hw_cuda(cudaMemcpyAsync(s->d_tiles, s->h_tiles, sizeof(Tile) * std::max(1, *s->h_ntiles),
+                                              cudaMemcpyHostToDevice, s->st), "upload tiles")) != HW_OK ||
+                (st = hw_cuda(cudaMemcpyAsync(s->d_ntiles, s->h_ntiles, sizeof(int), cudaMemcpyHostToDevice, s->st),
+                              "upload count")) != HW_OK ||
+                (st = hw_cuda(cudaEventRecord(s->upload_ev, s->st), "event record")) != HW_OK)
+                return st;
+            s->table_dirty = false;
+            s->upload_pending = true;
+        }
+        if ((st = hw_cuda(cudaGraphLaunch(s->graph, s->st), "cudaGraphLaunch")) != HW_OK) return st;
+        s->tick += s->K;
+    }
+    if (n_completed) *n_completed = done;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_server_poll(hw_server *s, int64_t *ids, int32_t max_ids, int32_t *n_ids)
+{
+    hw_clear_error();
+    if (!s || !n_ids || (max_ids > 0 && !ids)) return hw_fail(HW_EINVAL, "NULL argument");
+    const int32_t n = int32_t(std::min<size_t>(size_t(std::max(max_ids, 0)), s->completed.size()));
+    for (int32_t i = 0; i < n; ++i) ids[i] = s->completed[i];
+    s->completed.erase(s->completed.begin(), s->completed.begin() + n);
+    *n_ids = n;
+    return HW_OK;
+}
+
+extern "C" hw_status hw_server_result(hw_server *s, int64_t job_id, double *prob, int64_t n_prob, double *record,
+                                      int64_t n_record, double *latency_s)
+{
+    hw_clear_error();
+    if (!s) return hw_fail(HW_EINVAL, "server is NULL");
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return hw_fail(HW_EINVAL, "unknown job %lld", (long long)job_id);
+    Job &J = it->second;
+    if (J.state != DONE) return hw_fail(HW_EINVAL, "job %lld is not finished", (long long)job_id);
+    if (prob && n_prob != J.n) return hw_fail(HW_EINVAL, "prob needs %lld entries", (long long)J.n);
+    if (record && (n_record != J.spec.steps || !J.spec.n_marked))
+        return hw_fail(HW_EINVAL, "record needs %lld entries and a marked vertex", (long long)J.spec.steps);
+    const size_t prob_b = (size_t(J.n) * 8 + 255) & ~size_t(255);
+    if (prob) std::memcpy(prob, J.host, size_t(J.n) * 8);
+    if (record) std::memcpy(record, J.host + prob_b, size_t(J.spec.steps) * 8);
+    if (latency_s) *latency_s = J.t_done - J.t_submit;
+    s->host_arena.release(J.host);
+    s->jobs.erase(it);
+    return HW_OK;
+}
+
+extern "C" hw_status hw_server_stats(const hw_server *s, int64_t *queued, int64_t *resident, int64_t *arena_used,
+                                     int64_t *ticks)
+{
+    hw_clear_error();
+    if (!s) return hw_fail(HW_EINVAL, "server is NULL");
+    if (queued) *queued = int64_t(s->queue.size());
+    if (resident) {
+        int64_t r = 0;
+        for (const auto &kv : s->jobs) r += (kv.second.state == RESIDENT || kv.second.state == RETIRING);
+        *resident = r;
+    }
+    if (arena_used) *arena_used = int64_t(s->dev_arena.used());
+    if (ticks) *ticks = s->tick;
+    return HW_OK;
+}
