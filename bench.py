@@ -453,6 +453,125 @@ def run_workload_torus64(args):
           flush=True)
 
 
+def serving_jobs(count, seed=6):
+    """The serving mix: kind, graph family, size, steps, dtype and marks per job, all from
+    SplitMix64(seed).  n = 2^k with k uniform in 10..20 for coined jobs and in 10..13 for
+    CTQW jobs (log-uniform sizes); steps log-uniform in [10, 5000]; coined/CTQW and
+    complex64/complex128 50/50; 0-4 marked vertices; gamma = 1/degree, dt = 0.1."""
+    u = synth.uniform01(seed, 8 * count).reshape(count, 8)
+    fams = ["torus", "hypercube", "reg3", "reg4", "reg8"]
+    jobs = []
+    for i in range(count):
+        kind = int(u[i, 0] < 0.5)                       # 0 coined, 1 CTQW
+        fam = fams[min(4, int(u[i, 1] * 5))]
+        k = 10 + (min(10, int(u[i, 2] * 11)) if kind == 0 else min(3, int(u[i, 2] * 4)))
+        steps = int(round(math.exp(math.log(10) + u[i, 3] * (math.log(5000) - math.log(10)))))
+        dt = 1 if u[i, 4] < 0.5 else 2
+        nm = min(4, int(u[i, 5] * 5))
+        jobs.append({"kind": kind, "fam": fam, "k": k, "steps": steps, "dt": dt, "n_marked": nm,
+                     "mark_seed": 1000 + i})
+    return jobs
+
+
+class GraphMenu:
+    """Resident graphs of the serving mix, built on first use (outside the timed region)."""
+
+    def __init__(self, hw):
+        self.hw = hw
+        self.g = {}
+
+    def get(self, fam, k):
+        key = (fam, k)
+        if key not in self.g:
+            if fam == "torus":
+                L = int(round(math.sqrt(1 << k)))
+                n, eu, ev = synth.torus(L)
+                d = 4
+            elif fam == "hypercube":
+                n, eu, ev = synth.hypercube(k)
+                d = k
+            else:
+                d = int(fam[3:])
+                n, eu, ev = synth.random_regular(1 << k, d, seed=100 + k * 10 + d)
+            row_ptr, col = synth.adjacency_csr(n, eu, ev)
+            self.g[key] = (self.hw.hw_graph_csr(n, row_ptr, col), d)
+        return self.g[key]
+
+
+def run_workload_serving(args):
+    """Served mix of walk jobs (continuous batching) vs the plain one-job-at-a-time
+    complex128 path: walks/s, p50/p99 latency."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    jobs = serving_jobs(args.jobs)
+    menu = GraphMenu(hw)
+    for j in jobs:                                    # build every graph before timing
+        G, d = menu.get(j["fam"], j["k"])
+        j["G"], j["d"] = G, d
+        j["marked"] = sorted({synth.seeded_vertex(j["mark_seed"] + r, G.n) for r in range(j["n_marked"])})
+    arena = int(args.arena_gb * (1 << 30))
+
+    def serve(arrivals):
+        srv = hw.Server(arena, max_jobs=512, substeps=args.substeps, host_bytes=4 << 30)
+        t0 = time.perf_counter()
+        pending = sorted(range(len(jobs)), key=lambda i: arrivals[i])
+        nxt = 0
+        idmap, lat = {}, []
+        while len(lat) < len(jobs):
+            now = time.perf_counter() - t0
+            while nxt < len(pending) and arrivals[pending[nxt]] <= now:
+                i = pending[nxt]
+                j = jobs[i]
+                idmap[srv.submit(j["G"], j["kind"], j["dt"], j["steps"], j["marked"], gamma=1.0 / j["d"],
+                                 time=0.1)] = i
+                nxt += 1
+            srv.run()
+            for jid in srv.poll():
+                i = idmap.pop(jid)
+                lat.append(time.perf_counter() - t0 - arrivals[i])
+                srv.result(jid)
+            if nxt < len(pending) and not idmap:
+                time.sleep(max(0.0, min(0.001, arrivals[pending[nxt]] - (time.perf_counter() - t0))))
+        el = time.perf_counter() - t0
+        srv.close()
+        lat = np.sort(np.array(lat))
+        return {"walks_per_s": len(jobs) / el, "makespan_s": el, "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean())}
+
+    # saturated: every job arrives at t = 0
+    sat = serve([0.0] * len(jobs))
+    # Poisson arrivals at 0.8 x the saturated rate
+    lam = 0.8 * sat["walks_per_s"]
+    gaps = -np.log1p(-synth.uniform01(61, len(jobs))) / lam
+    poisson = serve(list(np.cumsum(gaps)))
+
+    # plain one-job-at-a-time complex128 path (a bounded prefix of the same jobs)
+    base_jobs = jobs[:min(len(jobs), args.baseline_jobs)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in base_jobs:
+        G = j["G"]
+        dim = G.num_arcs if j["kind"] == 0 else G.n
+        x = torch.full((dim,), 1.0 / math.sqrt(dim), dtype=torch.complex128, device="cuda")
+        y = torch.empty_like(x)
+        rec = torch.empty(j["steps"], dtype=torch.float64, device="cuda") if j["marked"] else None
+        if j["kind"] == 0:
+            hw.hw_coined_evolve(G, 0, j["marked"], hw.HW_C128, 1, j["steps"], x, y, rec)
+        else:
+            hw.hw_ctqw_evolve_sparse(G, 1.0 / j["d"], j["marked"], 0.1, hw.HW_C128, 1, j["steps"], x, y, rec)
+        prob = torch.empty(G.n, dtype=torch.float64, device="cuda")
+        hw.hw_probability(G if j["kind"] == 0 else None, G.n, hw.HW_C128, 1, y, prob)
+        prob.cpu()
+        if rec is not None:
+            rec.cpu()
+    base_rate = len(base_jobs) / (time.perf_counter() - t0)
+    print(json.dumps({"workload": "serving", "jobs": len(jobs), "metric": "walks/s", "unit": "walks/s",
+                      "saturated": sat, "poisson_0.8": poisson, "lambda_per_s": lam,
+                      "plain_c128_one_at_a_time": {"walks_per_s": base_rate, "jobs_timed": len(base_jobs)},
+                      "speedup_vs_plain": poisson["walks_per_s"] / base_rate,
+                      "substeps_per_round": args.substeps, "arena_gb": args.arena_gb}), flush=True)
+
+
 def run_profile(args):
     """A few launches of one kernel on the bench workload, for ncu captures."""
     import torch
@@ -498,8 +617,13 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--profile-tile", type=int, default=10)
     ap.add_argument("--workload", default="torus1024_search",
-                    choices=["torus1024_search", "torus64_center", "hypercube12_ctqw", "er_batched"],
+                    choices=["torus1024_search", "torus64_center", "hypercube12_ctqw", "er_batched",
+                             "serving"],
                     help="the default is the benchmarked workload; the others print their own line")
+    ap.add_argument("--jobs", type=int, default=10000, help="serving: number of jobs")
+    ap.add_argument("--baseline-jobs", type=int, default=200, help="serving: jobs timed on the plain path")
+    ap.add_argument("--substeps", type=int, default=16, help="serving: sub-steps per round")
+    ap.add_argument("--arena-gb", type=float, default=64.0, help="serving: device arena")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
@@ -509,6 +633,8 @@ def main():
         run_workload_ctqw(args)
     elif args.workload == "torus64_center":
         run_workload_torus64(args)
+    elif args.workload == "serving":
+        run_workload_serving(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_step(StepArgs a)
         const int a0 = s_rp[0];
         const int na = s_rp[nv] - a0;
         if (na > kTileArcs) {              // block-uniform branch: one heavy vertex
+            if (b == int(blockIdx.x)) pdl_wait();
             heavy_vertex<R, COIN>(a, v0, a0, na);
             __syncthreads();
             continue;
@@ -181,9 +182,14 @@ __global__ void __launch_bounds__(kThreads) k_coined_step(StepArgs a)
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int i = threadIdx.x + k * kThreads;
+            if (i < na) r[k] = a.rev[a0 + i];
+        }
+        if (b == int(blockIdx.x)) pdl_wait();
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = threadIdx.x + k * kThreads;
             if (i < na) {
                 p[k] = in[a0 + i];
-                r[k] = a.rev[a0 + i];
                 s_psi[i] = p[k];
             }
         }
@@ -236,6 +242,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_step(StepArgs a)
         }
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------- regular
@@ -282,51 +289,39 @@ __device__ __forceinline__ void load_rev(const int32_t *__restrict__ rev, int64_
     }
 }
 
-template <typename R, int D, int COIN, int VPT>
+template <typename R, int D, int COIN>
 __global__ void __launch_bounds__(kThreads) k_coined_vertex(RegArgs a)
 {
     using V = typename Cx<R>::T;
     const V *__restrict__ in = static_cast<const V *>(a.in);
     V *__restrict__ out = static_cast<V *>(a.out);
-    const int64_t base = int64_t(blockIdx.x) * blockDim.x * VPT + threadIdx.x;
-    V p[VPT][D];
-    int r[VPT][D];
-    // every load of this thread's vertices first, then the arithmetic
+    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    V p[D];
+    int r[D];
+    if (v < a.n) load_rev<D>(a.rev, v, r);    // constant table: fetched before the wait
+    pdl_wait();
+    if (v < a.n) {
 #pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-        const int64_t v = base + int64_t(u) * blockDim.x;
-        if (v < a.n) {
-#pragma unroll
-            for (int j = 0; j < D; ++j) p[u][j] = in[v * D + j];
-            load_rev<D>(a.rev, v, r[u]);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < VPT; ++u) {
-        const int64_t v = base + int64_t(u) * blockDim.x;
-        if (v >= a.n) continue;
+        for (int j = 0; j < D; ++j) p[j] = in[v * D + j];
         const int mi = find_marked(a.mk, int(v));
         if (mi >= 0) {
             if (a.rec_part && a.rec_slot >= 0) {
                 double acc = 0.0;
 #pragma unroll
                 for (int j = 0; j < D; ++j)
-                    acc += double(p[u][j].x) * double(p[u][j].x) + double(p[u][j].y) * double(p[u][j].y);
+                    acc += double(p[j].x) * double(p[j].x) + double(p[j].y) * double(p[j].y);
                 a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
             }
 #pragma unroll
-            for (int j = 0; j < D; ++j) out[r[u][j]] = mkv<V, R>(-p[u][j].x, -p[u][j].y);
-            continue;
-        }
-        if (COIN == HW_COIN_GROVER) {
-            R sx = p[u][0].x, sy = p[u][0].y;
+            for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(-p[j].x, -p[j].y);
+        } else if (COIN == HW_COIN_GROVER) {
+            R sx = p[0].x, sy = p[0].y;
 #pragma unroll
-            for (int j = 1; j < D; ++j) { sx += p[u][j].x; sy += p[u][j].y; }
+            for (int j = 1; j < D; ++j) { sx += p[j].x; sy += p[j].y; }
             const R f = grover_weight<R>(a);
             // c_j = (2/d) sum - psi_j, one fused multiply-add per component
 #pragma unroll
-            for (int j = 0; j < D; ++j)
-                out[r[u][j]] = mkv<V, R>(fma(f, sx, -p[u][j].x), fma(f, sy, -p[u][j].y));
+            for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
         } else {
             const R scale = R(1) / sqrt(R(D));
 #pragma unroll
@@ -335,13 +330,14 @@ __global__ void __launch_bounds__(kThreads) k_coined_vertex(RegArgs a)
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     const double2 w = c_tw[D * (D - 1) / 2 + (j * k) % D];
-                    cx += R(w.x) * p[u][k].x - R(w.y) * p[u][k].y;
-                    cy += R(w.x) * p[u][k].y + R(w.y) * p[u][k].x;
+                    cx += R(w.x) * p[k].x - R(w.y) * p[k].y;
+                    cy += R(w.x) * p[k].y + R(w.y) * p[k].x;
                 }
-                out[r[u][j]] = mkv<V, R>(cx * scale, cy * scale);
+                out[r[j]] = mkv<V, R>(cx * scale, cy * scale);
             }
         }
     }
+    pdl_trigger();
 }
 
 // Lane-group variant for complex64 (FP32 arithmetic is cheap; the limit is
@@ -368,14 +364,13 @@ __global__ void __launch_bounds__(kThreads) k_coined_lanes(RegArgs a, int d)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int64_t v = vbase + u * VPW;
-        if (v < a.n && j < d) {
-            const int64_t arc = v * d + j;
-            p[u] = in[arc];
-            r[u] = __ldg(a.rev + arc);
-        } else {
-            p[u] = mkv<V, R>(R(0), R(0));
-            r[u] = -1;
-        }
+        r[u] = (v < a.n && j < d) ? __ldg(a.rev + v * d + j) : -1;   // constant table
+    }
+    pdl_wait();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t v = vbase + u * VPW;
+        p[u] = (r[u] >= 0) ? in[v * d + j] : mkv<V, R>(R(0), R(0));
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -413,6 +408,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_lanes(RegArgs a, int d)
         }
         if (r[u] >= 0) out[r[u]] = c;
     }
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------- batched
@@ -843,17 +839,16 @@ __global__ void k_record_finalize(const double *__restrict__ part, int n_marked,
 template <typename R, int COIN>
 static void launch_vertex(int d, const RegArgs &a, cudaStream_t st)
 {
-    constexpr int VPT = 1;   // vertices per thread (2 doubles the registers; measured slower while FP64-bound)
-    const int64_t grid = (a.n + kThreads * VPT - 1) / (kThreads * VPT);
+    const dim3 grid(unsigned((a.n + kThreads - 1) / kThreads));
     switch (d) {
-    case 1: k_coined_vertex<R, 1, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
-    case 2: k_coined_vertex<R, 2, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
-    case 3: k_coined_vertex<R, 3, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
-    case 4: k_coined_vertex<R, 4, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
-    case 5: k_coined_vertex<R, 5, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
-    case 6: k_coined_vertex<R, 6, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
-    case 7: k_coined_vertex<R, 7, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
-    default: k_coined_vertex<R, 8, COIN, VPT><<<grid, kThreads, 0, st>>>(a); break;
+    case 1: launch_pdl(k_coined_vertex<R, 1, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 2: launch_pdl(k_coined_vertex<R, 2, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 3: launch_pdl(k_coined_vertex<R, 3, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 4: launch_pdl(k_coined_vertex<R, 4, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 5: launch_pdl(k_coined_vertex<R, 5, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 6: launch_pdl(k_coined_vertex<R, 6, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 7: launch_pdl(k_coined_vertex<R, 7, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    default: launch_pdl(k_coined_vertex<R, 8, COIN>, grid, dim3(kThreads), 0, st, a); break;
     }
 }
 
@@ -864,7 +859,7 @@ static void launch_lanes_g(const RegArgs &a, int d, cudaStream_t st)
     constexpr int VPW = 32 / G;
     const int64_t warps = (a.n + VPW * U - 1) / (VPW * U);
     const int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
-    k_coined_lanes<R, G, COIN, U><<<grid, kThreads, 0, st>>>(a, d);
+    launch_pdl(k_coined_lanes<R, G, COIN, U>, dim3(unsigned(grid)), dim3(kThreads), 0, st, a, d);
 }
 
 template <typename R, int COIN>
@@ -939,11 +934,11 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
     a.out = s.out;
     const int grid = g->nblk;
     if (dt == HW_C128) {
-        if (coin == HW_COIN_GROVER) k_coined_step<double, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
-        else k_coined_step<double, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+        if (coin == HW_COIN_GROVER) launch_pdl(k_coined_step<double, HW_COIN_GROVER>, dim3(grid), dim3(kThreads), 0, st, a);
+        else launch_pdl(k_coined_step<double, HW_COIN_FOURIER>, dim3(grid), dim3(kThreads), 0, st, a);
     } else {
-        if (coin == HW_COIN_GROVER) k_coined_step<float, HW_COIN_GROVER><<<grid, kThreads, 0, st>>>(a);
-        else k_coined_step<float, HW_COIN_FOURIER><<<grid, kThreads, 0, st>>>(a);
+        if (coin == HW_COIN_GROVER) launch_pdl(k_coined_step<float, HW_COIN_GROVER>, dim3(grid), dim3(kThreads), 0, st, a);
+        else launch_pdl(k_coined_step<float, HW_COIN_FOURIER>, dim3(grid), dim3(kThreads), 0, st, a);
     }
     return hw_cuda(cudaGetLastError(), "k_coined_step launch");
 }

@@ -184,6 +184,7 @@ k_apply(const void *U_, const void *x_, void *y_, int n, int batch, MarkedList m
     V *__restrict__ y = static_cast<V *>(y_);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (kApplyThreads / 32) + warp;
+    pdl_wait();   // x is the previous application's output
     for (int b0 = 0; b0 < batch; b0 += BT) {
         const int nb = min(BT, batch - b0);
         R ax[BT], ay[BT];
@@ -248,6 +249,7 @@ k_apply(const void *U_, const void *x_, void *y_, int n, int batch, MarkedList m
             }
         }
     }
+    pdl_trigger();
 }
 
 template <typename R, int BT>
@@ -259,7 +261,7 @@ hw_status launch_apply_bt(const void *U, const void *x, void *y, int n, int batc
     const size_t smem = sizeof(V) * kApplyChunk * BT;
     cudaError_t e = cudaFuncSetAttribute(k_apply<R, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply)");
-    k_apply<R, BT><<<grid, kApplyThreads, smem, st>>>(U, x, y, n, batch, mk, rec_part, rec_slot);
+    launch_pdl(k_apply<R, BT>, dim3(grid), dim3(kApplyThreads), smem, st, U, x, y, n, batch, mk, rec_part, rec_slot);
     return hw_cuda(cudaGetLastError(), "k_apply launch");
 }
 

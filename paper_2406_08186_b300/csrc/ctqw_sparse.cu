@@ -45,7 +45,11 @@ __global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *
     V *__restrict__ tout = static_cast<V *>(tout_);
     V *__restrict__ acc = static_cast<V *>(acc_);
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n * batch) return;
+    pdl_wait();   // t_in and acc come from the previous term
+    if (i >= n * batch) {
+        pdl_trigger();
+        return;
+    }
     const int64_t v = i / batch;
     const int b = int(i % batch);
     R sx = 0, sy = 0;
@@ -71,6 +75,7 @@ __global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *
     o.x = base.x + t.x;
     o.y = base.y + t.y;
     acc[i] = o;
+    pdl_trigger();
 }
 
 template <typename R>
@@ -79,8 +84,8 @@ hw_status launch_term(const hw_graph *g, int batch, const MarkedList &mk, double
 {
     const int64_t total = g->n * batch;
     const int64_t grid = (total + 255) / 256;
-    k_ctqw_term<R><<<grid, 256, 0, st>>>(g->d_row_ptr, g->d_head, g->n, batch, mk, gamma, coef, x, tin, tout, acc,
-                                         first);
+    launch_pdl(k_ctqw_term<R>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
+               (const int32_t *)g->d_head, g->n, batch, mk, gamma, coef, x, tin, tout, acc, first);
     return hw_cuda(cudaGetLastError(), "k_ctqw_term launch");
 }
 

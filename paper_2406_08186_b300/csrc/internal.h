@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <map>
+#include <utility>
 #include <mutex>
 #include <vector>
 
@@ -90,5 +91,32 @@ bool tc_gemm_available();
 hw_status tc_power_begin(int n, const double *Y, int ns, cudaStream_t st, TcPower **out);
 hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream_t st);
 hw_status tc_power_end(TcPower *p, cudaStream_t st, bool check);
+
+// Programmatic dependent launch: consecutive steps of a loop overlap the next
+// grid's launch with the current grid's tail.  A kernel launched this way
+// reads the previous step's output only after pdl_wait(), which returns once
+// the previous grid has completed and its writes are visible; pdl_trigger()
+// lets the next grid be scheduled.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
 
 inline size_t cplx_bytes(hw_dtype dt) { return dt == HW_C128 ? 16 : 8; }

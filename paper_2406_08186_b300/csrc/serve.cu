@@ -30,7 +30,8 @@
 namespace {
 
 constexpr int kServeThreads = 256;
-constexpr int kTileVertices = 1024;
+constexpr int kTileVertices = 1024;   // CTQW tiles
+constexpr int kServeTileArcs = 1024;  // coined tiles: whole vertices, at most this many arcs
 constexpr int kMaxServeMarked = 4;
 
 struct SJob {
@@ -155,24 +156,87 @@ __device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
         J.rec[w * J.n_marked + mi] = double(o.x) * double(o.x) + double(o.y) * double(o.y);
 }
 
+// A coined tile staged in shared memory: coalesced loads of the tile's arcs,
+// one sequential sum per vertex, then c = fma(2/d, sum, -psi) per arc -- the
+// same arithmetic as the single-job kernel, so results match it bit for bit.
+template <typename R>
+__device__ void serve_coined_tile(const SJob &J, int64_t w, int v0, int v1, unsigned char *smem)
+{
+    using V = typename CxS<R>::T;
+    V *sp = reinterpret_cast<V *>(smem);                       // [kServeTileArcs]
+    V *ss = sp + kServeTileArcs;                                    // per-vertex sums
+    const V *__restrict__ in = static_cast<const V *>(J.X[w & 1]);
+    V *__restrict__ out = static_cast<V *>(J.X[(w + 1) & 1]);
+    const int d = J.d;
+    const int64_t a0 = int64_t(v0) * d;
+    const int na = (v1 - v0) * d;
+    for (int i = threadIdx.x; i < na; i += blockDim.x) sp[i] = in[a0 + i];
+    __syncthreads();
+    for (int lv = threadIdx.x; lv < v1 - v0; lv += blockDim.x) {
+        const int v = v0 + lv;
+        R sx = 0, sy = 0;
+        for (int j = 0; j < d; ++j) {
+            sx += sp[lv * d + j].x;
+            sy += sp[lv * d + j].y;
+        }
+        V sm;
+        sm.x = sx;
+        sm.y = sy;
+        ss[lv] = sm;
+        const int mi = job_marked(J, v);
+        if (mi >= 0 && J.rec && w >= 1) {
+            double acc = 0.0;
+            for (int j = 0; j < d; ++j) {
+                const V p = sp[lv * d + j];
+                acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+            }
+            J.rec[(w - 1) * J.n_marked + mi] = acc;
+        }
+    }
+    __syncthreads();
+    const R f = R(J.two_over_d);
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        const int lv = i / d;
+        const V p = sp[i];
+        V c;
+        if (J.n_marked && job_marked(J, v0 + lv) >= 0) {
+            c.x = -p.x;
+            c.y = -p.y;
+        } else {
+            c.x = fma(f, ss[lv].x, -p.x);
+            c.y = fma(f, ss[lv].y, -p.y);
+        }
+        out[J.rev[a0 + i]] = c;
+    }
+    __syncthreads();
+}
+
 // One sub-step of every resident job.  Tiles are (job, vertex range); the
 // grid loops over them, so the launch shape never depends on the job mix.
 __global__ void __launch_bounds__(kServeThreads)
 k_serve_step(const SJob *__restrict__ jobs, const Tile *__restrict__ tiles, const int *__restrict__ ntiles,
              const int64_t *__restrict__ tick)
 {
+    extern __shared__ __align__(16) unsigned char smem[];   // 2 * kServeTileArcs complex values
     const int nt = *ntiles;
     const int64_t now = *tick;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const Tile tl = tiles[t];
         const SJob &J = jobs[tl.job];
         const int64_t local = now - J.start_tick;
-        if (local < 0 || local >= J.total_subs) continue;
-        for (int v = tl.v0 + threadIdx.x; v < tl.v1; v += blockDim.x) {
-            if (J.kind == 0) {
+        if (local < 0 || local >= J.total_subs) continue;   // uniform over the CTA
+        if (J.kind == 0 && J.d > 4) {
+            // higher degrees: coalesced loads through shared memory
+            if (J.dt == HW_C128) serve_coined_tile<double>(J, local, tl.v0, tl.v1, smem);
+            else serve_coined_tile<float>(J, local, tl.v0, tl.v1, smem);
+        } else if (J.kind == 0) {
+            // degree <= 4: a vertex's arcs are at most 64 contiguous bytes; read directly
+            for (int v = tl.v0 + threadIdx.x; v < tl.v1; v += blockDim.x) {
                 if (J.dt == HW_C128) serve_coined<double>(J, local, v);
                 else serve_coined<float>(J, local, v);
-            } else {
+            }
+        } else {
+            for (int v = tl.v0 + threadIdx.x; v < tl.v1; v += blockDim.x) {
                 if (J.dt == HW_C128) serve_ctqw<double>(J, local, v);
                 else serve_ctqw<float>(J, local, v);
             }
@@ -323,8 +387,16 @@ static hw_status server_capture(hw_server *s)
     if (st != HW_OK) return st;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    const int smem = 2 * kServeTileArcs * int(sizeof(double2));
+    st = hw_cuda(cudaFuncSetAttribute(k_serve_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                 "cudaFuncSetAttribute(k_serve_step)");
+    if (st != HW_OK) {
+        cudaStreamEndCapture(s->st, &g);
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
     for (int k = 0; k < s->K; ++k) {
-        k_serve_step<<<sms * 8, kServeThreads, 0, s->st>>>(s->d_jobs, s->d_tiles, s->d_ntiles, s->d_tick);
+        k_serve_step<<<sms * 6, kServeThreads, smem, s->st>>>(s->d_jobs, s->d_tiles, s->d_ntiles, s->d_tick);
         k_serve_tick<<<1, 1, 0, s->st>>>(s->d_tick);
     }
     st = hw_cuda(cudaStreamEndCapture(s->st, &g), "end capture");
@@ -348,7 +420,11 @@ extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int
     if (!s) return hw_fail(HW_ENOMEM, "host allocation failed");
     s->max_jobs = max_jobs;
     s->K = substeps_per_round;
-    s->max_tiles = max_jobs * 64;
+    // Every full tile owns at least 16 KiB of arena (two complex64 states of a
+    // 1024-arc coined tile with degree <= 32 holds >= 993 arcs; four of a
+    // 1024-vertex CTQW tile) and each job has at most one partial tile, so this
+    // bounds the tiles of any resident set.
+    s->max_tiles = int(std::min<int64_t>(int64_t(1) << 30, arena_bytes / 15000 + max_jobs));
     auto fail = [&](hw_status e) { hw_server_destroy(s); return e; };
     hw_status st;
     if ((st = hw_cuda(cudaGetDevice(&s->device), "cudaGetDevice")) != HW_OK) return fail(st);
@@ -461,21 +537,25 @@ extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *
     return HW_OK;
 }
 
-static void rebuild_tiles(hw_server *s)
+static hw_status rebuild_tiles(hw_server *s)
 {
     int nt = 0;
     for (int64_t id : s->resident) {
         const Job &J = s->jobs[id];
-        for (int64_t v0 = 0; v0 < J.n && nt < s->max_tiles; v0 += kTileVertices) {
+        const int64_t step = (J.spec.kind == HW_JOB_COINED) ? std::max<int64_t>(1, kServeTileArcs / J.spec.graph->max_degree)
+                                                            : kTileVertices;
+        for (int64_t v0 = 0; v0 < J.n; v0 += step) {
+            if (nt >= s->max_tiles) return hw_fail(HW_EUNSUPPORTED, "tile list overflow (%d tiles)", nt);
             Tile t;
             t.job = J.slot;
             t.v0 = int32_t(v0);
-            t.v1 = int32_t(std::min<int64_t>(J.n, v0 + kTileVertices));
+            t.v1 = int32_t(std::min<int64_t>(J.n, v0 + step));
             t.pad = 0;
             s->h_tiles[nt++] = t;
         }
     }
     *s->h_ntiles = nt;
+    return HW_OK;
 }
 
 static hw_status admit(hw_server *s, Job &J)
@@ -629,7 +709,7 @@ extern "C" hw_status hw_server_run(hw_server *s, int32_t *n_completed)
     // 4. launch K sub-steps of every resident job
     if (!s->resident.empty()) {
         if (s->table_dirty) {
-            rebuild_tiles(s);
+            if ((st = rebuild_tiles(s)) != HW_OK) return st;
             if ((st = hw_cuda(cudaMemcpyAsync(s->d_jobs, s->h_jobs, sizeof(SJob) * s->max_jobs, cudaMemcpyHostToDevice,
                                               s->st), "upload jobs")) != HW_OK ||
                 (st = hw_cuda(cudaMemcpyAsync(s->d_tiles, s->h_tiles, sizeof(Tile) * std::max(1, *s->h_ntiles),
