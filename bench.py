@@ -46,7 +46,11 @@ UNIT = "arc-updates/s"
 # DRAM bytes per launch of the coin+shift kernel (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # measured on; a changed kernel reports null until it is measured again.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/coined_step_c128_torus1024.md, profiles/coined_step_c64_torus1024.md
+    ("c128", "d5164d770f8873d40679b71eaded42b15fc21249"): 84142848 + 18922240,
+    ("c64", "d5164d770f8873d40679b71eaded42b15fc21249"): 50350848 + 1474560,
+}
 
 
 def workload():
@@ -296,7 +300,7 @@ def run_ours(args):
                    "coin": "grover", "marked": m, "state": "complex128", "record": "p_m(t) every step",
                    "l2": "256 MiB written between timed steps; working set 151 MB > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "kernel": "k_coined_step<double,grover>",
+        "roofline": {"bound": "hbm", "kernel": "k_coined_vertex<double,4,grover>",
                      "achieved": ach128, "peak": peak, "unit": "GB/s", "frac": ach128 / peak,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
                      "bytes_per_launch": bytes128, "launch_us": per_launch128 * 1e6,
@@ -591,6 +595,24 @@ def run_profile(args):
         print(json.dumps({"profile": args.profile, "steps": args.profile_steps, "tile": args.profile_tile}))
         G.free()
         return
+    if args.profile in ("expm_c64", "apply_c128", "apply_c64"):
+        # the 4096-vertex hypercube CTQW: one expm (11 tensor-core powers) or a few applications
+        n = 4096
+        m = synth.seeded_vertex(3, n)
+        row_ptr, col = synth.adjacency_csr(*synth.hypercube(12))
+        G = hw.hw_graph_csr(n, row_ptr, col)
+        dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        U = torch.empty((n, n), dtype=cdt, device="cuda")
+        hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+        if args.profile.startswith("apply"):
+            x = torch.full((n,), 1 / 64, dtype=cdt, device="cuda")
+            y = torch.empty_like(x)
+            hw.hw_ctqw_evolve(U, n, dt, 1, args.profile_steps, x, y, [m])
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile}))
+        G.free()
+        return
     n, eu, ev, row_ptr, col, m = workload()
     G = hw.hw_graph_csr(n, row_ptr, col)
     dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
@@ -612,7 +634,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["coined_c128", "coined_c64", "batched_c64"],
+    ap.add_argument("--profile", choices=["coined_c128", "coined_c64", "batched_c64", "expm_c64", "apply_c128",
+                                          "apply_c64"],
                     help="run a few coin+shift launches of the workload and exit (for ncu)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--profile-tile", type=int, default=10)
