@@ -47,7 +47,7 @@ UNIT = "arc-updates/s"
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # measured on; a changed kernel reports null until it is measured again.
 TRAFFIC = {
-    # profiles/coined_step_c128_torus1024.md, profiles/coined_step_c64_torus1024.md
+    # the 1024x1024 torus step: ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch
     ("c128", "d5164d770f8873d40679b71eaded42b15fc21249"): 84142848 + 18922240,
     ("c64", "d5164d770f8873d40679b71eaded42b15fc21249"): 50350848 + 1474560,
 }

@@ -62,7 +62,8 @@ typedef struct hw_opts {
     int32_t record_stride;     /* coined/CTQW record: one entry every `stride` steps (>= 1, default 1) */
     int32_t taylor_degree;     /* hw_ctqw_expm: Taylor degree m (0 = chosen for < 2^-60 truncation) */
     int32_t taylor_squarings;  /* hw_ctqw_expm: squarings s (-1 = chosen so ||H dt||_1 / 2^s <= 1/2) */
-    int32_t gemm_slices;       /* hw_ctqw_expm, HW_C64: bf16 slices per fp32 operand (2 or 3; 0 = 3) */
+    int32_t gemm_mode;         /* hw_ctqw_expm, HW_C64: tensor-core precision mode of the powers,
+                                  0 = default (fp16 x 2), else as hw_gemm_tc's mode */
     int32_t tile;              /* batched Grover kernel launch shape: 0 = autotuned on the first
                                   call per (graph, dtype, batch), which then synchronises the
                                   stream once; 1..12 = register-row kernel with (rows held
@@ -155,8 +156,9 @@ hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marke
  *   U_out    DEVICE [n][n] row-major complex (dt), caller-owned
  *   dt       HW_C128: products in double precision;
  *            HW_C64: products of the powers of H on the tensor cores from
- *            split-bf16 operands with fp32 accumulation; Taylor sums and
- *            squarings in double; U rounded to complex64 at the end.
+ *            16-bit slices of their operands (opts->gemm_mode, default fp16 x 2)
+ *            with fp32 accumulation; Taylor sums and squarings in double;
+ *            U rounded to complex64 at the end.
  * Scratch: a few n x n real buffers from the stream-ordered allocator.
  * With HW_C64 the call synchronises `stream` before returning, to report a
  * device-side pipeline timeout of the tensor-core kernel as HW_ETIMEDOUT.
@@ -226,22 +228,25 @@ hw_status hw_probability_noalloc(const hw_graph *g, int64_t n, hw_dtype dt, int3
                                  const void *psi, double *prob_out, double *norm_out, void *stream);
 
 /*
- * hw_gemm_tc -- C = A B^T on the tensor cores (tcgen05, bf16 inputs, fp32
- * accumulation) with each fp32 operand split into `slices` bf16 terms
- * (1: plain bf16; 2: ~2^-16 relative error, 3 products; 3: ~2^-24, 6 products).
+ * hw_gemm_tc -- C = A B^T on the tensor cores (tcgen05, 16-bit inputs, fp32
+ * accumulation) with each fp32 operand split into 16-bit slices; `mode`:
+ *   1 = bf16 x 1 (one product, ~2^-8),   2 = bf16 x 2 (3 products, ~2^-16),
+ *   3 = bf16 x 3 (6 products, ~2^-24),   4 = fp16 x 2 (3 products, ~2^-22;
+ *   each operand is first scaled by a power of two that puts its maximum in
+ *   [1/2, 1], so errors are relative to the operand's largest entry).
  * This is the contraction behind the complex64 Taylor series of
  * hw_ctqw_expm (there A = Y^(k-1)/(k-1)!, B = Y, symmetric), exposed for tests
  * and measurement.
  *   A  DEVICE float[m][k] row-major;  B  DEVICE float[n][k] row-major
  *   C  DEVICE float[m][n] row-major, caller-owned
- * Scratch (bf16 slices, 3(m+n)k x 2 bytes) comes from the stream-ordered
+ * Scratch (slices, 3(m+n)k x 2 bytes) comes from the stream-ordered
  * allocator.  The call synchronises `stream` before returning, to report a
  * device-side pipeline timeout as HW_ETIMEDOUT.
  * Errors: HW_EINVAL, HW_EUNSUPPORTED (not an sm_103 device), HW_ENOMEM,
  * HW_ECUDA, HW_ETIMEDOUT.
  */
 hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A, const float *B, float *C,
-                     int32_t slices, void *stream);
+                     int32_t mode, void *stream);
 
 /*
  * hw_ctqw_evolve_sparse -- psi_out = (e^{-iH time})^steps psi_in (Sec. 3.1)

@@ -41,7 +41,7 @@ class HWError(RuntimeError):
 
 class hw_opts(ctypes.Structure):
     _fields_ = [("record_stride", ctypes.c_int32), ("taylor_degree", ctypes.c_int32),
-                ("taylor_squarings", ctypes.c_int32), ("gemm_slices", ctypes.c_int32),
+                ("taylor_squarings", ctypes.c_int32), ("gemm_mode", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
@@ -289,12 +289,15 @@ def hw_probability_noalloc(g, n: int, dt: int, batch: int, psi, prob_out=None, n
                                         _stream(stream)))
 
 
-def hw_gemm_tc(A, B, C, slices: int = 3, stream=None):
-    """C = A @ B.T on the tensor cores from split-bf16 fp32 operands (device float32 tensors)."""
+HW_GEMM_BF16X1, HW_GEMM_BF16X2, HW_GEMM_BF16X3, HW_GEMM_F16X2 = 1, 2, 3, 4
+
+
+def hw_gemm_tc(A, B, C, mode: int = HW_GEMM_F16X2, stream=None):
+    """C = A @ B.T on the tensor cores from split 16-bit slices of fp32 operands (device float32 tensors)."""
     m, k = A.shape
     n = B.shape[0]
     _check(lib().hw_gemm_tc(int(m), int(n), int(k), _dev(A, "float32"), _dev(B, "float32"),
-                            _dev(C, "float32"), int(slices), _stream(stream)))
+                            _dev(C, "float32"), int(mode), _stream(stream)))
 
 
 def hw_ctqw_evolve_sparse(g: Graph, gamma: float, marked, time: float, dt: int, batch: int, steps: int,

@@ -46,7 +46,7 @@ extern "C" void hw_opts_init(hw_opts *o)
     o->record_stride = 1;
     o->taylor_degree = 0;
     o->taylor_squarings = -1;
-    o->gemm_slices = 0;
+    o->gemm_mode = 0;
     o->tile = 0;
 }
 

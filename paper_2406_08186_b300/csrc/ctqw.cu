@@ -133,6 +133,17 @@ __global__ void k_taylor_init(int n, const double *__restrict__ Y, double *__res
     }
 }
 
+// lower triangle -> upper triangle (the tensor-core series accumulates below the diagonal)
+__global__ void k_mirror_lower(int n, double *__restrict__ x)
+{
+    const int64_t total = int64_t(n) * n;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e / n, j = e % n;
+        if (j > i) x[e] = x[j * n + i];
+    }
+}
+
 // Im' = X + X^T
 __global__ void k_sym_add(int n, const double *__restrict__ X, double *__restrict__ out)
 {
@@ -353,8 +364,8 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     if (opts && opts->taylor_degree > 0) m_deg = opts->taylor_degree;
     if (opts && opts->taylor_squarings >= 0) sq = opts->taylor_squarings;
     if (m_deg > 40 || sq > 60) return hw_fail(HW_EINVAL, "Taylor degree %d / squarings %d out of range", m_deg, sq);
-    const int slices = (opts && opts->gemm_slices) ? opts->gemm_slices : 3;
-    if (slices != 2 && slices != 3) return hw_fail(HW_EINVAL, "gemm_slices must be 2 or 3");
+    const int gmode = opts ? opts->gemm_mode : 0;
+    if (gmode < 0 || gmode > 4) return hw_fail(HW_EINVAL, "gemm_mode must be 0..4");
     const double tau = time / std::ldexp(1.0, sq);
     const int64_t nn = int64_t(n) * n;
     const size_t bytes = sizeof(double) * nn;
@@ -377,7 +388,19 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     if (use_tc) {
         // complex64 path: powers on the tensor cores from split-bf16 operands
         TcPower *tp = nullptr;
-        if ((s = tc_power_begin(n, Y.as<double>(), slices, st, &tp)) != HW_OK) return s;
+        // host-known max |Y| (edge weight gamma tau, marked diagonal tau) and ||Y||_inf
+        double maxY = 0.0;
+        if (g->num_arcs) maxY = std::fabs(gamma * tau);
+        if (mk.n) maxY = std::max(maxY, std::fabs(tau));
+        double theta = 0.0;
+        {
+            std::vector<char> is_m(n, 0);
+            for (int32_t i = 0; i < n_marked; ++i) is_m[marked[i]] = 1;
+            for (int v = 0; v < n; ++v)
+                theta = std::max(theta, (std::fabs(gamma) * (g->h_row_ptr[v + 1] - g->h_row_ptr[v]) +
+                                         (is_m[v] ? 1.0 : 0.0)) * std::fabs(tau));
+        }
+        if ((s = tc_power_begin(n, Y.as<double>(), maxY, theta, gmode, st, &tp)) != HW_OK) return s;
         for (int k = 2; k <= m_deg && s == HW_OK; ++k) {
             double *accU = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
             const double sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
@@ -386,6 +409,9 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
         hw_status e = tc_power_end(tp, st, s == HW_OK);
         if (s == HW_OK) s = e;
         if (s != HW_OK) return s;
+        k_mirror_lower<<<ew_grid(nn), 256, 0, st>>>(n, Re.as<double>());
+        k_mirror_lower<<<ew_grid(nn), 256, 0, st>>>(n, Im.as<double>());
+        if ((s = hw_cuda(cudaGetLastError(), "mirror")) != HW_OK) return s;
     } else {
         double *Qk = Y.as<double>();   // Q_1 = Y
         double *dst = Q.as<double>();

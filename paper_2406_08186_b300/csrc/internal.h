@@ -88,7 +88,8 @@ void free_marked(MarkedList &m, cudaStream_t st);
 // split-bf16 operands, accU += sign Q_k in double
 struct TcPower;
 bool tc_gemm_available();
-hw_status tc_power_begin(int n, const double *Y, int ns, cudaStream_t st, TcPower **out);
+hw_status tc_power_begin(int n, const double *Y, double maxY, double theta, int mode, cudaStream_t st,
+                         TcPower **out);
 hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream_t st);
 hw_status tc_power_end(TcPower *p, cudaStream_t st, bool check);
 

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol():
 def test_version_and_opts():
     assert "sm_103a" in hw.hw_version()
     o = hw.hw_opts_init()
-    assert (o.record_stride, o.taylor_degree, o.taylor_squarings, o.gemm_slices, o.tile) == (1, 0, -1, 0, 0)
+    assert (o.record_stride, o.taylor_degree, o.taylor_squarings, o.gemm_mode, o.tile) == (1, 0, -1, 0, 0)
 
 
 def _graphs():

@@ -32,6 +32,17 @@ def test_small_integers_exact(hw, m, n, k):
     assert np.array_equal(C, (A.astype(np.float64) @ B.T.astype(np.float64)).astype(np.float32))
 
 
+def test_small_integers_exact_fp16_scaled(hw):
+    # fp16 mode scales each operand by a power of two (exact) and splits in two
+    # slices: integers up to 2^10 are exact in the leading slice
+    rng = np.random.default_rng(5)
+    A = rng.integers(-1000, 1001, size=(256, 320)).astype(np.float32)
+    B = rng.integers(-1000, 1001, size=(200, 320)).astype(np.float32)
+    C = _run(hw, A, B, 4)
+    ref = A.astype(np.float64) @ B.T.astype(np.float64)
+    assert np.max(np.abs(C - ref)) <= 2.0 ** -22 * np.abs(ref).max() * 4
+
+
 def test_identity_transposes(hw):
     n = 256
     B = synth.complex_gaussian(3, n * n).real.reshape(n, n).astype(np.float32)
@@ -39,7 +50,7 @@ def test_identity_transposes(hw):
     assert np.array_equal(C, B.T)
 
 
-@pytest.mark.parametrize("slices,rel", [(3, 2e-6), (2, 1e-4), (1, 2e-2)])
+@pytest.mark.parametrize("slices,rel", [(3, 2e-6), (2, 1e-4), (1, 2e-2), (4, 4e-6)])
 def test_split_accuracy(hw, slices, rel):
     m, n, k = 384, 256, 1024
     A = synth.complex_gaussian(1, m * k).real.reshape(m, k).astype(np.float32)
