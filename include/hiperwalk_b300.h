@@ -64,13 +64,17 @@ typedef struct hw_opts {
     int32_t taylor_squarings;  /* hw_ctqw_expm: squarings s (-1 = chosen so ||H dt||_1 / 2^s <= 1/2) */
     int32_t gemm_mode;         /* hw_ctqw_expm, HW_C64: tensor-core precision mode of the powers,
                                   0 = default (fp16 x 2), else as hw_gemm_tc's mode */
+    int32_t u_symmetric;       /* hw_ctqw_evolve: 1 = U is complex symmetric (U^T = U, true for
+                                  U from hw_ctqw_expm): each off-diagonal 64 x 64 block is read
+                                  once and used for both triangles (complex64, batch 1; other
+                                  cases use the dense path) */
     int32_t tile;              /* batched Grover kernel launch shape: 0 = autotuned on the first
                                   call per (graph, dtype, batch), which then synchronises the
                                   stream once; 1..12 = register-row kernel with (rows held
                                   in registers, threads per CTA, vertices per warp) in
                                   {8,16} x {128,256} x {1,2,4}, row-major; 13, 14 = TMA-staged
                                   ring kernel with 2 or 1 CTAs per SM */
-    int32_t reserved[3];
+    int32_t reserved[2];
 } hw_opts;
 
 /* Fill `opts` with the defaults. */

@@ -42,7 +42,8 @@ class HWError(RuntimeError):
 class hw_opts(ctypes.Structure):
     _fields_ = [("record_stride", ctypes.c_int32), ("taylor_degree", ctypes.c_int32),
                 ("taylor_squarings", ctypes.c_int32), ("gemm_mode", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("u_symmetric", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class hw_job(ctypes.Structure):

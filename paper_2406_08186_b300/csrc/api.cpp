@@ -48,6 +48,7 @@ extern "C" void hw_opts_init(hw_opts *o)
     o->taylor_squarings = -1;
     o->gemm_mode = 0;
     o->tile = 0;
+    o->u_symmetric = 0;
 }
 
 hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaStream_t st,

@@ -284,6 +284,155 @@ hw_status launch_apply(const void *U, const void *x, void *y, int n, int batch, 
     return launch_apply_bt<R, 4>(U, x, y, n, batch, mk, rec_part, rec_slot, st);
 }
 
+// ------------------------------------------------------------ apply a symmetric U
+// U = U^T (complex symmetric): every off-diagonal 64 x 64 block U_IJ (I < J) is
+// read once and gives both y_I += U_IJ x_J and y_J += U_IJ^T x_I, so one
+// application reads n^2/2 elements (for n = 4096 complex64, 68 MB: it stays in
+// L2 from one application to the next).  Pass 1: one CTA per upper block
+// stages it in shared memory, 64 threads form its row sums and 64 its column
+// sums (sequential, fixed order) into per-block partials.  Pass 2: one thread
+// per vertex adds its partials in a fixed order and writes y (and the record).
+constexpr int kSymB = 64;
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_apply_sym_blocks(const void *U_, const void *x_, int n, int nb,
+                                                          void *prow_, void *pcol_)
+{
+    using V = typename Cx2<R>::T;
+    extern __shared__ __align__(16) unsigned char sym_smem[];
+    V(*sU)[kSymB + 1] = reinterpret_cast<V(*)[kSymB + 1]>(sym_smem);                      // [kSymB][kSymB+1]
+    V(*sx)[kSymB] = reinterpret_cast<V(*)[kSymB]>(sym_smem + sizeof(V) * kSymB * (kSymB + 1));   // [2][kSymB]
+    const V *__restrict__ U = static_cast<const V *>(U_);
+    const V *__restrict__ x = static_cast<const V *>(x_);
+    V *__restrict__ prow = static_cast<V *>(prow_);
+    V *__restrict__ pcol = static_cast<V *>(pcol_);
+    // block index -> (I, J), I <= J, row-major over the upper triangle
+    int b = blockIdx.x, I = 0;
+    while (b >= nb - I) { b -= nb - I; ++I; }
+    const int J = I + b;
+    const int r0 = I * kSymB, c0 = J * kSymB;
+    const int t = threadIdx.x;
+    if (r0 + kSymB <= n && c0 + kSymB <= n && (n & 1) == 0 && sizeof(V) == 8) {
+        // interior block: 16-byte loads, consecutive threads on consecutive pairs of a row
+#pragma unroll
+        for (int i = 0; i < (kSymB * kSymB / 2) / 128; ++i) {
+            const int e2 = t + 128 * i;
+            const int r = e2 / (kSymB / 2), c = 2 * (e2 % (kSymB / 2));
+            const float4 w = *reinterpret_cast<const float4 *>(U + int64_t(r0 + r) * n + c0 + c);
+            sU[r][c].x = w.x;
+            sU[r][c].y = w.y;
+            sU[r][c + 1].x = w.z;
+            sU[r][c + 1].y = w.w;
+        }
+    } else {
+        for (int e = t; e < kSymB * kSymB; e += blockDim.x) {
+            const int r = e / kSymB, c = e % kSymB;
+            V u;
+            if (r0 + r < n && c0 + c < n) u = U[int64_t(r0 + r) * n + c0 + c];
+            else { u.x = 0; u.y = 0; }
+            sU[r][c] = u;
+        }
+    }
+    pdl_wait();   // x is the previous application's output
+    {
+        const int w = t / kSymB, k = t % kSymB;   // 128 threads: sx[0] = x_J (rows), sx[1] = x_I (columns)
+        const int g = (w ? r0 : c0) + k;
+        V v;
+        if (g < n) v = x[g];
+        else { v.x = 0; v.y = 0; }
+        sx[w][k] = v;
+    }
+    __syncthreads();
+    R ax = 0, ay = 0;
+    if (t < kSymB) {               // row t of the block: sum_c U[t][c] x_J[c]
+        for (int c = 0; c < kSymB; ++c) {
+            const V u = sU[t][c], q = sx[0][c];
+            ax = fma(u.x, q.x, fma(-u.y, q.y, ax));
+            ay = fma(u.x, q.y, fma(u.y, q.x, ay));
+        }
+        V o;
+        o.x = ax;
+        o.y = ay;
+        prow[(int64_t(I) * nb + J) * kSymB + t] = o;
+    } else if (I != J) {           // column c of the block: sum_r U[r][c] x_I[r]
+        const int c = t - kSymB;
+        for (int r = 0; r < kSymB; ++r) {
+            const V u = sU[r][c], q = sx[1][r];
+            ax = fma(u.x, q.x, fma(-u.y, q.y, ax));
+            ay = fma(u.x, q.y, fma(u.y, q.x, ay));
+        }
+        V o;
+        o.x = ax;
+        o.y = ay;
+        pcol[(int64_t(J) * nb + I) * kSymB + c] = o;
+    }
+    pdl_trigger();
+}
+
+// 8 threads per vertex: thread s adds the partials of blocks s, s+8, ... in
+// order, then a fixed shuffle tree combines the 8 sums
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_sym_reduce(const void *prow_, const void *pcol_, int n, int nb,
+                                                          void *y_, MarkedList mk, double *rec_part,
+                                                          int64_t rec_slot)
+{
+    using V = typename Cx2<R>::T;
+    const V *__restrict__ prow = static_cast<const V *>(prow_);
+    const V *__restrict__ pcol = static_cast<const V *>(pcol_);
+    V *__restrict__ y = static_cast<V *>(y_);
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    pdl_wait();
+    R sx = 0, sy = 0;
+    if (i < n) {
+        const int I = i / kSymB, r = i % kSymB;
+        for (int K = sub; K < nb; K += 8) {
+            // block (I, K) for K >= I, its mirror (K, I) for K < I
+            const V p = (K >= I) ? prow[(int64_t(I) * nb + K) * kSymB + r] : pcol[(int64_t(I) * nb + K) * kSymB + r];
+            sx += p.x;
+            sy += p.y;
+        }
+    }
+    for (int o = 1; o < 8; o <<= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (i < n && sub == 0) {
+        V o;
+        o.x = sx;
+        o.y = sy;
+        y[i] = o;
+        if (rec_part && rec_slot >= 0) {
+            int lo = 0, hi = mk.n, mi = -1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const int m = mk.dev ? mk.dev[mid] : mk.inl[mid];
+                if (m == i) { mi = mid; break; }
+                if (m < i) lo = mid + 1; else hi = mid;
+            }
+            if (mi >= 0) rec_part[rec_slot * mk.n + mi] = double(sx) * double(sx) + double(sy) * double(sy);
+        }
+    }
+    pdl_trigger();
+}
+
+template <typename R>
+hw_status launch_apply_sym(const void *U, const void *x, void *y, int n, void *prow, void *pcol,
+                           const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st)
+{
+    using V = typename Cx2<R>::T;
+    const int nb = (n + kSymB - 1) / kSymB;
+    const int blocks = nb * (nb + 1) / 2;
+    const size_t smem = sizeof(V) * (kSymB * (kSymB + 1) + 2 * kSymB);
+    cudaError_t e = cudaFuncSetAttribute(k_apply_sym_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym_blocks)");
+    e = launch_pdl(k_apply_sym_blocks<R>, dim3(blocks), dim3(128), smem, st, U, x, n, nb, prow, pcol);
+    if (e != cudaSuccess) return hw_cuda(e, "k_apply_sym_blocks launch");
+    e = launch_pdl(k_apply_sym_reduce<R>, dim3((n * 8 + 255) / 256), dim3(256), 0, st, (const void *)prow,
+                   (const void *)pcol, n, nb, y, mk, rec_part, rec_slot);
+    return hw_cuda(e, "k_apply_sym_reduce launch");
+}
+
 struct DevBuf {
     cudaStream_t st;
     void *p = nullptr;
@@ -485,8 +634,15 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     if ((s = make_marked(marked, n_marked, n, st, &mk)) != HW_OK) return s;
     struct Rel { MarkedList &m; cudaStream_t st; ~Rel() { free_marked(m, st); } } rel{mk, st};
     const int64_t slots = record ? steps / stride : 0;
+    // the symmetric path halves the bytes read; complex128 is bound by FP64
+    // arithmetic, which both paths share, so it keeps the dense path
+    const bool sym = opts && opts->u_symmetric && batch == 1 && dt == HW_C64;
+    const int nb = int((n + kSymB - 1) / kSymB);
+    const size_t part_bytes = sym ? size_t(nb) * nb * kSymB * esz : 0;   // one array of block partials
     DevBuf tmp(st), recbuf(st);
-    if ((s = tmp.get(bytes, "cudaMallocAsync(state scratch)")) != HW_OK) return s;
+    if ((s = tmp.get(bytes + 2 * part_bytes + 256, "cudaMallocAsync(state scratch)")) != HW_OK) return s;
+    void *prow = static_cast<char *>(tmp.p) + ((bytes + 255) & ~size_t(255));
+    void *pcol = static_cast<char *>(prow) + part_bytes;
     double *rec_part = nullptr;
     if (slots) {
         if (n_marked == 1) {
@@ -508,8 +664,12 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     for (int64_t k = 1; k <= steps; ++k) {
         void *dst = ((steps - k) % 2 == 0) ? P : T;
         const int64_t slot = (slots && k % stride == 0) ? k / stride - 1 : -1;
-        s = (dt == HW_C128) ? launch_apply<double>(U, src, dst, int(n), batch, mk, rec_part, slot, st)
-                            : launch_apply<float>(U, src, dst, int(n), batch, mk, rec_part, slot, st);
+        if (sym)
+            s = (dt == HW_C128) ? launch_apply_sym<double>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st)
+                                : launch_apply_sym<float>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st);
+        else
+            s = (dt == HW_C128) ? launch_apply<double>(U, src, dst, int(n), batch, mk, rec_part, slot, st)
+                                : launch_apply<float>(U, src, dst, int(n), batch, mk, rec_part, slot, st);
         if (s != HW_OK) return s;
         src = dst;
     }

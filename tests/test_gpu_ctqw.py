@@ -187,3 +187,35 @@ def test_config3_hypercube12_search_full_size(hw, dt):
 def torch_index(cols):
     import torch
     return torch.from_numpy(np.asarray(cols)).cuda()
+
+
+@pytest.mark.parametrize("dt", [2, 1])
+@pytest.mark.parametrize("n_bits,steps", [(7, 40), (12, 300)])
+def test_symmetric_apply_matches_dense_apply_and_oracle(hw, dt, n_bits, steps):
+    # U from hw_ctqw_expm is complex symmetric; reading one triangle of blocks
+    # must give the dense application's result (n = 128 spans two 64-blocks,
+    # n = 4096 is the benchmarked size)
+    import torch
+    k = n_bits
+    g = synth.hypercube(k)
+    N = 1 << k
+    m = synth.seeded_vertex(3, N)
+    G, U = gpu_expm(hw, g, 1.0 / k, [m], 0.1, dt=dt)
+    cdt = torch.complex128 if dt == 2 else torch.complex64
+    x = torch.full((N,), 1.0 / np.sqrt(N), dtype=cdt, device="cuda")
+    outs = []
+    for sym in (0, 1):
+        y = torch.empty_like(x)
+        rec = torch.empty(steps, dtype=torch.float64, device="cuda")
+        hw.hw_ctqw_evolve(U, N, dt, 1, steps, x, y, [m], rec, opts={"u_symmetric": sym})
+        outs.append((y.cpu().numpy().astype(np.complex128), rec.cpu().numpy()))
+    ar = oracle.Arcs(*g)
+    ref, rr = oracle.ctqw_evolve(ar, 1.0 / k, synth.uniform_state(N), 0.1, steps, marked=[m], record=True)
+    if dt == 2:
+        assert np.max(np.abs(outs[1][0] - outs[0][0])) <= TOL128
+        assert np.max(np.abs(outs[1][0] - ref)) <= TOL128
+        assert np.max(np.abs(outs[1][1] - rr)) <= TOL128
+    else:
+        assert np.sum(np.abs(np.abs(outs[1][0]) ** 2 - np.abs(ref) ** 2)) <= 1e-3
+        assert np.max(np.abs(outs[1][1] - rr)) <= 1e-4
+    G.free()
