@@ -338,6 +338,12 @@ hw_status hw_server_stats(const hw_server *s, int64_t *queued, int64_t *resident
 /* Wait for the server's stream and free everything it holds. */
 hw_status hw_server_destroy(hw_server *s);
 
+/* Scratch buffers of every call come from a stream-ordered pool per device
+   that keeps freed memory mapped for the next call.  This returns the pool's
+   unused memory to the driver (HW_ECUDA on a driver error).  Call it only
+   when no library call is in flight on any stream. */
+hw_status hw_trim_scratch(void);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *hw_last_error(void);
 

@@ -29,7 +29,8 @@ EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free"
            "hw_coined_evolve", "hw_ctqw_plan", "hw_ctqw_expm", "hw_ctqw_evolve", "hw_probability",
            "hw_probability_noalloc", "hw_gemm_tc", "hw_ctqw_evolve_sparse",
            "hw_server_create", "hw_server_submit", "hw_server_run", "hw_server_poll",
-           "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_last_error", "hw_version")
+           "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_trim_scratch", "hw_last_error",
+           "hw_version")
 
 
 class HWError(RuntimeError):
@@ -107,6 +108,8 @@ def lib():
         L.hw_server_stats.restype = st
         L.hw_server_destroy.argtypes = [P]
         L.hw_server_destroy.restype = st
+        L.hw_trim_scratch.argtypes = []
+        L.hw_trim_scratch.restype = st
         L.hw_last_error.argtypes = []
         L.hw_last_error.restype = ctypes.c_char_p
         L.hw_version.argtypes = []
@@ -171,6 +174,11 @@ def hw_opts_init() -> hw_opts:
 
 def hw_last_error() -> str:
     return lib().hw_last_error().decode()
+
+
+def hw_trim_scratch():
+    """Return the scratch pool's unused device memory to the driver."""
+    _check(lib().hw_trim_scratch())
 
 
 def hw_version() -> str:

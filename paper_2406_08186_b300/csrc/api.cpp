@@ -5,6 +5,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -34,6 +36,63 @@ hw_status hw_cuda(cudaError_t e, const char *what)
 }
 
 void hw_clear_error() { t_err.clear(); }
+
+// Scratch memory comes from one stream-ordered pool per device that keeps
+// freed blocks mapped for the next call (the default pool returns them to the
+// driver at every synchronisation, and mapping a few hundred MB again costs
+// milliseconds).  hw_trim_scratch releases what is not in use.
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaError_t pool_of(int dev, cudaMemPool_t *out)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+    }
+    g_pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t hw_malloc_async(void **p, size_t bytes, cudaStream_t st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (e == cudaSuccess) e = pool_of(dev, &pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, pool, st);
+    return e;
+}
+
+extern "C" hw_status hw_trim_scratch(void)
+{
+    hw_clear_error();
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto &kv : g_pools) {
+        hw_status s = hw_cuda(cudaMemPoolTrimTo(kv.second, 0), "cudaMemPoolTrimTo");
+        if (s != HW_OK) return s;
+    }
+    return HW_OK;
+}
 
 extern "C" const char *hw_last_error(void) { return t_err.c_str(); }
 
@@ -68,8 +127,8 @@ hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaSt
         return HW_OK;
     }
     int32_t *d = nullptr;
-    hw_status s = hw_cuda(cudaMallocAsync((void **)&d, sizeof(int32_t) * n_marked, st),
-                          "cudaMallocAsync(marked)");
+    hw_status s = hw_cuda(hw_malloc_async((void **)&d, sizeof(int32_t) * n_marked, st),
+                          "scratch allocation (marked)");
     if (s != HW_OK) return s;
     // the host vector dies on return, so this copy must have completed by then
     s = hw_cuda(cudaMemcpyAsync(d, m.data(), sizeof(int32_t) * n_marked, cudaMemcpyHostToDevice, st),
@@ -104,7 +163,7 @@ struct Scratch {
     explicit Scratch(cudaStream_t s) : st(s) {}
     hw_status get(size_t bytes, const char *what)
     {
-        return hw_cuda(cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st), what);
+        return hw_cuda(hw_malloc_async(&p, std::max<size_t>(bytes, 16), st), what);
     }
     ~Scratch() { if (p) cudaFreeAsync(p, st); }
 };
@@ -170,13 +229,13 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
 
     const int64_t slots = record ? steps / stride : 0;
     Scratch tmp(st), recbuf(st);
-    if ((s = tmp.get(bytes, "cudaMallocAsync(state scratch)")) != HW_OK) return s;
+    if ((s = tmp.get(bytes, "scratch allocation (state scratch)")) != HW_OK) return s;
     double *rec_part = nullptr;
     if (slots) {
         if (n_marked == 1) {
             rec_part = record;  // one marked vertex: partials are the record itself
         } else {
-            if ((s = recbuf.get(sizeof(double) * slots * n_marked * batch, "cudaMallocAsync(record)")) != HW_OK)
+            if ((s = recbuf.get(sizeof(double) * slots * n_marked * batch, "scratch allocation (record)")) != HW_OK)
                 return s;
             rec_part = static_cast<double *>(recbuf.p);
         }

@@ -439,7 +439,7 @@ struct DevBuf {
     explicit DevBuf(cudaStream_t s) : st(s) {}
     hw_status get(size_t bytes, const char *what)
     {
-        return hw_cuda(cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st), what);
+        return hw_cuda(hw_malloc_async(&p, std::max<size_t>(bytes, 16), st), what);
     }
     template <typename T> T *as() const { return static_cast<T *>(p); }
     ~DevBuf() { if (p) cudaFreeAsync(p, st); }
@@ -520,9 +520,9 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     const size_t bytes = sizeof(double) * nn;
 
     DevBuf Y(st), Q(st), Qn(st), Re(st), Im(st);
-    if ((s = Y.get(bytes, "cudaMallocAsync(Y)")) != HW_OK || (s = Q.get(bytes, "cudaMallocAsync(Q)")) != HW_OK ||
-        (s = Qn.get(bytes, "cudaMallocAsync(Q)")) != HW_OK || (s = Re.get(bytes, "cudaMallocAsync(ReU)")) != HW_OK ||
-        (s = Im.get(bytes, "cudaMallocAsync(ImU)")) != HW_OK)
+    if ((s = Y.get(bytes, "scratch allocation (Y)")) != HW_OK || (s = Q.get(bytes, "scratch allocation (Q)")) != HW_OK ||
+        (s = Qn.get(bytes, "scratch allocation (Q)")) != HW_OK || (s = Re.get(bytes, "scratch allocation (ReU)")) != HW_OK ||
+        (s = Im.get(bytes, "scratch allocation (ImU)")) != HW_OK)
         return s;
 
     // T1: Y = tau H
@@ -537,10 +537,12 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     if (use_tc) {
         // complex64 path: powers on the tensor cores from split-bf16 operands
         TcPower *tp = nullptr;
-        // host-known max |Y| (edge weight gamma tau, marked diagonal tau) and ||Y||_inf
-        double maxY = 0.0;
-        if (g->num_arcs) maxY = std::fabs(gamma * tau);
-        if (mk.n) maxY = std::max(maxY, std::fabs(tau));
+        // host-known magnitudes of Y's entries (edge weight gamma tau, marked
+        // diagonal tau) and ||Y||_inf
+        double yvals[2];
+        int nyvals = 0;
+        if (g->num_arcs && gamma != 0.0) yvals[nyvals++] = std::fabs(gamma * tau);
+        if (mk.n && tau != 0.0) yvals[nyvals++] = std::fabs(tau);
         double theta = 0.0;
         {
             std::vector<char> is_m(n, 0);
@@ -549,11 +551,11 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
                 theta = std::max(theta, (std::fabs(gamma) * (g->h_row_ptr[v + 1] - g->h_row_ptr[v]) +
                                          (is_m[v] ? 1.0 : 0.0)) * std::fabs(tau));
         }
-        if ((s = tc_power_begin(n, Y.as<double>(), maxY, theta, gmode, st, &tp)) != HW_OK) return s;
+        if ((s = tc_power_begin(n, Y.as<double>(), yvals, nyvals, theta, gmode, st, &tp)) != HW_OK) return s;
         for (int k = 2; k <= m_deg && s == HW_OK; ++k) {
             double *accU = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
             const double sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
-            s = tc_power_step(tp, k, accU, sign, st);
+            s = tc_power_step(tp, k, accU, sign);
         }
         hw_status e = tc_power_end(tp, st, s == HW_OK);
         if (s == HW_OK) s = e;
@@ -640,7 +642,7 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     const int nb = int((n + kSymB - 1) / kSymB);
     const size_t part_bytes = sym ? size_t(nb) * nb * kSymB * esz : 0;   // one array of block partials
     DevBuf tmp(st), recbuf(st);
-    if ((s = tmp.get(bytes + 2 * part_bytes + 256, "cudaMallocAsync(state scratch)")) != HW_OK) return s;
+    if ((s = tmp.get(bytes + 2 * part_bytes + 256, "scratch allocation (state scratch)")) != HW_OK) return s;
     void *prow = static_cast<char *>(tmp.p) + ((bytes + 255) & ~size_t(255));
     void *pcol = static_cast<char *>(prow) + part_bytes;
     double *rec_part = nullptr;
@@ -648,7 +650,7 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
         if (n_marked == 1) {
             rec_part = record;
         } else {
-            if ((s = recbuf.get(sizeof(double) * slots * n_marked * batch, "cudaMallocAsync(record)")) != HW_OK)
+            if ((s = recbuf.get(sizeof(double) * slots * n_marked * batch, "scratch allocation (record)")) != HW_OK)
                 return s;
             rec_part = recbuf.as<double>();
         }

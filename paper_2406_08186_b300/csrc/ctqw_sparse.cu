@@ -136,7 +136,7 @@ extern "C" hw_status hw_ctqw_evolve_sparse(const hw_graph *g, double gamma, cons
     const int64_t slots = record ? steps / stride : 0;
     void *mem = nullptr;
     const size_t rec_bytes = (slots && n_marked > 1) ? sizeof(double) * slots * n_marked * batch : 0;
-    if ((s = hw_cuda(cudaMallocAsync(&mem, 4 * bytes + rec_bytes + 64, st), "cudaMallocAsync(ctqw buffers)")) != HW_OK)
+    if ((s = hw_cuda(hw_malloc_async(&mem, 4 * bytes + rec_bytes + 64, st), "scratch allocation (ctqw buffers)")) != HW_OK)
         return s;
     struct Free { void *p; cudaStream_t st; ~Free() { cudaFreeAsync(p, st); } } fr{mem, st};
     char *b = static_cast<char *>(mem);

@@ -8,26 +8,38 @@
 //   fp16 x 2 slices, 3 products (default): about 2^-22 of the matrix maximum;
 //   bf16 x 3 slices, 6 products: about 2^-24; bf16 x 2: 2^-16; bf16 x 1: 2^-8.
 // fp16 slices are taken of the operand times a power of two that puts its
-// largest entry in [1/2, 1] (exact), so the 5-bit exponent never limits.
+// largest entry in [1/2, 1] (exact), so the 5-bit exponent never limits.  When
+// every entry of B is exact in one slice (the Taylor step's Y = tau H of an
+// unweighted graph, scaled by 1 / (gamma tau), has entries 0, 1 and 1/gamma),
+// B keeps one slice and the products with its lower slices are dropped.
 //
-// One CTA computes one 128 x 128 output tile with 4 warps: warp 0 lane 0
-// streams the K blocks (64 elements = one 128-byte swizzle atom) of every
-// slice of A and B with TMA into a shared-memory ring (2 to 6 stages,
-// 192 KiB); warp 1 lane 0 issues the MMAs and releases stages with
-// tcgen05.commit; after the last block all 4 warps drain the accumulator
-// (tcgen05.ld, warp w owns TMEM lanes 32w..32w+31 = tile rows) and run the
-// epilogue:
+// Work is cut into 128 x 256 CTA tiles, grouped 2 x 2 into thread-block
+// clusters (256 x 512 cluster tiles).  The two CTAs of a cluster row share
+// their A rows and the two of a cluster column share their B rows: each CTA
+// loads half of its A tile and half of its B tile with TMA and multicasts it
+// to the CTA that shares it, so every operand byte leaves L2 once per
+// cluster, not once per CTA.  Persistent clusters walk a list of cluster
+// tiles.  Per CTA, 6 warps: warp 4 lane 0 streams K blocks (32 elements = one
+// 64-byte swizzle row) of every slice into a shared-memory ring (3 to 8
+// stages, 216 KiB); warp 5 lane 0 issues the MMAs (M = 128, N = 256) into one
+// of two 256-column TMEM accumulators and releases each stage with a
+// tcgen05.commit that arrives on the stage's "empty" barrier in all three
+// CTAs that write into it; warps 0-3 drain the other accumulator (tcgen05.ld,
+// warp w owns TMEM lanes 32w..32w+31 = tile rows) and run the epilogue of the
+// previous tile:
 //   EPI_STORE:  C = scale * acc (fp32)
 //   EPI_TAYLOR: Q = scale * acc, written back as slices of qscale * Q (the
-//               next power's A operand) and added to the lower triangle of
-//               Re/Im U in double (the caller mirrors it after the series).
-// Tiles come from a host-built list in 8 x 8 supertile order, so CTAs that
-// run together share operand blocks in L2.  For a symmetric product (every
-// Taylor power of the symmetric Y is symmetric) only tiles with I <= J are
-// computed and the mirror block is written from the same accumulator with
-// coalesced transposed stores.
+//               next power's A operand); k_taylor_acc then adds Q to the lower
+//               triangle of Re/Im U in double on a second stream, overlapped
+//               with the next power's GEMM (the caller mirrors the sum).
+// For a symmetric product (every Taylor power of the symmetric Y is
+// symmetric) only cluster tiles that reach the upper triangle run, 128 x 128
+// blocks below the diagonal are not written, and each off-diagonal block is
+// also written to its mirror position with coalesced transposed stores.
 // Every wait on an mbarrier is bounded; a timeout sets an error flag that the
-// host reads, and the CTA still frees its tensor memory.
+// host reads, and the CTA still frees its tensor memory.  Before a CTA exits,
+// its producer waits until every stage it filled has been released by all
+// three consumers, so no peer signals a CTA that has left.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -37,42 +49,45 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
 
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = 64;
-constexpr int kTileBytes = TM * TK * 2;                   // 16 KB per slice tile (A or B)
-constexpr int kRingBytes = 192 * 1024;                    // shared-memory ring
-constexpr int kMaxStages = 6;
-constexpr int kSmemBytes = kRingBytes + 1024;             // + alignment slack
-constexpr int kTmemCols = 128;                            // 128 lanes x 128 fp32 columns
+constexpr int TM = 128, TN = 256, TK = 32;                // CTA tile; K block = one 64-byte swizzle row
+constexpr int kCM = 2, kCN = 1;                           // cluster of kCM x kCN CTAs: rank = i + kCM j
+constexpr int kCluster = kCM * kCN;
+constexpr int kATile = TM * TK * 2;                       // 8 KB per A slice
+constexpr int kBTile = TN * TK * 2;                       // 16 KB per B slice
+constexpr int kRingBytes = 216 * 1024;                    // shared-memory ring
+constexpr int kMaxStages = 8;
+constexpr int kSmemSlack = 2048;                          // alignment of the ring base + margin
+constexpr int kAccWarps = 8;                              // warps that only help with the accumulation
+constexpr int kThreads = 192 + 32 * kAccWarps;
+constexpr int kTmemCols = 2 * TN;                         // two accumulators
 constexpr uint64_t kWaitLimitNs = 2000000000ull;          // bounded mbarrier waits (2 s)
 
 enum { FMT_BF16 = 0, FMT_F16 = 1 };
 enum { EPI_STORE = 0, EPI_TAYLOR = 1 };
 
 struct TcArgs {
-    const int2 *tiles;       // (I, J) tile per CTA
+    const int2 *tiles;       // cluster tiles (P, Q): rows 256 P.., columns 512 Q..
     int m, n, k;
-    int ns;                  // operand slices (1..3)
-    int nprod;               // slice products
-    int prod[6][2];          // (A slice, B slice), smallest first
-    int stages;              // ring depth
     int epi;
-    int sym;                 // mirror each off-diagonal tile to (J, I)
+    int sym;                 // skip blocks below the diagonal, mirror the others
     float scale;             // acc multiplier (host-known part)
     const float *dscale;     // acc multiplier read on the device (or nullptr)
     float *C;                // EPI_STORE: [m][ldc]
     int ldc;
-    void *Q[3];              // EPI_TAYLOR: output slices [m][ldq] of qscale * Q
+    void *Q[3];              // EPI_TAYLOR: output slices [m][ldq] of qscale * Q (na of them)
     int ldq;
     float qscale;
-    double *accU;            // EPI_TAYLOR: [m][ldu]
-    int ldu;
-    double sign;
+    const void *accQ[3];     // EPI_TAYLOR: slices of the previous power, added to accU by the
+    double acc_coef;         // epilogue warps while the first tile multiplies (accU == nullptr: none)
+    double *accU;
     int *err;                // set to 1 on a wait timeout
 };
 
@@ -120,24 +135,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y)
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 2D tile load written to the same shared-memory offset of every CTA in mask,
+// each CTA's mbarrier at offset bar receiving the bytes it got
+__device__ __forceinline__ void tma_load_mc(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
+                                            uint16_t mask)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// groups 1024 bytes apart (the layout TMA writes for a 64-wide 16-bit box).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row
+// groups 512 bytes apart (the layout TMA writes for a 32-wide 16-bit box).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr)
 {
     uint64_t d = 0;
     d |= uint64_t((addr & 0x3FFFFu) >> 4);      // start address
     d |= uint64_t(1) << 16;                      // leading offset (unused when swizzled)
-    d |= uint64_t(1024 >> 4) << 32;              // stride offset between 8-row groups
+    d |= uint64_t(512 >> 4) << 32;               // stride offset between 8-row groups
     d |= uint64_t(1) << 46;                      // descriptor version
-    d |= uint64_t(2) << 61;                      // 128-byte swizzle
+    d |= uint64_t(4) << 61;                      // 64-byte swizzle
     return d;
 }
 
@@ -164,6 +195,15 @@ __device__ __forceinline__ void mma16(uint32_t tmem_d, uint64_t adesc, uint64_t 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// arrives once on the mbarrier at offset bar of every CTA in mask when this
+// thread's earlier MMAs have completed
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"(mask)
                  : "memory");
 }
 
@@ -204,34 +244,196 @@ __device__ __forceinline__ void split(float x, int ns, typename Sl<FMT>::T *s)
     }
 }
 
-template <int FMT>
-__global__ void __launch_bounds__(128, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
-          const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
-          const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, TcArgs a)
+// T3 of the series: accU[i][j] += coef * Q[i][j] for j <= i (the lower
+// triangle) over rows i = row0, row0 + rstride, ..., with Q given by its NA
+// slices (of Q / coef up to sign); the slices are summed in fp32 (what the
+// next power multiplies) and added in double.  nt threads (tid) split each
+// row; each takes 4 columns nt apart and issues their loads together.
+template <int FMT, int NA>
+__device__ __forceinline__ void acc_rows(int n, const void *q0, const void *q1, const void *q2, int ldq,
+                                         double coef, double *__restrict__ accU, int row0, int rstride, int tid,
+                                         int nt)
+{
+    using ST = typename Sl<FMT>::T;
+    constexpr int U = 4;
+    for (int i = row0; i < n; i += rstride) {
+        const ST *__restrict__ r0 = static_cast<const ST *>(q0) + int64_t(i) * ldq;
+        const ST *__restrict__ r1 = static_cast<const ST *>(q1) + int64_t(i) * ldq;
+        const ST *__restrict__ r2 = static_cast<const ST *>(q2) + int64_t(i) * ldq;
+        double *__restrict__ u = accU + int64_t(i) * n;
+        for (int j0 = tid; j0 <= i; j0 += U * nt) {
+            float q[U];
+            double x[U];
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const int j = j0 + t * nt;
+                if (j <= i) {
+                    q[t] = Sl<FMT>::to(r0[j]);
+                    if (NA > 1) q[t] += Sl<FMT>::to(r1[j]);
+                    if (NA > 2) q[t] += Sl<FMT>::to(r2[j]);
+                    x[t] = u[j];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const int j = j0 + t * nt;
+                if (j <= i) u[j] = fma(coef, double(q[t]), x[t]);
+            }
+        }
+    }
+}
+
+template <int FMT, int NA>
+__global__ void __launch_bounds__(256) k_taylor_acc(int n, const void *q0, const void *q1, const void *q2,
+                                                    int ldq, double coef, double *__restrict__ accU)
+{
+    acc_rows<FMT, NA>(n, q0, q1, q2, ldq, coef, accU, blockIdx.x, gridDim.x, threadIdx.x, blockDim.x);
+}
+
+// Epilogue of one 128 x 256 CTA tile whose accumulator is at TMEM column tacc;
+// Q is written as NA slices.
+template <int FMT, int NA>
+__device__ __forceinline__ void epilogue_tile(const TcArgs &a, int row0, int col0, uint32_t tacc, int warp, int lane)
 {
     using S = Sl<FMT>;
+    constexpr int na = NA;
+    const float mult = a.scale * (a.dscale ? *a.dscale : 1.0f);
+    const int row = row0 + warp * 32 + lane;    // tile row held by this thread
+    const int rblk = row0 / 128;
+    const bool c_vec = a.C && (a.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(a.C) % 16 == 0);
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+        const int col0c = col0 + c0;
+        const int cblk = col0c / 128;
+        if (a.sym && cblk < rblk) continue;     // below the diagonal: written as the mirror of (cblk, rblk)
+        uint32_t r[16];
+        tmem_ld16(tacc + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]) * mult;
+        if (a.epi == EPI_STORE) {
+            if (row < a.m) {
+                float *dst = a.C + int64_t(row) * a.ldc + col0c;
+                if (c_vec && col0c + 16 <= a.n) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (col0c + q < a.n) dst[q] = v[q];
+                }
+            }
+            continue;
+        }
+        // Taylor epilogue: slices of qscale * Q, written to both blocks of a
+        // mirrored pair (the next power's A operand and the input of the
+        // double-precision accumulation, k_taylor_acc)
+        const bool mirror = a.sym && cblk != rblk;
+        const bool in_row = row < a.m;
+        const bool do_mirror = mirror && row < a.n;
+        typename S::T sl[3][16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            typename S::T t3[3];
+            split<FMT>(v[q] * a.qscale, na, t3);
+            sl[0][q] = t3[0];
+            sl[1][q] = t3[1];
+            sl[2][q] = t3[2];
+        }
+        if (in_row) {
+            const bool full = col0c + 16 <= a.n;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (i >= na) break;
+                typename S::T *qd = static_cast<typename S::T *>(a.Q[i]) + int64_t(row) * a.ldq + col0c;
+                if (full) {
+                    // 16 slice values = 32 contiguous bytes (ldq is a multiple of 64)
+                    reinterpret_cast<uint4 *>(qd)[0] = *reinterpret_cast<const uint4 *>(&sl[i][0]);
+                    reinterpret_cast<uint4 *>(qd)[1] = *reinterpret_cast<const uint4 *>(&sl[i][8]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (col0c + q < a.n) qd[q] = sl[i][q];
+                }
+            }
+        }
+        if (do_mirror) {
+            // element (row, col) -> (col, row): consecutive lanes write consecutive columns
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int mrow = col0c + q;
+                if (mrow >= a.m) continue;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    if (i < na) static_cast<typename S::T *>(a.Q[i])[int64_t(mrow) * a.ldq + row] = sl[i][q];
+            }
+        }
+    }
+}
+
+// Ring geometry of a slice configuration: NA slices of A, NB of B per stage.
+template <int NA, int NB>
+struct Ring {
+    static constexpr int kStageBytes = NA * kATile + NB * kBTile;
+    static constexpr int kStages = (kRingBytes / kStageBytes < kMaxStages) ? kRingBytes / kStageBytes : kMaxStages;
+};
+
+// One K block of MMAs (TK / 16 steps x the slice products (i, j), i + j < NA,
+// j < NB, smaller products first) from the stage whose descriptors start at
+// dA (A slice 0) and dB (B slice 0).  Everything but the stage base is a
+// compile-time constant, so the issuing thread spends a few instructions per
+// MMA; acc0 = 0 starts the accumulator with the first product.
+template <int FMT, int NA, int NB>
+__device__ __forceinline__ void mma_block(uint32_t tacc, uint64_t dA, uint64_t dB, uint32_t acc0)
+{
+#pragma unroll
+    for (int kk = 0; kk < TK / 16; ++kk) {
+#pragma unroll
+        for (int d = NA - 1; d >= 0; --d) {
+#pragma unroll
+            for (int i = d; i >= 0; --i) {
+                const int j = d - i;
+                if (j < NB) {
+                    const uint64_t ad = dA + uint64_t((i * kATile) >> 4) + uint64_t(2 * kk);
+                    const uint64_t bd = dB + uint64_t((j * kBTile) >> 4) + uint64_t(2 * kk);
+                    const bool first = (kk == 0 && d == NA - 1 && i == d);
+                    mma16<FMT>(tacc, ad, bd, first ? acc0 : 1u);
+                }
+            }
+        }
+    }
+}
+
+template <int FMT, int NA, int NB>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+          const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+          const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, TcArgs a, int ntiles)
+{
+    constexpr int kStageBytes = Ring<NA, NB>::kStageBytes;
+    constexpr int S = Ring<NA, NB>::kStages;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_full[kMaxStages], bar_empty[kMaxStages], bar_done;
+    __shared__ __align__(8) uint64_t bar_full[kMaxStages], bar_empty[kMaxStages], bar_tfull[2], bar_tempty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int timed_out;
 
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 tile = a.tiles[blockIdx.x];
-    const int m0 = tile.x * TM, n0 = tile.y * TN;
-    const int ns = a.ns;
-    const int stage_bytes = 2 * ns * kTileBytes;
+    const uint32_t rank = cluster_rank();
+    const int ci = int(rank) % kCM, cj = int(rank) / kCM;     // position in the cluster
+    const int cid = int(blockIdx.x) / kCluster, ncl = int(gridDim.x) / kCluster;
     const int nkb = (a.k + TK - 1) / TK;
-    const CUtensorMap *mA[3] = {&tA0, &tA1, &tA2};
-    const CUtensorMap *mB[3] = {&tB0, &tB1, &tB2};
+    volatile int *tmo = &timed_out;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < a.stages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_empty[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1 + (kCM - 1) + (kCN - 1));   // this CTA and those sharing its loads
         }
-        mbar_init(smem_u32(&bar_done), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bar_tfull[b]), 1);
+            mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per epilogue warp
+        }
         timed_out = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -242,149 +444,136 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    cluster_sync();   // every CTA's barriers are initialised before any peer signals them
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // producer: TMA loads of every slice tile of A and B per K block
-        const uint32_t bytes = uint32_t(stage_bytes);
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % a.stages;
-            const uint32_t use = uint32_t(kb / a.stages);
-            if (kb >= a.stages && !mbar_wait(smem_u32(&bar_empty[s]), (use & 1u) ^ 1u)) {
-                timed_out = 1;
-                break;
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer: this CTA's half of the A tile goes to both CTAs of its
+            // cluster row, its half of the B tile to both CTAs of its column
+            const CUtensorMap *mA[3] = {&tA0, &tA1, &tA2};
+            const CUtensorMap *mB[3] = {&tB0, &tB1, &tB2};
+            // (with one CTA in a cluster row or column, the CTA loads both halves itself)
+            const uint16_t maskA = uint16_t(kCN == 2 ? (1u << ci) | (1u << (ci + kCM)) : (1u << rank));
+            const uint16_t maskB = uint16_t(kCM == 2 ? 3u << (kCM * cj) : (1u << rank));
+            const int ha0 = (kCN == 2) ? cj : 0, ha1 = (kCN == 2) ? cj + 1 : 2;   // A halves loaded here
+            const int hb0 = (kCM == 2) ? ci : 0, hb1 = (kCM == 2) ? ci + 1 : 2;   // B halves loaded here
+            uint32_t g = 0, phase = 0;
+            int s = 0;
+            for (int t = cid; t < ntiles && !*tmo; t += ncl) {
+                const int2 ct = a.tiles[t];
+                const int rowA = ct.x * kCM * TM + ci * TM;
+                const int rowB = ct.y * kCN * TN + cj * TN;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (g >= uint32_t(S) && !mbar_wait(smem_u32(&bar_empty[s]), phase ^ 1u)) {
+                        *tmo = 1;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&bar_full[s]);
+                    mbar_expect_tx(full, uint32_t(kStageBytes));   // all bytes landing here, from any CTA
+                    const uint32_t st = base + uint32_t(s * kStageBytes);
+#pragma unroll
+                    for (int i = 0; i < NA; ++i)
+                        for (int h = ha0; h < ha1; ++h)
+                            tma_load_mc(st + uint32_t(i * kATile + h * (kATile / 2)), mA[i], full, kb * TK,
+                                        rowA + h * (TM / 2), maskA);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        for (int h = hb0; h < hb1; ++h)
+                            tma_load_mc(st + uint32_t(NA * kATile + j * kBTile + h * (kBTile / 2)), mB[j], full,
+                                        kb * TK, rowB + h * (TN / 2), maskB);
+                    ++g;
+                    if (++s == S) { s = 0; phase ^= 1u; }
+                }
             }
-            const uint32_t full = smem_u32(&bar_full[s]);
-            mbar_expect_tx(full, bytes);
-            const uint32_t st = base + uint32_t(s * stage_bytes);
-            for (int i = 0; i < ns; ++i) {
-                tma_load_2d(st + uint32_t(i * kTileBytes), mA[i], full, kb * TK, m0);
-                tma_load_2d(st + uint32_t((ns + i) * kTileBytes), mB[i], full, kb * TK, n0);
+            // drain: the last fill of every stage released by all three consumers
+            for (uint32_t q = 0; q < uint32_t(S) && q < g; ++q) {
+                const uint32_t last_use = (g - 1 - q) / uint32_t(S);
+                if (!mbar_wait(smem_u32(&bar_empty[q]), last_use & 1u)) *tmo = 1;
             }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % a.stages;
-            const uint32_t use = uint32_t(kb / a.stages);
-            if (!mbar_wait(smem_u32(&bar_full[s]), use & 1u)) {
-                timed_out = 1;
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer: accumulator b = (local tile) & 1
+            // every CTA that writes into this CTA's stages: itself, the other
+            // CTA of its cluster row (A) and of its cluster column (B)
+            const uint16_t maskC = uint16_t((1u << rank) | (kCN == 2 ? 1u << (ci + kCM * (1 - cj)) : 0u) |
+                                            (kCM == 2 ? 1u << ((1 - ci) + kCM * cj) : 0u));
+            const uint64_t d0 = smem_desc_sw64(base);
+            uint32_t phase = 0, li = 0;
+            int s = 0;
+            for (int t = cid; t < ntiles && !*tmo; t += ncl, ++li) {
+                const int b = int(li & 1u);
+                const uint32_t ub = li >> 1;
+                if (ub > 0 && !mbar_wait(smem_u32(&bar_tempty[b]), (ub & 1u) ^ 1u)) {
+                    *tmo = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tacc = tmem + uint32_t(b * TN);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(smem_u32(&bar_full[s]), phase)) {
+                        *tmo = 1;
+                        break;
+                    }
+                    const uint64_t dA = d0 + uint64_t((s * kStageBytes) >> 4);
+                    mma_block<FMT, NA, NB>(tacc, dA, dA + uint64_t((NA * kATile) >> 4), kb > 0 ? 1u : 0u);
+                    mma_commit_mc(smem_u32(&bar_empty[s]), maskC);
+                    if (++s == S) { s = 0; phase ^= 1u; }
+                }
+                mma_commit(smem_u32(&bar_tfull[b]));
+            }
+        }
+    } else if (warp >= 6) {
+        // accumulation-only warps, see below
+        if (a.accU)
+            acc_rows<FMT, NA>(a.n, a.accQ[0], a.accQ[1], a.accQ[2], a.ldq, a.acc_coef, a.accU, int(blockIdx.x),
+                              int(gridDim.x), 128 + int(threadIdx.x) - 192, 128 + 32 * kAccWarps);
+    } else {
+        // epilogue warps 0-3 (with warps 6..): first the previous power's
+        // accumulation (its slices are this GEMM's A operand, so mostly L2
+        // hits), rows spread over all CTAs, while the tensor cores work on the
+        // first tile
+        if (a.accU)
+            acc_rows<FMT, NA>(a.n, a.accQ[0], a.accQ[1], a.accQ[2], a.ldq, a.acc_coef, a.accU, int(blockIdx.x),
+                              int(gridDim.x), int(threadIdx.x), 128 + 32 * kAccWarps);
+        uint32_t li = 0;
+        for (int t = cid; t < ntiles; t += ncl, ++li) {
+            const int b = int(li & 1u);
+            if (!mbar_wait(smem_u32(&bar_tfull[b]), (li >> 1) & 1u)) {
+                *tmo = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = base + uint32_t(s * stage_bytes);
-            for (int kk = 0; kk < TK / 16; ++kk) {
-                for (int p = 0; p < a.nprod; ++p) {
-                    const int i = a.prod[p][0], j = a.prod[p][1];
-                    const uint64_t ad = smem_desc_sw128(st + uint32_t(i * kTileBytes)) + uint64_t(2 * kk);
-                    const uint64_t bd = smem_desc_sw128(st + uint32_t((ns + j) * kTileBytes)) + uint64_t(2 * kk);
-                    mma16<FMT>(tmem, ad, bd, (kb > 0 || kk > 0 || p > 0) ? 1u : 0u);
-                }
-            }
-            mma_commit(smem_u32(&bar_empty[s]));
+            const int2 ct = a.tiles[t];
+            epilogue_tile<FMT, NA>(a, ct.x * kCM * TM + ci * TM, ct.y * kCN * TN + cj * TN, tmem + uint32_t(b * TN),
+                                   warp, lane);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_tempty[b])) : "memory");
         }
-        mma_commit(smem_u32(&bar_done));
     }
     __syncwarp();
-
-    // epilogue: every warp drains its 32 TMEM lanes (tile rows)
-    const bool done_ok = mbar_wait(smem_u32(&bar_done), 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!done_ok) timed_out = 1;
-    __syncthreads();
-    if (!timed_out) {
-        const float mult = a.scale * (a.dscale ? *a.dscale : 1.0f);
-        const int rl = warp * 32 + lane;            // tile row held by this thread
-        const int row = m0 + rl;
-        const bool mirror = a.sym && tile.x != tile.y;
-        for (int c0 = 0; c0 < TN; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
-            float v[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]) * mult;
-            const int col0 = n0 + c0;
-            if (a.epi == EPI_STORE) {
-                if (row < a.m) {
-                    float *dst = a.C + int64_t(row) * a.ldc + col0;
-#pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (col0 + q < a.n) dst[q] = v[q];
-                }
-                continue;
-            }
-            // Taylor epilogue: slices of qscale * Q (both blocks of a mirrored
-            // tile, the next power's A operand) and the double-precision sum,
-            // which is kept in the lower triangle only (block (J, I), I <= J) and
-            // mirrored once after the series.  The sum's stream uses evict-first
-            // loads and stores so it does not push operand blocks out of L2, and
-            // all of a chunk's loads are issued before its stores.
-            const bool in_row = row < a.m;
-            const bool do_mirror = mirror && row < a.n;
-            double um[16];
-            if (row < a.n) {
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    um[q] = (col0 + q < a.m) ? __ldcs(a.accU + int64_t(col0 + q) * a.ldu + row) : 0.0;
-            }
-            typename S::T sl[3][16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                typename S::T t3[3];
-                split<FMT>(v[q] * a.qscale, ns, t3);
-                sl[0][q] = t3[0];
-                sl[1][q] = t3[1];
-                sl[2][q] = t3[2];
-            }
-            if (in_row) {
-                const bool full = col0 + 16 <= a.n;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    if (i >= ns) break;
-                    typename S::T *qd = static_cast<typename S::T *>(a.Q[i]) + int64_t(row) * a.ldq + col0;
-                    if (full) {
-                        // 16 slice values = 32 contiguous bytes (ldq is a multiple of 64)
-                        reinterpret_cast<uint4 *>(qd)[0] = *reinterpret_cast<const uint4 *>(&sl[i][0]);
-                        reinterpret_cast<uint4 *>(qd)[1] = *reinterpret_cast<const uint4 *>(&sl[i][8]);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q)
-                            if (col0 + q < a.n) qd[q] = sl[i][q];
-                    }
-                }
-            }
-            if (row < a.n) {
-                // element (row, col) -> (col, row): consecutive lanes write consecutive columns
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int mrow = col0 + q;
-                    if (mrow >= a.m) continue;
-                    if (do_mirror) {
-#pragma unroll
-                        for (int i = 0; i < 3; ++i)
-                            if (i < ns) static_cast<typename S::T *>(a.Q[i])[int64_t(mrow) * a.ldq + row] = sl[i][q];
-                    }
-                    __stcs(a.accU + int64_t(mrow) * a.ldu + row, um[q] + a.sign * double(v[q]));
-                }
-            }
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    cluster_sync();   // no CTA leaves while a peer may still write to or signal it
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     if (threadIdx.x == 0 && timed_out) atomicExch(a.err, 1);
 }
 
-// largest |x| of a matrix as float bits (non-negative floats order like their bits)
+// largest |x| of a matrix as float bits (non-negative floats order like their bits);
+// blocks stride over rows, threads over columns
 template <typename T>
 __global__ void k_absmax(const T *__restrict__ x, int rows, int cols, int ldx, unsigned *out)
 {
-    const int64_t total = int64_t(rows) * cols;
     float mx = 0.f;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x)
-        mx = fmaxf(mx, fabsf(float(x[(e / cols) * ldx + e % cols])));
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const T *xr = x + int64_t(r) * ldx;
+        for (int c = threadIdx.x; c < cols; c += blockDim.x) mx = fmaxf(mx, fabsf(float(xr[c])));
+    }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
 }
@@ -401,29 +590,40 @@ __global__ void k_scales(const unsigned *mx, float *scale)
     scale[2] = 1.f / (s[0] * s[1]);
 }
 
-// matrix -> ns slices of (scale * x) with row stride ld (columns >= cols untouched)
+// matrix -> ns slices of (scale * x) with row stride ld (columns >= cols
+// untouched); blocks stride over rows, threads over columns
 template <int FMT, typename T>
 __global__ void k_split(const T *__restrict__ x, int rows, int cols, int ldx, int ns, int ld, const float *dscale,
                         double hscale, void *s0, void *s1, void *s2)
 {
     using ST = typename Sl<FMT>::T;
-    const int64_t total = int64_t(rows) * cols;
     const double sc = dscale ? double(*dscale) : hscale;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = e / cols, j = e % cols;
-        // the first subtraction runs in T (double for Y) so that fp64 inputs keep their low bits
-        const T xs = T(double(x[i * ldx + j]) * sc);
-        ST sl[3];
-        sl[0] = Sl<FMT>::from(float(xs));
-        if (ns > 1) {
-            const T r1 = xs - T(Sl<FMT>::to(sl[0]));
-            sl[1] = Sl<FMT>::from(float(r1));
-            if (ns > 2) sl[2] = Sl<FMT>::from(float(r1 - T(Sl<FMT>::to(sl[1]))));
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const T *xr = x + int64_t(r) * ldx;
+        ST *o0 = static_cast<ST *>(s0) + int64_t(r) * ld;
+        ST *o1 = static_cast<ST *>(s1) + int64_t(r) * ld;
+        ST *o2 = static_cast<ST *>(s2) + int64_t(r) * ld;
+        for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+            const T x0 = xr[c];
+            if (x0 == T(0)) {   // sparse Y: most entries are zero and so are their slices
+                o0[c] = Sl<FMT>::from(0.0f);
+                if (ns > 1) o1[c] = Sl<FMT>::from(0.0f);
+                if (ns > 2) o2[c] = Sl<FMT>::from(0.0f);
+                continue;
+            }
+            // the scale is applied and the first subtraction runs in T (double
+            // for Y, so that fp64 inputs keep their low bits; float inputs are
+            // scaled by powers of two, which is exact in float)
+            const T xs = x0 * T(sc);
+            const ST a0 = Sl<FMT>::from(float(xs));
+            o0[c] = a0;
+            if (ns > 1) {
+                const T r1 = xs - T(Sl<FMT>::to(a0));
+                const ST a1 = Sl<FMT>::from(float(r1));
+                o1[c] = a1;
+                if (ns > 2) o2[c] = Sl<FMT>::from(float(r1 - T(Sl<FMT>::to(a1))));
+            }
         }
-        static_cast<ST *>(s0)[i * ld + j] = sl[0];
-        if (ns > 1) static_cast<ST *>(s1)[i * ld + j] = sl[1];
-        if (ns > 2) static_cast<ST *>(s2)[i * ld + j] = sl[2];
     }
 }
 
@@ -443,18 +643,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
     return fn;
 }
 
-// 2D 16-bit map over a [rows][cols] slice with row stride ld, box 64 x 128, 128B swizzle
-hw_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int fmt)
+// 2D 16-bit map over a [rows][cols] slice with row stride ld: box TK x box_rows, 64-byte swizzle
+hw_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int fmt, int box_rows)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
     if (!enc) return hw_fail(HW_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
     cuuint64_t strides[1] = {cuuint64_t(ld) * 2};
-    cuuint32_t box[2] = {TK, TM};
+    cuuint32_t box[2] = {TK, cuuint32_t(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, fmt == FMT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                      const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return hw_fail(HW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
     return HW_OK;
 }
@@ -463,7 +663,8 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Slices {
     void *s[3] = {nullptr, nullptr, nullptr};
-    CUtensorMap map[3];
+    CUtensorMap mapA[3];     // half of an A tile (64 rows), as the multicast loads take it
+    CUtensorMap mapB[3];     // half of a B tile (128 rows)
 };
 
 // three slice planes of a rows x ld 16-bit matrix in one buffer, plus their maps
@@ -471,67 +672,115 @@ hw_status slices_make(Slices &S, uint16_t *buf, int rows, int cols, int ld, int 
 {
     for (int i = 0; i < 3; ++i) {
         S.s[i] = buf + size_t(i) * rows * ld;
-        hw_status st = make_map(&S.map[i], S.s[i], rows, cols, ld, fmt);
+        hw_status st = make_map(&S.mapA[i], S.s[i], rows, cols, ld, fmt, TM / 2);
+        if (st == HW_OK) st = make_map(&S.mapB[i], S.s[i], rows, cols, ld, fmt, TN / 2);
         if (st != HW_OK) return st;
     }
     return HW_OK;
 }
 
-// precision modes: (format, slices, products smallest first)
+// precision modes: (format, slices); the products are the slice pairs (i, j)
+// with i + j < slices (3 for two slices, 6 for three)
 struct Mode {
-    int fmt, ns, nprod;
-    int prod[6][2];
+    int fmt, ns;
 };
 const Mode kModes[5] = {
-    {FMT_F16, 2, 3, {{1, 0}, {0, 1}, {0, 0}}},                                   // 0: default = fp16 x 2
-    {FMT_BF16, 1, 1, {{0, 0}}},                                                   // 1: bf16 x 1
-    {FMT_BF16, 2, 3, {{1, 0}, {0, 1}, {0, 0}}},                                  // 2: bf16 x 2
-    {FMT_BF16, 3, 6, {{1, 1}, {2, 0}, {0, 2}, {1, 0}, {0, 1}, {0, 0}}},          // 3: bf16 x 3
-    {FMT_F16, 2, 3, {{1, 0}, {0, 1}, {0, 0}}},                                   // 4: fp16 x 2
+    {FMT_F16, 2},    // 0: default = fp16 x 2
+    {FMT_BF16, 1},   // 1: bf16 x 1
+    {FMT_BF16, 2},   // 2: bf16 x 2
+    {FMT_BF16, 3},   // 3: bf16 x 3
+    {FMT_F16, 2},    // 4: fp16 x 2
 };
 
-void fill_mode(TcArgs &a, const Mode &md)
+// cluster tiles (P, Q) of 256 x 512 in 4 x 4 groups; with sym only those with
+// a 128 x 128 block (r, c), r <= c: row blocks 2P, 2P+1, column blocks 4Q..4Q+3
+std::vector<int2> cluster_tiles(int m, int n, bool sym)
 {
-    a.ns = md.ns;
-    a.nprod = md.nprod;
-    std::memcpy(a.prod, md.prod, sizeof a.prod);
-    a.stages = std::min(kMaxStages, kRingBytes / (2 * md.ns * kTileBytes));
-}
-
-// tiles in 8 x 8 supertile order; with sym only I <= J
-std::vector<int2> tile_list(int tm, int tn, bool sym)
-{
+    const int tp = (m + kCM * TM - 1) / (kCM * TM), tq = (n + kCN * TN - 1) / (kCN * TN);
     std::vector<int2> t;
-    const int G = 8;
-    for (int bi = 0; bi < tm; bi += G)
-        for (int bj = 0; bj < tn; bj += G)
-            for (int i = bi; i < std::min(tm, bi + G); ++i)
-                for (int j = bj; j < std::min(tn, bj + G); ++j)
-                    if (!sym || i <= j) t.push_back(make_int2(i, j));
+    const int G = 4;
+    for (int bp = 0; bp < tp; bp += G)
+        for (int bq = 0; bq < tq; bq += G)
+            for (int p = bp; p < std::min(tp, bp + G); ++p)
+                for (int q = bq; q < std::min(tq, bq + G); ++q)
+                    if (!sym || kCM * p <= 2 * kCN * q + 2 * kCN - 1) t.push_back(make_int2(p, q));
     return t;
 }
 
-hw_status launch_tc(int fmt, const Slices &A, const Slices &B, const TcArgs &a, int ntiles, cudaStream_t st)
+using TcKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
+                         const CUtensorMap, const CUtensorMap, TcArgs, int);
+
+// dynamic shared memory of a configuration: its ring, no more, so that light
+// kernels (the Taylor accumulation) can share the SM with the GEMM
+int tc_smem_bytes(int na, int nb)
 {
-    static int attr_dev[2] = {-1, -1};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (attr_dev[fmt] != dev) {
-        cudaError_t e = cudaFuncSetAttribute(fmt == FMT_BF16 ? k_tc_gemm<FMT_BF16> : k_tc_gemm<FMT_F16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_tc_gemm)");
-        attr_dev[fmt] = dev;
-    }
-    if (fmt == FMT_BF16)
-        k_tc_gemm<FMT_BF16><<<ntiles, 128, kSmemBytes, st>>>(A.map[0], A.map[1], A.map[2], B.map[0], B.map[1],
-                                                             B.map[2], a);
-    else
-        k_tc_gemm<FMT_F16><<<ntiles, 128, kSmemBytes, st>>>(A.map[0], A.map[1], A.map[2], B.map[0], B.map[1],
-                                                            B.map[2], a);
-    return hw_cuda(cudaGetLastError(), "k_tc_gemm launch");
+    const int stage = na * kATile + nb * kBTile;
+    return std::min(kMaxStages, kRingBytes / stage) * stage + kSmemSlack;
 }
 
-int ew_grid(int64_t total) { return int(std::min<int64_t>(148 * 32, (total + 255) / 256)); }
+TcKernel tc_kernel(int fmt, int na, int nb)
+{
+    if (fmt == FMT_F16) {
+        if (na == 2 && nb == 2) return k_tc_gemm<FMT_F16, 2, 2>;
+        if (na == 2 && nb == 1) return k_tc_gemm<FMT_F16, 2, 1>;
+        return nullptr;
+    }
+    if (na == 1 && nb == 1) return k_tc_gemm<FMT_BF16, 1, 1>;
+    if (na == 2 && nb == 2) return k_tc_gemm<FMT_BF16, 2, 2>;
+    if (na == 2 && nb == 1) return k_tc_gemm<FMT_BF16, 2, 1>;
+    if (na == 3 && nb == 3) return k_tc_gemm<FMT_BF16, 3, 3>;
+    if (na == 3 && nb == 1) return k_tc_gemm<FMT_BF16, 3, 1>;
+    return nullptr;
+}
+
+// A with na slices times B with nb slices (nb = na, or 1 when B is exact in one)
+hw_status launch_tc(int fmt, int na, int nb, const Slices &A, const Slices &B, const TcArgs &a, int ntiles,
+                    cudaStream_t st)
+{
+    static std::mutex mu;
+    static std::map<std::pair<TcKernel, int>, int> max_clusters;   // (kernel, device) -> clusters at once
+    TcKernel kern = tc_kernel(fmt, na, nb);
+    if (!kern) return hw_fail(HW_EINVAL, "no tensor-core kernel for %d x %d slices", na, nb);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = tc_smem_bytes(na, nb);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = max_clusters.find({kern, dev});
+        if (it != max_clusters.end()) {
+            ncl = it->second;
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(cfg.dynamicSmemBytes));
+            if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_tc_gemm)");
+            int sms = 148;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cfg.gridDim = dim3(unsigned(sms / kCluster * kCluster));
+            e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+            if (e != cudaSuccess) return hw_cuda(e, "cudaOccupancyMaxActiveClusters(k_tc_gemm)");
+            if (ncl < 1) return hw_fail(HW_EUNSUPPORTED, "no cluster of k_tc_gemm fits on this device");
+            max_clusters[{kern, dev}] = ncl;
+        }
+    }
+    // persistent: as many clusters as run at once, each walking the cluster-tile list
+    cfg.gridDim = dim3(unsigned(std::min(ntiles, ncl) * kCluster));
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A.mapA[0], A.mapA[1], A.mapA[2], B.mapB[0], B.mapB[1],
+                                       B.mapB[2], a, ntiles);
+    return hw_cuda(e, "k_tc_gemm launch");
+}
+
+int row_grid(int64_t rows) { return int(std::min<int64_t>(148 * 16, std::max<int64_t>(rows, 1))); }
 
 hw_status read_err_flag(int *d_err, cudaStream_t st)
 {
@@ -547,11 +796,25 @@ double pow2_scale(double maxabs)
     return maxabs > 0 ? std::ldexp(1.0, -int(std::ceil(std::log2(maxabs)))) : 1.0;
 }
 
+// true when x leaves nothing for a second slice: the remainder after the
+// first slice rounds to zero, exactly as k_split computes it
+bool one_slice(int fmt, double x)
+{
+    if (fmt == FMT_F16) {
+        if (std::fabs(x) > 65504.0) return false;
+        const __half s0 = __float2half_rn(float(x));
+        return __half2float(__float2half_rn(float(x - double(__half2float(s0))))) == 0.0f;
+    }
+    const __nv_bfloat16 s0 = __float2bfloat16_rn(float(x));
+    return __bfloat162float(__float2bfloat16_rn(float(x - double(__bfloat162float(s0))))) == 0.0f;
+}
+
 }  // namespace
 
 struct TcPower {
     int n = 0, ld = 0;
     Mode md;
+    int nb = 0;              // slices of Y as the B operand (1 when Y / y_unit is exact in one)
     void *mem = nullptr;     // Y slices, two Q slice buffers, tile list, error flag
     Slices Y, Q[2];
     int2 *d_tiles = nullptr;
@@ -559,6 +822,12 @@ struct TcPower {
     int cur = 0;
     int *err = nullptr;
     double sY = 1, s_prev = 1, theta = 0;
+    cudaStream_t st = nullptr;
+    // the power whose accumulation is still to do (the next GEMM's epilogue
+    // warps do it, the last one a kernel of its own)
+    double *pend_accU = nullptr;
+    double pend_coef = 0;
+    int pend_buf = -1;
 };
 
 bool tc_gemm_available()
@@ -570,10 +839,13 @@ bool tc_gemm_available()
     return major == 10 && minor == 3 && encoder() != nullptr;
 }
 
-// Y: the n x n real symmetric matrix (double) whose powers are taken; maxY its
-// largest |entry| and theta a bound on its infinity norm (host-known).
-hw_status tc_power_begin(int n, const double *Y, double maxY, double theta, int mode, cudaStream_t st,
-                         TcPower **out)
+// Y: the n x n real symmetric matrix (double) whose powers are taken; yvals
+// the magnitudes of its distinct nonzero entries and theta a bound on its
+// infinity norm (all host-known).  Y is sliced at the scale 1 / min(yvals)
+// when that makes every entry exact in one slice, else at the power of two
+// that maps max(yvals) into [1/2, 1].
+hw_status tc_power_begin(int n, const double *Y, const double *yvals, int nyvals, double theta, int mode,
+                         cudaStream_t st, TcPower **out)
 {
     *out = nullptr;
     if (mode < 0 || mode > 4) return hw_fail(HW_EINVAL, "gemm precision mode %d", mode);
@@ -582,16 +854,24 @@ hw_status tc_power_begin(int n, const double *Y, double maxY, double theta, int 
     p->n = n;
     p->md = kModes[mode];
     p->ld = round_up(n, 64);
-    p->sY = pow2_scale(maxY);
+    double ymax = 0.0, ymin = 0.0;
+    for (int i = 0; i < nyvals; ++i) {
+        ymax = std::max(ymax, yvals[i]);
+        ymin = (ymin == 0.0) ? yvals[i] : std::min(ymin, yvals[i]);
+    }
+    bool exact = ymin > 0.0;
+    for (int i = 0; i < nyvals && exact; ++i) exact = one_slice(p->md.fmt, yvals[i] * (1.0 / ymin));
+    p->sY = exact ? 1.0 / ymin : pow2_scale(ymax);
+    p->nb = exact ? 1 : p->md.ns;
     p->s_prev = p->sY;
     p->theta = theta;
-    const int tm = (n + TM - 1) / TM;
-    const std::vector<int2> tiles = tile_list(tm, tm, true);
+    p->st = st;
+    const std::vector<int2> tiles = cluster_tiles(n, n, true);
     p->ntiles = int(tiles.size());
     const size_t one = size_t(n) * p->ld * 3;     // 16-bit elements per slice buffer (3 planes)
     const size_t tiles_b = sizeof(int2) * tiles.size();
     const size_t bytes = 3 * one * 2 + tiles_b + 256;
-    hw_status s = hw_cuda(cudaMallocAsync(&p->mem, bytes, st), "cudaMallocAsync(tensor-core slices)");
+    hw_status s = hw_cuda(hw_malloc_async(&p->mem, bytes, st), "scratch allocation (tensor-core slices)");
     if (s != HW_OK) { delete p; return s; }
     uint16_t *b = static_cast<uint16_t *>(p->mem);
     p->d_tiles = reinterpret_cast<int2 *>(b + 3 * one);
@@ -606,12 +886,11 @@ hw_status tc_power_begin(int n, const double *Y, double maxY, double theta, int 
         delete p;
         return s;
     }
-    const int64_t nn = int64_t(n) * n;
     if (fmt == FMT_BF16)
-        k_split<FMT_BF16, double><<<ew_grid(nn), 256, 0, st>>>(Y, n, n, n, p->md.ns, p->ld, nullptr, p->sY,
+        k_split<FMT_BF16, double><<<row_grid(n), 256, 0, st>>>(Y, n, n, n, p->md.ns, p->ld, nullptr, p->sY,
                                                                p->Y.s[0], p->Y.s[1], p->Y.s[2]);
     else
-        k_split<FMT_F16, double><<<ew_grid(nn), 256, 0, st>>>(Y, n, n, n, p->md.ns, p->ld, nullptr, p->sY,
+        k_split<FMT_F16, double><<<row_grid(n), 256, 0, st>>>(Y, n, n, n, p->md.ns, p->ld, nullptr, p->sY,
                                                               p->Y.s[0], p->Y.s[1], p->Y.s[2]);
     s = hw_cuda(cudaGetLastError(), "k_split launch");
     if (s != HW_OK) { cudaFreeAsync(p->mem, st); delete p; return s; }
@@ -620,9 +899,25 @@ hw_status tc_power_begin(int n, const double *Y, double maxY, double theta, int 
     return HW_OK;
 }
 
+hw_status launch_acc(const TcPower *p, const Slices &Q, double coef, double *accU)
+{
+    const int grid = std::min(p->n, 4 * 148);
+    if (p->md.fmt == FMT_F16)
+        k_taylor_acc<FMT_F16, 2><<<grid, 256, 0, p->st>>>(p->n, Q.s[0], Q.s[1], Q.s[2], p->ld, coef, accU);
+    else if (p->md.ns == 1)
+        k_taylor_acc<FMT_BF16, 1><<<grid, 256, 0, p->st>>>(p->n, Q.s[0], Q.s[1], Q.s[2], p->ld, coef, accU);
+    else if (p->md.ns == 2)
+        k_taylor_acc<FMT_BF16, 2><<<grid, 256, 0, p->st>>>(p->n, Q.s[0], Q.s[1], Q.s[2], p->ld, coef, accU);
+    else
+        k_taylor_acc<FMT_BF16, 3><<<grid, 256, 0, p->st>>>(p->n, Q.s[0], Q.s[1], Q.s[2], p->ld, coef, accU);
+    return hw_cuda(cudaGetLastError(), "k_taylor_acc launch");
+}
+
 // Q_k = Q_{k-1} Y / k (Y symmetric, so Y is its own K-major B operand; every
-// Q_k is symmetric, so only I <= J tiles run); accU += sign * Q_k in double.
-hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream_t st)
+// Q_k is symmetric, so only the upper triangle's tiles run).  The same launch
+// adds sign_{k-1} Q_{k-1} (its A operand) to accU_{k-1} in double below the
+// diagonal; Q_k's own term is added by the next step or by tc_power_end.
+hw_status tc_power_step(TcPower *p, int k, double *accU, double sign)
 {
     const Slices &A = (p->cur < 0) ? p->Y : p->Q[p->cur];
     const int nxt = (p->cur == 0) ? 1 : 0;
@@ -633,7 +928,6 @@ hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream
     TcArgs a{};
     a.tiles = p->d_tiles;
     a.m = a.n = a.k = p->n;
-    fill_mode(a, p->md);
     a.epi = EPI_TAYLOR;
     a.sym = 1;
     a.scale = float(1.0 / (double(k) * p->s_prev * p->sY));
@@ -641,11 +935,17 @@ hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream
     for (int i = 0; i < 3; ++i) a.Q[i] = p->Q[nxt].s[i];
     a.ldq = p->ld;
     a.qscale = float(s_k);
-    a.accU = accU;
-    a.ldu = p->n;
-    a.sign = sign;
     a.err = p->err;
-    hw_status s = launch_tc(p->md.fmt, A, p->Y, a, p->ntiles, st);
+    if (p->pend_accU) {
+        // the pending power is Q_{k-1}, this GEMM's A operand
+        for (int i = 0; i < 3; ++i) a.accQ[i] = p->Q[p->pend_buf].s[i];
+        a.acc_coef = p->pend_coef;
+        a.accU = p->pend_accU;
+    }
+    hw_status s = launch_tc(p->md.fmt, p->md.ns, p->nb, A, p->Y, a, p->ntiles, p->st);
+    p->pend_accU = accU;
+    p->pend_coef = sign / s_k;
+    p->pend_buf = nxt;
     p->cur = nxt;
     p->s_prev = s_k;
     return s;
@@ -654,7 +954,9 @@ hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream
 hw_status tc_power_end(TcPower *p, cudaStream_t st, bool check)
 {
     if (!p) return HW_OK;
-    hw_status s = check ? read_err_flag(p->err, st) : HW_OK;
+    hw_status s = HW_OK;
+    if (check && p->pend_accU) s = launch_acc(p, p->Q[p->pend_buf], p->pend_coef, p->pend_accU);
+    if (s == HW_OK && check) s = read_err_flag(p->err, st);
     cudaFreeAsync(p->mem, st);
     delete p;
     return s;
@@ -674,10 +976,10 @@ extern "C" hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A,
     const Mode &md = kModes[mode];
     const int ld = round_up(int(k), 64);
     const size_t sa = size_t(m) * ld * 3, sb = size_t(n) * ld * 3;
-    const std::vector<int2> tiles = tile_list(int((m + TM - 1) / TM), int((n + TN - 1) / TN), false);
+    const std::vector<int2> tiles = cluster_tiles(int(m), int(n), false);
     const size_t tiles_b = sizeof(int2) * tiles.size();
     void *mem = nullptr;
-    hw_status s = hw_cuda(cudaMallocAsync(&mem, (sa + sb) * 2 + tiles_b + 256, st), "cudaMallocAsync(slices)");
+    hw_status s = hw_cuda(hw_malloc_async(&mem, (sa + sb) * 2 + tiles_b + 256, st), "scratch allocation (slices)");
     if (s != HW_OK) return s;
     uint16_t *b = static_cast<uint16_t *>(mem);
     int2 *d_tiles = reinterpret_cast<int2 *>(b + sa + sb);
@@ -693,22 +995,22 @@ extern "C" hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A,
         const float *dsA = nullptr, *dsB = nullptr, *dinv = nullptr;
         if (md.fmt == FMT_F16) {
             // fp16 slices are taken of the operand scaled to a maximum in [1/2, 1]
-            k_absmax<float><<<ew_grid(m * k), 256, 0, st>>>(A, int(m), int(k), int(k), d_max);
-            k_absmax<float><<<ew_grid(n * k), 256, 0, st>>>(B, int(n), int(k), int(k), d_max + 1);
+            k_absmax<float><<<row_grid(m), 256, 0, st>>>(A, int(m), int(k), int(k), d_max);
+            k_absmax<float><<<row_grid(n), 256, 0, st>>>(B, int(n), int(k), int(k), d_max + 1);
             k_scales<<<1, 1, 0, st>>>(d_max, d_scale);
             dsA = d_scale;
             dsB = d_scale + 1;
             dinv = d_scale + 2;
         }
         if (md.fmt == FMT_BF16) {
-            k_split<FMT_BF16, float><<<ew_grid(m * k), 256, 0, st>>>(A, int(m), int(k), int(k), md.ns, ld, dsA, 1.0,
+            k_split<FMT_BF16, float><<<row_grid(m), 256, 0, st>>>(A, int(m), int(k), int(k), md.ns, ld, dsA, 1.0,
                                                                      SA.s[0], SA.s[1], SA.s[2]);
-            k_split<FMT_BF16, float><<<ew_grid(n * k), 256, 0, st>>>(B, int(n), int(k), int(k), md.ns, ld, dsB, 1.0,
+            k_split<FMT_BF16, float><<<row_grid(n), 256, 0, st>>>(B, int(n), int(k), int(k), md.ns, ld, dsB, 1.0,
                                                                      SB.s[0], SB.s[1], SB.s[2]);
         } else {
-            k_split<FMT_F16, float><<<ew_grid(m * k), 256, 0, st>>>(A, int(m), int(k), int(k), md.ns, ld, dsA, 1.0,
+            k_split<FMT_F16, float><<<row_grid(m), 256, 0, st>>>(A, int(m), int(k), int(k), md.ns, ld, dsA, 1.0,
                                                                     SA.s[0], SA.s[1], SA.s[2]);
-            k_split<FMT_F16, float><<<ew_grid(n * k), 256, 0, st>>>(B, int(n), int(k), int(k), md.ns, ld, dsB, 1.0,
+            k_split<FMT_F16, float><<<row_grid(n), 256, 0, st>>>(B, int(n), int(k), int(k), md.ns, ld, dsB, 1.0,
                                                                     SB.s[0], SB.s[1], SB.s[2]);
         }
         TcArgs a{};
@@ -716,7 +1018,6 @@ extern "C" hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A,
         a.m = int(m);
         a.n = int(n);
         a.k = int(k);
-        fill_mode(a, md);
         a.epi = EPI_STORE;
         a.sym = 0;
         a.scale = 1.0f;
@@ -725,7 +1026,7 @@ extern "C" hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A,
         a.ldc = int(n);
         a.err = err;
         s = hw_cuda(cudaGetLastError(), "k_split launch");
-        if (s == HW_OK) s = launch_tc(md.fmt, SA, SB, a, int(tiles.size()), st);
+        if (s == HW_OK) s = launch_tc(md.fmt, md.ns, md.ns, SA, SB, a, int(tiles.size()), st);
         if (s == HW_OK) s = read_err_flag(err, st);
     }
     cudaFreeAsync(mem, st);

@@ -40,6 +40,8 @@ struct hw_graph {
 // ---- errors (api.cpp)
 hw_status hw_fail(hw_status s, const char *fmt, ...);
 hw_status hw_cuda(cudaError_t e, const char *what);
+// stream-ordered scratch from the library's per-device pool (free with cudaFreeAsync)
+cudaError_t hw_malloc_async(void **p, size_t bytes, cudaStream_t st);
 void hw_clear_error();
 
 // ---- host graph construction (graph.cpp)
@@ -88,9 +90,9 @@ void free_marked(MarkedList &m, cudaStream_t st);
 // split-bf16 operands, accU += sign Q_k in double
 struct TcPower;
 bool tc_gemm_available();
-hw_status tc_power_begin(int n, const double *Y, double maxY, double theta, int mode, cudaStream_t st,
-                         TcPower **out);
-hw_status tc_power_step(TcPower *p, int k, double *accU, double sign, cudaStream_t st);
+hw_status tc_power_begin(int n, const double *Y, const double *yvals, int nyvals, double theta, int mode,
+                         cudaStream_t st, TcPower **out);
+hw_status tc_power_step(TcPower *p, int k, double *accU, double sign);
 hw_status tc_power_end(TcPower *p, cudaStream_t st, bool check);
 
 // Programmatic dependent launch: consecutive steps of a loop overlap the next

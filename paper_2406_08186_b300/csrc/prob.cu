@@ -152,8 +152,8 @@ hw_status launch_probability(const hw_graph *g, int64_t n, hw_dtype dt, int batc
         const int64_t rows = g ? g->num_arcs : n;
         if (rows == 0) return hw_cuda(cudaMemsetAsync(norm, 0, sizeof(double) * batch, st), "memset norm");
         void *partial = nullptr;
-        if ((s = hw_cuda(cudaMallocAsync(&partial, norm_scratch_bytes(rows, batch), st),
-                         "cudaMallocAsync(norm partials)")) != HW_OK)
+        if ((s = hw_cuda(hw_malloc_async(&partial, norm_scratch_bytes(rows, batch), st),
+                         "scratch allocation (norm partials)")) != HW_OK)
             return s;
         s = launch_norm(dt, batch, psi, rows, static_cast<double *>(partial), norm, st);
         cudaFreeAsync(partial, st);
@@ -168,7 +168,7 @@ hw_status launch_probability(const hw_graph *g, int64_t n, hw_dtype dt, int batc
 // and platforms where the stream-ordered allocator is unavailable
 // (cudaDevAttrMemoryPoolsSupported == 0, as under some virtualised or MPS
 // setups).  The norm's per-CTA partials live in this file-scope device
-// array instead of coming from cudaMallocAsync.  Every device that loads the
+// array instead of coming from the scratch pool.  Every device that loads the
 // library holds the array until the process exits.
 namespace {
 

@@ -84,6 +84,28 @@ def test_expm_c64_close(hw):
     G.free()
 
 
+@pytest.mark.parametrize("name,g,gamma,marked,t", [
+    # 1/gamma = 3 is exact in one fp16 slice: Y keeps one slice (two products)
+    ("reg3_exact", synth.random_regular(778, 3, seed=4), 1 / 3, [5, 700], 0.4),
+    # gamma = 0.3: Y needs two slices (three products)
+    ("er_two_slices", synth.erdos_renyi(1000, 0.006, seed=6), 0.3, [990], 0.25),
+])
+def test_expm_c64_ragged_multi_tile(hw, name, g, gamma, marked, t):
+    # n not a multiple of the 128 x 256 tiles, several cluster tiles and
+    # mirrored blocks; columns checked against the oracle's action
+    n = g[0]
+    G, U = gpu_expm(hw, g, gamma, marked, t, dt=1)
+    ar = oracle.Arcs(*g)
+    cols = np.array([0, 1, 130, 257, n // 2, n - 2, n - 1])
+    ref = oracle.ctqw_columns(ar, gamma, t, cols, marked=marked)
+    got = U.cpu().numpy()[:, cols]
+    assert np.max(np.abs(got - ref)) < 2e-6
+    # rows equal columns: U is symmetric because H is
+    Uh = U.cpu().numpy()
+    assert np.max(np.abs(Uh - Uh.T)) < 2e-6
+    G.free()
+
+
 def test_expm_hypercube_closed_form(hw):
     # no marks: U[u, v] = cos(gamma t)^(k-h) (i sin(gamma t))^h, h = Hamming distance
     k, gamma, t = 8, 0.25, 3.0
