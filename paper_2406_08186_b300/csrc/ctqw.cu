@@ -18,6 +18,7 @@
 #include <cmath>
 #include <vector>
 
+#include "fpconv.cuh"
 #include "internal.h"
 
 namespace {
@@ -120,6 +121,16 @@ __global__ void k_mark_diag(MarkedList mk, int n, double diag, double *__restric
     Y[int64_t(m) * n + m] += diag;
 }
 
+// Re U = I, Im U = 0 on and below the diagonal (the rest is never read)
+__global__ void k_init_lower(int n, double *__restrict__ re, double *__restrict__ im)
+{
+    for (int i = blockIdx.x; i < n; i += gridDim.x)
+        for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+            re[int64_t(i) * n + j] = (i == j) ? 1.0 : 0.0;
+            im[int64_t(i) * n + j] = 0.0;
+        }
+}
+
 // Re U = I, Im U = -Y (the k = 0 and k = 1 terms); Q_1 = Y.
 __global__ void k_taylor_init(int n, const double *__restrict__ Y, double *__restrict__ re,
                               double *__restrict__ im)
@@ -155,6 +166,12 @@ __global__ void k_sym_add(int n, const double *__restrict__ X, double *__restric
     }
 }
 
+__device__ __forceinline__ void pack1(double2 &u, double re, double im) { u = make_double2(re, im); }
+__device__ __forceinline__ void pack1(float2 &u, double re, double im)
+{
+    u = make_float2(fpconv::f64_to_f32_rn(re), fpconv::f64_to_f32_rn(im));
+}
+
 template <typename V>
 __global__ void k_pack_u(int64_t total, const double *__restrict__ re, const double *__restrict__ im,
                          V *__restrict__ U)
@@ -162,13 +179,13 @@ __global__ void k_pack_u(int64_t total, const double *__restrict__ re, const dou
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         V u;
-        u.x = decltype(u.x)(re[e]);
-        u.y = decltype(u.y)(im[e]);
+        pack1(u, re[e], im[e]);
         U[e] = u;
     }
 }
 
 int ew_grid(int64_t total) { return int(std::min<int64_t>(148 * 32, (total + 255) / 256)); }
+int row_grid(int64_t rows) { return int(std::min<int64_t>(148 * 16, std::max<int64_t>(rows, 1))); }
 
 // ------------------------------------------------------------ apply U
 // y[i][b] = sum_j U[i][j] x[j][b].  One warp per row; lanes stride the
@@ -519,23 +536,24 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     const int64_t nn = int64_t(n) * n;
     const size_t bytes = sizeof(double) * nn;
 
-    DevBuf Y(st), Q(st), Qn(st), Re(st), Im(st);
-    if ((s = Y.get(bytes, "scratch allocation (Y)")) != HW_OK || (s = Q.get(bytes, "scratch allocation (Q)")) != HW_OK ||
-        (s = Qn.get(bytes, "scratch allocation (Q)")) != HW_OK || (s = Re.get(bytes, "scratch allocation (ReU)")) != HW_OK ||
-        (s = Im.get(bytes, "scratch allocation (ImU)")) != HW_OK)
-        return s;
-
-    // T1: Y = tau H
-    if ((s = hw_cuda(cudaMemsetAsync(Y.p, 0, bytes, st), "memset Y")) != HW_OK) return s;
-    k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, n, -gamma * tau, Y.as<double>());
-    if (mk.n) k_mark_diag<<<(mk.n + 127) / 128, 128, 0, st>>>(mk, n, -tau, Y.as<double>());
-    k_taylor_init<<<ew_grid(nn), 256, 0, st>>>(n, Y.as<double>(), Re.as<double>(), Im.as<double>());
-    if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;
-
-    // T2 + T3: Q_k = Q_{k-1} Y / k, accumulated into Re/Im U with the sign of (-i)^k
     const bool use_tc = (dt == HW_C64) && tc_gemm_available();
+    DevBuf Y(st), Q(st), Qn(st), Re(st), Im(st);
+    if ((s = Re.get(bytes, "scratch allocation (ReU)")) != HW_OK || (s = Im.get(bytes, "scratch allocation (ImU)")) != HW_OK)
+        return s;
+    if (!use_tc || sq > 0) {
+        // the FP64 powers and the squarings need two n x n work matrices, the FP64 powers also Y
+        if ((s = Q.get(bytes, "scratch allocation (Q)")) != HW_OK || (s = Qn.get(bytes, "scratch allocation (Q)")) != HW_OK)
+            return s;
+    }
+    bool packed = false;
     if (use_tc) {
-        // complex64 path: powers on the tensor cores from split-bf16 operands
+        // complex64 path: powers on the tensor cores from 16-bit slices; the
+        // series is summed below the diagonal only.
+        // T1 + the k = 0, 1 terms: Re U = I, Im U = -Y = gamma tau A + tau sum_m |m><m|
+        k_init_lower<<<row_grid(n), 256, 0, st>>>(n, Re.as<double>(), Im.as<double>());
+        k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, n, gamma * tau, Im.as<double>());
+        if (mk.n) k_mark_diag<<<(mk.n + 127) / 128, 128, 0, st>>>(mk, n, tau, Im.as<double>());
+        if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;
         TcPower *tp = nullptr;
         // host-known magnitudes of Y's entries (edge weight gamma tau, marked
         // diagonal tau) and ||Y||_inf
@@ -551,19 +569,36 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
                 theta = std::max(theta, (std::fabs(gamma) * (g->h_row_ptr[v + 1] - g->h_row_ptr[v]) +
                                          (is_m[v] ? 1.0 : 0.0)) * std::fabs(tau));
         }
-        if ((s = tc_power_begin(n, Y.as<double>(), yvals, nyvals, theta, gmode, st, &tp)) != HW_OK) return s;
+        const SymSparse ys{g->d_row_ptr, g->d_head, n, -gamma * tau, mk, -tau};
+        if ((s = tc_power_begin(ys, yvals, nyvals, theta, gmode, st, &tp)) != HW_OK) return s;
         for (int k = 2; k <= m_deg && s == HW_OK; ++k) {
             double *accU = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
             const double sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
             s = tc_power_step(tp, k, accU, sign);
         }
-        hw_status e = tc_power_end(tp, st, s == HW_OK);
-        if (s == HW_OK) s = e;
-        if (s != HW_OK) return s;
-        k_mirror_lower<<<ew_grid(nn), 256, 0, st>>>(n, Re.as<double>());
-        k_mirror_lower<<<ew_grid(nn), 256, 0, st>>>(n, Im.as<double>());
-        if ((s = hw_cuda(cudaGetLastError(), "mirror")) != HW_OK) return s;
+        if (s != HW_OK) {
+            tc_power_end(tp, st, false);
+            return s;
+        }
+        if (sq == 0) {
+            // last term, mirror and complex64 packing in one pass
+            if ((s = tc_power_finish_c64(tp, Re.as<double>(), Im.as<double>(), U_out, st)) != HW_OK) return s;
+            packed = true;
+        } else {
+            if ((s = tc_power_end(tp, st, true)) != HW_OK) return s;
+            k_mirror_lower<<<ew_grid(nn), 256, 0, st>>>(n, Re.as<double>());
+            k_mirror_lower<<<ew_grid(nn), 256, 0, st>>>(n, Im.as<double>());
+            if ((s = hw_cuda(cudaGetLastError(), "mirror")) != HW_OK) return s;
+        }
     } else {
+        // T1: Y = tau H
+        if ((s = Y.get(bytes, "scratch allocation (Y)")) != HW_OK) return s;
+        if ((s = hw_cuda(cudaMemsetAsync(Y.p, 0, bytes, st), "memset Y")) != HW_OK) return s;
+        k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, n, -gamma * tau, Y.as<double>());
+        if (mk.n) k_mark_diag<<<(mk.n + 127) / 128, 128, 0, st>>>(mk, n, -tau, Y.as<double>());
+        k_taylor_init<<<ew_grid(nn), 256, 0, st>>>(n, Y.as<double>(), Re.as<double>(), Im.as<double>());
+        if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;
+        // T2 + T3: Q_k = Q_{k-1} Y / k, accumulated into Re/Im U with the sign of (-i)^k
         double *Qk = Y.as<double>();   // Q_1 = Y
         double *dst = Q.as<double>();
         for (int k = 2; k <= m_deg; ++k) {
@@ -599,6 +634,7 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
         if ((s = hw_cuda(cudaGetLastError(), "squaring")) != HW_OK) return s;
     }
 
+    if (packed) return HW_OK;
     if (dt == HW_C128) k_pack_u<double2><<<ew_grid(nn), 256, 0, st>>>(nn, Re.as<double>(), Im.as<double>(), static_cast<double2 *>(U_out));
     else k_pack_u<float2><<<ew_grid(nn), 256, 0, st>>>(nn, Re.as<double>(), Im.as<double>(), static_cast<float2 *>(U_out));
     return hw_cuda(cudaGetLastError(), "pack U");

@@ -53,6 +53,7 @@
 #include <mutex>
 #include <vector>
 
+#include "fpconv.cuh"
 #include "internal.h"
 
 namespace {
@@ -65,7 +66,7 @@ constexpr int kBTile = TN * TK * 2;                       // 16 KB per B slice
 constexpr int kRingBytes = 216 * 1024;                    // shared-memory ring
 constexpr int kMaxStages = 8;
 constexpr int kSmemSlack = 2048;                          // alignment of the ring base + margin
-constexpr int kAccWarps = 8;                              // warps that only help with the accumulation
+constexpr int kAccWarps = 8;                              // warps 6..13: accumulation (6..9 also epilogues)
 constexpr int kThreads = 192 + 32 * kAccWarps;
 constexpr int kTmemCols = 2 * TN;                         // two accumulators
 constexpr uint64_t kWaitLimitNs = 2000000000ull;          // bounded mbarrier waits (2 s)
@@ -277,7 +278,7 @@ __device__ __forceinline__ void acc_rows(int n, const void *q0, const void *q1, 
 #pragma unroll
             for (int t = 0; t < U; ++t) {
                 const int j = j0 + t * nt;
-                if (j <= i) u[j] = fma(coef, double(q[t]), x[t]);
+                if (j <= i) u[j] = fma(coef, fpconv::f32_to_f64(q[t]), x[t]);
             }
         }
     }
@@ -290,23 +291,25 @@ __global__ void __launch_bounds__(256) k_taylor_acc(int n, const void *q0, const
     acc_rows<FMT, NA>(n, q0, q1, q2, ldq, coef, accU, blockIdx.x, gridDim.x, threadIdx.x, blockDim.x);
 }
 
-// Epilogue of one 128 x 256 CTA tile whose accumulator is at TMEM column tacc;
+// Epilogue of columns [cb, ce) of one 128 x 256 CTA tile whose accumulator is
+// at TMEM column tacc, by a warp of lane quadrant quad (tile rows 32 quad..);
 // Q is written as NA slices.
 template <int FMT, int NA>
-__device__ __forceinline__ void epilogue_tile(const TcArgs &a, int row0, int col0, uint32_t tacc, int warp, int lane)
+__device__ __forceinline__ void epilogue_tile(const TcArgs &a, int row0, int col0, uint32_t tacc, int quad, int lane,
+                                              int cb, int ce)
 {
     using S = Sl<FMT>;
     constexpr int na = NA;
     const float mult = a.scale * (a.dscale ? *a.dscale : 1.0f);
-    const int row = row0 + warp * 32 + lane;    // tile row held by this thread
+    const int row = row0 + quad * 32 + lane;    // tile row held by this thread
     const int rblk = row0 / 128;
     const bool c_vec = a.C && (a.ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(a.C) % 16 == 0);
-    for (int c0 = 0; c0 < TN; c0 += 16) {
+    for (int c0 = cb; c0 < ce; c0 += 16) {
         const int col0c = col0 + c0;
         const int cblk = col0c / 128;
         if (a.sym && cblk < rblk) continue;     // below the diagonal: written as the mirror of (cblk, rblk)
         uint32_t r[16];
-        tmem_ld16(tacc + (uint32_t(warp * 32) << 16) + uint32_t(c0), r);
+        tmem_ld16(tacc + (uint32_t(quad * 32) << 16) + uint32_t(c0), r);
         float v[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]) * mult;
@@ -432,7 +435,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&bar_tfull[b]), 1);
-            mbar_init(smem_u32(&bar_tempty[b]), 4);  // one arrival per epilogue warp
+            mbar_init(smem_u32(&bar_tempty[b]), 8);  // one arrival per epilogue warp
         }
         timed_out = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -525,21 +528,20 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
                 mma_commit(smem_u32(&bar_tfull[b]));
             }
         }
-    } else if (warp >= 6) {
-        // accumulation-only warps, see below
-        if (a.accU)
-            acc_rows<FMT, NA>(a.n, a.accQ[0], a.accQ[1], a.accQ[2], a.ldq, a.acc_coef, a.accU, int(blockIdx.x),
-                              int(gridDim.x), 128 + int(threadIdx.x) - 192, 128 + 32 * kAccWarps);
     } else {
-        // epilogue warps 0-3 (with warps 6..): first the previous power's
-        // accumulation (its slices are this GEMM's A operand, so mostly L2
-        // hits), rows spread over all CTAs, while the tensor cores work on the
-        // first tile
+        // warps 0-3 and 6-13: first the previous power's accumulation (its
+        // slices are this GEMM's A operand, so mostly L2 hits), rows spread
+        // over all CTAs, while the tensor cores work on the first tile; then
+        // warps 0-3 and 6-9 run the epilogues, warp w on TMEM lane quadrant
+        // w % 4 and half of the tile's columns
         if (a.accU)
             acc_rows<FMT, NA>(a.n, a.accQ[0], a.accQ[1], a.accQ[2], a.ldq, a.acc_coef, a.accU, int(blockIdx.x),
-                              int(gridDim.x), int(threadIdx.x), 128 + 32 * kAccWarps);
+                              int(gridDim.x), warp < 4 ? int(threadIdx.x) : int(threadIdx.x) - 64,
+                              128 + 32 * kAccWarps);
+        const bool epi = warp < 10;
+        const int quad = warp & 3, cb = (warp < 4) ? 0 : TN / 2;
         uint32_t li = 0;
-        for (int t = cid; t < ntiles; t += ncl, ++li) {
+        for (int t = cid; t < ntiles && epi; t += ncl, ++li) {
             const int b = int(li & 1u);
             if (!mbar_wait(smem_u32(&bar_tfull[b]), (li >> 1) & 1u)) {
                 *tmo = 1;
@@ -548,7 +550,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int2 ct = a.tiles[t];
             epilogue_tile<FMT, NA>(a, ct.x * kCM * TM + ci * TM, ct.y * kCN * TN + cj * TN, tmem + uint32_t(b * TN),
-                                   warp, lane);
+                                   quad, lane, cb, cb + TN / 2);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0)
@@ -624,6 +626,97 @@ __global__ void k_split(const T *__restrict__ x, int rows, int cols, int ldx, in
                 if (ns > 2) o2[c] = Sl<FMT>::from(float(r1 - T(Sl<FMT>::to(a1))));
             }
         }
+    }
+}
+
+// Slices of the sparse Y * scale written straight from the graph (the planes
+// are zeroed first): the same arithmetic as k_split applies to each nonzero.
+template <int FMT>
+__device__ __forceinline__ void put_slices(double xs, int ns, int64_t at, void *s0, void *s1, void *s2)
+{
+    using ST = typename Sl<FMT>::T;
+    const ST a0 = Sl<FMT>::from(float(xs));
+    static_cast<ST *>(s0)[at] = a0;
+    if (ns > 1) {
+        const double r1 = xs - double(Sl<FMT>::to(a0));
+        const ST a1 = Sl<FMT>::from(float(r1));
+        static_cast<ST *>(s1)[at] = a1;
+        if (ns > 2) static_cast<ST *>(s2)[at] = Sl<FMT>::from(float(r1 - double(Sl<FMT>::to(a1))));
+    }
+}
+
+template <int FMT>
+__global__ void k_scatter_slices(SymSparse Y, double sc, int ns, int ld, void *s0, void *s1, void *s2)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < Y.n) {
+        const double xs = Y.off * sc;
+        for (int a = Y.row_ptr[v]; a < Y.row_ptr[v + 1]; ++a)
+            put_slices<FMT>(xs, ns, int64_t(v) * ld + Y.col[a], s0, s1, s2);
+    }
+    if (v < Y.mk.n) {
+        const int m = Y.mk.dev ? Y.mk.dev[v] : Y.mk.inl[v];
+        put_slices<FMT>(Y.diag * sc, ns, int64_t(m) * ld + m, s0, s1, s2);
+    }
+}
+
+// U[i][j] = (Re + i Im)[max(i,j)][min(i,j)] (+ coef * Q[i][j] on Re or Im: the
+// last Taylor power, given by its slices) rounded to complex64.  A block takes
+// a 32 x 32 tile (bi, bj) on or below the diagonal, reads it once (rows of Re,
+// Im and Q into shared memory) and writes both U tiles (bi, bj) and (bj, bi),
+// the second from the transposed shared copy, so every global access runs
+// along a row and every element is read once.
+template <int FMT, int NA>
+__global__ void __launch_bounds__(256) k_finish_c64(int n, const double *__restrict__ re,
+                                                    const double *__restrict__ im, const void *q0, const void *q1,
+                                                    const void *q2, int ldq, double coef, int last_im,
+                                                    float2 *__restrict__ U)
+{
+    using ST = typename Sl<FMT>::T;
+    __shared__ double tr[32][33], ti[32][33];
+    __shared__ float tq[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bj > bi) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int gi = bi * 32 + r, gj = bj * 32 + tx;
+        if (gi < n && gj < n && gj <= gi) {
+            tr[r][tx] = re[int64_t(gi) * n + gj];
+            ti[r][tx] = im[int64_t(gi) * n + gj];
+            if (q0) {
+                const int64_t at = int64_t(gi) * ldq + gj;
+                float q = Sl<FMT>::to(static_cast<const ST *>(q0)[at]);
+                if (NA > 1) q += Sl<FMT>::to(static_cast<const ST *>(q1)[at]);
+                if (NA > 2) q += Sl<FMT>::to(static_cast<const ST *>(q2)[at]);
+                tq[r][tx] = q;
+            }
+        }
+    }
+    __syncthreads();
+    // the tile itself (on the diagonal, elements above it come from their mirror)
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bi * 32 + r, j = bj * 32 + tx;
+        if (i >= n || j >= n) continue;
+        const bool flip = (bi == bj && tx > r);
+        const int lr = flip ? tx : r, lc = flip ? r : tx;
+        double x = tr[lr][lc], y = ti[lr][lc];
+        if (q0) {
+            if (last_im) y = fma(coef, fpconv::f32_to_f64(tq[lr][lc]), y);
+            else x = fma(coef, fpconv::f32_to_f64(tq[lr][lc]), x);
+        }
+        U[int64_t(i) * n + j] = make_float2(fpconv::f64_to_f32_rn(x), fpconv::f64_to_f32_rn(y));
+    }
+    if (bi == bj) return;
+    // the mirror tile (bj, bi): element (bj*32 + r, bi*32 + c) = tile element (c, r)
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bj * 32 + r, j = bi * 32 + tx;
+        if (i >= n || j >= n) continue;
+        double x = tr[tx][r], y = ti[tx][r];
+        if (q0) {
+            if (last_im) y = fma(coef, fpconv::f32_to_f64(tq[tx][r]), y);
+            else x = fma(coef, fpconv::f32_to_f64(tq[tx][r]), x);
+        }
+        U[int64_t(i) * n + j] = make_float2(fpconv::f64_to_f32_rn(x), fpconv::f64_to_f32_rn(y));
     }
 }
 
@@ -844,9 +937,10 @@ bool tc_gemm_available()
 // infinity norm (all host-known).  Y is sliced at the scale 1 / min(yvals)
 // when that makes every entry exact in one slice, else at the power of two
 // that maps max(yvals) into [1/2, 1].
-hw_status tc_power_begin(int n, const double *Y, const double *yvals, int nyvals, double theta, int mode,
+hw_status tc_power_begin(const SymSparse &Y, const double *yvals, int nyvals, double theta, int mode,
                          cudaStream_t st, TcPower **out)
 {
+    const int n = Y.n;
     *out = nullptr;
     if (mode < 0 || mode > 4) return hw_fail(HW_EINVAL, "gemm precision mode %d", mode);
     TcPower *p = new (std::nothrow) TcPower;
@@ -886,13 +980,16 @@ hw_status tc_power_begin(int n, const double *Y, const double *yvals, int nyvals
         delete p;
         return s;
     }
-    if (fmt == FMT_BF16)
-        k_split<FMT_BF16, double><<<row_grid(n), 256, 0, st>>>(Y, n, n, n, p->md.ns, p->ld, nullptr, p->sY,
-                                                               p->Y.s[0], p->Y.s[1], p->Y.s[2]);
-    else
-        k_split<FMT_F16, double><<<row_grid(n), 256, 0, st>>>(Y, n, n, n, p->md.ns, p->ld, nullptr, p->sY,
-                                                              p->Y.s[0], p->Y.s[1], p->Y.s[2]);
-    s = hw_cuda(cudaGetLastError(), "k_split launch");
+    // Y's slices: zero planes, then the nonzeros straight from the graph
+    s = hw_cuda(cudaMemsetAsync(p->Y.s[0], 0, one * 2, st), "memset Y slices");
+    if (s == HW_OK) {
+        const int grid = (std::max(n, Y.mk.n) + 255) / 256;
+        if (fmt == FMT_BF16)
+            k_scatter_slices<FMT_BF16><<<grid, 256, 0, st>>>(Y, p->sY, p->md.ns, p->ld, p->Y.s[0], p->Y.s[1], p->Y.s[2]);
+        else
+            k_scatter_slices<FMT_F16><<<grid, 256, 0, st>>>(Y, p->sY, p->md.ns, p->ld, p->Y.s[0], p->Y.s[1], p->Y.s[2]);
+        s = hw_cuda(cudaGetLastError(), "k_scatter_slices launch");
+    }
     if (s != HW_OK) { cudaFreeAsync(p->mem, st); delete p; return s; }
     p->cur = -1;   // Q_1 = Y: the first step reads the Y slices as A
     *out = p;
@@ -957,6 +1054,30 @@ hw_status tc_power_end(TcPower *p, cudaStream_t st, bool check)
     hw_status s = HW_OK;
     if (check && p->pend_accU) s = launch_acc(p, p->Q[p->pend_buf], p->pend_coef, p->pend_accU);
     if (s == HW_OK && check) s = read_err_flag(p->err, st);
+    cudaFreeAsync(p->mem, st);
+    delete p;
+    return s;
+}
+
+hw_status tc_power_finish_c64(TcPower *p, const double *Re, const double *Im, void *U, cudaStream_t st)
+{
+    const int n = p->n;
+    const bool last = p->pend_accU != nullptr;
+    const Slices &Q = p->Q[last ? p->pend_buf : 0];
+    const void *q0 = last ? Q.s[0] : nullptr;
+    const int last_im = (p->pend_accU == Im) ? 1 : 0;
+    const dim3 grid((n + 31) / 32, (n + 31) / 32);   // blocks above the diagonal return at once
+    float2 *u = static_cast<float2 *>(U);
+    if (p->md.fmt == FMT_F16)
+        k_finish_c64<FMT_F16, 2><<<grid, 256, 0, st>>>(n, Re, Im, q0, Q.s[1], Q.s[2], p->ld, p->pend_coef, last_im, u);
+    else if (p->md.ns == 1)
+        k_finish_c64<FMT_BF16, 1><<<grid, 256, 0, st>>>(n, Re, Im, q0, Q.s[1], Q.s[2], p->ld, p->pend_coef, last_im, u);
+    else if (p->md.ns == 2)
+        k_finish_c64<FMT_BF16, 2><<<grid, 256, 0, st>>>(n, Re, Im, q0, Q.s[1], Q.s[2], p->ld, p->pend_coef, last_im, u);
+    else
+        k_finish_c64<FMT_BF16, 3><<<grid, 256, 0, st>>>(n, Re, Im, q0, Q.s[1], Q.s[2], p->ld, p->pend_coef, last_im, u);
+    hw_status s = hw_cuda(cudaGetLastError(), "k_finish_c64 launch");
+    if (s == HW_OK) s = read_err_flag(p->err, st);
     cudaFreeAsync(p->mem, st);
     delete p;
     return s;

@@ -88,12 +88,27 @@ void free_marked(MarkedList &m, cudaStream_t st);
 
 // tensor-core Taylor powers (gemm_tc.cu): Q_k = Q_{k-1} Y / k on tcgen05 from
 // split-bf16 operands, accU += sign Q_k in double
+// Y = off on every arc of the CSR (row_ptr, col) plus diag on the marked
+// vertices' diagonal: the sparse symmetric matrix whose powers are taken
+struct SymSparse {
+    const int32_t *row_ptr;
+    const int32_t *col;
+    int n;
+    double off;
+    MarkedList mk;
+    double diag;
+};
+
 struct TcPower;
 bool tc_gemm_available();
-hw_status tc_power_begin(int n, const double *Y, const double *yvals, int nyvals, double theta, int mode,
+hw_status tc_power_begin(const SymSparse &Y, const double *yvals, int nyvals, double theta, int mode,
                          cudaStream_t st, TcPower **out);
 hw_status tc_power_step(TcPower *p, int k, double *accU, double sign);
+// adds the last power to its sum and frees the state
 hw_status tc_power_end(TcPower *p, cudaStream_t st, bool check);
+// adds the last power while writing U = Re + i Im (complex64, n x n) from the
+// lower triangles of Re and Im, and frees the state
+hw_status tc_power_finish_c64(TcPower *p, const double *Re, const double *Im, void *U, cudaStream_t st);
 
 // Programmatic dependent launch: consecutive steps of a loop overlap the next
 // grid's launch with the current grid's tail.  A kernel launched this way
