@@ -596,7 +596,7 @@ def run_profile(args):
         print(json.dumps({"profile": args.profile, "steps": args.profile_steps, "tile": args.profile_tile}))
         G.free()
         return
-    if args.profile in ("expm_c64", "apply_c128", "apply_c64"):
+    if args.profile in ("expm_c64", "apply_c128", "apply_c64", "apply_sym_c64"):
         # the 4096-vertex hypercube CTQW: one expm (11 tensor-core powers) or a few applications
         n = 4096
         m = synth.seeded_vertex(3, n)
@@ -609,7 +609,8 @@ def run_profile(args):
         if args.profile.startswith("apply"):
             x = torch.full((n,), 1 / 64, dtype=cdt, device="cuda")
             y = torch.empty_like(x)
-            hw.hw_ctqw_evolve(U, n, dt, 1, args.profile_steps, x, y, [m])
+            opts = {"u_symmetric": 1} if args.profile == "apply_sym_c64" else None
+            hw.hw_ctqw_evolve(U, n, dt, 1, args.profile_steps, x, y, [m], opts=opts)
         torch.cuda.synchronize()
         print(json.dumps({"profile": args.profile}))
         G.free()
@@ -636,7 +637,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["coined_c128", "coined_c64", "batched_c64", "expm_c64", "apply_c128",
-                                          "apply_c64"],
+                                          "apply_c64", "apply_sym_c64"],
                     help="run a few coin+shift launches of the workload and exit (for ncu)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--profile-tile", type=int, default=10)
