@@ -248,39 +248,53 @@ __device__ __forceinline__ void split(float x, int ns, typename Sl<FMT>::T *s)
 // T3 of the series: accU[i][j] += coef * Q[i][j] for j <= i (the lower
 // triangle) over rows i = row0, row0 + rstride, ..., with Q given by its NA
 // slices (of Q / coef up to sign); the slices are summed in fp32 (what the
-// next power multiplies) and added in double.  nt threads (tid) split each
-// row; each takes 4 columns nt apart and issues their loads together.
+// next power multiplies) and added in double.  The rows' elements are taken
+// as one flat sequence, element e by thread e % nt, in batches of U elements
+// per thread whose loads are all issued before their stores, so that each
+// thread keeps U reads in flight whatever the rows' lengths.
 template <int FMT, int NA>
 __device__ __forceinline__ void acc_rows(int n, const void *q0, const void *q1, const void *q2, int ldq,
                                          double coef, double *__restrict__ accU, int row0, int rstride, int tid,
                                          int nt)
 {
     using ST = typename Sl<FMT>::T;
-    constexpr int U = 4;
-    for (int i = row0; i < n; i += rstride) {
-        const ST *__restrict__ r0 = static_cast<const ST *>(q0) + int64_t(i) * ldq;
-        const ST *__restrict__ r1 = static_cast<const ST *>(q1) + int64_t(i) * ldq;
-        const ST *__restrict__ r2 = static_cast<const ST *>(q2) + int64_t(i) * ldq;
-        double *__restrict__ u = accU + int64_t(i) * n;
-        for (int j0 = tid; j0 <= i; j0 += U * nt) {
-            float q[U];
-            double x[U];
+    constexpr int U = 8;
+    if (row0 >= n) return;
+    // current row r (flat offset base of its first element) of this thread's walk
+    int r = row0;
+    int64_t base = 0;
+    int64_t e = tid;
+    while (true) {
+        int64_t at_q[U], at_u[U];
+        bool ok[U];
 #pragma unroll
-            for (int t = 0; t < U; ++t) {
-                const int j = j0 + t * nt;
-                if (j <= i) {
-                    q[t] = Sl<FMT>::to(r0[j]);
-                    if (NA > 1) q[t] += Sl<FMT>::to(r1[j]);
-                    if (NA > 2) q[t] += Sl<FMT>::to(r2[j]);
-                    x[t] = u[j];
-                }
+        for (int t = 0; t < U; ++t) {
+            const int64_t et = e + int64_t(t) * nt;
+            while (r < n && et >= base + r + 1) {   // past the end of row r
+                base += r + 1;
+                r += rstride;
             }
+            ok[t] = r < n;
+            const int64_t col = et - base;
+            at_q[t] = int64_t(r) * ldq + col;
+            at_u[t] = int64_t(r) * n + col;
+        }
+        float q[U];
+        double x[U];
 #pragma unroll
-            for (int t = 0; t < U; ++t) {
-                const int j = j0 + t * nt;
-                if (j <= i) u[j] = fma(coef, fpconv::f32_to_f64(q[t]), x[t]);
+        for (int t = 0; t < U; ++t) {
+            if (ok[t]) {
+                q[t] = Sl<FMT>::to(static_cast<const ST *>(q0)[at_q[t]]);
+                if (NA > 1) q[t] += Sl<FMT>::to(static_cast<const ST *>(q1)[at_q[t]]);
+                if (NA > 2) q[t] += Sl<FMT>::to(static_cast<const ST *>(q2)[at_q[t]]);
+                x[t] = accU[at_u[t]];
             }
         }
+#pragma unroll
+        for (int t = 0; t < U; ++t)
+            if (ok[t]) accU[at_u[t]] = fma(coef, fpconv::f32_to_f64(q[t]), x[t]);
+        if (!ok[U - 1]) break;
+        e += int64_t(U) * nt;
     }
 }
 
