@@ -13,6 +13,13 @@
 // are produced on the device and copied to a pinned host arena; the caller
 // collects them with hw_server_result.
 //
+// A continuous-time job whose three working vectors fit in one CTA's shared
+// memory (complex64 up to 8192 vertices, complex128 up to 4096) is "local":
+// a CTA of its own (k_serve_local, launched beside k_serve_step in every
+// sub-step of the graph) keeps the state and the series terms in shared
+// memory and advances the job by a whole walk step per sub-step, with block
+// barriers between the Taylor terms instead of one launch per term.
+//
 // Each job's arithmetic depends only on its own data and a fixed per-vertex
 // order, so its result is the same alone and in any mix.
 #include <cuda_runtime.h>
@@ -33,6 +40,9 @@ constexpr int kServeThreads = 256;
 constexpr int kTileVertices = 1024;   // CTQW tiles
 constexpr int kServeTileArcs = 1024;  // coined tiles: whole vertices, at most this many arcs
 constexpr int kMaxServeMarked = 4;
+constexpr int kLocalBytes = 3 * 8192 * 8;  // shared memory of a local CTQW job: state and two terms
+constexpr int kLocalThreads = 512;
+constexpr int kLocalCtas = 64;             // local jobs advanced at once (each CTA takes one SM's memory)
 
 struct SJob {
     const int32_t *row_ptr;
@@ -54,6 +64,8 @@ struct SJob {
     int32_t q;               // CTQW: parts per application
     int32_t n_marked;
     int32_t marked[kMaxServeMarked];
+    int32_t local;           // CTQW job run by one CTA from shared memory
+    int32_t pad;
 };
 
 struct Tile {
@@ -156,6 +168,68 @@ __device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
         J.rec[w * J.n_marked + mi] = double(o.x) * double(o.x) + double(o.y) * double(o.y);
 }
 
+// The same step for a tile of vertices of a degree known at compile time:
+// the job's pointers and marked vertices are read once per tile, each thread
+// loads its vertex's D arcs and reversal indices before any arithmetic, and
+// the loops unroll.  Arithmetic and order are serve_coined's.
+template <typename R, int D>
+__device__ void serve_coined_fixed(const SJob &Jg, int64_t w, int v0, int v1)
+{
+    using V = typename CxS<R>::T;
+    const V *__restrict__ in = static_cast<const V *>(Jg.X[w & 1]);
+    V *__restrict__ out = static_cast<V *>(Jg.X[(w + 1) & 1]);
+    const int32_t *__restrict__ rev = Jg.rev;
+    const int nm = Jg.n_marked;
+    int mk[kMaxServeMarked];
+#pragma unroll
+    for (int i = 0; i < kMaxServeMarked; ++i) mk[i] = (i < nm) ? Jg.marked[i] : -1;
+    double *rec = Jg.rec;
+    const R f = R(Jg.two_over_d);
+    for (int v = v0 + int(threadIdx.x); v < v1; v += blockDim.x) {
+        const int64_t s = int64_t(v) * D;
+        V p[D];
+        int r[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            p[j] = in[s + j];
+            r[j] = rev[s + j];
+        }
+        int mi = -1;
+#pragma unroll
+        for (int i = 0; i < kMaxServeMarked; ++i)
+            if (mk[i] == v) mi = i;
+        if (mi >= 0) {
+            if (rec && w >= 1) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) acc += double(p[j].x) * double(p[j].x) + double(p[j].y) * double(p[j].y);
+                rec[(w - 1) * nm + mi] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                V c;
+                c.x = -p[j].x;
+                c.y = -p[j].y;
+                out[r[j]] = c;
+            }
+            continue;
+        }
+        R sx = 0, sy = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            sx += p[j].x;
+            sy += p[j].y;
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            V c;
+            c.x = fma(f, sx, -p[j].x);
+            c.y = fma(f, sy, -p[j].y);
+            out[r[j]] = c;
+        }
+    }
+}
+
 // A coined tile staged in shared memory: coalesced loads of the tile's arcs,
 // one sequential sum per vertex, then c = fma(2/d, sum, -psi) per arc -- the
 // same arithmetic as the single-job kernel, so results match it bit for bit.
@@ -211,22 +285,131 @@ __device__ void serve_coined_tile(const SJob &J, int64_t w, int v0, int v1, unsi
     __syncthreads();
 }
 
+// Walk steps w0 .. w0 + ns - 1 (each q parts of m Taylor terms) of a local
+// CTQW job: the state (acc) and the terms (T0, T1) live in shared memory for
+// all of them.  The arithmetic of every term is serve_ctqw's, in the same
+// order: t_1 is formed from the part's start state, and acc takes t_1, t_2,
+// ... one at a time.
+template <typename R>
+__device__ void serve_ctqw_local(const SJob &J, int64_t w0, int ns, unsigned char *smem)
+{
+    using V = typename CxS<R>::T;
+    const int n = int(J.n);
+    V *acc = reinterpret_cast<V *>(smem);
+    V *T0 = acc + n;
+    V *T1 = T0 + n;
+    const V *__restrict__ in = static_cast<const V *>(J.X[w0 & 1]);
+    V *__restrict__ out = static_cast<V *>(J.X[(w0 + ns) & 1]);
+    for (int v = threadIdx.x; v < n; v += blockDim.x) acc[v] = in[v];
+    __syncthreads();
+    const R mg = R(-J.gamma);
+    for (int64_t w = w0; w < w0 + ns; ++w) {
+        for (int r = 0; r < J.q; ++r) {
+            for (int k = 1; k <= J.m; ++k) {
+                const V *tin = (k == 1) ? acc : ((k & 1) ? T1 : T0);   // t_{k-1}
+                V *tout = (k & 1) ? T0 : T1;                            // t_k
+                const R c = R(J.tau / double(k));
+                for (int v = threadIdx.x; v < n; v += blockDim.x) {
+                    R sx = 0, sy = 0;
+                    for (int a = J.row_ptr[v]; a < J.row_ptr[v + 1]; ++a) {
+                        const V q = tin[J.head[a]];
+                        sx += q.x;
+                        sy += q.y;
+                    }
+                    R hx = mg * sx, hy = mg * sy;
+                    const int mi = job_marked(J, v);
+                    if (mi >= 0) {
+                        hx -= tin[v].x;
+                        hy -= tin[v].y;
+                    }
+                    V t;
+                    t.x = c * hy;
+                    t.y = -c * hx;
+                    tout[v] = t;
+                    // acc takes t_{k-1} now (t_1 only once every gather of the
+                    // start state is done, i.e. at k = 2) and t_m at the end
+                    if (k >= 2) {
+                        V o = acc[v];
+                        const V tp = tin[v];
+                        o.x = o.x + tp.x;
+                        o.y = o.y + tp.y;
+                        if (k == J.m) {
+                            o.x = o.x + t.x;
+                            o.y = o.y + t.y;
+                        }
+                        acc[v] = o;
+                    }
+                }
+                __syncthreads();
+                if (k == 1 && J.m == 1) {   // a single term: acc = x + t_1 after every gather
+                    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+                        V o = acc[v];
+                        o.x = o.x + T0[v].x;
+                        o.y = o.y + T0[v].y;
+                        acc[v] = o;
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        if (J.rec)
+            for (int i = threadIdx.x; i < J.n_marked; i += blockDim.x) {
+                const V o = acc[J.marked[i]];
+                J.rec[w * J.n_marked + i] = double(o.x) * double(o.x) + double(o.y) * double(o.y);
+            }
+    }
+    for (int v = threadIdx.x; v < n; v += blockDim.x) out[v] = acc[v];
+}
+
+// K sub-steps (walk steps) of every resident local CTQW job, a CTA per job;
+// this kernel runs beside the K tiled sub-step kernels of a round.
+__global__ void __launch_bounds__(kLocalThreads)
+k_serve_local(const SJob *__restrict__ jobs, const int *__restrict__ local, const int *__restrict__ nlocal,
+              const int64_t *__restrict__ tick, int K)
+{
+    extern __shared__ __align__(16) unsigned char lsmem[];
+    const int nl = *nlocal;
+    const int64_t now = *tick;
+    for (int i = blockIdx.x; i < nl; i += gridDim.x) {
+        const SJob &J = jobs[local[i]];
+        const int64_t w0 = std::max<int64_t>(0, now - J.start_tick);
+        const int64_t w1 = std::min<int64_t>(J.total_subs, now + K - J.start_tick);
+        if (w1 <= w0) continue;   // uniform over the CTA
+        if (J.dt == HW_C128) serve_ctqw_local<double>(J, w0, int(w1 - w0), lsmem);
+        else serve_ctqw_local<float>(J, w0, int(w1 - w0), lsmem);
+        __syncthreads();   // the next job reuses the shared memory
+    }
+}
+
 // One sub-step of every resident job.  Tiles are (job, vertex range); the
 // grid loops over them, so the launch shape never depends on the job mix.
 __global__ void __launch_bounds__(kServeThreads)
 k_serve_step(const SJob *__restrict__ jobs, const Tile *__restrict__ tiles, const int *__restrict__ ntiles,
-             const int64_t *__restrict__ tick)
+             const int64_t *__restrict__ tick, int sub)
 {
     extern __shared__ __align__(16) unsigned char smem[];   // 2 * kServeTileArcs complex values
     const int nt = *ntiles;
-    const int64_t now = *tick;
+    const int64_t now = *tick + sub;   // the tick advances once per round, after all its sub-steps
+    pdl_trigger();
+    pdl_wait();   // the previous sub-step's states
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const Tile tl = tiles[t];
         const SJob &J = jobs[tl.job];
         const int64_t local = now - J.start_tick;
         if (local < 0 || local >= J.total_subs) continue;   // uniform over the CTA
-        if (J.kind == 0 && J.d > 4) {
-            // higher degrees: coalesced loads through shared memory
+        if (J.kind == 0 && (J.d == 3 || J.d == 4 || J.d == 8)) {
+            // common degrees: fixed-degree path
+            if (J.dt == HW_C128) {
+                if (J.d == 3) serve_coined_fixed<double, 3>(J, local, tl.v0, tl.v1);
+                else if (J.d == 4) serve_coined_fixed<double, 4>(J, local, tl.v0, tl.v1);
+                else serve_coined_fixed<double, 8>(J, local, tl.v0, tl.v1);
+            } else {
+                if (J.d == 3) serve_coined_fixed<float, 3>(J, local, tl.v0, tl.v1);
+                else if (J.d == 4) serve_coined_fixed<float, 4>(J, local, tl.v0, tl.v1);
+                else serve_coined_fixed<float, 8>(J, local, tl.v0, tl.v1);
+            }
+        } else if (J.kind == 0 && J.d > 4) {
+            // other degrees above 4: coalesced loads through shared memory
             if (J.dt == HW_C128) serve_coined_tile<double>(J, local, tl.v0, tl.v1, smem);
             else serve_coined_tile<float>(J, local, tl.v0, tl.v1, smem);
         } else if (J.kind == 0) {
@@ -244,7 +427,7 @@ k_serve_step(const SJob *__restrict__ jobs, const Tile *__restrict__ tiles, cons
     }
 }
 
-__global__ void k_serve_tick(int64_t *tick) { *tick += 1; }
+__global__ void k_serve_tick(int64_t *tick, int K) { *tick += K; }
 
 template <typename V>
 __global__ void k_fill(V *x, int64_t count, double value)
@@ -342,6 +525,7 @@ struct Job {
     int64_t end_tick = 0;
     int32_t m = 1, q = 1;
     size_t dev_bytes = 0, host_bytes = 0;
+    bool local = false;         // CTQW job run from shared memory by k_serve_local
     cudaEvent_t done_ev = nullptr;
     double t_submit = 0, t_done = 0;
 };
@@ -364,6 +548,10 @@ struct hw_server {
     SJob *d_jobs = nullptr, *h_jobs = nullptr;       // device table + pinned mirror
     Tile *d_tiles = nullptr, *h_tiles = nullptr;
     int *d_ntiles = nullptr, *h_ntiles = nullptr;
+    int *d_local = nullptr, *h_local = nullptr;       // slots of the resident local CTQW jobs
+    int *d_nlocal = nullptr, *h_nlocal = nullptr;
+    cudaStream_t st2 = nullptr;                       // second branch of the captured sub-step
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     int64_t *d_tick = nullptr;
     int64_t tick = 0;
     int max_tiles = 0;
@@ -390,15 +578,27 @@ static hw_status server_capture(hw_server *s)
     const int smem = 2 * kServeTileArcs * int(sizeof(double2));
     st = hw_cuda(cudaFuncSetAttribute(k_serve_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                  "cudaFuncSetAttribute(k_serve_step)");
+    if (st == HW_OK)
+        st = hw_cuda(cudaFuncSetAttribute(k_serve_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kLocalBytes),
+                     "cudaFuncSetAttribute(k_serve_local)");
     if (st != HW_OK) {
         cudaStreamEndCapture(s->st, &g);
         if (g) cudaGraphDestroy(g);
         return st;
     }
-    for (int k = 0; k < s->K; ++k) {
-        k_serve_step<<<sms * 6, kServeThreads, smem, s->st>>>(s->d_jobs, s->d_tiles, s->d_ntiles, s->d_tick);
-        k_serve_tick<<<1, 1, 0, s->st>>>(s->d_tick);
-    }
+    // a round: the K tiled sub-steps (chained by programmatic dependent
+    // launch) beside one launch that advances the local CTQW jobs by K steps,
+    // then the tick
+    cudaEventRecord(s->fork_ev, s->st);
+    cudaStreamWaitEvent(s->st2, s->fork_ev, 0);
+    k_serve_local<<<kLocalCtas, kLocalThreads, kLocalBytes, s->st2>>>(s->d_jobs, s->d_local, s->d_nlocal, s->d_tick,
+                                                                      s->K);
+    cudaEventRecord(s->join_ev, s->st2);
+    for (int k = 0; k < s->K; ++k)
+        launch_pdl(k_serve_step, dim3(sms * 6), dim3(kServeThreads), smem, s->st, (const SJob *)s->d_jobs,
+                   (const Tile *)s->d_tiles, (const int *)s->d_ntiles, (const int64_t *)s->d_tick, k);
+    cudaStreamWaitEvent(s->st, s->join_ev, 0);
+    k_serve_tick<<<1, 1, 0, s->st>>>(s->d_tick, s->K);
     st = hw_cuda(cudaStreamEndCapture(s->st, &g), "end capture");
     if (st != HW_OK) return st;
     st = hw_cuda(cudaGraphInstantiate(&s->graph, g, 0), "graph instantiate");
@@ -432,6 +632,10 @@ extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int
     if ((st = hw_cuda(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking), "cudaStreamCreate")) != HW_OK)
         return fail(st);
     s->own_stream = true;
+    if ((st = hw_cuda(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking), "cudaStreamCreate")) != HW_OK ||
+        (st = hw_cuda(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming), "event")) != HW_OK ||
+        (st = hw_cuda(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming), "event")) != HW_OK)
+        return fail(st);
     if ((st = hw_cuda(cudaMalloc(&s->dev_base, size_t(arena_bytes)), "cudaMalloc(serving arena)")) != HW_OK ||
         (st = hw_cuda(cudaHostAlloc(&s->host_base, size_t(host_bytes), cudaHostAllocDefault), "cudaHostAlloc(results)")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_jobs, sizeof(SJob) * max_jobs), "cudaMalloc(job table)")) != HW_OK ||
@@ -441,15 +645,21 @@ extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int
         (st = hw_cuda(cudaMalloc(&s->d_ntiles, sizeof(int)), "cudaMalloc")) != HW_OK ||
         (st = hw_cuda(cudaHostAlloc(&s->h_ntiles, sizeof(int), cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_tick, sizeof(int64_t)), "cudaMalloc")) != HW_OK ||
+        (st = hw_cuda(cudaMalloc(&s->d_local, sizeof(int) * max_jobs), "cudaMalloc(local jobs)")) != HW_OK ||
+        (st = hw_cuda(cudaHostAlloc(&s->h_local, sizeof(int) * max_jobs, cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
+        (st = hw_cuda(cudaMalloc(&s->d_nlocal, sizeof(int)), "cudaMalloc")) != HW_OK ||
+        (st = hw_cuda(cudaHostAlloc(&s->h_nlocal, sizeof(int), cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
         (st = hw_cuda(cudaEventCreateWithFlags(&s->upload_ev, cudaEventDisableTiming), "event")) != HW_OK)
         return fail(st);
     s->dev_arena.init(s->dev_base, size_t(arena_bytes));
     s->host_arena.init(s->host_base, size_t(host_bytes));
     std::memset(s->h_jobs, 0, sizeof(SJob) * max_jobs);
     *s->h_ntiles = 0;
+    *s->h_nlocal = 0;
     for (int i = max_jobs - 1; i >= 0; --i) s->free_slots.push_back(i);
     if ((st = hw_cuda(cudaMemsetAsync(s->d_tick, 0, sizeof(int64_t), s->st), "memset tick")) != HW_OK ||
         (st = hw_cuda(cudaMemsetAsync(s->d_ntiles, 0, sizeof(int), s->st), "memset")) != HW_OK ||
+        (st = hw_cuda(cudaMemsetAsync(s->d_nlocal, 0, sizeof(int), s->st), "memset")) != HW_OK ||
         (st = server_capture(s)) != HW_OK)
         return fail(st);
     *out = s;
@@ -474,6 +684,13 @@ extern "C" hw_status hw_server_destroy(hw_server *s)
     cudaFree(s->d_ntiles);
     cudaFreeHost(s->h_ntiles);
     cudaFree(s->d_tick);
+    cudaFree(s->d_local);
+    cudaFreeHost(s->h_local);
+    cudaFree(s->d_nlocal);
+    cudaFreeHost(s->h_nlocal);
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    if (s->join_ev) cudaEventDestroy(s->join_ev);
+    if (s->st2) cudaStreamDestroy(s->st2);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     cudaGetLastError();
     delete s;
@@ -519,12 +736,13 @@ extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *
         J.m = m;
         J.q = 1 << sq;
         J.dim = g->n;
-        J.total_subs = job->steps * int64_t(J.q) * J.m;
+        J.local = 3 * size_t(g->n) * esz <= size_t(kLocalBytes);
+        J.total_subs = J.local ? job->steps : job->steps * int64_t(J.q) * J.m;
     }
     const size_t state = (size_t(J.dim) * esz + 255) & ~size_t(255);
     const size_t rec = job->n_marked ? ((size_t(job->steps) * job->n_marked * 8 + 255) & ~size_t(255)) : 0;
     const size_t prob = (size_t(J.n) * 8 + 255) & ~size_t(255);
-    J.dev_bytes = (job->kind == HW_JOB_COINED ? 2 : 4) * state + rec + prob +
+    J.dev_bytes = ((job->kind == HW_JOB_COINED || J.local) ? 2 : 4) * state + rec + prob +
                   ((size_t(job->steps) * 8 + 255) & ~size_t(255));
     J.host_bytes = prob + ((size_t(job->steps) * 8 + 255) & ~size_t(255));
     if (J.dev_bytes > s->dev_arena.size() || J.host_bytes > s->host_arena.size())
@@ -539,9 +757,13 @@ extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *
 
 static hw_status rebuild_tiles(hw_server *s)
 {
-    int nt = 0;
+    int nt = 0, nl = 0;
     for (int64_t id : s->resident) {
         const Job &J = s->jobs[id];
+        if (J.local) {
+            s->h_local[nl++] = J.slot;
+            continue;
+        }
         const int64_t step = (J.spec.kind == HW_JOB_COINED) ? std::max<int64_t>(1, kServeTileArcs / J.spec.graph->max_degree)
                                                             : kTileVertices;
         for (int64_t v0 = 0; v0 < J.n; v0 += step) {
@@ -555,6 +777,7 @@ static hw_status rebuild_tiles(hw_server *s)
         }
     }
     *s->h_ntiles = nt;
+    *s->h_nlocal = nl;
     return HW_OK;
 }
 
@@ -581,7 +804,7 @@ static hw_status admit(hw_server *s, Job &J)
     D.rev = g->d_rev;
     D.X[0] = dev;
     D.X[1] = dev + state;
-    const int nstates = (J.spec.kind == HW_JOB_COINED) ? 2 : 4;
+    const int nstates = (J.spec.kind == HW_JOB_COINED || J.local) ? 2 : 4;
     if (nstates == 4) {
         D.T[0] = dev + 2 * state;
         D.T[1] = dev + 3 * state;
@@ -600,6 +823,7 @@ static hw_status admit(hw_server *s, Job &J)
     D.q = J.q;
     D.n_marked = J.spec.n_marked;
     for (int i = 0; i < J.spec.n_marked; ++i) D.marked[i] = J.marked[i];
+    D.local = J.local ? 1 : 0;
     // uniform start over the basis: arcs (coined) or vertices (CTQW)
     const double amp = 1.0 / std::sqrt(double(J.dim));
     const int grid = int(std::min<int64_t>(148 * 16, (J.dim + 255) / 256));
@@ -618,14 +842,14 @@ static hw_status retire(hw_server *s, Job &J)
     const SJob &D = s->h_jobs[J.slot];
     const hw_dtype dt = hw_dtype(J.spec.dt);
     const size_t esz = cplx_bytes(dt);
-    const int nstates = (J.spec.kind == HW_JOB_COINED) ? 2 : 4;
+    const int nstates = (J.spec.kind == HW_JOB_COINED || J.local) ? 2 : 4;
     const size_t state = (size_t(J.dim) * esz + 255) & ~size_t(255);
     const size_t rec = J.spec.n_marked ? ((size_t(J.spec.steps) * J.spec.n_marked * 8 + 255) & ~size_t(255)) : 0;
     double *d_prob = reinterpret_cast<double *>(J.dev + nstates * state + rec);
     double *d_record = reinterpret_cast<double *>(J.dev + nstates * state + rec +
                                                   ((size_t(J.n) * 8 + 255) & ~size_t(255)));
-    const int64_t final_parity = (J.spec.kind == HW_JOB_COINED) ? (J.spec.steps & 1)
-                                                                 : ((J.spec.steps * J.q) & 1);
+    const int64_t final_parity = (J.spec.kind == HW_JOB_COINED || J.local) ? (J.spec.steps & 1)
+                                                                            : ((J.spec.steps * J.q) & 1);
     const void *psi = D.X[final_parity];
     hw_status st = launch_probability(J.spec.kind == HW_JOB_COINED ? g : nullptr, J.n, dt, 1, psi, d_prob, nullptr,
                                       s->st);
@@ -715,6 +939,10 @@ extern "C" hw_status hw_server_run(hw_server *s, int32_t *n_completed)
                 (st = hw_cuda(cudaMemcpyAsync(s->d_tiles, s->h_tiles, sizeof(Tile) * std::max(1, *s->h_ntiles),
                                               cudaMemcpyHostToDevice, s->st), "upload tiles")) != HW_OK ||
                 (st = hw_cuda(cudaMemcpyAsync(s->d_ntiles, s->h_ntiles, sizeof(int), cudaMemcpyHostToDevice, s->st),
+                              "upload count")) != HW_OK ||
+                (st = hw_cuda(cudaMemcpyAsync(s->d_local, s->h_local, sizeof(int) * std::max(1, *s->h_nlocal),
+                                              cudaMemcpyHostToDevice, s->st), "upload local jobs")) != HW_OK ||
+                (st = hw_cuda(cudaMemcpyAsync(s->d_nlocal, s->h_nlocal, sizeof(int), cudaMemcpyHostToDevice, s->st),
                               "upload count")) != HW_OK ||
                 (st = hw_cuda(cudaEventRecord(s->upload_ev, s->st), "event record")) != HW_OK)
                 return st;

@@ -67,7 +67,7 @@ def _plain(hw, G, kind, dt, steps, marked, gamma=0.0, t=0.0):
     return prob.cpu().numpy(), None if rec is None else rec.cpu().numpy()
 
 
-DEGREE = {"torus": 4, "Q9": 9, "reg3": 3, "reg8": 8, "t": 4}
+DEGREE = {"torus": 4, "Q9": 9, "reg3": 3, "reg8": 8, "t": 4, "torus72": 4}
 
 
 def _mix(hw):
@@ -76,6 +76,9 @@ def _mix(hw):
         "Q9": _graph(hw, synth.hypercube(9)),
         "reg3": _graph(hw, synth.random_regular(2000, 3, seed=1)),
         "reg8": _graph(hw, synth.random_regular(1500, 8, seed=2)),
+        # 5184 vertices: too many for a complex128 job in one CTA's shared
+        # memory, so this CTQW job takes the tiled path (one launch per term)
+        "torus72": _graph(hw, synth.torus(72)),
     }
     jobs = [
         ("torus", hw.HW_JOB_COINED, 2, 37, [5, 600]),
@@ -87,6 +90,7 @@ def _mix(hw):
         ("reg3", hw.HW_JOB_CTQW, 1, 12, [10, 20]),
         ("torus", hw.HW_JOB_CTQW, 2, 8, []),
         ("reg8", hw.HW_JOB_CTQW, 1, 50, [1499]),
+        ("torus72", hw.HW_JOB_CTQW, 2, 6, [100, 5000]),
     ]
     return graphs, jobs
 
@@ -116,7 +120,7 @@ def test_served_jobs_match_plain_calls_and_are_mix_independent(hw):
         assert abs(prob.sum() - 1.0) < (1e-12 if dt == 2 else 1e-4)
         assert lat > 0
     # each job alone gives bit-identical results to the same job in the mix
-    for k in (0, 3, 5, 6):
+    for k in (0, 3, 5, 6, 9):
         alone = _serve(hw, graphs, [jobs[k]])[0]
         assert np.array_equal(alone[0], mixed[k][0])
         if jobs[k][4]:
