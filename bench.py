@@ -47,9 +47,6 @@ UNIT = "arc-updates/s"
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # measured on; a changed kernel reports null until it is measured again.
 TRAFFIC = {
-    # the 1024x1024 torus step: ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch
-    ("c128", "d5164d770f8873d40679b71eaded42b15fc21249"): 84142848 + 18922240,
-    ("c64", "d5164d770f8873d40679b71eaded42b15fc21249"): 50350848 + 1474560,
 }
 
 
@@ -202,7 +199,8 @@ def run_ours(args):
                     prob=torch.empty(n, dtype=torch.float64, device="cuda"),
                     norm=torch.empty(1, dtype=torch.float64, device="cuda"))
 
-    launches_per_run = WALK_STEPS + 1 + 1 + 2   # steps, final record, probability, norm (2)
+    # steps, layout in and out, final record, probability, norm (2)
+    launches_per_run = WALK_STEPS + 2 + 1 + 1 + 2
 
     def run(b, ev_evolve=None):
         if ev_evolve:
@@ -300,7 +298,7 @@ def run_ours(args):
                    "coin": "grover", "marked": m, "state": "complex128", "record": "p_m(t) every step",
                    "l2": "256 MiB written between timed steps; working set 151 MB > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "kernel": "k_coined_vertex<double,4,grover>",
+        "roofline": {"bound": "hbm", "kernel": "k_coined_em<double,4,grover>",
                      "achieved": ach128, "peak": peak, "unit": "GB/s", "frac": ach128 / peak,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
                      "bytes_per_launch": bytes128, "launch_us": per_launch128 * 1e6,

@@ -229,7 +229,6 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
 
     const int64_t slots = record ? steps / stride : 0;
     Scratch tmp(st), recbuf(st);
-    if ((s = tmp.get(bytes, "scratch allocation (state scratch)")) != HW_OK) return s;
     double *rec_part = nullptr;
     if (slots) {
         if (n_marked == 1) {
@@ -241,6 +240,27 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
         }
     }
 
+    if (batch == 1 && coined_em_supported(g, coin, dt)) {
+        // regular graph: the steps run in the edge-major layout between two
+        // scratch buffers; the state is transposed in and out once
+        Scratch em(st);
+        if ((s = em.get(2 * bytes, "scratch allocation (edge-major states)")) != HW_OK) return s;
+        void *E[2] = {em.p, static_cast<char *>(em.p) + bytes};
+        if ((s = launch_layout(g, dt, psi_in, E[0], true, st)) != HW_OK) return s;
+        int cur = 0;
+        for (int64_t k = 1; k <= steps; ++k) {
+            CoinedStep cs;
+            cs.in = E[cur];
+            cs.out = E[1 - cur];
+            cs.marked = mk;
+            cs.rec_part = rec_part;
+            cs.rec_slot = (slots && (k - 1) >= stride && (k - 1) % stride == 0) ? (k - 1) / stride - 1 : -1;
+            if ((s = launch_coined_step_em(g, dt, coin, cs, st)) != HW_OK) return s;
+            cur = 1 - cur;
+        }
+        if ((s = launch_layout(g, dt, E[cur], psi_out, false, st)) != HW_OK) return s;
+    } else {
+    if ((s = tmp.get(bytes, "scratch allocation (state scratch)")) != HW_OK) return s;
     // Ping-pong so that the last step lands in psi_out: step k (1-based) writes
     // psi_out when (steps - k) is even and the scratch otherwise.  In place
     // with an odd step count, step 1 would read and write psi_out, so it reads
@@ -264,6 +284,7 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
                          : launch_coined_step_batched(g, dt, coin, batch, cs, opts ? opts->tile : 0, st);
         if (s != HW_OK) return s;
         src = dst;
+    }
     }
     if (slots && steps % stride == 0) {
         s = launch_marked_prob(g->d_row_ptr, dt, batch, psi_out, mk,

@@ -265,80 +265,7 @@ struct RegArgs {
 };
 
 template <typename R> __device__ __forceinline__ R grover_weight(const RegArgs &a);
-template <> __device__ __forceinline__ double grover_weight<double>(const RegArgs &a) { return a.two_over_d; }
 template <> __device__ __forceinline__ float grover_weight<float>(const RegArgs &a) { return a.two_over_d_f; }
-
-template <int D>
-__device__ __forceinline__ void load_rev(const int32_t *__restrict__ rev, int64_t v, int *r)
-{
-    const int32_t *p = rev + v * D;
-    if (D == 4) {
-        const int4 q = __ldg(reinterpret_cast<const int4 *>(p));
-        r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
-    } else if (D == 8) {
-        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p));
-        const int4 q1 = __ldg(reinterpret_cast<const int4 *>(p) + 1);
-        r[0] = q0.x; r[1] = q0.y; r[2] = q0.z; r[3] = q0.w;
-        r[4] = q1.x; r[5] = q1.y; r[6] = q1.z; r[7] = q1.w;
-    } else if (D == 2) {
-        const int2 q = __ldg(reinterpret_cast<const int2 *>(p));
-        r[0] = q.x; r[1] = q.y;
-    } else {
-#pragma unroll
-        for (int j = 0; j < D; ++j) r[j] = __ldg(p + j);
-    }
-}
-
-template <typename R, int D, int COIN>
-__global__ void __launch_bounds__(kThreads) k_coined_vertex(RegArgs a)
-{
-    using V = typename Cx<R>::T;
-    const V *__restrict__ in = static_cast<const V *>(a.in);
-    V *__restrict__ out = static_cast<V *>(a.out);
-    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    V p[D];
-    int r[D];
-    if (v < a.n) load_rev<D>(a.rev, v, r);    // constant table: fetched before the wait
-    pdl_wait();
-    if (v < a.n) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) p[j] = in[v * D + j];
-        const int mi = find_marked(a.mk, int(v));
-        if (mi >= 0) {
-            if (a.rec_part && a.rec_slot >= 0) {
-                double acc = 0.0;
-#pragma unroll
-                for (int j = 0; j < D; ++j)
-                    acc += double(p[j].x) * double(p[j].x) + double(p[j].y) * double(p[j].y);
-                a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
-            }
-#pragma unroll
-            for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(-p[j].x, -p[j].y);
-        } else if (COIN == HW_COIN_GROVER) {
-            R sx = p[0].x, sy = p[0].y;
-#pragma unroll
-            for (int j = 1; j < D; ++j) { sx += p[j].x; sy += p[j].y; }
-            const R f = grover_weight<R>(a);
-            // c_j = (2/d) sum - psi_j, one fused multiply-add per component
-#pragma unroll
-            for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
-        } else {
-            const R scale = R(1) / sqrt(R(D));
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                R cx = 0, cy = 0;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const double2 w = c_tw[D * (D - 1) / 2 + (j * k) % D];
-                    cx += R(w.x) * p[k].x - R(w.y) * p[k].y;
-                    cy += R(w.x) * p[k].y + R(w.y) * p[k].x;
-                }
-                out[r[j]] = mkv<V, R>(cx * scale, cy * scale);
-            }
-        }
-    }
-    pdl_trigger();
-}
 
 // Lane-group variant for complex64 (FP32 arithmetic is cheap; the limit is
 // memory requests): a group of G = 2^ceil(log2 d) consecutive lanes owns one
@@ -834,23 +761,151 @@ __global__ void k_record_finalize(const double *__restrict__ part, int n_marked,
     record[i] = acc;
 }
 
-}  // namespace
+// ---- edge-major layout (regular graphs): E[j][v] = psi[v d + j]
+// Arc j of every vertex forms a contiguous row, so a warp of consecutive
+// vertices reads each of its rows as one 256/512-byte segment, and the
+// reversal E'[revE[j n + v]] lands, for structured graphs (torus, hypercube),
+// on consecutive vertices of one row as well: the shift writes whole sectors.
+// hw_coined_evolve transposes in and out once per call.
 
-template <typename R, int COIN>
-static void launch_vertex(int d, const RegArgs &a, cudaStream_t st)
+struct EmArgs {
+    const int32_t *revE;
+    double *rec_part;
+    const void *in;
+    void *out;
+    int64_t rec_slot;
+    int64_t n;
+    int32_t d;
+    double two_over_d;
+    float two_over_d_f;
+    MarkedList mk;
+};
+
+template <typename R> __device__ __forceinline__ R em_weight(const EmArgs &a);
+template <> __device__ __forceinline__ double em_weight<double>(const EmArgs &a) { return a.two_over_d; }
+template <> __device__ __forceinline__ float em_weight<float>(const EmArgs &a) { return a.two_over_d_f; }
+
+// thread per vertex, degree D known at compile time (the same arithmetic as
+// the arc-major kernels: Grover sum in arc order from arc 0, one FMA per component)
+template <typename R, int D, int COIN>
+__global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
 {
-    const dim3 grid(unsigned((a.n + kThreads - 1) / kThreads));
-    switch (d) {
-    case 1: launch_pdl(k_coined_vertex<R, 1, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 2: launch_pdl(k_coined_vertex<R, 2, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 3: launch_pdl(k_coined_vertex<R, 3, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 4: launch_pdl(k_coined_vertex<R, 4, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 5: launch_pdl(k_coined_vertex<R, 5, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 6: launch_pdl(k_coined_vertex<R, 6, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 7: launch_pdl(k_coined_vertex<R, 7, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    default: launch_pdl(k_coined_vertex<R, 8, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    using V = typename Cx<R>::T;
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t n = a.n;
+    V p[D];
+    int r[D];
+    if (v < n) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) r[j] = __ldg(a.revE + j * n + v);   // constant table: before the wait
+    }
+    pdl_wait();
+    if (v < n) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) p[j] = in[j * n + v];
+        const int mi = find_marked(a.mk, int(v));
+        if (mi >= 0) {
+            if (a.rec_part && a.rec_slot >= 0) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < D; ++j)
+                    acc += double(p[j].x) * double(p[j].x) + double(p[j].y) * double(p[j].y);
+                a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(-p[j].x, -p[j].y);
+        } else if (COIN == HW_COIN_GROVER) {
+            R sx = p[0].x, sy = p[0].y;
+#pragma unroll
+            for (int j = 1; j < D; ++j) { sx += p[j].x; sy += p[j].y; }
+            const R f = em_weight<R>(a);
+#pragma unroll
+            for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
+        } else {
+            const R scale = R(1) / sqrt(R(D));
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                R cx = 0, cy = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const double2 w = c_tw[D * (D - 1) / 2 + (j * k) % D];
+                    cx += R(w.x) * p[k].x - R(w.y) * p[k].y;
+                    cy += R(w.x) * p[k].y + R(w.y) * p[k].x;
+                }
+                out[r[j]] = mkv<V, R>(cx * scale, cy * scale);
+            }
+        }
+    }
+    pdl_trigger();
+}
+
+// Grover, any degree: thread per vertex, a pass for the sum and a pass (rows
+// read again, from L2) for the outputs
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
+{
+    using V = typename Cx<R>::T;
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t n = a.n;
+    const int d = a.d;
+    pdl_wait();
+    if (v < n) {
+        const int mi = find_marked(a.mk, int(v));
+        if (mi >= 0) {
+            if (a.rec_part && a.rec_slot >= 0) {
+                double acc = 0.0;
+                for (int j = 0; j < d; ++j) {
+                    const V p = in[j * n + v];
+                    acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+                }
+                a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+            }
+            for (int j = 0; j < d; ++j) {
+                const V p = in[j * n + v];
+                out[__ldg(a.revE + j * n + v)] = mkv<V, R>(-p.x, -p.y);
+            }
+        } else {
+            const V p0 = in[v];
+            R sx = p0.x, sy = p0.y;
+#pragma unroll 4
+            for (int j = 1; j < d; ++j) {
+                const V p = in[j * n + v];
+                sx += p.x;
+                sy += p.y;
+            }
+            const R f = em_weight<R>(a);
+#pragma unroll 4
+            for (int j = 0; j < d; ++j) {
+                const V p = in[j * n + v];
+                out[__ldg(a.revE + j * n + v)] = mkv<V, R>(fma(f, sx, -p.x), fma(f, sy, -p.y));
+            }
+        }
+    }
+    pdl_trigger();
+}
+
+// arc-major [n][d] <-> edge-major [d][n]: element e of the source, read in order
+template <typename V, bool TO_EDGE>
+__global__ void k_layout(const V *__restrict__ in, V *__restrict__ out, int64_t n, int d)
+{
+    const int64_t total = n * d;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        if (TO_EDGE) {
+            const int64_t v = e / d, j = e - v * d;
+            out[j * n + v] = in[e];
+        } else {
+            const int64_t j = e / n, v = e - j * n;
+            out[v * d + j] = in[e];
+        }
     }
 }
+
+}  // namespace
 
 template <typename R, int G, int COIN>
 static void launch_lanes_g(const RegArgs &a, int d, cudaStream_t st)
@@ -900,7 +955,9 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
         if (ts != HW_OK) return ts;
     }
     const bool regular = g->min_degree == g->max_degree && g->max_degree >= 1;
-    if (regular && ((dt == HW_C128 && g->max_degree <= 8) || (dt == HW_C64 && g->max_degree <= 32))) {
+    // complex64 regular graphs up to degree 32: lane groups (complex128
+    // regular graphs always take the edge-major path)
+    if (regular && dt == HW_C64 && g->max_degree <= 32) {
         const int d = g->max_degree;
         RegArgs r;
         r.rev = g->d_rev;
@@ -912,14 +969,9 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
         r.two_over_d = 2.0 / double(d);
         r.two_over_d_f = float(2.0 / double(d));
         r.mk = s.marked;
-        if (dt == HW_C128) {
-            if (coin == HW_COIN_GROVER) launch_vertex<double, HW_COIN_GROVER>(d, r, st);
-            else launch_vertex<double, HW_COIN_FOURIER>(d, r, st);
-        } else {
-            if (coin == HW_COIN_GROVER) launch_lanes<float, HW_COIN_GROVER>(d, r, st);
-            else launch_lanes<float, HW_COIN_FOURIER>(d, r, st);
-        }
-        return hw_cuda(cudaGetLastError(), "k_coined_vertex/k_coined_lanes launch");
+        if (coin == HW_COIN_GROVER) launch_lanes<float, HW_COIN_GROVER>(d, r, st);
+        else launch_lanes<float, HW_COIN_FOURIER>(d, r, st);
+        return hw_cuda(cudaGetLastError(), "k_coined_lanes launch");
     }
     StepArgs a;
     a.two_over_d = g->d_two_over_d;
@@ -941,6 +993,76 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
         else launch_pdl(k_coined_step<float, HW_COIN_FOURIER>, dim3(grid), dim3(kThreads), 0, st, a);
     }
     return hw_cuda(cudaGetLastError(), "k_coined_step launch");
+}
+
+// The edge-major path serves every regular graph except complex64 walks of
+// degree 9..16, where full lane groups of the arc-major k_coined_lanes were
+// measured faster (2^16-vertex hypercube: 8.2 vs 10.5 us per step); complex128
+// above degree 8 and complex64 above 16 use the two-pass k_coined_em_rt
+// (2^20-vertex hypercube: 180 vs 409 us complex128, 89 vs 254 us complex64).
+bool coined_em_supported(const hw_graph *g, hw_coin coin, hw_dtype dt)
+{
+    if (!g->d_revE || (coin == HW_COIN_FOURIER && g->max_degree > 8)) return false;
+    return !(dt == HW_C64 && g->max_degree >= 9 && g->max_degree <= 16);
+}
+
+hw_status launch_layout(const hw_graph *g, hw_dtype dt, const void *in, void *out, bool to_edge, cudaStream_t st)
+{
+    const int64_t total = g->num_arcs;
+    const int grid = int(std::min<int64_t>(148 * 16, (total + 255) / 256));
+    const int d = g->max_degree;
+    if (dt == HW_C128) {
+        if (to_edge) k_layout<double2, true><<<grid, 256, 0, st>>>(static_cast<const double2 *>(in), static_cast<double2 *>(out), g->n, d);
+        else k_layout<double2, false><<<grid, 256, 0, st>>>(static_cast<const double2 *>(in), static_cast<double2 *>(out), g->n, d);
+    } else {
+        if (to_edge) k_layout<float2, true><<<grid, 256, 0, st>>>(static_cast<const float2 *>(in), static_cast<float2 *>(out), g->n, d);
+        else k_layout<float2, false><<<grid, 256, 0, st>>>(static_cast<const float2 *>(in), static_cast<float2 *>(out), g->n, d);
+    }
+    return hw_cuda(cudaGetLastError(), "k_layout launch");
+}
+
+template <typename R, int COIN>
+static void launch_em(int d, const EmArgs &a, cudaStream_t st)
+{
+    const dim3 grid(unsigned((a.n + kThreads - 1) / kThreads));
+    switch (d) {
+    case 1: launch_pdl(k_coined_em<R, 1, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 2: launch_pdl(k_coined_em<R, 2, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 3: launch_pdl(k_coined_em<R, 3, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 4: launch_pdl(k_coined_em<R, 4, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 5: launch_pdl(k_coined_em<R, 5, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 6: launch_pdl(k_coined_em<R, 6, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 7: launch_pdl(k_coined_em<R, 7, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    case 8: launch_pdl(k_coined_em<R, 8, COIN>, grid, dim3(kThreads), 0, st, a); break;
+    default: launch_pdl(k_coined_em_rt<R>, grid, dim3(kThreads), 0, st, a); break;   // Grover only
+    }
+}
+
+hw_status launch_coined_step_em(const hw_graph *g, hw_dtype dt, hw_coin coin, const CoinedStep &s, cudaStream_t st)
+{
+    if (coin == HW_COIN_FOURIER) {
+        hw_status ts = upload_twiddles();
+        if (ts != HW_OK) return ts;
+    }
+    EmArgs a;
+    a.revE = g->d_revE;
+    a.rec_part = s.rec_part;
+    a.in = s.in;
+    a.out = s.out;
+    a.rec_slot = s.rec_slot;
+    a.n = g->n;
+    a.d = g->max_degree;
+    a.two_over_d = 2.0 / double(g->max_degree);
+    a.two_over_d_f = float(2.0 / double(g->max_degree));
+    a.mk = s.marked;
+    if (dt == HW_C128) {
+        if (coin == HW_COIN_GROVER) launch_em<double, HW_COIN_GROVER>(a.d, a, st);
+        else launch_em<double, HW_COIN_FOURIER>(a.d, a, st);
+    } else {
+        if (coin == HW_COIN_GROVER) launch_em<float, HW_COIN_GROVER>(a.d, a, st);
+        else launch_em<float, HW_COIN_FOURIER>(a.d, a, st);
+    }
+    return hw_cuda(cudaGetLastError(), "k_coined_em launch");
 }
 
 // Launch shapes of the batched Grover kernel: (threads per CTA, vertices per

@@ -97,10 +97,23 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [&](hw_status e) { hw_graph_free(g); return e; };
     if ((s = hw_cuda(cudaGetDevice(&g->device), "cudaGetDevice")) != HW_OK) return fail(s);
+    // edge-major reversal table of a regular graph (see hw_graph::d_revE)
+    std::vector<int32_t> revE;
+    const bool regular = n > 0 && g->min_degree == g->max_degree && g->max_degree >= 1;
+    if (regular) {
+        const int64_t d = g->max_degree;
+        revE.resize(size_t(g->num_arcs));
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t j = 0; j < d; ++j) {
+                const int64_t r = rev[size_t(v * d + j)];
+                revE[size_t(j * n + v)] = int32_t((r % d) * n + r / d);
+            }
+    }
     const size_t arcs_b = sizeof(int32_t) * std::max<int64_t>(g->num_arcs, 1);
     if (cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&g->d_head, arcs_b) != cudaSuccess ||
         cudaMalloc(&g->d_rev, arcs_b) != cudaSuccess ||
+        (regular && cudaMalloc(&g->d_revE, arcs_b) != cudaSuccess) ||
         cudaMalloc(&g->d_blk, sizeof(int32_t) * g->h_blk.size()) != cudaSuccess ||
         cudaMalloc(&g->d_two_over_d, sizeof(double) * (g->max_degree + 1)) != cudaSuccess ||
         cudaHostAlloc(&g->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
@@ -114,6 +127,8 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
                                      cudaMemcpyHostToDevice, st), "upload head")) != HW_OK ||
         (s = hw_cuda(cudaMemcpyAsync(g->d_rev, rev.data(), sizeof(int32_t) * g->num_arcs,
                                      cudaMemcpyHostToDevice, st), "upload rev")) != HW_OK ||
+        (regular && (s = hw_cuda(cudaMemcpyAsync(g->d_revE, revE.data(), sizeof(int32_t) * g->num_arcs,
+                                                 cudaMemcpyHostToDevice, st), "upload revE")) != HW_OK) ||
         (s = hw_cuda(cudaMemcpyAsync(g->d_blk, g->h_blk.data(), sizeof(int32_t) * g->h_blk.size(),
                                      cudaMemcpyHostToDevice, st), "upload blocks")) != HW_OK ||
         (s = hw_cuda(cudaMemcpyAsync(g->d_two_over_d, w.data(), sizeof(double) * w.size(),
@@ -132,6 +147,7 @@ extern "C" hw_status hw_graph_free(hw_graph *g)
     cudaFree(g->d_row_ptr);
     cudaFree(g->d_head);
     cudaFree(g->d_rev);
+    cudaFree(g->d_revE);
     cudaFree(g->d_blk);
     cudaFree(g->d_two_over_d);
     if (g->h_err) cudaFreeHost(g->h_err);

@@ -26,6 +26,10 @@ struct hw_graph {
     int32_t *d_row_ptr = nullptr;    // [n+1]
     int32_t *d_head = nullptr;       // [num_arcs]
     int32_t *d_rev = nullptr;        // [num_arcs]
+    // regular graphs (degree d >= 1): the reversal table of the edge-major
+    // layout E[j][v] = psi[v d + j]: revE[j n + v] = j' n + w where arc
+    // v d + j = (v, w) reverses to w d + j'; nullptr otherwise
+    int32_t *d_revE = nullptr;       // [num_arcs]
     int32_t *d_blk = nullptr;        // [nblk+1] first vertex of each block
     double *d_two_over_d = nullptr;  // [max_degree+1], 2/d (0 for d = 0): the Grover weight
     int *h_err = nullptr;            // zero-copy word: a kernel's bounded wait ran out of time
@@ -69,6 +73,10 @@ struct CoinedStep {
     double *rec_part;        // [slots][n_marked] or nullptr
     int64_t rec_slot;        // slot receiving the marked probability of `in`, or -1
 };
+// edge-major layout of regular graphs (see hw_graph::d_revE)
+bool coined_em_supported(const hw_graph *g, hw_coin coin, hw_dtype dt);
+hw_status launch_layout(const hw_graph *g, hw_dtype dt, const void *in, void *out, bool to_edge, cudaStream_t st);
+hw_status launch_coined_step_em(const hw_graph *g, hw_dtype dt, hw_coin coin, const CoinedStep &s, cudaStream_t st);
 hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const CoinedStep &s,
                              cudaStream_t st);
 hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coin, int batch,
