@@ -47,6 +47,9 @@ UNIT = "arc-updates/s"
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # measured on; a changed kernel reports null until it is measured again.
 TRAFFIC = {
+    # the 1024x1024 torus step (k_coined_em<R,4,grover>), one launch, cold L2
+    ("c128", "bbf1c30839e5040f7fedd718501bb72d6eba4d97"): 83898880 + 22641664,
+    ("c64", "bbf1c30839e5040f7fedd718501bb72d6eba4d97"): 50341376 + 2242048,
 }
 
 
