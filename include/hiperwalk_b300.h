@@ -281,7 +281,7 @@ hw_status hw_ctqw_evolve_sparse(const hw_graph *g, double gamma, const int32_t *
 typedef enum { HW_JOB_COINED = 0, HW_JOB_CTQW = 1 } hw_job_kind;
 
 typedef struct hw_job {
-    const hw_graph *graph;   /* resident graph; coined jobs need a regular graph, degree 1..32 */
+    const hw_graph *graph;   /* resident graph; coined jobs need a regular graph */
     int32_t kind;            /* hw_job_kind; coined jobs use the Grover coin */
     int32_t dt;              /* HW_C64 or HW_C128 */
     int64_t steps;           /* walk steps / applications of e^{-iH time} (>= 1) */

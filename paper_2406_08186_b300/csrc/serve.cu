@@ -48,6 +48,7 @@ struct SJob {
     const int32_t *row_ptr;
     const int32_t *head;
     const int32_t *rev;
+    const int32_t *revE;     // coined: edge-major reversal table (states are edge-major while resident)
     void *X[2];              // state ping-pong
     void *T[2];              // CTQW series terms
     double *rec;             // [steps][n_marked] per-marked partials (nullptr if no marks)
@@ -81,50 +82,6 @@ __device__ __forceinline__ int job_marked(const SJob &J, int v)
     for (int i = 0; i < J.n_marked; ++i)
         if (J.marked[i] == v) return i;
     return -1;
-}
-
-// one coined walk step for vertex v (regular degree d), step index w
-template <typename R>
-__device__ void serve_coined(const SJob &J, int64_t w, int v)
-{
-    using V = typename CxS<R>::T;
-    const V *__restrict__ in = static_cast<const V *>(J.X[w & 1]);
-    V *__restrict__ out = static_cast<V *>(J.X[(w + 1) & 1]);
-    const int d = J.d;
-    const int64_t s = int64_t(v) * d;
-    const int mi = job_marked(J, v);
-    if (mi >= 0) {
-        if (J.rec && w >= 1) {
-            double acc = 0.0;
-            for (int j = 0; j < d; ++j) {
-                const V p = in[s + j];
-                acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
-            }
-            J.rec[(w - 1) * J.n_marked + mi] = acc;
-        }
-        for (int j = 0; j < d; ++j) {
-            const V p = in[s + j];
-            V c;
-            c.x = -p.x;
-            c.y = -p.y;
-            out[J.rev[s + j]] = c;
-        }
-        return;
-    }
-    R sx = 0, sy = 0;
-    for (int j = 0; j < d; ++j) {
-        const V p = in[s + j];
-        sx += p.x;
-        sy += p.y;
-    }
-    const R f = R(J.two_over_d);
-    for (int j = 0; j < d; ++j) {
-        const V p = in[s + j];
-        V c;
-        c.x = fma(f, sx, -p.x);
-        c.y = fma(f, sy, -p.y);
-        out[J.rev[s + j]] = c;
-    }
 }
 
 // one Taylor term of a CTQW job for vertex v, sub-step index ls
@@ -168,17 +125,20 @@ __device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
         J.rec[w * J.n_marked + mi] = double(o.x) * double(o.x) + double(o.y) * double(o.y);
 }
 
-// The same step for a tile of vertices of a degree known at compile time:
-// the job's pointers and marked vertices are read once per tile, each thread
-// loads its vertex's D arcs and reversal indices before any arithmetic, and
-// the loops unroll.  Arithmetic and order are serve_coined's.
+// One coined step of the tile's vertices in the edge-major layout E[j][v]
+// (thread per vertex, degree D known at compile time): the job's pointers and
+// marked vertices are read once per tile, each thread loads its vertex's D
+// arcs (D row segments across the warp) and reversal entries before any
+// arithmetic.  The Grover sum runs in arc order from arc 0, one FMA per
+// component, as in the single-walk kernels.
 template <typename R, int D>
-__device__ void serve_coined_fixed(const SJob &Jg, int64_t w, int v0, int v1)
+__device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
 {
     using V = typename CxS<R>::T;
     const V *__restrict__ in = static_cast<const V *>(Jg.X[w & 1]);
     V *__restrict__ out = static_cast<V *>(Jg.X[(w + 1) & 1]);
-    const int32_t *__restrict__ rev = Jg.rev;
+    const int32_t *__restrict__ revE = Jg.revE;
+    const int64_t n = Jg.n;
     const int nm = Jg.n_marked;
     int mk[kMaxServeMarked];
 #pragma unroll
@@ -186,13 +146,12 @@ __device__ void serve_coined_fixed(const SJob &Jg, int64_t w, int v0, int v1)
     double *rec = Jg.rec;
     const R f = R(Jg.two_over_d);
     for (int v = v0 + int(threadIdx.x); v < v1; v += blockDim.x) {
-        const int64_t s = int64_t(v) * D;
         V p[D];
         int r[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            p[j] = in[s + j];
-            r[j] = rev[s + j];
+            p[j] = in[j * n + v];
+            r[j] = revE[j * n + v];
         }
         int mi = -1;
 #pragma unroll
@@ -214,9 +173,9 @@ __device__ void serve_coined_fixed(const SJob &Jg, int64_t w, int v0, int v1)
             }
             continue;
         }
-        R sx = 0, sy = 0;
+        R sx = p[0].x, sy = p[0].y;
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
+        for (int j = 1; j < D; ++j) {
             sx += p[j].x;
             sy += p[j].y;
         }
@@ -230,59 +189,62 @@ __device__ void serve_coined_fixed(const SJob &Jg, int64_t w, int v0, int v1)
     }
 }
 
-// A coined tile staged in shared memory: coalesced loads of the tile's arcs,
-// one sequential sum per vertex, then c = fma(2/d, sum, -psi) per arc -- the
-// same arithmetic as the single-job kernel, so results match it bit for bit.
+// The same for any degree: a pass for the sum and a pass for the outputs.
 template <typename R>
-__device__ void serve_coined_tile(const SJob &J, int64_t w, int v0, int v1, unsigned char *smem)
+__device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
 {
     using V = typename CxS<R>::T;
-    V *sp = reinterpret_cast<V *>(smem);                       // [kServeTileArcs]
-    V *ss = sp + kServeTileArcs;                                    // per-vertex sums
-    const V *__restrict__ in = static_cast<const V *>(J.X[w & 1]);
-    V *__restrict__ out = static_cast<V *>(J.X[(w + 1) & 1]);
-    const int d = J.d;
-    const int64_t a0 = int64_t(v0) * d;
-    const int na = (v1 - v0) * d;
-    for (int i = threadIdx.x; i < na; i += blockDim.x) sp[i] = in[a0 + i];
-    __syncthreads();
-    for (int lv = threadIdx.x; lv < v1 - v0; lv += blockDim.x) {
-        const int v = v0 + lv;
-        R sx = 0, sy = 0;
-        for (int j = 0; j < d; ++j) {
-            sx += sp[lv * d + j].x;
-            sy += sp[lv * d + j].y;
-        }
-        V sm;
-        sm.x = sx;
-        sm.y = sy;
-        ss[lv] = sm;
-        const int mi = job_marked(J, v);
-        if (mi >= 0 && J.rec && w >= 1) {
-            double acc = 0.0;
-            for (int j = 0; j < d; ++j) {
-                const V p = sp[lv * d + j];
-                acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+    const V *__restrict__ in = static_cast<const V *>(Jg.X[w & 1]);
+    V *__restrict__ out = static_cast<V *>(Jg.X[(w + 1) & 1]);
+    const int32_t *__restrict__ revE = Jg.revE;
+    const int64_t n = Jg.n;
+    const int d = Jg.d;
+    const int nm = Jg.n_marked;
+    int mk[kMaxServeMarked];
+#pragma unroll
+    for (int i = 0; i < kMaxServeMarked; ++i) mk[i] = (i < nm) ? Jg.marked[i] : -1;
+    double *rec = Jg.rec;
+    const R f = R(Jg.two_over_d);
+    for (int v = v0 + int(threadIdx.x); v < v1; v += blockDim.x) {
+        int mi = -1;
+#pragma unroll
+        for (int i = 0; i < kMaxServeMarked; ++i)
+            if (mk[i] == v) mi = i;
+        if (mi >= 0) {
+            if (rec && w >= 1) {
+                double acc = 0.0;
+                for (int j = 0; j < d; ++j) {
+                    const V p = in[j * n + v];
+                    acc += double(p.x) * double(p.x) + double(p.y) * double(p.y);
+                }
+                rec[(w - 1) * nm + mi] = acc;
             }
-            J.rec[(w - 1) * J.n_marked + mi] = acc;
+            for (int j = 0; j < d; ++j) {
+                const V p = in[j * n + v];
+                V c;
+                c.x = -p.x;
+                c.y = -p.y;
+                out[revE[j * n + v]] = c;
+            }
+            continue;
+        }
+        const V p0 = in[v];
+        R sx = p0.x, sy = p0.y;
+#pragma unroll 4
+        for (int j = 1; j < d; ++j) {
+            const V p = in[j * n + v];
+            sx += p.x;
+            sy += p.y;
+        }
+#pragma unroll 4
+        for (int j = 0; j < d; ++j) {
+            const V p = in[j * n + v];
+            V c;
+            c.x = fma(f, sx, -p.x);
+            c.y = fma(f, sy, -p.y);
+            out[revE[j * n + v]] = c;
         }
     }
-    __syncthreads();
-    const R f = R(J.two_over_d);
-    for (int i = threadIdx.x; i < na; i += blockDim.x) {
-        const int lv = i / d;
-        const V p = sp[i];
-        V c;
-        if (J.n_marked && job_marked(J, v0 + lv) >= 0) {
-            c.x = -p.x;
-            c.y = -p.y;
-        } else {
-            c.x = fma(f, ss[lv].x, -p.x);
-            c.y = fma(f, ss[lv].y, -p.y);
-        }
-        out[J.rev[a0 + i]] = c;
-    }
-    __syncthreads();
 }
 
 // Walk steps w0 .. w0 + ns - 1 (each q parts of m Taylor terms) of a local
@@ -387,7 +349,6 @@ __global__ void __launch_bounds__(kServeThreads)
 k_serve_step(const SJob *__restrict__ jobs, const Tile *__restrict__ tiles, const int *__restrict__ ntiles,
              const int64_t *__restrict__ tick, int sub)
 {
-    extern __shared__ __align__(16) unsigned char smem[];   // 2 * kServeTileArcs complex values
     const int nt = *ntiles;
     const int64_t now = *tick + sub;   // the tick advances once per round, after all its sub-steps
     pdl_trigger();
@@ -397,26 +358,18 @@ k_serve_step(const SJob *__restrict__ jobs, const Tile *__restrict__ tiles, cons
         const SJob &J = jobs[tl.job];
         const int64_t local = now - J.start_tick;
         if (local < 0 || local >= J.total_subs) continue;   // uniform over the CTA
-        if (J.kind == 0 && (J.d == 3 || J.d == 4 || J.d == 8)) {
-            // common degrees: fixed-degree path
+        if (J.kind == 0) {
+            // coined, edge-major: unrolled for the common degrees, two passes otherwise
             if (J.dt == HW_C128) {
-                if (J.d == 3) serve_coined_fixed<double, 3>(J, local, tl.v0, tl.v1);
-                else if (J.d == 4) serve_coined_fixed<double, 4>(J, local, tl.v0, tl.v1);
-                else serve_coined_fixed<double, 8>(J, local, tl.v0, tl.v1);
+                if (J.d == 3) serve_coined_em<double, 3>(J, local, tl.v0, tl.v1);
+                else if (J.d == 4) serve_coined_em<double, 4>(J, local, tl.v0, tl.v1);
+                else if (J.d == 8) serve_coined_em<double, 8>(J, local, tl.v0, tl.v1);
+                else serve_coined_em_rt<double>(J, local, tl.v0, tl.v1);
             } else {
-                if (J.d == 3) serve_coined_fixed<float, 3>(J, local, tl.v0, tl.v1);
-                else if (J.d == 4) serve_coined_fixed<float, 4>(J, local, tl.v0, tl.v1);
-                else serve_coined_fixed<float, 8>(J, local, tl.v0, tl.v1);
-            }
-        } else if (J.kind == 0 && J.d > 4) {
-            // other degrees above 4: coalesced loads through shared memory
-            if (J.dt == HW_C128) serve_coined_tile<double>(J, local, tl.v0, tl.v1, smem);
-            else serve_coined_tile<float>(J, local, tl.v0, tl.v1, smem);
-        } else if (J.kind == 0) {
-            // degree <= 4: a vertex's arcs are at most 64 contiguous bytes; read directly
-            for (int v = tl.v0 + threadIdx.x; v < tl.v1; v += blockDim.x) {
-                if (J.dt == HW_C128) serve_coined<double>(J, local, v);
-                else serve_coined<float>(J, local, v);
+                if (J.d == 3) serve_coined_em<float, 3>(J, local, tl.v0, tl.v1);
+                else if (J.d == 4) serve_coined_em<float, 4>(J, local, tl.v0, tl.v1);
+                else if (J.d == 8) serve_coined_em<float, 8>(J, local, tl.v0, tl.v1);
+                else serve_coined_em_rt<float>(J, local, tl.v0, tl.v1);
             }
         } else {
             for (int v = tl.v0 + threadIdx.x; v < tl.v1; v += blockDim.x) {
@@ -575,11 +528,8 @@ static hw_status server_capture(hw_server *s)
     if (st != HW_OK) return st;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    const int smem = 2 * kServeTileArcs * int(sizeof(double2));
-    st = hw_cuda(cudaFuncSetAttribute(k_serve_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-                 "cudaFuncSetAttribute(k_serve_step)");
-    if (st == HW_OK)
-        st = hw_cuda(cudaFuncSetAttribute(k_serve_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kLocalBytes),
+    const int smem = 0;
+    st = hw_cuda(cudaFuncSetAttribute(k_serve_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kLocalBytes),
                      "cudaFuncSetAttribute(k_serve_local)");
     if (st != HW_OK) {
         cudaStreamEndCapture(s->st, &g);
@@ -709,8 +659,8 @@ extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *
     if (job->steps < 1) return hw_fail(HW_EINVAL, "steps must be >= 1");
     if (job->n_marked < 0 || job->n_marked > kMaxServeMarked || (job->n_marked && !job->marked))
         return hw_fail(HW_EINVAL, "0..%d marked vertices", kMaxServeMarked);
-    if (job->kind == HW_JOB_COINED && (g->min_degree != g->max_degree || g->max_degree < 1 || g->max_degree > 32))
-        return hw_fail(HW_EUNSUPPORTED, "served coined jobs need a regular graph of degree 1..32");
+    if (job->kind == HW_JOB_COINED && (!g->d_revE || g->min_degree != g->max_degree || g->max_degree < 1))
+        return hw_fail(HW_EUNSUPPORTED, "served coined jobs need a regular graph");
     if (g->n >= (int64_t(1) << 30)) return hw_fail(HW_EUNSUPPORTED, "graph too large to serve");
     Job J;
     J.id = s->next_id++;
@@ -764,8 +714,10 @@ static hw_status rebuild_tiles(hw_server *s)
             s->h_local[nl++] = J.slot;
             continue;
         }
-        const int64_t step = (J.spec.kind == HW_JOB_COINED) ? std::max<int64_t>(1, kServeTileArcs / J.spec.graph->max_degree)
-                                                            : kTileVertices;
+        // coined: a vertex per thread, and at least kServeTileArcs arcs per tile
+        const int64_t step = (J.spec.kind == HW_JOB_COINED)
+                                 ? std::max<int64_t>(kServeThreads, kServeTileArcs / J.spec.graph->max_degree)
+                                 : kTileVertices;
         for (int64_t v0 = 0; v0 < J.n; v0 += step) {
             if (nt >= s->max_tiles) return hw_fail(HW_EUNSUPPORTED, "tile list overflow (%d tiles)", nt);
             Tile t;
@@ -802,6 +754,7 @@ static hw_status admit(hw_server *s, Job &J)
     D.row_ptr = g->d_row_ptr;
     D.head = g->d_head;
     D.rev = g->d_rev;
+    D.revE = g->d_revE;
     D.X[0] = dev;
     D.X[1] = dev + state;
     const int nstates = (J.spec.kind == HW_JOB_COINED || J.local) ? 2 : 4;
@@ -851,6 +804,12 @@ static hw_status retire(hw_server *s, Job &J)
     const int64_t final_parity = (J.spec.kind == HW_JOB_COINED || J.local) ? (J.spec.steps & 1)
                                                                             : ((J.spec.steps * J.q) & 1);
     const void *psi = D.X[final_parity];
+    if (J.spec.kind == HW_JOB_COINED) {
+        // back to the public arc order, into the other (free) state buffer
+        hw_status ls = launch_layout(g, dt, psi, D.X[1 - final_parity], false, s->st);
+        if (ls != HW_OK) return ls;
+        psi = D.X[1 - final_parity];
+    }
     hw_status st = launch_probability(J.spec.kind == HW_JOB_COINED ? g : nullptr, J.n, dt, 1, psi, d_prob, nullptr,
                                       s->st);
     if (st != HW_OK) return st;
