@@ -138,6 +138,38 @@ def test_record_stride(hw):
     assert np.max(np.abs(got["rec"] - rec_ref[3::4])) <= TOL128
 
 
+@pytest.mark.parametrize("name,g,coin", [
+    ("torus64_grover", synth.torus(64), 0),      # edge-major, unrolled (degree 4)
+    ("torus64_fourier", synth.torus(64), 1),
+    ("reg5", synth.random_regular(3001 * 2, 5, seed=3), 0),
+    ("Q9", synth.hypercube(9), 0),                # degree 9..16: arc-major lane groups
+    ("reg20", synth.random_regular(3000, 20, seed=4), 0),   # degree > 16: edge-major, two passes
+    ("Q9_fourier", synth.hypercube(9), 1),        # Fourier above degree 8: arc-major
+])
+def test_c64_regular_graph_paths(hw, name, g, coin):
+    # complex64 on every kernel path of a regular graph, against the FP64 oracle
+    ar = oracle.Arcs(*g)
+    psi0 = synth.random_state(ar.num_arcs, seed=21)
+    marked = [1, g[0] - 2]
+    ref, rec_ref = oracle.coined_evolve(ar, psi0, 60, coin_kind=coin, marked=marked, record=True)
+    got = run_gpu(hw, g, psi0, 60, coin=coin, marked=marked, dt=1, record=True)
+    assert np.max(np.abs(got["psi"] - ref)) < 2e-5
+    assert np.sum(np.abs(got["prob"] - oracle.prob_coined(ar, ref))) <= 1e-4
+    assert np.max(np.abs(got["rec"] - rec_ref)) < 1e-5
+
+
+@pytest.mark.parametrize("steps", [1, 2, 5])
+def test_in_place_regular_graph(hw, steps):
+    # the edge-major path with psi_in == psi_out
+    g = synth.random_regular(4000, 4, seed=13)
+    ar = oracle.Arcs(*g)
+    psi0 = synth.random_state(ar.num_arcs, seed=14)
+    ref = oracle.coined_evolve(ar, psi0, steps, marked=[0, 3999])
+    for inplace in (False, True):
+        got = run_gpu(hw, g, psi0, steps, marked=[0, 3999], inplace=inplace)
+        assert np.max(np.abs(got["psi"] - ref)) <= TOL128
+
+
 def test_c64_probability_l1_after_1000_steps(hw):
     g = synth.erdos_renyi(5000, 8 / 4999, seed=11)
     ar = oracle.Arcs(*g)
