@@ -459,6 +459,45 @@ def run_workload_torus64(args):
           flush=True)
 
 
+def run_workload_sampled(args):
+    """The 1024 x 1024 torus search sampled like simulate(range=(0, 3000, 100)): the
+    per-vertex probabilities of 30 states (states not kept) and the search curve, for
+    complex128 and complex64, against one plain 3000-step evolve of the same walk."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    n, eu, ev, row_ptr, col, m = workload()
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    stream = torch.cuda.current_stream()
+    res = {"workload": "torus1024_sampled", "metric": METRIC, "unit": UNIT, "range": [0, WALK_STEPS, 100]}
+    R = hw.sample_count(0, WALK_STEPS, 100)
+    for dt, name in ((hw.HW_C128, "c128"), (hw.HW_C64, "c64")):
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        psi0 = torch.full((G.num_arcs,), 1.0 / math.sqrt(G.num_arcs), dtype=cdt, device="cuda")
+        out = torch.empty_like(psi0)
+        prob = torch.empty((R, n), dtype=torch.float64, device="cuda")
+        steps_total = (R - 1) * 100
+        for _ in range(max(1, args.warmup)):
+            hw.hw_coined_sample(G, 0, [m], dt, 1, 0, WALK_STEPS, 100, psi0, None, prob)
+        torch.cuda.synchronize()
+        e = _events(4)
+        e[0].record(stream)
+        for _ in range(args.steps):
+            hw.hw_coined_sample(G, 0, [m], dt, 1, 0, WALK_STEPS, 100, psi0, None, prob)
+        e[1].record(stream)
+        for _ in range(args.steps):
+            hw.hw_coined_evolve(G, 0, [m], dt, 1, steps_total, psi0, out)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        t_s = e[0].elapsed_time(e[1]) / 1e3 / args.steps
+        t_p = e[1].elapsed_time(e[2]) / 1e3 / args.steps
+        curve, k, pmax = hw.success_curve(prob.cpu().numpy(), [m])
+        res[name] = {"samples": R, "value": G.num_arcs * steps_total / t_s, "ms_sampled": t_s * 1e3,
+                     "ms_plain_evolve": t_p * 1e3, "overhead": t_s / t_p - 1.0,
+                     "best_sample_step": k * 100, "best_p_m": pmax}
+    print(json.dumps(res), flush=True)
+    G.free()
+
+
 def serving_jobs(count, seed=6):
     """The serving mix: kind, graph family, size, steps, dtype and marks per job, all from
     SplitMix64(seed).  n = 2^k with k uniform in 10..20 for coined jobs and in 10..13 for
@@ -644,7 +683,7 @@ def main():
     ap.add_argument("--profile-tile", type=int, default=10)
     ap.add_argument("--workload", default="torus1024_search",
                     choices=["torus1024_search", "torus64_center", "hypercube12_ctqw", "er_batched",
-                             "serving"],
+                             "serving", "sampled"],
                     help="the default is the benchmarked workload; the others print their own line")
     ap.add_argument("--jobs", type=int, default=10000, help="serving: number of jobs")
     ap.add_argument("--baseline-jobs", type=int, default=200, help="serving: jobs timed on the plain path")
@@ -659,6 +698,8 @@ def main():
         run_workload_ctqw(args)
     elif args.workload == "torus64_center":
         run_workload_torus64(args)
+    elif args.workload == "sampled":
+        run_workload_sampled(args)
     elif args.workload == "serving":
         run_workload_serving(args)
     elif args.impl == "reference":

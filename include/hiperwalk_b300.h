@@ -154,6 +154,28 @@ hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marke
                            const hw_opts *opts, void *stream);
 
 /*
+ * hw_coined_sample -- the states of a coined walk at sampled times: the
+ * paper's simulate(range=(start, end, stride)) (Sec. 3.2, 4.2), which returns
+ * |psi(k)> for k = start, start + stride, ... < end, k counting walk steps,
+ * and its probability_distribution of each of them.
+ *   start, end, stride  0 <= start <= end, stride >= 1; the call produces
+ *                       R = ceil((end - start) / stride) samples (none when
+ *                       end == start)
+ *   psi_in              DEVICE [num_arcs][batch], the state at k = 0
+ *   states_out          DEVICE [R][num_arcs][batch] or NULL; must not overlap psi_in
+ *   prob_out            DEVICE double[R][n][batch] or NULL: per-vertex
+ *                       probabilities of each sample (summed in double)
+ *   coin, marked, dt, batch, opts as in hw_coined_evolve (no record)
+ * Results equal hw_coined_evolve's for the same step counts.  Scratch: up to
+ * four state-sized buffers from the stream-ordered allocator.
+ * Errors: HW_EINVAL, HW_EUNSUPPORTED, HW_ENOMEM, HW_ECUDA, HW_ETIMEDOUT.
+ */
+hw_status hw_coined_sample(const hw_graph *g, hw_coin coin, const int32_t *marked, int32_t n_marked,
+                           hw_dtype dt, int32_t batch, int64_t start, int64_t end, int64_t stride,
+                           const void *psi_in, void *states_out, double *prob_out,
+                           const hw_opts *opts, void *stream);
+
+/*
  * hw_ctqw_expm -- U = e^{-i H time} with H = -gamma A - sum_{m in M} |m><m|
  * (Sec. 3.1), dense, by a truncated Taylor series with scaling and squaring:
  * U = (sum_{k<=m} (-i H time/2^s)^k / k!)^(2^s).
@@ -195,6 +217,20 @@ hw_status hw_ctqw_plan(const hw_graph *g, double gamma, const int32_t *marked, i
 hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32_t batch, int64_t steps,
                          const void *psi_in, void *psi_out, const int32_t *marked,
                          int32_t n_marked, double *record, const hw_opts *opts, void *stream);
+
+/*
+ * hw_ctqw_sample -- U^k psi_in for k = start, start + stride, ... < end (the
+ * paper's simulate(range=...) of a continuous-time walk, Sec. 3.1, 4.1),
+ * k counting applications of U = e^{-iH dt}.
+ *   U, n, dt, batch, opts  as in hw_ctqw_evolve
+ *   start, end, stride     as in hw_coined_sample
+ *   states_out             DEVICE [R][n][batch] or NULL; must not overlap psi_in
+ *   prob_out               DEVICE double[R][n][batch] or NULL
+ * Errors: HW_EINVAL, HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_ctqw_sample(const void *U, int64_t n, hw_dtype dt, int32_t batch, int64_t start, int64_t end,
+                         int64_t stride, const void *psi_in, void *states_out, double *prob_out,
+                         const hw_opts *opts, void *stream);
 
 /*
  * hw_probability -- per-vertex probabilities, summed in double precision.

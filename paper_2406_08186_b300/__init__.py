@@ -30,7 +30,7 @@ EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free"
            "hw_probability_noalloc", "hw_gemm_tc", "hw_ctqw_evolve_sparse",
            "hw_server_create", "hw_server_submit", "hw_server_run", "hw_server_poll",
            "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_trim_scratch", "hw_last_error",
-           "hw_version")
+           "hw_version", "hw_coined_sample", "hw_ctqw_sample")
 
 
 class HWError(RuntimeError):
@@ -85,6 +85,10 @@ def lib():
         L.hw_ctqw_expm.restype = st
         L.hw_ctqw_evolve.argtypes = [P, i64, st, i32, i64, P, P, P, i32, P, ctypes.POINTER(hw_opts), P]
         L.hw_ctqw_evolve.restype = st
+        L.hw_coined_sample.argtypes = [P, st, P, i32, st, i32, i64, i64, i64, P, P, P, ctypes.POINTER(hw_opts), P]
+        L.hw_coined_sample.restype = st
+        L.hw_ctqw_sample.argtypes = [P, i64, st, i32, i64, i64, i64, P, P, P, ctypes.POINTER(hw_opts), P]
+        L.hw_ctqw_sample.restype = st
         L.hw_probability.argtypes = [P, i64, st, i32, P, P, P, P]
         L.hw_probability.restype = st
         L.hw_probability_noalloc.argtypes = [P, i64, st, i32, P, P, P, P]
@@ -283,6 +287,40 @@ def hw_ctqw_evolve(U, n: int, dt: int, batch: int, steps: int, psi_in, psi_out, 
                                 _dev(psi_in, _CPLX[dt]), _dev(psi_out, _CPLX[dt]),
                                 None if m is None else m.ctypes.data_as(ctypes.c_void_p), nm,
                                 _dev(record, "float64"), _opts(opts), _stream(stream)))
+
+
+def hw_coined_sample(g: Graph, coin: int, marked, dt: int, batch: int, start: int, end: int, stride: int,
+                     psi_in, states_out=None, prob_out=None, opts=None, stream=None):
+    """States (and per-vertex probabilities) after start, start + stride, ... < end steps."""
+    m, nm = _host_i32(marked)
+    _check(lib().hw_coined_sample(g, int(coin), None if m is None else m.ctypes.data_as(ctypes.c_void_p), nm,
+                                  int(dt), int(batch), int(start), int(end), int(stride), _dev(psi_in, _CPLX[dt]),
+                                  _dev(states_out, _CPLX[dt]), _dev(prob_out, "float64"), _opts(opts),
+                                  _stream(stream)))
+
+
+def hw_ctqw_sample(U, n: int, dt: int, batch: int, start: int, end: int, stride: int, psi_in, states_out=None,
+                   prob_out=None, opts=None, stream=None):
+    """U^k psi_in for k = start, start + stride, ... < end (and their probabilities)."""
+    _check(lib().hw_ctqw_sample(_dev(U, _CPLX[dt]), int(n), int(dt), int(batch), int(start), int(end),
+                                int(stride), _dev(psi_in, _CPLX[dt]), _dev(states_out, _CPLX[dt]),
+                                _dev(prob_out, "float64"), _opts(opts), _stream(stream)))
+
+
+def sample_count(start: int, end: int, stride: int) -> int:
+    """Number of samples of range(start, end, stride)."""
+    return max(0, (end - start + stride - 1) // stride)
+
+
+def success_curve(prob, marked):
+    """Success probability of a search at each sample (the sum over the marked
+    vertices of the per-vertex probabilities, prob shaped [samples][n]) and the
+    sample where it peaks: (curve, index of the maximum, maximum).  Host only."""
+    import numpy as np
+    p = np.asarray(prob, dtype=np.float64)
+    curve = p[:, np.asarray(list(marked), dtype=np.int64)].sum(axis=1)
+    k = int(np.argmax(curve)) if curve.size else -1
+    return curve, k, (float(curve[k]) if curve.size else 0.0)
 
 
 def hw_probability(g, n: int, dt: int, batch: int, psi, prob_out=None, norm_out=None, stream=None):

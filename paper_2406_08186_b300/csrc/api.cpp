@@ -297,6 +297,91 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
     return HW_OK;
 }
 
+// Sampled evolution (the paper's simulate(range=(start, end, stride))): the
+// states after start, start + stride, ... < end walk steps.  On the
+// edge-major path the state stays edge-major between samples and only each
+// sample is transposed out; otherwise every segment is one hw_coined_evolve.
+extern "C" hw_status hw_coined_sample(const hw_graph *g, hw_coin coin, const int32_t *marked, int32_t n_marked,
+                                      hw_dtype dt, int32_t batch, int64_t start, int64_t end, int64_t stride,
+                                      const void *psi_in, void *states_out, double *prob_out,
+                                      const hw_opts *opts, void *stream)
+{
+    hw_clear_error();
+    if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
+    if (start < 0 || end < start || stride < 1) return hw_fail(HW_EINVAL, "need 0 <= start <= end and stride >= 1");
+    if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
+    if (!psi_in) return hw_fail(HW_EINVAL, "psi_in is NULL");
+    const int64_t R = (end - start + stride - 1) / stride;
+    if (R == 0) return HW_OK;
+    const size_t esz = cplx_bytes(dt);
+    const size_t bytes = size_t(g->num_arcs) * batch * esz;
+    const size_t pbytes = size_t(g->n) * batch;   // doubles per probability sample
+    if (states_out) {
+        const char *ip = static_cast<const char *>(psi_in);
+        const char *op = static_cast<const char *>(states_out);
+        if (ip < op + bytes * R && op < ip + bytes) return hw_fail(HW_EINVAL, "psi_in overlaps states_out");
+        if ((uintptr_t)states_out % esz) return hw_fail(HW_EINVAL, "states_out misaligned");
+    }
+    hw_status s = check_device(g);
+    if (s != HW_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Scratch buf(st);
+    // where sample r goes when the caller keeps no states
+    auto slot = [&](int64_t r) -> void * {
+        return states_out ? static_cast<void *>(static_cast<char *>(states_out) + bytes * size_t(r))
+                          : static_cast<void *>(static_cast<char *>(buf.p) + bytes * size_t(r & 1));
+    };
+    const bool em = batch == 1 && g->num_arcs > 0 && coined_em_supported(g, coin, dt);
+    if ((s = buf.get((states_out ? 0 : 2 * bytes) + (em ? 2 * bytes : 0), "scratch allocation (samples)")) != HW_OK)
+        return s;
+    if (em) {
+        if (coin != HW_COIN_GROVER && coin != HW_COIN_FOURIER) return hw_fail(HW_EINVAL, "unknown coin");
+        MarkedList mk;
+        if ((s = make_marked(marked, n_marked, g->n, st, &mk)) != HW_OK) return s;
+        struct FreeMarked {
+            MarkedList &m; cudaStream_t st;
+            ~FreeMarked() { free_marked(m, st); }
+        } release_marked{mk, st};
+        char *eb = static_cast<char *>(buf.p) + (states_out ? 0 : 2 * bytes);
+        void *E[2] = {eb, eb + bytes};
+        if ((s = launch_layout(g, dt, psi_in, E[0], true, st)) != HW_OK) return s;
+        int cur = 0;
+        int64_t t = 0;
+        for (int64_t r = 0; r < R; ++r) {
+            for (const int64_t tr = start + r * stride; t < tr; ++t) {
+                CoinedStep cs;
+                cs.in = E[cur];
+                cs.out = E[1 - cur];
+                cs.marked = mk;
+                cs.rec_part = nullptr;
+                cs.rec_slot = -1;
+                if ((s = launch_coined_step_em(g, dt, coin, cs, st)) != HW_OK) return s;
+                cur = 1 - cur;
+            }
+            if ((s = launch_layout(g, dt, E[cur], slot(r), false, st)) != HW_OK) return s;
+            if (prob_out && (s = launch_probability(g, g->n, dt, batch, slot(r), prob_out + pbytes * r, nullptr, st)) !=
+                                HW_OK)
+                return s;
+        }
+        return HW_OK;
+    }
+    const void *src = psi_in;
+    int64_t t = 0;
+    for (int64_t r = 0; r < R; ++r) {
+        const int64_t tr = start + r * stride;
+        if ((s = hw_coined_evolve(g, coin, marked, n_marked, dt, batch, tr - t, src, slot(r), nullptr, opts,
+                                  stream)) != HW_OK)
+            return s;
+        if (prob_out && (s = launch_probability(g, g->n, dt, batch, slot(r), prob_out + pbytes * r, nullptr, st)) !=
+                            HW_OK)
+            return s;
+        src = slot(r);
+        t = tr;
+    }
+    return HW_OK;
+}
+
 extern "C" hw_status hw_probability(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batch,
                                     const void *psi, double *prob_out, double *norm_out, void *stream)
 {

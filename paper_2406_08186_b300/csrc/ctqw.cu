@@ -715,3 +715,46 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
         if ((s = launch_record_finalize(rec_part, n_marked, slots, batch, record, st)) != HW_OK) return s;
     return HW_OK;
 }
+
+// Sampled CTQW (the paper's simulate(range=...)): U^t psi for t = start,
+// start + stride, ... < end applications, each segment one hw_ctqw_evolve.
+extern "C" hw_status hw_ctqw_sample(const void *U, int64_t n, hw_dtype dt, int32_t batch, int64_t start,
+                                    int64_t end, int64_t stride, const void *psi_in, void *states_out,
+                                    double *prob_out, const hw_opts *opts, void *stream)
+{
+    hw_clear_error();
+    if (start < 0 || end < start || stride < 1) return hw_fail(HW_EINVAL, "need 0 <= start <= end and stride >= 1");
+    if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
+    if (n < 1 || batch < 1) return hw_fail(HW_EINVAL, "bad n or batch");
+    if (!U || !psi_in) return hw_fail(HW_EINVAL, "NULL buffer");
+    const int64_t R = (end - start + stride - 1) / stride;
+    if (R == 0) return HW_OK;
+    const size_t bytes = size_t(n) * batch * cplx_bytes(dt);
+    if (states_out) {
+        const char *ip = static_cast<const char *>(psi_in);
+        const char *op = static_cast<const char *>(states_out);
+        if (ip < op + bytes * R && op < ip + bytes) return hw_fail(HW_EINVAL, "psi_in overlaps states_out");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf buf(st);
+    hw_status s;
+    if (!states_out && (s = buf.get(2 * bytes, "scratch allocation (samples)")) != HW_OK) return s;
+    auto slot = [&](int64_t r) -> void * {
+        return states_out ? static_cast<void *>(static_cast<char *>(states_out) + bytes * size_t(r))
+                          : static_cast<void *>(buf.as<char>() + bytes * size_t(r & 1));
+    };
+    const void *src = psi_in;
+    int64_t t = 0;
+    for (int64_t r = 0; r < R; ++r) {
+        const int64_t tr = start + r * stride;
+        if ((s = hw_ctqw_evolve(U, n, dt, batch, tr - t, src, slot(r), nullptr, 0, nullptr, opts, stream)) != HW_OK)
+            return s;
+        if (prob_out &&
+            (s = launch_probability(nullptr, n, dt, batch, slot(r), prob_out + size_t(n) * batch * r, nullptr, st)) !=
+                HW_OK)
+            return s;
+        src = slot(r);
+        t = tr;
+    }
+    return HW_OK;
+}
