@@ -498,6 +498,49 @@ def run_workload_sampled(args):
     G.free()
 
 
+def run_workload_sparse_ctqw(args):
+    """Continuous-time walk by the sparse action of e^{-iH dt} (no dense U) on the
+    2^20-vertex hypercube: gamma = 1/20, one seeded mark, dt = 0.1, uniform start,
+    20 walk steps of m Taylor terms each; complex128 and complex64."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    k = 20
+    n, eu, ev = synth.hypercube(k)
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    m = synth.seeded_vertex(3, n)
+    gamma, tstep, walk = 1.0 / k, 0.1, 20
+    deg, sq = hw.hw_ctqw_plan(G, gamma, [m], tstep)
+    terms = walk * deg * (1 << sq)
+    stream = torch.cuda.current_stream()
+    res = {"workload": "hypercube20_sparse_ctqw", "n": n, "arcs": G.num_arcs, "walk_steps": walk,
+           "taylor_degree": deg, "terms": terms}
+    peak, _ = measured_peaks()
+    for dt, name, esz in ((hw.HW_C128, "c128", 16), (hw.HW_C64, "c64", 8)):
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        x = torch.full((n,), 1.0 / math.sqrt(n), dtype=cdt, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(max(1, args.warmup)):
+            hw.hw_ctqw_evolve_sparse(G, gamma, [m], tstep, dt, 1, 2, x, y)
+        torch.cuda.synchronize()
+        e = _events(2)
+        e[0].record(stream)
+        for _ in range(args.steps):
+            hw.hw_ctqw_evolve_sparse(G, gamma, [m], tstep, dt, 1, walk, x, y)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        t = e[0].elapsed_time(e[1]) / 1e3 / args.steps
+        # compulsory bytes per term: row_ptr and head once, t_{k-1} once (its
+        # neighbour gathers hit L2), t_k written, the sum (or x) read and written
+        term_bytes = 4 * (n + 1) + 4 * G.num_arcs + 4 * esz * n
+        per_term = t / terms
+        res[name] = {"ms": t * 1e3, "us_per_term": per_term * 1e6, "gathers_per_s": (G.num_arcs + n) / per_term,
+                     "bytes_per_term": term_bytes, "achieved_gbs": term_bytes / per_term / 1e9,
+                     "frac_hbm": term_bytes / per_term / 1e9 / peak}
+    print(json.dumps(res), flush=True)
+    G.free()
+
+
 def serving_jobs(count, seed=6):
     """The serving mix: kind, graph family, size, steps, dtype and marks per job, all from
     SplitMix64(seed).  n = 2^k with k uniform in 10..20 for coined jobs and in 10..13 for
@@ -683,7 +726,7 @@ def main():
     ap.add_argument("--profile-tile", type=int, default=10)
     ap.add_argument("--workload", default="torus1024_search",
                     choices=["torus1024_search", "torus64_center", "hypercube12_ctqw", "er_batched",
-                             "serving", "sampled"],
+                             "serving", "sampled", "sparse_ctqw"],
                     help="the default is the benchmarked workload; the others print their own line")
     ap.add_argument("--jobs", type=int, default=10000, help="serving: number of jobs")
     ap.add_argument("--baseline-jobs", type=int, default=200, help="serving: jobs timed on the plain path")
@@ -700,6 +743,8 @@ def main():
         run_workload_torus64(args)
     elif args.workload == "sampled":
         run_workload_sampled(args)
+    elif args.workload == "sparse_ctqw":
+        run_workload_sparse_ctqw(args)
     elif args.workload == "serving":
         run_workload_serving(args)
     elif args.impl == "reference":
