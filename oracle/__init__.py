@@ -17,6 +17,8 @@ Readings where the paper is silent (stated here and in the design notes):
     the positions of the arcs inside the vertex's block (basis order).
   * Marked vertex in the coined walk: its coin block is -I.
   * One coined step applies the coin first, then the shift (U = S C).
+  * Persistent shift (torus only): the walker keeps its direction of motion,
+    arc (v, w) -> arc (w, u) with u - w = w - v on the torus's coordinates.
 """
 from __future__ import annotations
 
@@ -65,6 +67,10 @@ def _load():
         lib.oracle_coin.restype = None
         lib.oracle_shift.argtypes = [i64, P, P, P, P]
         lib.oracle_shift.restype = None
+        lib.oracle_shift_persistent_torus.argtypes = [i64, i64, P, P, P, P]
+        lib.oracle_shift_persistent_torus.restype = None
+        lib.oracle_coined_evolve_persistent_torus.argtypes = [i64, i64, P, P, ctypes.c_int, P, P, i64, P]
+        lib.oracle_coined_evolve_persistent_torus.restype = ctypes.c_int
         lib.oracle_prob_coined.argtypes = [i64, P, P, P]
         lib.oracle_prob_coined.restype = None
         lib.oracle_coined_evolve.argtypes = [i64, P, P, ctypes.c_int, P, P, i64, P]
@@ -133,14 +139,31 @@ def shift(arcs: Arcs, psi: np.ndarray) -> np.ndarray:
     return out
 
 
+def shift_persistent_torus(arcs: Arcs, L1: int, L2: int, psi: np.ndarray) -> np.ndarray:
+    """The persistent shift of the L1 x L2 torus (vertex x*L2 + y): arc (v, w) -> (w, w + (w - v))."""
+    assert arcs.n == L1 * L2
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.empty_like(psi)
+    _load().oracle_shift_persistent_torus(int(L1), int(L2), _p(arcs.row_ptr), _p(arcs.head), _p(psi), _p(out))
+    return out
+
+
 def coined_evolve(arcs: Arcs, psi0: np.ndarray, steps: int, coin_kind: int = GROVER,
-                  marked=None, record: bool = False):
-    """(S C)^steps psi0; with ``record`` also the marked-vertex probability after each step."""
+                  marked=None, record: bool = False, persistent_torus=None):
+    """(S C)^steps psi0; with ``record`` also the marked-vertex probability after each step.
+    ``persistent_torus = (L1, L2)`` takes the torus's persistent shift for S instead of
+    the flip-flop shift."""
     psi = np.array(psi0, dtype=np.complex128, copy=True)
     rec = np.zeros(max(steps, 1), dtype=np.float64) if record else None
     flags = arcs.flags(marked) if marked is not None and len(marked) else None
-    rc = _load().oracle_coined_evolve(arcs.n, _p(arcs.row_ptr), _p(arcs.head), coin_kind,
-                                      _p(flags), _p(psi), int(steps), _p(rec))
+    if persistent_torus is not None:
+        L1, L2 = persistent_torus
+        assert arcs.n == L1 * L2
+        rc = _load().oracle_coined_evolve_persistent_torus(int(L1), int(L2), _p(arcs.row_ptr), _p(arcs.head),
+                                                           coin_kind, _p(flags), _p(psi), int(steps), _p(rec))
+    else:
+        rc = _load().oracle_coined_evolve(arcs.n, _p(arcs.row_ptr), _p(arcs.head), coin_kind,
+                                          _p(flags), _p(psi), int(steps), _p(rec))
     if rc != 0:
         raise MemoryError("oracle_coined_evolve")
     if record:

@@ -167,6 +167,30 @@ void oracle_shift(int64_t n, const int64_t *row_ptr, const int32_t *head, const 
     }
 }
 
+/* Persistent shift on the L1 x L2 torus (Sec. 3.2: the persistent shift that
+ * the Grid class offers, where the walker keeps its direction): the amplitude
+ * of arc (v, w) moves to arc (w, u), u being one more step from w in the
+ * direction that led from v to w.  Vertex v = x L2 + y; the direction is the
+ * difference of coordinates modulo L1 and L2 (L1, L2 >= 3, so it is one of
+ * +-1 along exactly one axis). */
+void oracle_shift_persistent_torus(int64_t L1, int64_t L2, const int64_t *row_ptr, const int32_t *head,
+                                   const cplx *psi, cplx *out)
+{
+    int64_t n = L1 * L2;
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t xv = v / L2, yv = v % L2;
+        for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) {
+            int64_t w = head[a];
+            int64_t xw = w / L2, yw = w % L2;
+            int64_t dx = (xw - xv + L1) % L1, dy = (yw - yv + L2) % L2;
+            int64_t u = ((xw + dx) % L1) * L2 + (yw + dy) % L2;
+            int64_t b = arc_in_row(row_ptr, head, w, u);
+            out[b] = psi[a];
+        }
+    }
+}
+
 /* p_v = sum over arcs (v, w) of |<v,w|psi>|^2 (Sec. 3.2). */
 void oracle_prob_coined(int64_t n, const int64_t *row_ptr, const cplx *psi, double *p)
 {
@@ -206,6 +230,24 @@ int oracle_coined_evolve(int64_t n, const int64_t *row_ptr, const int32_t *head,
     for (int64_t t = 1; t <= steps; ++t) {
         oracle_coin(n, row_ptr, coin, marked, psi, tmp);
         oracle_shift(n, row_ptr, head, tmp, psi);
+        if (record && marked) record[t - 1] = marked_prob_coined(n, row_ptr, marked, psi);
+    }
+    free(tmp);
+    return 0;
+}
+
+/* The same evolution with the persistent shift of the L1 x L2 torus in place
+ * of the flip-flop shift. */
+int oracle_coined_evolve_persistent_torus(int64_t L1, int64_t L2, const int64_t *row_ptr,
+                                          const int32_t *head, int coin, const uint8_t *marked,
+                                          cplx *psi, int64_t steps, double *record)
+{
+    int64_t n = L1 * L2, num = row_ptr[n];
+    cplx *tmp = malloc(sizeof(cplx) * (size_t)(num > 0 ? num : 1));
+    if (!tmp) return -4;
+    for (int64_t t = 1; t <= steps; ++t) {
+        oracle_coin(n, row_ptr, coin, marked, psi, tmp);
+        oracle_shift_persistent_torus(L1, L2, row_ptr, head, tmp, psi);
         if (record && marked) record[t - 1] = marked_prob_coined(n, row_ptr, marked, psi);
     }
     free(tmp);

@@ -69,6 +69,17 @@ def torus(L: int):
     return L * L, np.concatenate([v, v]), np.concatenate([right, up])
 
 
+def torus_rect(L1: int, L2: int):
+    """L1 x L2 torus, vertex v = x*L2 + y, edges to (x+1 mod L1, y) and (x, y+1 mod L2)."""
+    if L1 < 3 or L2 < 3:
+        raise ValueError("torus needs L1, L2 >= 3")
+    v = np.arange(L1 * L2, dtype=np.int64)
+    x, y = v // L2, v % L2
+    down = ((x + 1) % L1) * L2 + y
+    right = x * L2 + (y + 1) % L2
+    return L1 * L2, np.concatenate([v, v]), np.concatenate([down, right])
+
+
 def cycle(N: int):
     if N < 3:
         raise ValueError("cycle needs N >= 3")

@@ -26,6 +26,10 @@ MUTATIONS = {
     "marked_plus_identity": ("c = (j == k) ? -1.0 : 0.0;", "c = (j == k) ? 1.0 : 0.0;"),
     "shift_identity": ("int64_t b = arc_in_row(row_ptr, head, head[a], v);",
                        "int64_t b = arc_in_row(row_ptr, head, v, head[a]);"),
+    "persistent_turns_back": ("int64_t u = ((xw + dx) % L1) * L2 + (yw + dy) % L2;",
+                              "int64_t u = ((xw - dx + L1) % L1) * L2 + (yw - dy + L2) % L2;"),
+    "persistent_axes_swapped": ("int64_t u = ((xw + dx) % L1) * L2 + (yw + dy) % L2;",
+                                "int64_t u = ((xw + dy) % L1) * L2 + (yw + dx) % L2;"),
     "rev_self": ("rev[a] = find_arc(arcs, num, arcs[a].head, arcs[a].tail);",
                  "rev[a] = find_arc(arcs, num, arcs[a].tail, arcs[a].head);"),
     "ham_gamma_sign": ("acc = -gamma * acc;", "acc = gamma * acc;"),
@@ -52,6 +56,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     env = dict(os.environ, HW_ORACLE_LIB_OVERRIDE=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_coined.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_ctqw.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_ctqw.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_persistent.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "planted mistake %r was not caught:\n%s" % (name, r.stdout[-2000:])
