@@ -60,9 +60,25 @@ def workload():
     return n, eu, ev, row_ptr, col, m
 
 
-def coin_shift_bytes(n, arcs, esz):
-    """Algorithmic bytes of one coin+shift launch: read psi and rev, write psi, read row_ptr."""
-    return arcs * (2 * esz + 4) + 4 * (n + 1)
+def kernel_source_hash():
+    """SHA-1 of the sources of the coin+shift kernels (the ncu traffic below is
+    valid only for the kernels it was taken on)."""
+    h = hashlib.sha1()
+    for f in ("coined.cu", "family.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2406_08186_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def coin_shift_bytes(arcs, esz, index_free):
+    """Algorithmic bytes of one edge-major coin+shift launch: read and write the
+    state, plus the reversal table unless the positions come from the labels."""
+    return arcs * (2 * esz + (0 if index_free else 4))
+
+
+# FP64 operations of one Grover step of a degree-4 vertex, per component:
+# three adds for the sum, four FMAs (2/d) S - psi_j
+FP64_OPS_PER_VERTEX_D4 = 2 * (3 + 4)
 
 
 def measured_peaks():
@@ -236,6 +252,10 @@ def run_ours(args):
         return total, evolve
 
     peak, peak_src = measured_peaks()
+    fp64_peak = hw.hw_measure_fp64()
+    l2_peak = hw.hw_measure_l2()
+    kind, _ = hw.hw_graph_structure(G)
+    index_free = kind == hw.HW_GRAPH_TORUS   # the default addressing on a recognised torus
     b128 = make(hw.HW_C128)
     with Clocks(local) as clk:
         t128, ev128 = timed(b128)
@@ -287,10 +307,10 @@ def run_ours(args):
     value = work / t128
     per_launch128 = ev128 / (args.steps * WALK_STEPS)
     per_launch64 = ev64 / (args.steps * WALK_STEPS)
-    bytes128 = coin_shift_bytes(n, arcs, 16)
-    bytes64 = coin_shift_bytes(n, arcs, 8)
-    src_hash = hashlib.sha1(open(os.path.join(ROOT, "paper_2406_08186_b300", "csrc", "coined.cu"),
-                                 "rb").read()).hexdigest()
+    bytes128 = coin_shift_bytes(arcs, 16, index_free)
+    bytes64 = coin_shift_bytes(arcs, 8, index_free)
+    ops128 = FP64_OPS_PER_VERTEX_D4 * n
+    src_hash = kernel_source_hash()
     ach128 = bytes128 / per_launch128 / 1e9
     ach64 = bytes64 / per_launch64 / 1e9
     line = {
@@ -301,18 +321,24 @@ def run_ours(args):
                    "coin": "grover", "marked": m, "state": "complex128", "record": "p_m(t) every step",
                    "l2": "256 MiB written between timed steps; working set 151 MB > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "kernel": "k_coined_em<double,4,grover>",
-                     "achieved": ach128, "peak": peak, "unit": "GB/s", "frac": ach128 / peak,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src,
-                     "bytes_per_launch": bytes128, "launch_us": per_launch128 * 1e6,
-                     "traffic": TRAFFIC.get(("c128", src_hash))},
+        "roofline": {"bound": "fp64",
+                     "kernel": "k_coined_em<double,4,grover,%s>" % ("torus" if index_free else "table"),
+                     "achieved": ops128 / per_launch128, "peak": fp64_peak, "unit": "FP64 op/s",
+                     "frac": ops128 / per_launch128 / fp64_peak,
+                     "peak_source": "hw_measure_fp64 (FMA chains on this GPU); nominal 0.625e12",
+                     "ops_per_launch": ops128, "launch_us": per_launch128 * 1e6,
+                     "traffic": TRAFFIC.get(("c128", src_hash)),
+                     "hbm": {"achieved": ach128, "peak": peak, "unit": "GB/s", "frac": ach128 / peak,
+                             "bytes_per_launch": bytes128,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}},
         "c64_mixed": {"value": work / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / args.steps,
                       "dtype": "f32 (fp64 probability sums)",
-                      "roofline": {"bound": "hbm", "achieved": ach64, "peak": peak, "unit": "GB/s",
-                                   "frac": ach64 / peak, "bytes_per_launch": bytes64,
+                      "roofline": {"bound": "l2", "achieved": ach64, "peak": l2_peak, "unit": "GB/s",
+                                   "frac": ach64 / l2_peak, "bytes_per_launch": bytes64,
+                                   "peak_source": "hw_measure_l2 (32 MB copy, L2-resident, read + write)",
                                    "launch_us": per_launch64 * 1e6,
                                    "traffic": TRAFFIC.get(("c64", src_hash)),
-                                   "note": "working set 88 MB fits in L2"}},
+                                   "note": "the two 32 MB state buffers stay in the 126 MB L2"}},
         "e2e": {"value": work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": arcs * 16,
                 "d2h_bytes_per_step": n * 8 + WALK_STEPS * 8},
         "gpu_launches": launches_per_run * args.steps,
@@ -498,10 +524,16 @@ def run_workload_sampled(args):
     G.free()
 
 
+# nominal FP64 rate of the B300 (1.25 TFLOP/s): 0.625e12 FP64 pipe operations
+# (FMA, add or multiply) per second
+FP64_OPS_NOMINAL = 0.625e12
+
+
 def run_workload_sparse_ctqw(args):
     """Continuous-time walk by the sparse action of e^{-iH dt} (no dense U) on the
     2^20-vertex hypercube: gamma = 1/20, one seeded mark, dt = 0.1, uniform start,
-    20 walk steps of m Taylor terms each; complex128 and complex64."""
+    20 walk steps of m Taylor terms each; complex128 and complex64, with the
+    neighbours computed from the labels (default) and read from the CSR."""
     import torch
     import paper_2406_08186_b300 as hw
     k = 20
@@ -520,23 +552,34 @@ def run_workload_sparse_ctqw(args):
         cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
         x = torch.full((n,), 1.0 / math.sqrt(n), dtype=cdt, device="cuda")
         y = torch.empty_like(x)
-        for _ in range(max(1, args.warmup)):
-            hw.hw_ctqw_evolve_sparse(G, gamma, [m], tstep, dt, 1, 2, x, y)
-        torch.cuda.synchronize()
-        e = _events(2)
-        e[0].record(stream)
-        for _ in range(args.steps):
-            hw.hw_ctqw_evolve_sparse(G, gamma, [m], tstep, dt, 1, walk, x, y)
-        e[1].record(stream)
-        torch.cuda.synchronize()
-        t = e[0].elapsed_time(e[1]) / 1e3 / args.steps
-        # compulsory bytes per term: row_ptr and head once, t_{k-1} once (its
-        # neighbour gathers hit L2), t_k written, the sum (or x) read and written
-        term_bytes = 4 * (n + 1) + 4 * G.num_arcs + 4 * esz * n
-        per_term = t / terms
-        res[name] = {"ms": t * 1e3, "us_per_term": per_term * 1e6, "gathers_per_s": (G.num_arcs + n) / per_term,
-                     "bytes_per_term": term_bytes, "achieved_gbs": term_bytes / per_term / 1e9,
-                     "frac_hbm": term_bytes / per_term / 1e9 / peak}
+        for addressing, tag in ((0, ""), (1, "_csr")):
+            opts = {"addressing": addressing}
+            for _ in range(max(1, args.warmup)):
+                hw.hw_ctqw_evolve_sparse(G, gamma, [m], tstep, dt, 1, 2, x, y, opts=opts)
+            torch.cuda.synchronize()
+            e = _events(2)
+            e[0].record(stream)
+            for _ in range(args.steps):
+                hw.hw_ctqw_evolve_sparse(G, gamma, [m], tstep, dt, 1, walk, x, y, opts=opts)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            t = e[0].elapsed_time(e[1]) / 1e3 / args.steps
+            per_term = t / terms
+            # compulsory DRAM bytes per term: t_{k-1} once (its neighbour gathers
+            # hit L2), t_k written, the sum (or x) read and written; the CSR path
+            # adds row_ptr and head.  The complex64 working set (four 8 MB
+            # vectors) stays in L2, so its bytes are L2 traffic.
+            term_bytes = 4 * esz * n + (4 * (n + 1) + 4 * G.num_arcs if addressing else 0)
+            # FP64 operations per term (complex128): d - 1 adds per component for
+            # the neighbour sum, two multiplies, two adds into the sum
+            fp64_ops = n * (2 * (k - 1) + 4)
+            r = {"ms": t * 1e3, "us_per_term": per_term * 1e6, "gathers_per_s": (G.num_arcs + n) / per_term,
+                 "bytes_per_term": term_bytes, "achieved_gbs": term_bytes / per_term / 1e9,
+                 "frac_hbm": term_bytes / per_term / 1e9 / peak}
+            if dt == hw.HW_C128:
+                r["fp64_ops_per_s"] = fp64_ops / per_term
+                r["frac_fp64_nominal"] = fp64_ops / per_term / FP64_OPS_NOMINAL
+            res[name + tag] = r
     print(json.dumps(res), flush=True)
     G.free()
 
@@ -698,6 +741,27 @@ def run_profile(args):
         print(json.dumps({"profile": args.profile}))
         G.free()
         return
+    if args.profile.startswith("sparse_"):
+        # sparse-action CTQW on the 1024 x 1024 torus or the 2^20-vertex hypercube,
+        # gamma = 1/4 (1/20), one seeded mark, dt = 0.1, profile_steps applications
+        if "torus" in args.profile:
+            n, eu, ev = synth.torus(1024)
+            gamma = 0.25
+        else:
+            n, eu, ev = synth.hypercube(20)
+            gamma = 1.0 / 20
+        row_ptr, col = synth.adjacency_csr(n, eu, ev)
+        G = hw.hw_graph_csr(n, row_ptr, col)
+        m = synth.seeded_vertex(3, n)
+        dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        x = torch.full((n,), 1.0 / math.sqrt(n), dtype=cdt, device="cuda")
+        y = torch.empty_like(x)
+        hw.hw_ctqw_evolve_sparse(G, gamma, [m], 0.1, dt, 1, args.profile_steps, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "steps": args.profile_steps}))
+        G.free()
+        return
     n, eu, ev, row_ptr, col, m = workload()
     G = hw.hw_graph_csr(n, row_ptr, col)
     dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
@@ -720,7 +784,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["coined_c128", "coined_c64", "batched_c64", "expm_c64", "apply_c128",
-                                          "apply_c64", "apply_sym_c64"],
+                                          "apply_c64", "apply_sym_c64", "sparse_torus_c64", "sparse_torus_c128",
+                                          "sparse_cube_c64", "sparse_cube_c128"],
                     help="run a few coin+shift launches of the workload and exit (for ncu)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--profile-tile", type=int, default=10)

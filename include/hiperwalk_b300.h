@@ -74,6 +74,16 @@ typedef struct hw_opts {
                                   in registers, threads per CTA, vertices per warp) in
                                   {8,16} x {128,256} x {1,2,4}, row-major; 13, 14 = TMA-staged
                                   ring kernel with 2 or 1 CTAs per SM */
+    int32_t addressing;        /* coined (edge-major path) and sparse-action CTQW on a graph that
+                                  hw_graph_structure recognises as a torus or a hypercube:
+                                  0 = default, neighbour and reversed-arc positions computed
+                                  from the vertex label (no index table is read); 1 = read
+                                  the reversal / head tables as for any other graph.  Both
+                                  give bit-identical results. */
+    int32_t shift;             /* coined walk's shift operator (Sec. 3.2): 0 = flip-flop
+                                  S|v,w> = |w,v> (default); 1 = persistent, S|v,w> = |w,u> with
+                                  u - w = w - v, the walker keeping its direction (graphs that
+                                  hw_graph_structure recognises as a torus only, else HW_EINVAL) */
     int32_t reserved[2];
 } hw_opts;
 
@@ -126,6 +136,35 @@ hw_status hw_graph_free(hw_graph *g);
 hw_status hw_graph_info(const hw_graph *g, int64_t *n, int64_t *num_arcs,
                         const int32_t **d_row_ptr, const int32_t **d_head,
                         const int32_t **d_rev);
+
+/*
+ * Graph families whose arc basis the library recognises from the adjacency
+ * alone (the Grid and Hypercube classes of Sec. 3.1 and 3.2, with their labels):
+ *   HW_GRAPH_TORUS      dims = {L1, L2}, L1, L2 >= 3, n = L1 L2: vertex
+ *                       v = x L2 + y is adjacent to ((x +- 1) mod L1, y) and
+ *                       (x, (y +- 1) mod L2)
+ *   HW_GRAPH_HYPERCUBE  dims = {k, 0}, k >= 1, n = 2^k: v is adjacent to
+ *                       v XOR 2^b for b = 0..k-1
+ *   HW_GRAPH_GENERIC    anything else (dims = {0, 0})
+ * The test is exact (every row is compared with the family's neighbour list),
+ * so a relabelled torus or hypercube is GENERIC.
+ */
+typedef enum { HW_GRAPH_GENERIC = 0, HW_GRAPH_TORUS = 1, HW_GRAPH_HYPERCUBE = 2 } hw_graph_kind;
+
+/*
+ * hw_graph_structure -- the family of a graph built by hw_graph_csr.
+ *   kind   receives an hw_graph_kind
+ *   dims   HOST int64[2], receives the family's parameters (may be NULL)
+ * Errors: HW_EINVAL (NULL graph or kind).
+ */
+hw_status hw_graph_structure(const hw_graph *g, int32_t *kind, int64_t *dims);
+
+/*
+ * hw_graph_structure_host -- the same test on a host CSR (no device is
+ * touched); input rules and errors as hw_graph_arcs_host.
+ */
+hw_status hw_graph_structure_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                  int32_t *kind, int64_t *dims);
 
 /*
  * hw_coined_evolve -- |psi(t)> = (S C)^steps |psi(0)> (Sec. 3.2), coin first,
@@ -385,6 +424,23 @@ const char *hw_last_error(void);
 
 /* Library version string. */
 const char *hw_version(void);
+
+/*
+ * hw_measure_fp64 -- measured double-precision FMA throughput of the current
+ * device, in operations per second (one FMA, add or multiply = one operation),
+ * for the roofline of kernels bound by FP64 arithmetic.  Runs a grid of
+ * independent FMA chains for a few milliseconds on `stream` and synchronises
+ * it.  Errors: HW_EINVAL (NULL output), HW_ECUDA.
+ */
+hw_status hw_measure_fp64(double *ops_per_s, void *stream);
+
+/*
+ * hw_measure_l2 -- measured copy bandwidth (read + write bytes per second,
+ * reported in GB/s) of a 32 MB working set that stays in the L2 cache, for the
+ * roofline of kernels whose data fits in L2.  Synchronises `stream`.
+ * Errors: HW_EINVAL (NULL output), HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_measure_l2(double *gbs, void *stream);
 
 #ifdef __cplusplus
 }

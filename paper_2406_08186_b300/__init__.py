@@ -20,6 +20,8 @@ HW_OK, HW_EINVAL, HW_ENOMEM, HW_ECUDA, HW_ETIMEDOUT, HW_EUNSUPPORTED = 0, -1, -2
 HW_C64, HW_C128 = 1, 2
 HW_COIN_GROVER, HW_COIN_FOURIER = 0, 1
 HW_JOB_COINED, HW_JOB_CTQW = 0, 1
+HW_GRAPH_GENERIC, HW_GRAPH_TORUS, HW_GRAPH_HYPERCUBE = 0, 1, 2
+HW_SHIFT_FLIPFLOP, HW_SHIFT_PERSISTENT = 0, 1
 
 STATUS_NAMES = {0: "HW_OK", -1: "HW_EINVAL", -2: "HW_ENOMEM", -3: "HW_ECUDA",
                 -4: "HW_ETIMEDOUT", -5: "HW_EUNSUPPORTED"}
@@ -30,7 +32,8 @@ EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free"
            "hw_probability_noalloc", "hw_gemm_tc", "hw_ctqw_evolve_sparse",
            "hw_server_create", "hw_server_submit", "hw_server_run", "hw_server_poll",
            "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_trim_scratch", "hw_last_error",
-           "hw_version", "hw_coined_sample", "hw_ctqw_sample")
+           "hw_version", "hw_coined_sample", "hw_ctqw_sample", "hw_graph_structure",
+           "hw_graph_structure_host", "hw_measure_fp64", "hw_measure_l2")
 
 
 class HWError(RuntimeError):
@@ -44,6 +47,7 @@ class hw_opts(ctypes.Structure):
     _fields_ = [("record_stride", ctypes.c_int32), ("taylor_degree", ctypes.c_int32),
                 ("taylor_squarings", ctypes.c_int32), ("gemm_mode", ctypes.c_int32),
                 ("u_symmetric", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("addressing", ctypes.c_int32), ("shift", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 2)]
 
 
@@ -72,6 +76,10 @@ def lib():
         L.hw_graph_csr.restype = st
         L.hw_graph_arcs_host.argtypes = [i64, P, P, P, P, P]
         L.hw_graph_arcs_host.restype = st
+        L.hw_graph_structure.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        L.hw_graph_structure.restype = st
+        L.hw_graph_structure_host.argtypes = [i64, P, P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        L.hw_graph_structure_host.restype = st
         L.hw_graph_free.argtypes = [P]
         L.hw_graph_free.restype = st
         L.hw_graph_info.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
@@ -116,6 +124,10 @@ def lib():
         L.hw_trim_scratch.restype = st
         L.hw_last_error.argtypes = []
         L.hw_last_error.restype = ctypes.c_char_p
+        L.hw_measure_fp64.argtypes = [ctypes.POINTER(d), P]
+        L.hw_measure_fp64.restype = st
+        L.hw_measure_l2.argtypes = [ctypes.POINTER(d), P]
+        L.hw_measure_l2.restype = st
         L.hw_version.argtypes = []
         L.hw_version.restype = ctypes.c_char_p
         _lib = L
@@ -185,6 +197,20 @@ def hw_trim_scratch():
     _check(lib().hw_trim_scratch())
 
 
+def hw_measure_fp64(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device (operations per second)."""
+    r = ctypes.c_double()
+    _check(lib().hw_measure_fp64(ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
+def hw_measure_l2(stream=None) -> float:
+    """Measured copy bandwidth (GB/s, read + write) of an L2-resident 32 MB working set."""
+    r = ctypes.c_double()
+    _check(lib().hw_measure_l2(ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
 def hw_version() -> str:
     return lib().hw_version().decode()
 
@@ -240,6 +266,25 @@ def hw_graph_arcs_host(n: int, row_ptr, col_idx):
                                     head.ctypes.data_as(ctypes.c_void_p),
                                     rev.ctypes.data_as(ctypes.c_void_p)))
     return rp_out, head, rev
+
+
+def hw_graph_structure(g: Graph):
+    """(kind, (a, b)): HW_GRAPH_TORUS with (L1, L2), HW_GRAPH_HYPERCUBE with (k, 0), else HW_GRAPH_GENERIC."""
+    kind = ctypes.c_int32()
+    dims = (ctypes.c_int64 * 2)()
+    _check(lib().hw_graph_structure(g, ctypes.byref(kind), dims))
+    return kind.value, (dims[0], dims[1])
+
+
+def hw_graph_structure_host(n: int, row_ptr, col_idx):
+    """hw_graph_structure's test on a host CSR (no device)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    kind = ctypes.c_int32()
+    dims = (ctypes.c_int64 * 2)()
+    _check(lib().hw_graph_structure_host(int(n), rp.ctypes.data_as(ctypes.c_void_p),
+                                         ci.ctypes.data_as(ctypes.c_void_p), ctypes.byref(kind), dims))
+    return kind.value, (dims[0], dims[1])
 
 
 def hw_graph_free(g: Graph):

@@ -108,6 +108,8 @@ extern "C" void hw_opts_init(hw_opts *o)
     o->gemm_mode = 0;
     o->tile = 0;
     o->u_symmetric = 0;
+    o->addressing = 0;
+    o->shift = 0;
 }
 
 hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaStream_t st,
@@ -167,6 +169,20 @@ struct Scratch {
     }
     ~Scratch() { if (p) cudaFreeAsync(p, st); }
 };
+
+// shift operator and addressing of a coined call (hw_opts.shift, .addressing)
+hw_status coined_opts(const hw_graph *g, const hw_opts *opts, int *shift, bool *index_free)
+{
+    *shift = opts ? opts->shift : kShiftFlipFlop;
+    const int addressing = opts ? opts->addressing : 0;
+    if (*shift != kShiftFlipFlop && *shift != kShiftPersistent)
+        return hw_fail(HW_EINVAL, "shift must be 0 (flip-flop) or 1 (persistent)");
+    if (addressing != 0 && addressing != 1) return hw_fail(HW_EINVAL, "addressing must be 0 or 1");
+    if (*shift == kShiftPersistent && g->kind != HW_GRAPH_TORUS)
+        return hw_fail(HW_EINVAL, "the persistent shift needs a graph recognised as a torus");
+    *index_free = addressing == 0;
+    return HW_OK;
+}
 }  // namespace
 
 extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marked,
@@ -188,6 +204,9 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
     const int stride = opts ? opts->record_stride : 1;
     if (stride < 1) return hw_fail(HW_EINVAL, "record_stride must be >= 1");
     if (opts && (opts->tile < 0 || opts->tile > 14)) return hw_fail(HW_EINVAL, "tile must be 0..14");
+    int shift = kShiftFlipFlop;
+    bool index_free = false;
+    if (hw_status so = coined_opts(g, opts, &shift, &index_free); so != HW_OK) return so;
     if (record && n_marked == 0) return hw_fail(HW_EINVAL, "record needs at least one marked vertex");
     if (record && (uintptr_t)record % 8) return hw_fail(HW_EINVAL, "record must be 8-byte aligned");
     if (coin == HW_COIN_FOURIER && g->max_degree > 4096)
@@ -255,6 +274,8 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
             cs.marked = mk;
             cs.rec_part = rec_part;
             cs.rec_slot = (slots && (k - 1) >= stride && (k - 1) % stride == 0) ? (k - 1) / stride - 1 : -1;
+            cs.shift = shift;
+            cs.index_free = index_free;
             if ((s = launch_coined_step_em(g, dt, coin, cs, st)) != HW_OK) return s;
             cur = 1 - cur;
         }
@@ -280,6 +301,8 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
         cs.marked = mk;
         cs.rec_part = rec_part;
         cs.rec_slot = (slots && (k - 1) >= stride && (k - 1) % stride == 0) ? (k - 1) / stride - 1 : -1;
+        cs.shift = shift;
+        cs.index_free = index_free;
         s = (batch == 1) ? launch_coined_step(g, dt, coin, cs, st)
                          : launch_coined_step_batched(g, dt, coin, batch, cs, opts ? opts->tile : 0, st);
         if (s != HW_OK) return s;
@@ -312,6 +335,9 @@ extern "C" hw_status hw_coined_sample(const hw_graph *g, hw_coin coin, const int
     if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
     if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
     if (!psi_in) return hw_fail(HW_EINVAL, "psi_in is NULL");
+    int shift = kShiftFlipFlop;
+    bool index_free = false;
+    if (hw_status so = coined_opts(g, opts, &shift, &index_free); so != HW_OK) return so;
     const int64_t R = (end - start + stride - 1) / stride;
     if (R == 0) return HW_OK;
     const size_t esz = cplx_bytes(dt);
@@ -356,6 +382,8 @@ extern "C" hw_status hw_coined_sample(const hw_graph *g, hw_coin coin, const int
                 cs.marked = mk;
                 cs.rec_part = nullptr;
                 cs.rec_slot = -1;
+                cs.shift = shift;
+                cs.index_free = index_free;
                 if ((s = launch_coined_step_em(g, dt, coin, cs, st)) != HW_OK) return s;
                 cur = 1 - cur;
             }

@@ -15,6 +15,7 @@
 #include <mutex>
 #include <vector>
 
+#include "family.cuh"
 #include "internal.h"
 
 namespace {
@@ -32,6 +33,10 @@ __device__ __forceinline__ V mkv(R x, R y) { V r; r.x = x; r.y = y; return r; }
 // at c_tw[d*(d-1)/2 + r] (filled once from the host); larger d use sincospi.
 constexpr int kTwMax = 32;
 __constant__ double2 c_tw[kTwMax * (kTwMax + 1) / 2];
+__constant__ float2 c_twf[kTwMax * (kTwMax + 1) / 2];   // the same rounded to float
+
+__device__ __forceinline__ double2 tw_entry(int i, double) { return c_tw[i]; }
+__device__ __forceinline__ float2 tw_entry(int i, float) { return c_twf[i]; }
 
 __device__ __forceinline__ void twiddle(int r, int d, double *s, double *c)
 {
@@ -46,26 +51,20 @@ __device__ __forceinline__ void twiddle(int r, int d, double *s, double *c)
 __device__ __forceinline__ void twiddle(int r, int d, float *s, float *c)
 {
     if (d <= kTwMax) {
-        const double2 w = c_tw[d * (d - 1) / 2 + r];
-        *c = float(w.x);
-        *s = float(w.y);
+        const float2 w = c_twf[d * (d - 1) / 2 + r];
+        *c = w.x;
+        *s = w.y;
     } else {
         sincospif(2.0f * float(r) / float(d), s, c);
     }
 }
 
 // index of v in the sorted marked list, or -1
-__device__ __forceinline__ int find_marked(const MarkedList &mk, int v)
-{
-    int lo = 0, hi = mk.n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int m = mk.dev ? __ldg(mk.dev + mid) : mk.inl[mid];
-        if (m == v) return mid;
-        if (m < v) lo = mid + 1; else hi = mid;
-    }
-    return -1;
-}
+__device__ __forceinline__ int find_marked(const MarkedList &mk, int v) { return marked_find(mk, v); }
+
+// the Grover weight 2/d in the kernel's precision, from the graph's tables
+template <typename A> __device__ __forceinline__ double grover_w(const A &a, int d, double) { return a.two_over_d[d]; }
+template <typename A> __device__ __forceinline__ float grover_w(const A &a, int d, float) { return __ldg(a.two_over_d_f + d); }
 
 // deterministic block sum (fixed shuffle tree, then fixed order over warps)
 template <typename T>
@@ -83,6 +82,7 @@ __device__ __forceinline__ T block_sum(T x, T *red)
 
 struct StepArgs {
     const double *two_over_d;
+    const float *two_over_d_f;   // the same in float
     const int32_t *row_ptr;
     const int32_t *rev;
     const int32_t *blk;
@@ -129,7 +129,7 @@ __device__ void heavy_vertex(const StepArgs &a, int v, int a0, int d)
         }
         sx = block_sum(sx, red_r);
         sy = block_sum(sy, red_r);
-        const R f = R(a.two_over_d[d]);
+        const R f = grover_w(a, d, R(0));
         const R mx = sx * f, my = sy * f;
         for (int i = threadIdx.x; i < d; i += blockDim.x) {
             const V p = in[a0 + i];
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_step(StepArgs a)
             if (COIN == HW_COIN_GROVER) {
                 R sx = 0, sy = 0;
                 for (int j = s; j < e; ++j) { sx += s_psi[j].x; sy += s_psi[j].y; }
-                const R f = (mi < 0) ? R(a.two_over_d[e - s]) : R(0);
+                const R f = (mi < 0) ? grover_w(a, e - s, R(0)) : R(0);
                 s_coef[lv] = mkv<V, R>(sx * f, sy * f);
             } else {
                 s_coef[lv] = mkv<V, R>(mi >= 0 ? R(1) : R(0), R(0));
@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_lanes(RegArgs a, int d)
 // writes each coin output row to its reversed arc.
 struct BatchArgs {
     const double *two_over_d;
+    const float *two_over_d_f;   // the same in float
     const int32_t *row_ptr;
     const int32_t *rev;
     double *rec_part;
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_step_batched(BatchArgs a)
                     sx += p.x;
                     sy += p.y;
                 }
-                const R f = R(a.two_over_d[d]);
+                const R f = grover_w(a, d, R(0));
                 sx *= f;
                 sy *= f;
                 for (int j = s; j < e; ++j) {
@@ -421,6 +422,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_step_batched(BatchArgs a)
 // stay in registers between the sum and the stores; larger vertices re-read.
 struct RowsArgs {
     const double *two_over_d;
+    const float *two_over_d_f;   // the same in float
     const int32_t *row_ptr;
     const int32_t *rev;
     double *rec_part;
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(256) k_coined_rows(RowsArgs a)
         if (d == 0) continue;
         const int mi = find_marked(a.mk, int(v));
         const int rv = (lane < d) ? __ldg(a.rev + s + lane) : 0;
-        const R f = (mi >= 0) ? R(0) : R(a.two_over_d[d]);
+        const R f = (mi >= 0) ? R(0) : grover_w(a, d, R(0));
         for (int c0 = 0; c0 < BV; c0 += 32) {
             const int cv = c0 + lane;             // this lane's vector column
             const bool act = cv < BV;
@@ -564,6 +566,7 @@ constexpr uint64_t kRingWaitNs = 2000000000ull;
 
 struct RingArgs {
     const double *two_over_d;
+    const float *two_over_d_f;   // the same in float
     const int32_t *row_ptr;
     const int32_t *rev;
     double *rec_part;
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(kRingWarps * 32) k_coined_ring(RingArgs a)
                     }
                 }
             } else {
-                const R f = R(a.two_over_d[d]);
+                const R f = grover_w(a, d, R(0));
                 for (int cv = lane; cv < BV; cv += 32) {
                     T sum = RV::zero();
                     for (int j = 0; j < d; ++j) add_row(sum, rows[j * BV + cv]);
@@ -738,7 +741,7 @@ __global__ void k_marked_prob(const int32_t *__restrict__ row_ptr, const void *p
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= mk.n * batch) return;
     const int mi = i / batch, b = i % batch;
-    const int v = mk.dev ? mk.dev[mi] : mk.inl[mi];
+    const int v = marked_id(mk, mi);
     const int s = row_ptr ? row_ptr[v] : v;
     const int e = row_ptr ? row_ptr[v + 1] : v + 1;
     double acc = 0.0;
@@ -769,13 +772,14 @@ __global__ void k_record_finalize(const double *__restrict__ part, int n_marked,
 // hw_coined_evolve transposes in and out once per call.
 
 struct EmArgs {
-    const int32_t *revE;
+    const int32_t *revE;     // the shift as an edge-major table (table addressing)
     double *rec_part;
     const void *in;
     void *out;
     int64_t rec_slot;
     int64_t n;
     int32_t d;
+    int32_t L1, L2;          // torus addressing: rows, columns
     double two_over_d;
     float two_over_d_f;
     MarkedList mk;
@@ -787,7 +791,7 @@ template <> __device__ __forceinline__ float em_weight<float>(const EmArgs &a) {
 
 // thread per vertex, degree D known at compile time (the same arithmetic as
 // the arc-major kernels: Grover sum in arc order from arc 0, one FMA per component)
-template <typename R, int D, int COIN>
+template <typename R, int D, int COIN, int ADDR>
 __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
 {
     using V = typename Cx<R>::T;
@@ -797,9 +801,14 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
     const int64_t n = a.n;
     V p[D];
     int r[D];
-    if (v < n) {
+    if (v < n) {   // targets depend on the graph only: before the wait
+        if constexpr (ADDR == kAddrTable) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) r[j] = __ldg(a.revE + j * n + v);   // constant table: before the wait
+            for (int j = 0; j < D; ++j) r[j] = __ldg(a.revE + j * n + v);
+        } else {
+            static_assert(D == 4, "torus addressing is for degree 4");
+            torus_targets<ADDR>(v, n, a.L1, a.L2, r);
+        }
     }
     pdl_wait();
     if (v < n) {
@@ -830,9 +839,9 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
                 R cx = 0, cy = 0;
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    const double2 w = c_tw[D * (D - 1) / 2 + (j * k) % D];
-                    cx += R(w.x) * p[k].x - R(w.y) * p[k].y;
-                    cy += R(w.x) * p[k].y + R(w.y) * p[k].x;
+                    const auto w = tw_entry(D * (D - 1) / 2 + (j * k) % D, R(0));
+                    cx += w.x * p[k].x - w.y * p[k].y;
+                    cy += w.x * p[k].y + w.y * p[k].x;
                 }
                 out[r[j]] = mkv<V, R>(cx * scale, cy * scale);
             }
@@ -843,7 +852,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
 
 // Grover, any degree: thread per vertex, a pass for the sum and a pass (rows
 // read again, from L2) for the outputs
-template <typename R>
+template <typename R, int ADDR>
 __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
 {
     using V = typename Cx<R>::T;
@@ -864,9 +873,11 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
                 }
                 a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
             }
+            CubeWalk cw(v, d);
             for (int j = 0; j < d; ++j) {
                 const V p = in[j * n + v];
-                out[__ldg(a.revE + j * n + v)] = mkv<V, R>(-p.x, -p.y);
+                const int r = (ADDR == kAddrCube) ? cw.target(cw.next_bit(), n) : __ldg(a.revE + j * n + v);
+                out[r] = mkv<V, R>(-p.x, -p.y);
             }
         } else {
             const V p0 = in[v];
@@ -878,10 +889,12 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
                 sy += p.y;
             }
             const R f = em_weight<R>(a);
+            CubeWalk cw(v, d);
 #pragma unroll 4
             for (int j = 0; j < d; ++j) {
                 const V p = in[j * n + v];
-                out[__ldg(a.revE + j * n + v)] = mkv<V, R>(fma(f, sx, -p.x), fma(f, sy, -p.y));
+                const int r = (ADDR == kAddrCube) ? cw.target(cw.next_bit(), n) : __ldg(a.revE + j * n + v);
+                out[r] = mkv<V, R>(fma(f, sx, -p.x), fma(f, sy, -p.y));
             }
         }
     }
@@ -896,10 +909,12 @@ __global__ void k_layout(const V *__restrict__ in, V *__restrict__ out, int64_t 
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         if (TO_EDGE) {
-            const int64_t v = e / d, j = e - v * d;
+            int64_t j;
+            const int64_t v = idx_div(e, d, j);
             out[j * n + v] = in[e];
         } else {
-            const int64_t j = e / n, v = e - j * n;
+            int64_t v;
+            const int64_t j = idx_div(e, n, v);
             out[v * d + j] = in[e];
         }
     }
@@ -941,8 +956,13 @@ static hw_status upload_twiddles()
             const double ang = 2.0 * 3.14159265358979323846 * double(r) / double(d);
             tw[d * (d - 1) / 2 + r] = make_double2(std::cos(ang), std::sin(ang));
         }
+    std::vector<float2> twf(tw.size());
+    for (size_t i = 0; i < tw.size(); ++i) twf[i] = make_float2(float(tw[i].x), float(tw[i].y));
     hw_status s = hw_cuda(cudaMemcpyToSymbol(c_tw, tw.data(), sizeof(double2) * tw.size()),
                           "cudaMemcpyToSymbol(twiddles)");
+    if (s == HW_OK)
+        s = hw_cuda(cudaMemcpyToSymbol(c_twf, twf.data(), sizeof(float2) * twf.size()),
+                    "cudaMemcpyToSymbol(twiddles, float)");
     if (s == HW_OK) { done = true; dev_done = dev; }
     return s;
 }
@@ -960,7 +980,7 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
     if (regular && dt == HW_C64 && g->max_degree <= 32) {
         const int d = g->max_degree;
         RegArgs r;
-        r.rev = g->d_rev;
+        r.rev = shift_table(g, s.shift);
         r.rec_part = s.rec_part;
         r.in = s.in;
         r.out = s.out;
@@ -975,8 +995,9 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
     }
     StepArgs a;
     a.two_over_d = g->d_two_over_d;
+    a.two_over_d_f = g->d_two_over_d_f;
     a.row_ptr = g->d_row_ptr;
-    a.rev = g->d_rev;
+    a.rev = shift_table(g, s.shift);
     a.blk = g->d_blk;
     a.nblk = g->nblk;
     a.mk = s.marked;
@@ -1022,19 +1043,26 @@ hw_status launch_layout(const hw_graph *g, hw_dtype dt, const void *in, void *ou
 }
 
 template <typename R, int COIN>
-static void launch_em(int d, const EmArgs &a, cudaStream_t st)
+static void launch_em(int d, int addr, const EmArgs &a, cudaStream_t st)
 {
     const dim3 grid(unsigned((a.n + kThreads - 1) / kThreads));
     switch (d) {
-    case 1: launch_pdl(k_coined_em<R, 1, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 2: launch_pdl(k_coined_em<R, 2, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 3: launch_pdl(k_coined_em<R, 3, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 4: launch_pdl(k_coined_em<R, 4, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 5: launch_pdl(k_coined_em<R, 5, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 6: launch_pdl(k_coined_em<R, 6, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 7: launch_pdl(k_coined_em<R, 7, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    case 8: launch_pdl(k_coined_em<R, 8, COIN>, grid, dim3(kThreads), 0, st, a); break;
-    default: launch_pdl(k_coined_em_rt<R>, grid, dim3(kThreads), 0, st, a); break;   // Grover only
+    case 1: launch_pdl(k_coined_em<R, 1, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
+    case 2: launch_pdl(k_coined_em<R, 2, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
+    case 3: launch_pdl(k_coined_em<R, 3, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
+    case 4:
+        if (addr == kAddrTorusFF) launch_pdl(k_coined_em<R, 4, COIN, kAddrTorusFF>, grid, dim3(kThreads), 0, st, a);
+        else if (addr == kAddrTorusPS) launch_pdl(k_coined_em<R, 4, COIN, kAddrTorusPS>, grid, dim3(kThreads), 0, st, a);
+        else launch_pdl(k_coined_em<R, 4, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a);
+        break;
+    case 5: launch_pdl(k_coined_em<R, 5, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
+    case 6: launch_pdl(k_coined_em<R, 6, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
+    case 7: launch_pdl(k_coined_em<R, 7, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
+    case 8: launch_pdl(k_coined_em<R, 8, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
+    default:   // Grover only
+        if (addr == kAddrCube) launch_pdl(k_coined_em_rt<R, kAddrCube>, grid, dim3(kThreads), 0, st, a);
+        else launch_pdl(k_coined_em_rt<R, kAddrTable>, grid, dim3(kThreads), 0, st, a);
+        break;
     }
 }
 
@@ -1045,22 +1073,30 @@ hw_status launch_coined_step_em(const hw_graph *g, hw_dtype dt, hw_coin coin, co
         if (ts != HW_OK) return ts;
     }
     EmArgs a;
-    a.revE = g->d_revE;
+    a.revE = shift_table_em(g, s.shift);
+    if (!a.revE) return hw_fail(HW_EINVAL, "the persistent shift needs a graph recognised as a torus");
     a.rec_part = s.rec_part;
     a.in = s.in;
     a.out = s.out;
     a.rec_slot = s.rec_slot;
     a.n = g->n;
     a.d = g->max_degree;
+    a.L1 = int32_t(g->dims[0]);
+    a.L2 = int32_t(g->dims[1]);
     a.two_over_d = 2.0 / double(g->max_degree);
     a.two_over_d_f = float(2.0 / double(g->max_degree));
     a.mk = s.marked;
+    int addr = kAddrTable;
+    if (s.index_free && g->kind == HW_GRAPH_TORUS)
+        addr = (s.shift == kShiftPersistent) ? kAddrTorusPS : kAddrTorusFF;
+    else if (s.index_free && g->kind == HW_GRAPH_HYPERCUBE && a.d > 8)
+        addr = kAddrCube;
     if (dt == HW_C128) {
-        if (coin == HW_COIN_GROVER) launch_em<double, HW_COIN_GROVER>(a.d, a, st);
-        else launch_em<double, HW_COIN_FOURIER>(a.d, a, st);
+        if (coin == HW_COIN_GROVER) launch_em<double, HW_COIN_GROVER>(a.d, addr, a, st);
+        else launch_em<double, HW_COIN_FOURIER>(a.d, addr, a, st);
     } else {
-        if (coin == HW_COIN_GROVER) launch_em<float, HW_COIN_GROVER>(a.d, a, st);
-        else launch_em<float, HW_COIN_FOURIER>(a.d, a, st);
+        if (coin == HW_COIN_GROVER) launch_em<float, HW_COIN_GROVER>(a.d, addr, a, st);
+        else launch_em<float, HW_COIN_FOURIER>(a.d, addr, a, st);
     }
     return hw_cuda(cudaGetLastError(), "k_coined_em launch");
 }
@@ -1124,6 +1160,7 @@ static hw_status launch_shape(const hw_graph *g, hw_dtype dt, int batch, const R
     }
     RingArgs r;
     r.two_over_d = a.two_over_d;
+    r.two_over_d_f = a.two_over_d_f;
     r.row_ptr = a.row_ptr;
     r.rev = a.rev;
     r.rec_part = a.rec_part;
@@ -1192,8 +1229,9 @@ hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coi
         if (ts != HW_OK) return ts;
         BatchArgs a;
         a.two_over_d = g->d_two_over_d;
+        a.two_over_d_f = g->d_two_over_d_f;
         a.row_ptr = g->d_row_ptr;
-        a.rev = g->d_rev;
+        a.rev = shift_table(g, s.shift);
         a.mk = s.marked;
         a.rec_part = s.rec_part;
         a.rec_slot = s.rec_slot;
@@ -1210,8 +1248,9 @@ hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coi
     }
     RowsArgs a;
     a.two_over_d = g->d_two_over_d;
+    a.two_over_d_f = g->d_two_over_d_f;
     a.row_ptr = g->d_row_ptr;
-    a.rev = g->d_rev;
+    a.rev = shift_table(g, s.shift);
     a.rec_part = s.rec_part;
     a.in = s.in;
     a.out = s.out;

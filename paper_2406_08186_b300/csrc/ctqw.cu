@@ -117,7 +117,7 @@ __global__ void k_mark_diag(MarkedList mk, int n, double diag, double *__restric
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= mk.n) return;
-    const int m = mk.dev ? mk.dev[i] : mk.inl[i];
+    const int m = marked_id(mk, i);
     Y[int64_t(m) * n + m] += diag;
 }
 
@@ -138,7 +138,8 @@ __global__ void k_taylor_init(int n, const double *__restrict__ Y, double *__res
     const int64_t total = int64_t(n) * n;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = e / n, j = e % n;
+        int64_t j;
+        const int64_t i = idx_div(e, n, j);
         re[e] = (i == j) ? 1.0 : 0.0;
         im[e] = -Y[e];
     }
@@ -150,7 +151,8 @@ __global__ void k_mirror_lower(int n, double *__restrict__ x)
     const int64_t total = int64_t(n) * n;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = e / n, j = e % n;
+        int64_t j;
+        const int64_t i = idx_div(e, n, j);
         if (j > i) x[e] = x[j * n + i];
     }
 }
@@ -161,7 +163,8 @@ __global__ void k_sym_add(int n, const double *__restrict__ X, double *__restric
     const int64_t total = int64_t(n) * n;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t i = e / n, j = e % n;
+        int64_t j;
+        const int64_t i = idx_div(e, n, j);
         out[e] = X[e] + X[j * n + i];
     }
 }
@@ -263,13 +266,7 @@ k_apply(const void *U_, const void *x_, void *y_, int n, int batch, MarkedList m
                 y[int64_t(i) * batch + b0 + lane] = o;
                 if (rec_part && rec_slot >= 0) {
                     // marked rows: |y|^2 into the partials [slot][mi][batch]
-                    int lo = 0, hi = mk.n, mi = -1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        const int m = mk.dev ? mk.dev[mid] : mk.inl[mid];
-                        if (m == i) { mi = mid; break; }
-                        if (m < i) lo = mid + 1; else hi = mid;
-                    }
+                    const int mi = marked_find(mk, int(i));
                     if (mi >= 0)
                         rec_part[(rec_slot * mk.n + mi) * batch + b0 + lane] =
                             double(ox) * double(ox) + double(oy) * double(oy);
@@ -420,13 +417,7 @@ __global__ void __launch_bounds__(256) k_apply_sym_reduce(const void *prow_, con
         o.y = sy;
         y[i] = o;
         if (rec_part && rec_slot >= 0) {
-            int lo = 0, hi = mk.n, mi = -1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                const int m = mk.dev ? mk.dev[mid] : mk.inl[mid];
-                if (m == i) { mi = mid; break; }
-                if (m < i) lo = mid + 1; else hi = mid;
-            }
+            const int mi = marked_find(mk, int(i));
             if (mi >= 0) rec_part[rec_slot * mk.n + mi] = double(sx) * double(sx) + double(sy) * double(sy);
         }
     }
@@ -487,14 +478,15 @@ extern "C" hw_status hw_ctqw_plan(const hw_graph *g, double gamma, const int32_t
 {
     hw_clear_error();
     if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
-    std::vector<char> is_m(g->n, 0);
+    // ||H||_1 = max over v of (gamma d_v + [v in M]): the largest degree's row,
+    // or a marked vertex's row, whichever is larger (O(n_marked), no pass over
+    // the graph)
+    double norm1 = std::fabs(gamma) * double(g->max_degree);
     for (int32_t i = 0; i < n_marked; ++i)
-        if (marked[i] >= 0 && marked[i] < g->n) is_m[marked[i]] = 1;
-    double norm1 = 0.0;
-    for (int64_t v = 0; v < g->n; ++v) {
-        const double r = std::fabs(gamma) * (g->h_row_ptr[v + 1] - g->h_row_ptr[v]) + (is_m[v] ? 1.0 : 0.0);
-        norm1 = std::max(norm1, r);
-    }
+        if (marked && marked[i] >= 0 && marked[i] < g->n) {
+            const int64_t v = marked[i];
+            norm1 = std::max(norm1, std::fabs(gamma) * double(g->h_row_ptr[v + 1] - g->h_row_ptr[v]) + 1.0);
+        }
     norm1 *= std::fabs(time);
     int m, s;
     ctqw_plan(norm1, &m, &s);

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "family.cuh"
 #include "internal.h"
 
 namespace {
@@ -20,23 +21,39 @@ template <typename R> struct Cx3;
 template <> struct Cx3<double> { using T = double2; };
 template <> struct Cx3<float> { using T = float2; };
 
-__device__ __forceinline__ int marked_index(const MarkedList &mk, int v)
+__device__ __forceinline__ int marked_index(const MarkedList &mk, int v) { return marked_find(mk, v); }
+
+// With s the sum of t_in over v's neighbours, (H t_in)_v = -gamma s - [v in M]
+// t_in[v], and multiplying by -i c turns h = hx + i hy into c hy - i c hx:
+//   t = (-(c gamma) s_y - c q_y, (c gamma) s_x + c q_x),  q = t_in[v] if v is
+// marked, else 0.  Writes t_out[i] = t and acc[i] = (first ? x : acc)[i] + t.
+template <typename R, typename V>
+__device__ __forceinline__ void term_tail(R sx, R sy, const MarkedList &mk, int v, R cg, R c, const V *tin,
+                                          const V *x, V *tout, V *acc, int64_t i, int first)
 {
-    int lo = 0, hi = mk.n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int m = mk.dev ? mk.dev[mid] : mk.inl[mid];
-        if (m == v) return mid;
-        if (m < v) lo = mid + 1; else hi = mid;
+    V t;
+    if (mk.n && marked_index(mk, v) >= 0) {
+        const V q = tin[i];
+        t.x = -fma(cg, sy, c * q.y);
+        t.y = fma(cg, sx, c * q.x);
+    } else {
+        t.x = -(cg * sy);
+        t.y = cg * sx;
     }
-    return -1;
+    tout[i] = t;
+    const V base = first ? x[i] : acc[i];
+    V o;
+    o.x = base.x + t.x;
+    o.y = base.y + t.y;
+    acc[i] = o;
 }
 
 // t_out = (-i tau/k) H t_in; acc = (first ? x + t_out : acc + t_out).
-// Thread per (vertex, column); neighbours in sorted order.
+// Thread per (vertex, column); neighbours in sorted order, the sum starting
+// from the first one.
 template <typename R>
 __global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ head, int64_t n,
-                            int batch, MarkedList mk, double gamma, double coef, const void *x_,
+                            int batch, MarkedList mk, R cg, R coef, const void *x_,
                             const void *tin_, void *tout_, void *acc_, int first)
 {
     using V = typename Cx3<R>::T;
@@ -50,42 +67,96 @@ __global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *
         pdl_trigger();
         return;
     }
-    const int64_t v = i / batch;
-    const int b = int(i % batch);
+    int64_t rb;
+    const int64_t v = (batch == 1) ? i : idx_div(i, batch, rb);
+    const int b = (batch == 1) ? 0 : int(rb);
     R sx = 0, sy = 0;
-    for (int a = row_ptr[v]; a < row_ptr[v + 1]; ++a) {
+    int a = row_ptr[v];
+    const int e = row_ptr[v + 1];
+    if (a < e) {
+        const V q = tin[int64_t(head[a]) * batch + b];
+        sx = q.x;
+        sy = q.y;
+        ++a;
+    }
+    for (; a < e; ++a) {
         const V q = tin[int64_t(head[a]) * batch + b];
         sx += q.x;
         sy += q.y;
     }
-    R hx = R(-gamma) * sx, hy = R(-gamma) * sy;
-    if (mk.n && marked_index(mk, int(v)) >= 0) {
-        const V q = tin[i];
-        hx -= q.x;
-        hy -= q.y;
+    term_tail<R, V>(sx, sy, mk, int(v), cg, coef, tin, x, tout, acc, i, first);
+    pdl_trigger();
+}
+
+// The same term on a torus or hypercube: neighbour labels computed from v in
+// ascending order (the order of the CSR row), so the sums are bit-identical
+// to k_ctqw_term's, without the row_ptr and head reads.
+template <typename R, int FAM>
+__global__ void k_ctqw_term_fam(int64_t n, int batch, int L1, int L2, MarkedList mk, R cg, R coef,
+                                const void *x_, const void *tin_, void *tout_, void *acc_, int first)
+{
+    using V = typename Cx3<R>::T;
+    const V *__restrict__ x = static_cast<const V *>(x_);
+    const V *__restrict__ tin = static_cast<const V *>(tin_);
+    V *__restrict__ tout = static_cast<V *>(tout_);
+    V *__restrict__ acc = static_cast<V *>(acc_);
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    pdl_wait();   // t_in and acc come from the previous term
+    if (i >= n * batch) {
+        pdl_trigger();
+        return;
     }
-    // (-i c) (hx + i hy) = c hy - i c hx
-    const R c = R(coef);
-    V t;
-    t.x = c * hy;
-    t.y = -c * hx;
-    tout[i] = t;
-    const V base = first ? x[i] : acc[i];
-    V o;
-    o.x = base.x + t.x;
-    o.y = base.y + t.y;
-    acc[i] = o;
+    int64_t rb;
+    const int64_t v = (batch == 1) ? i : idx_div(i, batch, rb);
+    const int b = (batch == 1) ? 0 : int(rb);
+    R sx, sy;
+    if constexpr (FAM == HW_GRAPH_TORUS) {
+        int w[4];
+        TorusVertex(v, n, L1, L2).sorted(w);
+        V q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j] = tin[int64_t(w[j]) * batch + b];
+        sx = q[0].x;
+        sy = q[0].y;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            sx += q[j].x;
+            sy += q[j].y;
+        }
+    } else {
+        CubeWalk cw(v, L1);   // L1 = k >= 1
+        const V q0 = tin[int64_t(uint32_t(v) ^ (1u << cw.next_bit())) * batch + b];
+        sx = q0.x;
+        sy = q0.y;
+#pragma unroll 4
+        for (int j = 1; j < L1; ++j) {
+            const V q = tin[int64_t(uint32_t(v) ^ (1u << cw.next_bit())) * batch + b];
+            sx += q.x;
+            sy += q.y;
+        }
+    }
+    term_tail<R, V>(sx, sy, mk, int(v), cg, coef, tin, x, tout, acc, i, first);
     pdl_trigger();
 }
 
 template <typename R>
-hw_status launch_term(const hw_graph *g, int batch, const MarkedList &mk, double gamma, double coef, const void *x,
-                      const void *tin, void *tout, void *acc, int first, cudaStream_t st)
+hw_status launch_term(const hw_graph *g, bool index_free, int batch, const MarkedList &mk, double gamma, double coef,
+                      const void *x, const void *tin, void *tout, void *acc, int first, cudaStream_t st)
 {
+    // the constants in the kernel's precision, converted here once (a
+    // conversion in the kernel would run per thread on the FP64 pipe)
+    const R cg = R(coef * gamma), c = R(coef);
     const int64_t total = g->n * batch;
     const int64_t grid = (total + 255) / 256;
-    launch_pdl(k_ctqw_term<R>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
-               (const int32_t *)g->d_head, g->n, batch, mk, gamma, coef, x, tin, tout, acc, first);
+    if (index_free && g->kind == HW_GRAPH_TORUS)
+        launch_pdl(k_ctqw_term_fam<R, HW_GRAPH_TORUS>, dim3(unsigned(grid)), dim3(256), 0, st, g->n, batch,
+                   int(g->dims[0]), int(g->dims[1]), mk, cg, c, x, tin, tout, acc, first);
+    else if (index_free && g->kind == HW_GRAPH_HYPERCUBE)
+        launch_pdl(k_ctqw_term_fam<R, HW_GRAPH_HYPERCUBE>, dim3(unsigned(grid)), dim3(256), 0, st, g->n, batch,
+                   int(g->dims[0]), 0, mk, cg, c, x, tin, tout, acc, first);
+    else
+        launch_pdl(k_ctqw_term<R>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
+                   (const int32_t *)g->d_head, g->n, batch, mk, cg, c, x, tin, tout, acc, first);
     return hw_cuda(cudaGetLastError(), "k_ctqw_term launch");
 }
 
@@ -128,6 +199,8 @@ extern "C" hw_status hw_ctqw_evolve_sparse(const hw_graph *g, double gamma, cons
     if (opts && opts->taylor_degree > 0) m_deg = opts->taylor_degree;
     if (opts && opts->taylor_squarings >= 0) sq = opts->taylor_squarings;
     if (m_deg > 40 || sq > 30) return hw_fail(HW_EINVAL, "Taylor degree %d / splits 2^%d out of range", m_deg, sq);
+    if (opts && opts->addressing != 0 && opts->addressing != 1) return hw_fail(HW_EINVAL, "addressing must be 0 or 1");
+    const bool index_free = !(opts && opts->addressing == 1);
     const int64_t parts = int64_t(1) << sq;
     const double tau = time / double(parts);
     MarkedList mk;
@@ -151,8 +224,8 @@ extern "C" hw_status hw_ctqw_evolve_sparse(const hw_graph *g, double gamma, cons
                 const void *tin = (k == 1) ? X[cur] : T[(k - 1) % 2];
                 const double coef = tau / double(k);
                 s = (dt == HW_C128)
-                        ? launch_term<double>(g, batch, mk, gamma, coef, X[cur], tin, T[k % 2], X[1 - cur], k == 1, st)
-                        : launch_term<float>(g, batch, mk, gamma, coef, X[cur], tin, T[k % 2], X[1 - cur], k == 1, st);
+                        ? launch_term<double>(g, index_free, batch, mk, gamma, coef, X[cur], tin, T[k % 2], X[1 - cur], k == 1, st)
+                        : launch_term<float>(g, index_free, batch, mk, gamma, coef, X[cur], tin, T[k % 2], X[1 - cur], k == 1, st);
                 if (s != HW_OK) return s;
             }
             cur = 1 - cur;

@@ -669,7 +669,7 @@ __global__ void k_scatter_slices(SymSparse Y, double sc, int ns, int ld, void *s
             put_slices<FMT>(xs, ns, int64_t(v) * ld + Y.col[a], s0, s1, s2);
     }
     if (v < Y.mk.n) {
-        const int m = Y.mk.dev ? Y.mk.dev[v] : Y.mk.inl[v];
+        const int m = marked_id(Y.mk, v);
         put_slices<FMT>(Y.diag * sc, ns, int64_t(m) * ld + m, s0, s1, s2);
     }
 }

@@ -69,6 +69,102 @@ void hw_partition_blocks(const std::vector<int32_t> &rp, int tile_arcs, int tile
     }
 }
 
+// ---- recognised families (the Grid and Hypercube classes of Sec. 3.1, 3.2)
+// Torus L1 x L2 (L1, L2 >= 3), v = x L2 + y: the sorted neighbours of vertex 0
+// are 1, L2 - 1, L2, n - L2, which gives L2; every row is then compared with
+// the four labels (x +- 1, y), (x, y +- 1) sorted.  Hypercube: n = 2^k, rows
+// equal to the sorted v XOR 2^b.
+static void torus_row(int64_t v, int64_t L1, int64_t L2, int32_t out[4])
+{
+    const int64_t x = v / L2, y = v % L2;
+    out[0] = int32_t(((x + L1 - 1) % L1) * L2 + y);
+    out[1] = int32_t(x * L2 + (y + L2 - 1) % L2);
+    out[2] = int32_t(x * L2 + (y + 1) % L2);
+    out[3] = int32_t(((x + 1) % L1) * L2 + y);
+    std::sort(out, out + 4);
+}
+
+void hw_detect_family(int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &head,
+                      int32_t *kind, int64_t dims[2])
+{
+    *kind = HW_GRAPH_GENERIC;
+    dims[0] = dims[1] = 0;
+    bool all4 = n >= 9, cube = n >= 2 && (n & (n - 1)) == 0;
+    int k = 0;
+    while (cube && (int64_t(1) << k) < n) ++k;
+    for (int64_t v = 0; v < n && (all4 || cube); ++v) {
+        const int32_t d = rp[v + 1] - rp[v];
+        all4 = all4 && d == 4;
+        cube = cube && d == k;
+    }
+    if (cube) {
+        std::vector<int32_t> row(k);
+        bool ok = true;
+        for (int64_t v = 0; v < n && ok; ++v) {
+            for (int b = 0; b < k; ++b) row[b] = int32_t(v ^ (int64_t(1) << b));
+            std::sort(row.begin(), row.end());
+            ok = std::equal(row.begin(), row.end(), head.begin() + rp[v]);
+        }
+        if (ok) {
+            *kind = HW_GRAPH_HYPERCUBE;
+            dims[0] = k;
+            return;
+        }
+    }
+    if (!all4) return;
+    const int64_t L2 = head[2];
+    if (L2 < 3 || n % L2 != 0 || n / L2 < 3) return;
+    const int64_t L1 = n / L2;
+    int32_t row[4];
+    for (int64_t v = 0; v < n; ++v) {
+        torus_row(v, L1, L2, row);
+        if (!std::equal(row, row + 4, head.begin() + rp[v])) return;
+    }
+    *kind = HW_GRAPH_TORUS;
+    dims[0] = L1;
+    dims[1] = L2;
+}
+
+// persistent shift of the torus: arc (v, w) -> (w, u), u - w = w - v
+static void torus_persistent(int64_t L1, int64_t L2, const std::vector<int32_t> &rp,
+                             const std::vector<int32_t> &head, std::vector<int32_t> &pers)
+{
+    const int64_t n = L1 * L2;
+    pers.resize(size_t(4 * n));
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t xv = v / L2, yv = v % L2;
+        for (int32_t a = rp[v]; a < rp[v + 1]; ++a) {
+            const int64_t w = head[a], xw = w / L2, yw = w % L2;
+            const int64_t u = ((2 * xw - xv + L1) % L1) * L2 + (2 * yw - yv + L2) % L2;
+            const int32_t *b = head.data() + rp[w], *e = head.data() + rp[w + 1];
+            pers[a] = int32_t(std::lower_bound(b, e, int32_t(u)) - head.data());
+        }
+    }
+}
+
+extern "C" hw_status hw_graph_structure_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                             int32_t *kind, int64_t *dims)
+{
+    hw_clear_error();
+    if (!kind) return hw_fail(HW_EINVAL, "kind is NULL");
+    std::vector<int32_t> rp, head, rev;
+    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, rp, head, rev);
+    if (s != HW_OK) return s;
+    int64_t d[2];
+    hw_detect_family(n, rp, head, kind, d);
+    if (dims) { dims[0] = d[0]; dims[1] = d[1]; }
+    return HW_OK;
+}
+
+extern "C" hw_status hw_graph_structure(const hw_graph *g, int32_t *kind, int64_t *dims)
+{
+    hw_clear_error();
+    if (!g || !kind) return hw_fail(HW_EINVAL, "graph or kind is NULL");
+    *kind = g->kind;
+    if (dims) { dims[0] = g->dims[0]; dims[1] = g->dims[1]; }
+    return HW_OK;
+}
+
 extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                                   void *stream, hw_graph **out)
 {
@@ -94,6 +190,8 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
 
     std::vector<double> w(g->max_degree + 1, 0.0);
     for (int32_t d = 1; d <= g->max_degree; ++d) w[d] = 2.0 / double(d);
+    std::vector<float> wf(w.size());
+    for (size_t d = 0; d < w.size(); ++d) wf[d] = float(w[d]);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [&](hw_status e) { hw_graph_free(g); return e; };
     if ((s = hw_cuda(cudaGetDevice(&g->device), "cudaGetDevice")) != HW_OK) return fail(s);
@@ -109,13 +207,28 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
                 revE[size_t(j * n + v)] = int32_t((r % d) * n + r / d);
             }
     }
+    hw_detect_family(n, g->h_row_ptr, head, &g->kind, g->dims);
+    std::vector<int32_t> pers, persE;
+    const bool torus = g->kind == HW_GRAPH_TORUS;
+    if (torus) {
+        torus_persistent(g->dims[0], g->dims[1], g->h_row_ptr, head, pers);
+        persE.resize(pers.size());
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t j = 0; j < 4; ++j) {
+                const int64_t r = pers[size_t(v * 4 + j)];
+                persE[size_t(j * n + v)] = int32_t((r % 4) * n + r / 4);
+            }
+    }
     const size_t arcs_b = sizeof(int32_t) * std::max<int64_t>(g->num_arcs, 1);
     if (cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * (n + 1)) != cudaSuccess ||
         cudaMalloc(&g->d_head, arcs_b) != cudaSuccess ||
         cudaMalloc(&g->d_rev, arcs_b) != cudaSuccess ||
         (regular && cudaMalloc(&g->d_revE, arcs_b) != cudaSuccess) ||
+        (torus && cudaMalloc(&g->d_pers, arcs_b) != cudaSuccess) ||
+        (torus && cudaMalloc(&g->d_persE, arcs_b) != cudaSuccess) ||
         cudaMalloc(&g->d_blk, sizeof(int32_t) * g->h_blk.size()) != cudaSuccess ||
         cudaMalloc(&g->d_two_over_d, sizeof(double) * (g->max_degree + 1)) != cudaSuccess ||
+        cudaMalloc(&g->d_two_over_d_f, sizeof(float) * (g->max_degree + 1)) != cudaSuccess ||
         cudaHostAlloc(&g->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer(&g->d_err, g->h_err, 0) != cudaSuccess) {
         cudaGetLastError();
@@ -129,10 +242,16 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
                                      cudaMemcpyHostToDevice, st), "upload rev")) != HW_OK ||
         (regular && (s = hw_cuda(cudaMemcpyAsync(g->d_revE, revE.data(), sizeof(int32_t) * g->num_arcs,
                                                  cudaMemcpyHostToDevice, st), "upload revE")) != HW_OK) ||
+        (torus && (s = hw_cuda(cudaMemcpyAsync(g->d_pers, pers.data(), sizeof(int32_t) * g->num_arcs,
+                                               cudaMemcpyHostToDevice, st), "upload pers")) != HW_OK) ||
+        (torus && (s = hw_cuda(cudaMemcpyAsync(g->d_persE, persE.data(), sizeof(int32_t) * g->num_arcs,
+                                               cudaMemcpyHostToDevice, st), "upload persE")) != HW_OK) ||
         (s = hw_cuda(cudaMemcpyAsync(g->d_blk, g->h_blk.data(), sizeof(int32_t) * g->h_blk.size(),
                                      cudaMemcpyHostToDevice, st), "upload blocks")) != HW_OK ||
         (s = hw_cuda(cudaMemcpyAsync(g->d_two_over_d, w.data(), sizeof(double) * w.size(),
                                      cudaMemcpyHostToDevice, st), "upload weights")) != HW_OK ||
+        (s = hw_cuda(cudaMemcpyAsync(g->d_two_over_d_f, wf.data(), sizeof(float) * wf.size(),
+                                     cudaMemcpyHostToDevice, st), "upload weights (float)")) != HW_OK ||
         (s = hw_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HW_OK)
         return fail(s);
     *g->h_err = 0;
@@ -148,8 +267,11 @@ extern "C" hw_status hw_graph_free(hw_graph *g)
     cudaFree(g->d_head);
     cudaFree(g->d_rev);
     cudaFree(g->d_revE);
+    cudaFree(g->d_pers);
+    cudaFree(g->d_persE);
     cudaFree(g->d_blk);
     cudaFree(g->d_two_over_d);
+    cudaFree(g->d_two_over_d_f);
     if (g->h_err) cudaFreeHost(g->h_err);
     cudaGetLastError();
     delete g;

@@ -30,8 +30,17 @@ struct hw_graph {
     // layout E[j][v] = psi[v d + j]: revE[j n + v] = j' n + w where arc
     // v d + j = (v, w) reverses to w d + j'; nullptr otherwise
     int32_t *d_revE = nullptr;       // [num_arcs]
+    // recognised family (hw_graph_kind) and its parameters: torus {L1, L2},
+    // hypercube {k, 0}
+    int32_t kind = HW_GRAPH_GENERIC;
+    int64_t dims[2] = {0, 0};
+    // tori: the persistent shift as arc tables, arc-major (pers[a]) and
+    // edge-major (persE[j n + v]); nullptr otherwise
+    int32_t *d_pers = nullptr;       // [num_arcs]
+    int32_t *d_persE = nullptr;      // [num_arcs]
     int32_t *d_blk = nullptr;        // [nblk+1] first vertex of each block
     double *d_two_over_d = nullptr;  // [max_degree+1], 2/d (0 for d = 0): the Grover weight
+    float *d_two_over_d_f = nullptr; // the same rounded to float
     int *h_err = nullptr;            // zero-copy word: a kernel's bounded wait ran out of time
     int *d_err = nullptr;            // its device alias
     std::vector<int32_t> h_row_ptr;  // host copy for launch decisions
@@ -55,6 +64,9 @@ hw_status hw_build_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *c
                              std::vector<int32_t> &rev);
 void hw_partition_blocks(const std::vector<int32_t> &rp, int tile_arcs, int tile_verts,
                          std::vector<int32_t> &blk);
+// family of a sorted arc basis (exact comparison of every row)
+void hw_detect_family(int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &head,
+                      int32_t *kind, int64_t dims[2]);
 
 // ---- device launchers (coined.cu, prob.cu, ctqw.cu)
 // Marked lists up to this length travel inside the kernel parameters (no
@@ -66,13 +78,58 @@ struct MarkedList {
     int32_t inl[kInlineMarked];  // sorted ids when n <= kInlineMarked
 };
 
+#ifdef __CUDACC__
+// Position of v in the marked list, or -1.  Inline ids are compared at
+// constant indices (an unrolled scan stopping at the uniform count), so the
+// list is read from the kernel's parameter bank: a computed index into a
+// parameter array makes the compiler copy the whole list to local memory in
+// every thread.
+__device__ __forceinline__ int marked_find(const MarkedList &mk, int v)
+{
+    if (mk.dev) {
+        int lo = 0, hi = mk.n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int m = __ldg(mk.dev + mid);
+            if (m == v) return mid;
+            if (m < v) lo = mid + 1; else hi = mid;
+        }
+        return -1;
+    }
+#pragma unroll
+    for (int k = 0; k < kInlineMarked; ++k) {
+        if (k >= mk.n) break;
+        if (mk.inl[k] == v) return k;
+    }
+    return -1;
+}
+
+// the i-th marked id (0 <= i < n), by the same constant-index selection
+__device__ __forceinline__ int marked_id(const MarkedList &mk, int i)
+{
+    if (mk.dev) return __ldg(mk.dev + i);
+    int m = -1;
+#pragma unroll
+    for (int k = 0; k < kInlineMarked; ++k)
+        if (k == i) m = mk.inl[k];
+    return m;
+}
+#endif
+
+enum { kShiftFlipFlop = 0, kShiftPersistent = 1 };
+
 struct CoinedStep {
     const void *in;
     void *out;
     MarkedList marked;
     double *rec_part;        // [slots][n_marked] or nullptr
     int64_t rec_slot;        // slot receiving the marked probability of `in`, or -1
+    int shift = kShiftFlipFlop;   // kShiftPersistent needs a torus (hw_graph::d_pers)
+    bool index_free = false;      // edge-major path on a torus / hypercube: positions from labels
 };
+// the shift as an arc table: out[table[a]] = (C psi)[a]
+inline const int32_t *shift_table(const hw_graph *g, int shift) { return shift == kShiftPersistent ? g->d_pers : g->d_rev; }
+inline const int32_t *shift_table_em(const hw_graph *g, int shift) { return shift == kShiftPersistent ? g->d_persE : g->d_revE; }
 // edge-major layout of regular graphs (see hw_graph::d_revE)
 bool coined_em_supported(const hw_graph *g, hw_coin coin, hw_dtype dt);
 hw_status launch_layout(const hw_graph *g, hw_dtype dt, const void *in, void *out, bool to_edge, cudaStream_t st);
@@ -124,6 +181,22 @@ hw_status tc_power_finish_c64(TcPower *p, const double *Re, const double *Im, vo
 // the previous grid has completed and its writes are visible; pdl_trigger()
 // lets the next grid be scheduled.
 #ifdef __CUDACC__
+// q = e / d, r = e - q d for non-negative indices: a 32-bit division when both
+// fit in 32 bits (the usual case), the 64-bit one otherwise.  The 64-bit
+// integer division is a long instruction sequence; in a thread-per-element
+// kernel it can cost more than the element's own work.
+__device__ __forceinline__ int64_t idx_div(int64_t e, int64_t d, int64_t &r)
+{
+    if (((uint64_t(e) | uint64_t(d)) >> 32) == 0) {
+        const uint32_t q = uint32_t(e) / uint32_t(d);
+        r = int64_t(uint32_t(e) - q * uint32_t(d));
+        return int64_t(q);
+    }
+    const int64_t q = e / d;
+    r = e - q * d;
+    return q;
+}
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

@@ -26,8 +26,9 @@ __global__ void k_prob_coined(const int32_t *__restrict__ row_ptr, int64_t n, in
     const V *__restrict__ psi = static_cast<const V *>(psi_);
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n * batch) return;
-    const int64_t v = i / batch;
-    const int b = int(i % batch);
+    int64_t rb;
+    const int64_t v = (batch == 1) ? i : idx_div(i, batch, rb);
+    const int b = (batch == 1) ? 0 : int(rb);
     double acc = 0.0;
     for (int a = row_ptr[v]; a < row_ptr[v + 1]; ++a) {
         const V p = psi[int64_t(a) * batch + b];

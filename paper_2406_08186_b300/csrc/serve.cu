@@ -40,6 +40,7 @@ constexpr int kServeThreads = 256;
 constexpr int kTileVertices = 1024;   // CTQW tiles
 constexpr int kServeTileArcs = 1024;  // coined tiles: whole vertices, at most this many arcs
 constexpr int kMaxServeMarked = 4;
+constexpr int kServeMaxDeg = 32;           // series degree bound (hw_ctqw_plan gives m <= 30)
 constexpr int kLocalBytes = 3 * 8192 * 8;  // shared memory of a local CTQW job: state and two terms
 constexpr int kLocalThreads = 512;
 constexpr int kLocalCtas = 64;             // local jobs advanced at once (each CTA takes one SM's memory)
@@ -56,8 +57,15 @@ struct SJob {
     int64_t start_tick;
     int64_t total_subs;
     double two_over_d;
+    float two_over_d_f;
+    int32_t pad0;
     double gamma;
     double tau;
+    // CTQW term k = 1..m: t_k = (-(cg_k) s_y - c_k q_y, cg_k s_x + c_k q_x) with
+    // c_k = tau / k, cg_k = c_k gamma (s the neighbour sum of t_{k-1}, q its
+    // own entry on a marked vertex), in both precisions (set on the host)
+    double cd[kServeMaxDeg + 1], cgd[kServeMaxDeg + 1];
+    float cf[kServeMaxDeg + 1], cgf[kServeMaxDeg + 1];
     int32_t kind;            // 0 coined, 1 CTQW
     int32_t dt;              // HW_C64 / HW_C128
     int32_t d;               // coined: the graph's (regular) degree
@@ -77,6 +85,12 @@ template <typename R> struct CxS;
 template <> struct CxS<double> { using T = double2; };
 template <> struct CxS<float> { using T = float2; };
 
+// the job's constants in the kernel's precision (no per-thread conversion)
+__device__ __forceinline__ void term_coef(const SJob &J, int k, double &c, double &cg) { c = J.cd[k]; cg = J.cgd[k]; }
+__device__ __forceinline__ void term_coef(const SJob &J, int k, float &c, float &cg) { c = J.cf[k]; cg = J.cgf[k]; }
+__device__ __forceinline__ double grover_weight(const SJob &J, double) { return J.two_over_d; }
+__device__ __forceinline__ float grover_weight(const SJob &J, float) { return J.two_over_d_f; }
+
 __device__ __forceinline__ int job_marked(const SJob &J, int v)
 {
     for (int i = 0; i < J.n_marked; ++i)
@@ -90,10 +104,10 @@ __device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
 {
     using V = typename CxS<R>::T;
     const int64_t per = int64_t(J.q) * J.m;
-    const int64_t w = ls / per;
-    const int64_t rem = ls % per;
-    const int64_t r = rem / J.m;
-    const int k = int(rem % J.m) + 1;
+    int64_t rem, kk;
+    const int64_t w = idx_div(ls, per, rem);
+    const int64_t r = idx_div(rem, J.m, kk);
+    const int k = int(kk) + 1;
     const int cur = int((w * J.q + r) & 1);
     const V *__restrict__ x = static_cast<const V *>(J.X[cur]);
     const V *__restrict__ tin = (k == 1) ? x : static_cast<const V *>(J.T[(k - 1) & 1]);
@@ -105,16 +119,18 @@ __device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
         sx += q.x;
         sy += q.y;
     }
-    R hx = R(-J.gamma) * sx, hy = R(-J.gamma) * sy;
+    R c, cg;
+    term_coef(J, k, c, cg);
     const int mi = job_marked(J, v);
-    if (mi >= 0) {
-        hx -= tin[v].x;
-        hy -= tin[v].y;
-    }
-    const R c = R(J.tau / double(k));
     V t;
-    t.x = c * hy;
-    t.y = -c * hx;
+    if (mi >= 0) {
+        const V q = tin[v];
+        t.x = -fma(cg, sy, c * q.y);
+        t.y = fma(cg, sx, c * q.x);
+    } else {
+        t.x = -(cg * sy);
+        t.y = cg * sx;
+    }
     tout[v] = t;
     const V base = (k == 1) ? x[v] : acc[v];
     V o;
@@ -144,7 +160,7 @@ __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
 #pragma unroll
     for (int i = 0; i < kMaxServeMarked; ++i) mk[i] = (i < nm) ? Jg.marked[i] : -1;
     double *rec = Jg.rec;
-    const R f = R(Jg.two_over_d);
+    const R f = grover_weight(Jg, R(0));
     for (int v = v0 + int(threadIdx.x); v < v1; v += blockDim.x) {
         V p[D];
         int r[D];
@@ -204,7 +220,7 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
 #pragma unroll
     for (int i = 0; i < kMaxServeMarked; ++i) mk[i] = (i < nm) ? Jg.marked[i] : -1;
     double *rec = Jg.rec;
-    const R f = R(Jg.two_over_d);
+    const R f = grover_weight(Jg, R(0));
     for (int v = v0 + int(threadIdx.x); v < v1; v += blockDim.x) {
         int mi = -1;
 #pragma unroll
@@ -264,13 +280,13 @@ __device__ void serve_ctqw_local(const SJob &J, int64_t w0, int ns, unsigned cha
     V *__restrict__ out = static_cast<V *>(J.X[(w0 + ns) & 1]);
     for (int v = threadIdx.x; v < n; v += blockDim.x) acc[v] = in[v];
     __syncthreads();
-    const R mg = R(-J.gamma);
     for (int64_t w = w0; w < w0 + ns; ++w) {
         for (int r = 0; r < J.q; ++r) {
             for (int k = 1; k <= J.m; ++k) {
                 const V *tin = (k == 1) ? acc : ((k & 1) ? T1 : T0);   // t_{k-1}
                 V *tout = (k & 1) ? T0 : T1;                            // t_k
-                const R c = R(J.tau / double(k));
+                R c, cg;
+                term_coef(J, k, c, cg);
                 for (int v = threadIdx.x; v < n; v += blockDim.x) {
                     R sx = 0, sy = 0;
                     for (int a = J.row_ptr[v]; a < J.row_ptr[v + 1]; ++a) {
@@ -278,15 +294,15 @@ __device__ void serve_ctqw_local(const SJob &J, int64_t w0, int ns, unsigned cha
                         sx += q.x;
                         sy += q.y;
                     }
-                    R hx = mg * sx, hy = mg * sy;
-                    const int mi = job_marked(J, v);
-                    if (mi >= 0) {
-                        hx -= tin[v].x;
-                        hy -= tin[v].y;
-                    }
                     V t;
-                    t.x = c * hy;
-                    t.y = -c * hx;
+                    if (job_marked(J, v) >= 0) {
+                        const V q = tin[v];
+                        t.x = -fma(cg, sy, c * q.y);
+                        t.y = fma(cg, sx, c * q.x);
+                    } else {
+                        t.x = -(cg * sy);
+                        t.y = cg * sx;
+                    }
                     tout[v] = t;
                     // acc takes t_{k-1} now (t_1 only once every gather of the
                     // start state is done, i.e. at k = 2) and t_m at the end
@@ -683,6 +699,7 @@ extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *
         hw_status st = hw_ctqw_plan(g, job->gamma, J.marked.data(), job->n_marked, job->time, &m, &sq);
         if (st != HW_OK) return st;
         if (sq > 20) return hw_fail(HW_EUNSUPPORTED, "||H dt|| too large to serve");
+        if (m > kServeMaxDeg) return hw_fail(HW_EUNSUPPORTED, "series degree %d above %d", m, kServeMaxDeg);
         J.m = m;
         J.q = 1 << sq;
         J.dim = g->n;
@@ -767,8 +784,15 @@ static hw_status admit(hw_server *s, Job &J)
     D.start_tick = s->tick;
     D.total_subs = J.total_subs;
     D.two_over_d = g->max_degree ? 2.0 / double(g->max_degree) : 0.0;
+    D.two_over_d_f = float(D.two_over_d);
     D.gamma = J.spec.gamma;
     D.tau = J.spec.time / double(J.q);
+    for (int k = 1; k <= J.m && k <= kServeMaxDeg; ++k) {
+        D.cd[k] = D.tau / double(k);
+        D.cgd[k] = D.cd[k] * D.gamma;
+        D.cf[k] = float(D.cd[k]);
+        D.cgf[k] = float(D.cgd[k]);
+    }
     D.kind = J.spec.kind;
     D.dt = J.spec.dt;
     D.d = g->max_degree;
