@@ -217,41 +217,43 @@ static double marked_prob_coined(int64_t n, const int64_t *row_ptr, const uint8_
 
 /*
  * |psi(t)> = (S C)^t |psi(0)> (Sec. 3.2): each step applies the coin, then the
- * shift.  psi holds |psi(0)> on entry and |psi(steps)> on exit.  If record is
- * not NULL and marked is not NULL, record[t-1] receives the total probability
- * on the marked vertices after step t.  Returns 0 or -4 (out of memory).
+ * shift: the flip-flop shift when L1 == 0, else the persistent shift of the
+ * L1 x L2 torus.  psi holds |psi(0)> on entry and |psi(steps)> on exit.  If
+ * record is not NULL and marked is not NULL, record[t-1] receives the total
+ * probability on the marked vertices after step t.  Returns 0 or -4 (out of
+ * memory).
  */
-int oracle_coined_evolve(int64_t n, const int64_t *row_ptr, const int32_t *head, int coin,
-                         const uint8_t *marked, cplx *psi, int64_t steps, double *record)
+static int coined_loop(int64_t n, const int64_t *row_ptr, const int32_t *head, int coin,
+                       const uint8_t *marked, cplx *psi, int64_t steps, double *record,
+                       int64_t L1, int64_t L2)
 {
     int64_t num = row_ptr[n];
     cplx *tmp = malloc(sizeof(cplx) * (size_t)(num > 0 ? num : 1));
     if (!tmp) return -4;
     for (int64_t t = 1; t <= steps; ++t) {
         oracle_coin(n, row_ptr, coin, marked, psi, tmp);
-        oracle_shift(n, row_ptr, head, tmp, psi);
+        if (L1 == 0)
+            oracle_shift(n, row_ptr, head, tmp, psi);
+        else
+            oracle_shift_persistent_torus(L1, L2, row_ptr, head, tmp, psi);
         if (record && marked) record[t - 1] = marked_prob_coined(n, row_ptr, marked, psi);
     }
     free(tmp);
     return 0;
 }
 
-/* The same evolution with the persistent shift of the L1 x L2 torus in place
- * of the flip-flop shift. */
+int oracle_coined_evolve(int64_t n, const int64_t *row_ptr, const int32_t *head, int coin,
+                         const uint8_t *marked, cplx *psi, int64_t steps, double *record)
+{
+    return coined_loop(n, row_ptr, head, coin, marked, psi, steps, record, 0, 0);
+}
+
+/* The same evolution with the persistent shift of the L1 x L2 torus. */
 int oracle_coined_evolve_persistent_torus(int64_t L1, int64_t L2, const int64_t *row_ptr,
                                           const int32_t *head, int coin, const uint8_t *marked,
                                           cplx *psi, int64_t steps, double *record)
 {
-    int64_t n = L1 * L2, num = row_ptr[n];
-    cplx *tmp = malloc(sizeof(cplx) * (size_t)(num > 0 ? num : 1));
-    if (!tmp) return -4;
-    for (int64_t t = 1; t <= steps; ++t) {
-        oracle_coin(n, row_ptr, coin, marked, psi, tmp);
-        oracle_shift_persistent_torus(L1, L2, row_ptr, head, tmp, psi);
-        if (record && marked) record[t - 1] = marked_prob_coined(n, row_ptr, marked, psi);
-    }
-    free(tmp);
-    return 0;
+    return coined_loop(L1 * L2, row_ptr, head, coin, marked, psi, steps, record, L1, L2);
 }
 
 /* ------------------------------------------------------------ CTQW (Sec. 3.1) */
