@@ -47,9 +47,10 @@ UNIT = "arc-updates/s"
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # measured on; a changed kernel reports null until it is measured again.
 TRAFFIC = {
-    # the 1024x1024 torus step (k_coined_em<R,4,grover>), one launch, cold L2
-    ("c128", "bbf1c30839e5040f7fedd718501bb72d6eba4d97"): 83898880 + 22641664,
-    ("c64", "bbf1c30839e5040f7fedd718501bb72d6eba4d97"): 50341376 + 2242048,
+    # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free), one
+    # launch, cold L2 (profiles/coined_step_c{128,64}_torus1024.md)
+    ("c128", "4d4787c45ce968546a5a6f94f2728daed7ba1f2c"): 67124480 + 17122816,
+    ("c64", "4d4787c45ce968546a5a6f94f2728daed7ba1f2c"): 33565184 + 208640,
 }
 
 
