@@ -2,6 +2,7 @@
 
 A plain, slow restatement of the definitions in Motta et al., "Hiperwalk"
 (arXiv 2406.08186): Sec. 3.1 (CTQW: H = -gamma A - sum_m |m><m|, U(t) = e^{-iHt},
+with A optionally a weighted, Hermitian adjacency W,
 probability |<v|psi>|^2) and Sec. 3.2 (coined walk: U = S C, flip-flop shift
 S|v,w> = |w,v>, Grover coin, p_v = sum_w |<v,w|psi>|^2, arcs ordered by tail
 then head).  The arithmetic lives in ``hw_oracle.c``; this module builds it
@@ -77,6 +78,12 @@ def _load():
         lib.oracle_coined_evolve.restype = ctypes.c_int
         lib.oracle_ctqw_evolve.argtypes = [i64, P, P, ctypes.c_double, P, ctypes.c_double, P, i64, P]
         lib.oracle_ctqw_evolve.restype = ctypes.c_int
+        lib.oracle_ctqw_evolve_w.argtypes = [i64, P, P, ctypes.c_double, P, P, ctypes.c_double, P, i64, P]
+        lib.oracle_ctqw_evolve_w.restype = ctypes.c_int
+        lib.oracle_ctqw_columns_w.argtypes = [i64, P, P, ctypes.c_double, P, P, ctypes.c_double, P, i64, P]
+        lib.oracle_ctqw_columns_w.restype = ctypes.c_int
+        lib.oracle_arc_weights.argtypes = [i64, P, P, i64, P, P, P, P]
+        lib.oracle_arc_weights.restype = ctypes.c_int
         lib.oracle_ctqw_columns.argtypes = [i64, P, P, ctypes.c_double, P, ctypes.c_double, P, i64, P]
         lib.oracle_ctqw_columns.restype = ctypes.c_int
         lib.oracle_ctqw_action.argtypes = [i64, P, P, ctypes.c_double, P, ctypes.c_double, P]
@@ -117,6 +124,19 @@ class Arcs:
 
     def tail(self) -> np.ndarray:
         return np.repeat(np.arange(self.n, dtype=np.int64), np.diff(self.row_ptr))
+
+    def weights(self, eu, ev, we) -> np.ndarray:
+        """Arc weights in basis order from one value per edge {eu, ev}: arc (eu, ev)
+        gets we, arc (ev, eu) its conjugate (a Hermitian weighted adjacency)."""
+        eu = np.ascontiguousarray(eu, dtype=np.int64)
+        ev = np.ascontiguousarray(ev, dtype=np.int64)
+        we = np.ascontiguousarray(we, dtype=np.complex128)
+        out = np.zeros(self.num_arcs, dtype=np.complex128)
+        rc = _load().oracle_arc_weights(self.n, _p(self.row_ptr), _p(self.head), eu.size, _p(eu), _p(ev),
+                                        _p(we), _p(out))
+        if rc != 0:
+            raise ValueError("edge without arc")
+        return out
 
     def flags(self, marked) -> np.ndarray:
         f = np.zeros(self.n, dtype=np.uint8)
@@ -179,23 +199,26 @@ def prob_coined(arcs: Arcs, psi: np.ndarray) -> np.ndarray:
 
 
 def ctqw_evolve(arcs: Arcs, gamma: float, psi0: np.ndarray, dt: float, steps: int,
-                marked=None, record: bool = False):
-    """U(dt)^steps psi0 with U = e^{-iH dt}, H = -gamma A - sum_m |m><m|."""
+                marked=None, record: bool = False, weights=None):
+    """U(dt)^steps psi0 with U = e^{-iH dt}, H = -gamma W - sum_m |m><m|; W = A, or the
+    weighted adjacency whose arc weights (basis order, ``Arcs.weights``) are given."""
     psi = np.array(psi0, dtype=np.complex128, copy=True)
     rec = np.zeros(max(steps, 1), dtype=np.float64) if record else None
-    rc = _load().oracle_ctqw_evolve(arcs.n, _p(arcs.row_ptr), _p(arcs.head), float(gamma),
-                                    _p(arcs.flags(marked)), float(dt), _p(psi), int(steps), _p(rec))
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.complex128)
+    rc = _load().oracle_ctqw_evolve_w(arcs.n, _p(arcs.row_ptr), _p(arcs.head), float(gamma),
+                                      _p(arcs.flags(marked)), _p(w), float(dt), _p(psi), int(steps), _p(rec))
     if rc != 0:
         raise MemoryError("oracle_ctqw_evolve")
     return (psi, rec[:steps]) if record else psi
 
 
-def ctqw_columns(arcs: Arcs, gamma: float, dt: float, cols, marked=None) -> np.ndarray:
+def ctqw_columns(arcs: Arcs, gamma: float, dt: float, cols, marked=None, weights=None) -> np.ndarray:
     """Columns U(dt)[:, j] for j in cols, returned as an [n, len(cols)] array."""
     cols = np.ascontiguousarray(cols, dtype=np.int64)
     out = np.empty((cols.size, arcs.n), dtype=np.complex128)
-    rc = _load().oracle_ctqw_columns(arcs.n, _p(arcs.row_ptr), _p(arcs.head), float(gamma),
-                                     _p(arcs.flags(marked)), float(dt), _p(cols), cols.size, _p(out))
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.complex128)
+    rc = _load().oracle_ctqw_columns_w(arcs.n, _p(arcs.row_ptr), _p(arcs.head), float(gamma),
+                                       _p(arcs.flags(marked)), _p(w), float(dt), _p(cols), cols.size, _p(out))
     if rc != 0:
         raise MemoryError("oracle_ctqw_columns")
     return out.T.copy()

@@ -258,14 +258,17 @@ int oracle_coined_evolve_persistent_torus(int64_t L1, int64_t L2, const int64_t 
 
 /* ------------------------------------------------------------ CTQW (Sec. 3.1) */
 
-/* y = H x with H = -gamma A - sum_{m in M} |m><m| (Sec. 3.1), A from the arc list. */
+/* y = H x with H = -gamma W - sum_{m in M} |m><m| (Sec. 3.1, with the adjacency
+ * A generalised to a weighted one): W = A when w is NULL, else row v of W holds
+ * w[a] at column head[a] for each arc a of v (for a Hermitian W, arc (u, v)
+ * carries the conjugate of arc (v, u)'s weight). */
 static void ham_apply(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
-                      const uint8_t *marked, const cplx *x, cplx *y)
+                      const uint8_t *marked, const cplx *w, const cplx *x, cplx *y)
 {
     #pragma omp parallel for schedule(static)
     for (int64_t v = 0; v < n; ++v) {
         cplx acc = 0.0;
-        for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) acc += x[head[a]];
+        for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) acc += (w ? w[a] : 1.0) * x[head[a]];
         acc = -gamma * acc;
         if (marked && marked[v]) acc -= x[v];
         y[v] = acc;
@@ -280,11 +283,13 @@ static void ham_apply(int64_t n, const int64_t *row_ptr, const int32_t *head, do
  * work: 2n complex.  Returns the total number of series terms used.
  */
 static int64_t ctqw_apply(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
-                          const uint8_t *marked, double dt, cplx *psi, cplx *work)
+                          const uint8_t *marked, const cplx *w, double dt, cplx *psi, cplx *work)
 {
     double hnorm = 0.0;                       /* max row sum of |H| */
     for (int64_t v = 0; v < n; ++v) {
-        double r = fabs(gamma) * (double)(row_ptr[v + 1] - row_ptr[v]);
+        double rw = 0.0;
+        for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) rw += w ? cabs(w[a]) : 1.0;
+        double r = fabs(gamma) * rw;
         if (marked && marked[v]) r += 1.0;
         if (r > hnorm) hnorm = r;
     }
@@ -296,7 +301,7 @@ static int64_t ctqw_apply(int64_t n, const int64_t *row_ptr, const int32_t *head
     for (int64_t r = 0; r < q; ++r) {
         memcpy(term, psi, sizeof(cplx) * (size_t)n);
         for (int k = 1; k <= 200; ++k) {
-            ham_apply(n, row_ptr, head, gamma, marked, term, next);
+            ham_apply(n, row_ptr, head, gamma, marked, w, term, next);
             double mx = 0.0;
             cplx f = -I * tau / (double)k;
             for (int64_t v = 0; v < n; ++v) {
@@ -319,14 +324,14 @@ static int64_t ctqw_apply(int64_t n, const int64_t *row_ptr, const int32_t *head
  * |psi(steps dt)> out.  record[k-1] (if not NULL) = total probability on the
  * marked vertices at time k dt.  Returns 0 or -4.
  */
-int oracle_ctqw_evolve(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
-                       const uint8_t *marked, double dt, cplx *psi, int64_t steps,
-                       double *record)
+int oracle_ctqw_evolve_w(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
+                         const uint8_t *marked, const cplx *w, double dt, cplx *psi, int64_t steps,
+                         double *record)
 {
     cplx *work = malloc(sizeof(cplx) * (size_t)(2 * (n > 0 ? n : 1)));
     if (!work) return -4;
     for (int64_t k = 1; k <= steps; ++k) {
-        ctqw_apply(n, row_ptr, head, gamma, marked, dt, psi, work);
+        ctqw_apply(n, row_ptr, head, gamma, marked, w, dt, psi, work);
         if (record) {
             double acc = 0.0;
             for (int64_t v = 0; v < n; ++v)
@@ -338,11 +343,19 @@ int oracle_ctqw_evolve(int64_t n, const int64_t *row_ptr, const int32_t *head, d
     return 0;
 }
 
+int oracle_ctqw_evolve(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
+                       const uint8_t *marked, double dt, cplx *psi, int64_t steps,
+                       double *record)
+{
+    return oracle_ctqw_evolve_w(n, row_ptr, head, gamma, marked, NULL, dt, psi, steps, record);
+}
+
 /* Columns U(dt) e_j of the evolution operator for the listed j (ncols of them):
- * out is row-major [ncols][n], out[c][i] = U[i][cols[c]].  Returns 0 or -4. */
-int oracle_ctqw_columns(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
-                        const uint8_t *marked, double dt, const int64_t *cols, int64_t ncols,
-                        cplx *out)
+ * out is row-major [ncols][n], out[c][i] = U[i][cols[c]].  w as in ham_apply.
+ * Returns 0 or -4. */
+int oracle_ctqw_columns_w(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
+                          const uint8_t *marked, const cplx *w, double dt, const int64_t *cols,
+                          int64_t ncols, cplx *out)
 {
     cplx *work = malloc(sizeof(cplx) * (size_t)(2 * (n > 0 ? n : 1)));
     if (!work) return -4;
@@ -350,10 +363,17 @@ int oracle_ctqw_columns(int64_t n, const int64_t *row_ptr, const int32_t *head, 
         cplx *col = out + c * n;
         for (int64_t v = 0; v < n; ++v) col[v] = 0.0;
         col[cols[c]] = 1.0;
-        ctqw_apply(n, row_ptr, head, gamma, marked, dt, col, work);
+        ctqw_apply(n, row_ptr, head, gamma, marked, w, dt, col, work);
     }
     free(work);
     return 0;
+}
+
+int oracle_ctqw_columns(int64_t n, const int64_t *row_ptr, const int32_t *head, double gamma,
+                        const uint8_t *marked, double dt, const int64_t *cols, int64_t ncols,
+                        cplx *out)
+{
+    return oracle_ctqw_columns_w(n, row_ptr, head, gamma, marked, NULL, dt, cols, ncols, out);
 }
 
 /* U(dt) x for one vector x (in place).  Returns the number of series terms. */
@@ -362,9 +382,27 @@ int64_t oracle_ctqw_action(int64_t n, const int64_t *row_ptr, const int32_t *hea
 {
     cplx *work = malloc(sizeof(cplx) * (size_t)(2 * (n > 0 ? n : 1)));
     if (!work) return -4;
-    int64_t used = ctqw_apply(n, row_ptr, head, gamma, marked, dt, x, work);
+    int64_t used = ctqw_apply(n, row_ptr, head, gamma, marked, NULL, dt, x, work);
     free(work);
     return used;
+}
+
+/* Weights of the arcs of an edge list in basis order: edge e = {eu[e], ev[e]}
+ * with value we[e] gives arc (eu, ev) the weight we[e] and arc (ev, eu) its
+ * conjugate (a Hermitian W; a real we gives a symmetric one).  Arcs are found
+ * by bisection in their rows.  Returns 0, or -1 when an edge has no arc. */
+int oracle_arc_weights(int64_t n, const int64_t *row_ptr, const int32_t *head, int64_t n_edges,
+                       const int64_t *eu, const int64_t *ev, const cplx *we, cplx *w_arc)
+{
+    (void)n;
+    for (int64_t e = 0; e < n_edges; ++e) {
+        int64_t a = arc_in_row(row_ptr, head, eu[e], ev[e]);
+        int64_t b = arc_in_row(row_ptr, head, ev[e], eu[e]);
+        if (a < 0 || b < 0) return -1;
+        w_arc[a] = we[e];
+        w_arc[b] = conj(we[e]);
+    }
+    return 0;
 }
 
 /* |<v|psi>|^2 (Sec. 3.1). */

@@ -220,6 +220,33 @@ def adjacency_csr(n: int, eu: np.ndarray, ev: np.ndarray, scramble_seed: int | N
     return row_ptr, heads[order].astype(np.int32)
 
 
+def edge_weights(count: int, seed: int, complex_phase: bool = False) -> np.ndarray:
+    """One weight per edge: modulus uniform in [0.25, 1.75) and, with
+    ``complex_phase``, a phase uniform in [0, 2 pi) (SplitMix64 draws)."""
+    r = 0.25 + 1.5 * uniform01(seed, count)
+    if not complex_phase:
+        return r.astype(np.float64)
+    ph = 2 * np.pi * uniform01(seed, count, offset=count)
+    return r * np.exp(1j * ph)
+
+
+def weighted_csr(n: int, eu: np.ndarray, ev: np.ndarray, we: np.ndarray, scramble_seed: int | None = 7):
+    """``adjacency_csr`` plus the weight of each entry: entry (eu, ev) holds we and
+    entry (ev, eu) its conjugate, so the matrix is Hermitian (symmetric for real we).
+    Returns (row_ptr, col, w) with w complex128 or float64 like ``we``."""
+    tails = np.concatenate([eu, ev])
+    heads = np.concatenate([ev, eu])
+    vals = np.concatenate([we, np.conj(we)])
+    if scramble_seed is None:
+        key = np.arange(tails.size)
+    else:
+        key = splitmix64(scramble_seed, tails.size)
+    order = np.lexsort((key, tails))
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(tails, minlength=n), out=row_ptr[1:])
+    return row_ptr, heads[order].astype(np.int32), vals[order]
+
+
 def arc_offsets(n: int, eu: np.ndarray, ev: np.ndarray) -> np.ndarray:
     """Start of each vertex's arc block in the tail-major arc order: a prefix sum of
     degrees, int64[n+1] (independent of how heads are ordered inside a block)."""

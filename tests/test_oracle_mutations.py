@@ -30,6 +30,9 @@ MUTATIONS = {
                               "int64_t u = ((xw - dx + L1) % L1) * L2 + (yw - dy + L2) % L2;"),
     "persistent_axes_swapped": ("int64_t u = ((xw + dx) % L1) * L2 + (yw + dy) % L2;",
                                 "int64_t u = ((xw + dy) % L1) * L2 + (yw + dx) % L2;"),
+    "weight_conjugated": ("acc += (w ? w[a] : 1.0) * x[head[a]];", "acc += (w ? conj(w[a]) : 1.0) * x[head[a]];"),
+    "weight_ignored": ("acc += (w ? w[a] : 1.0) * x[head[a]];", "acc += x[head[a]];"),
+    "arc_weight_not_conjugate": ("w_arc[b] = conj(we[e]);", "w_arc[b] = we[e];"),
     "rev_self": ("rev[a] = find_arc(arcs, num, arcs[a].head, arcs[a].tail);",
                  "rev[a] = find_arc(arcs, num, arcs[a].tail, arcs[a].head);"),
     "ham_gamma_sign": ("acc = -gamma * acc;", "acc = gamma * acc;"),
@@ -57,6 +60,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_coined.py"),
                         os.path.join(ROOT, "tests", "test_oracle_ctqw.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_persistent.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_persistent.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_weighted.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "planted mistake %r was not caught:\n%s" % (name, r.stdout[-2000:])
