@@ -458,6 +458,72 @@ def run_workload_ctqw(args):
     print(json.dumps(res), flush=True)
 
 
+def run_workload_weighted(args):
+    """CTQW with a weighted adjacency H = -gamma W - |m><m|: (1) the Q_12 search of the
+    CTQW workload with seeded real edge weights in [0.25, 1.75) (dense U by the
+    Taylor series; complex64 needs two fp16 slices of Y, the unweighted walk one),
+    (2) the sparse-action series on the 2^20-vertex hypercube with real and with
+    complex (Hermitian) weights, gamma = 1/20, dt = 0.1, 20 applications."""
+    import torch
+    import paper_2406_08186_b300 as hw
+    stream = torch.cuda.current_stream()
+    fp64 = hw.hw_measure_fp64()
+    res = {"workload": "weighted_ctqw", "fp64_peak_ops": fp64}
+    n, eu, ev = synth.hypercube(12)
+    m = synth.seeded_vertex(3, n)
+    rp, col, w = synth.weighted_csr(n, eu, ev, synth.edge_weights(eu.size, seed=9))
+    G = hw.hw_graph_csr_weighted(n, rp, col, w)
+    for dt, name in ((hw.HW_C128, "q12_expm_c128"), (hw.HW_C64, "q12_expm_c64")):
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        U = torch.empty((n, n), dtype=cdt, device="cuda")
+        for _ in range(max(1, args.warmup)):
+            hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+        torch.cuda.synchronize()
+        e = _events(2)
+        e[0].record(stream)
+        for _ in range(args.steps):
+            hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        t = e[0].elapsed_time(e[1]) / 1e3 / args.steps
+        deg, sq = hw.hw_ctqw_plan(G, 1 / 12, [m], 0.1)
+        res[name] = {"ms": t * 1e3, "taylor_degree": deg, "squarings": sq,
+                     "gemm_tflops_useful": (deg - 1) * 2.0 * n ** 3 / t / 1e12}
+    G.free()
+    k = 20
+    n, eu, ev = synth.hypercube(k)
+    m = synth.seeded_vertex(3, n)
+    walk = 20
+    for cplx in (False, True):
+        rp, col, w = synth.weighted_csr(n, eu, ev, synth.edge_weights(eu.size, seed=5, complex_phase=cplx))
+        G = hw.hw_graph_csr_weighted(n, rp, col, w)
+        deg, sq = hw.hw_ctqw_plan(G, 1.0 / k, [m], 0.1)
+        terms = walk * deg * (1 << sq)
+        for dt, esz in ((hw.HW_C128, 16), (hw.HW_C64, 8)):
+            cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+            x = torch.full((n,), 1.0 / math.sqrt(n), dtype=cdt, device="cuda")
+            y = torch.empty_like(x)
+            hw.hw_ctqw_evolve_sparse(G, 1.0 / k, [m], 0.1, dt, 1, 2, x, y)
+            torch.cuda.synchronize()
+            e = _events(2)
+            e[0].record(stream)
+            for _ in range(args.steps):
+                hw.hw_ctqw_evolve_sparse(G, 1.0 / k, [m], 0.1, dt, 1, walk, x, y)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            per_term = e[0].elapsed_time(e[1]) / 1e3 / args.steps / terms
+            r = {"us_per_term": per_term * 1e6, "terms": terms, "gathers_per_s": (G.num_arcs + n) / per_term}
+            if dt == hw.HW_C128:
+                # FP64 operations per vertex: 2 (real) or 4 (complex) FMAs per
+                # neighbour, two multiplies and two adds for the term and the sum
+                ops = n * ((4 if cplx else 2) * k + 4)
+                r["fp64_ops_per_s"] = ops / per_term
+                r["frac_fp64_measured"] = ops / per_term / fp64
+            res["q20_sparse_%s_%s" % ("complex" if cplx else "real", "c128" if dt == hw.HW_C128 else "c64")] = r
+        G.free()
+    print(json.dumps(res), flush=True)
+
+
 def run_workload_torus64(args):
     """64 x 64 torus, Grover, no mark, start on the 4 arcs of (32, 32), 100 steps, complex128."""
     import torch
@@ -792,7 +858,7 @@ def main():
     ap.add_argument("--profile-tile", type=int, default=10)
     ap.add_argument("--workload", default="torus1024_search",
                     choices=["torus1024_search", "torus64_center", "hypercube12_ctqw", "er_batched",
-                             "serving", "sampled", "sparse_ctqw"],
+                             "serving", "sampled", "sparse_ctqw", "weighted_ctqw"],
                     help="the default is the benchmarked workload; the others print their own line")
     ap.add_argument("--jobs", type=int, default=10000, help="serving: number of jobs")
     ap.add_argument("--baseline-jobs", type=int, default=200, help="serving: jobs timed on the plain path")
@@ -811,6 +877,8 @@ def main():
         run_workload_sampled(args)
     elif args.workload == "sparse_ctqw":
         run_workload_sparse_ctqw(args)
+    elif args.workload == "weighted_ctqw":
+        run_workload_weighted(args)
     elif args.workload == "serving":
         run_workload_serving(args)
     elif args.impl == "reference":

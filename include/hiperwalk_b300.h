@@ -111,6 +111,25 @@ hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx
                        void *stream, hw_graph **out);
 
 /*
+ * hw_graph_csr_weighted -- hw_graph_csr with a weighted adjacency W for the
+ * continuous-time calls: H = -gamma W - sum_{m in M} |m><m| (Sec. 3.1 with A
+ * generalised to edge weights).
+ *   w_re     HOST double[row_ptr[n]], aligned with col_idx: W[v][col_idx[a]]
+ *   w_im     HOST double[row_ptr[n]] or NULL.  NULL: W is real and must be
+ *            symmetric, W[u][v] == W[v][u] exactly; else W = w_re + i w_im must
+ *            be Hermitian, W[v][u] == conj(W[u][v]) exactly
+ * Weights must be finite; a zero weight keeps its arc in the basis.  The
+ * structure rules and the arc basis are those of hw_graph_csr.  Weighted
+ * graphs serve hw_ctqw_plan, hw_ctqw_expm (real W only: a complex W gives
+ * HW_EUNSUPPORTED) and hw_ctqw_evolve_sparse (real or complex W); coined walks
+ * and served jobs need an unweighted graph (HW_EINVAL / HW_EUNSUPPORTED).
+ * Errors: as hw_graph_csr, plus HW_EINVAL for w_re NULL, a non-finite weight
+ * or a W that is not symmetric / Hermitian.
+ */
+hw_status hw_graph_csr_weighted(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                const double *w_re, const double *w_im, void *stream, hw_graph **out);
+
+/*
  * hw_graph_arcs_host -- the same arc basis as hw_graph_csr, computed on the
  * host only (no device is touched).  Same input rules and errors.
  *   row_ptr_out  HOST int32[n+1]           (may be NULL)

@@ -33,7 +33,8 @@ EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free"
            "hw_server_create", "hw_server_submit", "hw_server_run", "hw_server_poll",
            "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_trim_scratch", "hw_last_error",
            "hw_version", "hw_coined_sample", "hw_ctqw_sample", "hw_graph_structure",
-           "hw_graph_structure_host", "hw_measure_fp64", "hw_measure_l2")
+           "hw_graph_structure_host", "hw_measure_fp64", "hw_measure_l2",
+           "hw_graph_csr_weighted")
 
 
 class HWError(RuntimeError):
@@ -74,6 +75,8 @@ def lib():
         L.hw_opts_init.restype = None
         L.hw_graph_csr.argtypes = [i64, P, P, P, ctypes.POINTER(P)]
         L.hw_graph_csr.restype = st
+        L.hw_graph_csr_weighted.argtypes = [i64, P, P, P, P, P, ctypes.POINTER(P)]
+        L.hw_graph_csr_weighted.restype = st
         L.hw_graph_arcs_host.argtypes = [i64, P, P, P, P, P]
         L.hw_graph_arcs_host.restype = st
         L.hw_graph_structure.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64)]
@@ -247,6 +250,24 @@ def hw_graph_csr(n: int, row_ptr, col_idx, stream=None) -> Graph:
     h = ctypes.c_void_p()
     _check(lib().hw_graph_csr(int(n), rp.ctypes.data_as(ctypes.c_void_p),
                               ci.ctypes.data_as(ctypes.c_void_p), _stream(stream), ctypes.byref(h)))
+    g = Graph(h, int(n), 0)
+    g.num_arcs = hw_graph_info(g)["num_arcs"]
+    return g
+
+
+def hw_graph_csr_weighted(n: int, row_ptr, col_idx, weights, stream=None) -> Graph:
+    """A graph whose CTQW Hamiltonian uses the weighted adjacency: ``weights`` is
+    aligned with ``col_idx``, real (symmetric W) or complex (Hermitian W)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    w = np.asarray(weights)
+    wre = np.ascontiguousarray(w.real, dtype=np.float64)
+    wim = np.ascontiguousarray(w.imag, dtype=np.float64) if np.iscomplexobj(w) else None
+    h = ctypes.c_void_p()
+    _check(lib().hw_graph_csr_weighted(int(n), rp.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p),
+                                       wre.ctypes.data_as(ctypes.c_void_p),
+                                       None if wim is None else wim.ctypes.data_as(ctypes.c_void_p),
+                                       _stream(stream), ctypes.byref(h)))
     g = Graph(h, int(n), 0)
     g.num_arcs = hw_graph_info(g)["num_arcs"]
     return g

@@ -173,6 +173,8 @@ struct Scratch {
 // shift operator and addressing of a coined call (hw_opts.shift, .addressing)
 hw_status coined_opts(const hw_graph *g, const hw_opts *opts, int *shift, bool *index_free)
 {
+    if (g->weighted)
+        return hw_fail(HW_EINVAL, "coined walks take the adjacency of an unweighted graph (hw_graph_csr)");
     *shift = opts ? opts->shift : kShiftFlipFlop;
     const int addressing = opts ? opts->addressing : 0;
     if (*shift != kShiftFlipFlop && *shift != kShiftPersistent)

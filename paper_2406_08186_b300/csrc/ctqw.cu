@@ -104,13 +104,14 @@ hw_status dgemm(const GemmArgs &a, cudaStream_t st)
 }
 
 // ------------------------------------------------------------ elementwise
-// Y = tau * H: -gamma*tau on every arc, -tau added on marked diagonals.
+// Y = tau * H: -gamma*tau (times the arc's weight for a weighted W) on every
+// arc, -tau added on marked diagonals.
 __global__ void k_scatter_y(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ head,
-                            int n, double off, double *__restrict__ Y)
+                            const double *__restrict__ w, int n, double off, double *__restrict__ Y)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    for (int a = row_ptr[v]; a < row_ptr[v + 1]; ++a) Y[int64_t(v) * n + head[a]] = off;
+    for (int a = row_ptr[v]; a < row_ptr[v + 1]; ++a) Y[int64_t(v) * n + head[a]] = w ? off * w[a] : off;
 }
 
 __global__ void k_mark_diag(MarkedList mk, int n, double diag, double *__restrict__ Y)
@@ -478,15 +479,16 @@ extern "C" hw_status hw_ctqw_plan(const hw_graph *g, double gamma, const int32_t
 {
     hw_clear_error();
     if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
-    // ||H||_1 = max over v of (gamma d_v + [v in M]): the largest degree's row,
-    // or a marked vertex's row, whichever is larger (O(n_marked), no pass over
-    // the graph)
-    double norm1 = std::fabs(gamma) * double(g->max_degree);
+    // ||H||_1 = max over v of (gamma sum_w |W_vw| + [v in M]) (= gamma d_v + [v
+    // in M] unweighted): the largest row of W, or a marked vertex's row,
+    // whichever is larger (O(n_marked), no pass over the graph)
+    auto row = [&](int64_t v) {
+        return g->weighted ? g->h_rowabs[size_t(v)] : double(g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
+    };
+    double norm1 = std::fabs(gamma) * (g->weighted ? g->max_rowabs : double(g->max_degree));
     for (int32_t i = 0; i < n_marked; ++i)
-        if (marked && marked[i] >= 0 && marked[i] < g->n) {
-            const int64_t v = marked[i];
-            norm1 = std::max(norm1, std::fabs(gamma) * double(g->h_row_ptr[v + 1] - g->h_row_ptr[v]) + 1.0);
-        }
+        if (marked && marked[i] >= 0 && marked[i] < g->n)
+            norm1 = std::max(norm1, std::fabs(gamma) * row(marked[i]) + 1.0);
     norm1 *= std::fabs(time);
     int m, s;
     ctqw_plan(norm1, &m, &s);
@@ -507,6 +509,9 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     if (!std::isfinite(gamma) || !std::isfinite(time)) return hw_fail(HW_EINVAL, "gamma/time not finite");
     if (n_marked < 0 || (n_marked > 0 && !marked)) return hw_fail(HW_EINVAL, "bad marked list");
     if (g->n > 32768) return hw_fail(HW_EUNSUPPORTED, "dense U limited to n <= 32768 (n = %lld)", (long long)g->n);
+    if (g->complex_weights)
+        return hw_fail(HW_EUNSUPPORTED, "the dense U takes a real symmetric W; complex weights run through "
+                                        "hw_ctqw_evolve_sparse");
     int dev = -1;
     hw_status s = hw_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (s != HW_OK) return s;
@@ -543,26 +548,31 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
         // series is summed below the diagonal only.
         // T1 + the k = 0, 1 terms: Re U = I, Im U = -Y = gamma tau A + tau sum_m |m><m|
         k_init_lower<<<row_grid(n), 256, 0, st>>>(n, Re.as<double>(), Im.as<double>());
-        k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, n, gamma * tau, Im.as<double>());
+        k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, g->d_wre, n, gamma * tau, Im.as<double>());
         if (mk.n) k_mark_diag<<<(mk.n + 127) / 128, 128, 0, st>>>(mk, n, tau, Im.as<double>());
         if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;
         TcPower *tp = nullptr;
-        // host-known magnitudes of Y's entries (edge weight gamma tau, marked
-        // diagonal tau) and ||Y||_inf
-        double yvals[2];
-        int nyvals = 0;
-        if (g->num_arcs && gamma != 0.0) yvals[nyvals++] = std::fabs(gamma * tau);
-        if (mk.n && tau != 0.0) yvals[nyvals++] = std::fabs(tau);
+        // host-known magnitudes of Y's entries (edge weights gamma tau |w|,
+        // marked diagonal tau) and ||Y||_inf
+        std::vector<double> yvals;
+        if (g->num_arcs && gamma != 0.0) {
+            if (g->weighted)
+                for (double wa : g->h_wabs) yvals.push_back(std::fabs(gamma * tau) * wa);
+            else
+                yvals.push_back(std::fabs(gamma * tau));
+        }
+        if (mk.n && tau != 0.0) yvals.push_back(std::fabs(tau));
         double theta = 0.0;
         {
             std::vector<char> is_m(n, 0);
             for (int32_t i = 0; i < n_marked; ++i) is_m[marked[i]] = 1;
-            for (int v = 0; v < n; ++v)
-                theta = std::max(theta, (std::fabs(gamma) * (g->h_row_ptr[v + 1] - g->h_row_ptr[v]) +
-                                         (is_m[v] ? 1.0 : 0.0)) * std::fabs(tau));
+            for (int v = 0; v < n; ++v) {
+                const double rw = g->weighted ? g->h_rowabs[v] : double(g->h_row_ptr[v + 1] - g->h_row_ptr[v]);
+                theta = std::max(theta, (std::fabs(gamma) * rw + (is_m[v] ? 1.0 : 0.0)) * std::fabs(tau));
+            }
         }
-        const SymSparse ys{g->d_row_ptr, g->d_head, n, -gamma * tau, mk, -tau};
-        if ((s = tc_power_begin(ys, yvals, nyvals, theta, gmode, st, &tp)) != HW_OK) return s;
+        const SymSparse ys{g->d_row_ptr, g->d_head, g->d_wre, n, -gamma * tau, mk, -tau};
+        if ((s = tc_power_begin(ys, yvals.data(), int(yvals.size()), theta, gmode, st, &tp)) != HW_OK) return s;
         for (int k = 2; k <= m_deg && s == HW_OK; ++k) {
             double *accU = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
             const double sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
@@ -586,7 +596,7 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
         // T1: Y = tau H
         if ((s = Y.get(bytes, "scratch allocation (Y)")) != HW_OK) return s;
         if ((s = hw_cuda(cudaMemsetAsync(Y.p, 0, bytes, st), "memset Y")) != HW_OK) return s;
-        k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, n, -gamma * tau, Y.as<double>());
+        k_scatter_y<<<(n + 255) / 256, 256, 0, st>>>(g->d_row_ptr, g->d_head, g->d_wre, n, -gamma * tau, Y.as<double>());
         if (mk.n) k_mark_diag<<<(mk.n + 127) / 128, 128, 0, st>>>(mk, n, -tau, Y.as<double>());
         k_taylor_init<<<ew_grid(nn), 256, 0, st>>>(n, Y.as<double>(), Re.as<double>(), Im.as<double>());
         if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;

@@ -3,7 +3,8 @@
 // (e^{-iH dt} = (e^{-iH dt/q})^q) and sums the exponential series of each
 // part to degree m, with (s, m) from the same rule as hw_ctqw_plan
 // (||H dt/q|| <= 1/2, truncation < 2^-60).  A term is
-//   t_k = (-i tau / k) H t_{k-1},  (H x)_v = -gamma sum_{w ~ v} x_w - [v in M] x_v,
+//   t_k = (-i tau / k) H t_{k-1},  (H x)_v = -gamma sum_{w ~ v} W_vw x_w - [v in M] x_v,
+// with W = A or a weighted Hermitian adjacency (hw_graph_csr_weighted),
 // one CSR gather per vertex; the partial sum is accumulated in the same pass.
 // Work per application: q*m sparse products of 2|E| + n entries, so large
 // graphs that have no room for a dense n x n U stay cheap.
@@ -49,10 +50,12 @@ __device__ __forceinline__ void term_tail(R sx, R sy, const MarkedList &mk, int 
 }
 
 // t_out = (-i tau/k) H t_in; acc = (first ? x + t_out : acc + t_out).
-// Thread per (vertex, column); neighbours in sorted order, the sum starting
-// from the first one.
-template <typename R>
-__global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ head, int64_t n,
+// Thread per (vertex, column); neighbours in sorted order.  WT: 0 unweighted
+// (the sum starts from the first neighbour), 1 real weights wr, 2 complex
+// weights wr + i wi (the sum of w_a t_in[head a] by FMAs from zero).
+template <typename R, int WT>
+__global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ head,
+                            const R *__restrict__ wr, const R *__restrict__ wi, int64_t n,
                             int batch, MarkedList mk, R cg, R coef, const void *x_,
                             const void *tin_, void *tout_, void *acc_, int first)
 {
@@ -73,16 +76,30 @@ __global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *
     R sx = 0, sy = 0;
     int a = row_ptr[v];
     const int e = row_ptr[v + 1];
-    if (a < e) {
-        const V q = tin[int64_t(head[a]) * batch + b];
-        sx = q.x;
-        sy = q.y;
-        ++a;
-    }
-    for (; a < e; ++a) {
-        const V q = tin[int64_t(head[a]) * batch + b];
-        sx += q.x;
-        sy += q.y;
+    if constexpr (WT == 0) {
+        if (a < e) {
+            const V q = tin[int64_t(head[a]) * batch + b];
+            sx = q.x;
+            sy = q.y;
+            ++a;
+        }
+        for (; a < e; ++a) {
+            const V q = tin[int64_t(head[a]) * batch + b];
+            sx += q.x;
+            sy += q.y;
+        }
+    } else {
+        for (; a < e; ++a) {
+            const V q = tin[int64_t(head[a]) * batch + b];
+            const R w = wr[a];
+            sx = fma(w, q.x, sx);
+            sy = fma(w, q.y, sy);
+            if constexpr (WT == 2) {
+                const R u = wi[a];
+                sx = fma(-u, q.y, sx);
+                sy = fma(u, q.x, sy);
+            }
+        }
     }
     term_tail<R, V>(sx, sy, mk, int(v), cg, coef, tin, x, tout, acc, i, first);
     pdl_trigger();
@@ -148,15 +165,31 @@ hw_status launch_term(const hw_graph *g, bool index_free, int batch, const Marke
     const R cg = R(coef * gamma), c = R(coef);
     const int64_t total = g->n * batch;
     const int64_t grid = (total + 255) / 256;
-    if (index_free && g->kind == HW_GRAPH_TORUS)
+    const R *wr = nullptr, *wi = nullptr;
+    if constexpr (sizeof(R) == 8) {
+        wr = reinterpret_cast<const R *>(g->d_wre);
+        wi = reinterpret_cast<const R *>(g->d_wim);
+    } else {
+        wr = reinterpret_cast<const R *>(g->d_wre_f);
+        wi = reinterpret_cast<const R *>(g->d_wim_f);
+    }
+    if (g->weighted) {
+        // weights are per arc of the CSR: the table path, no label arithmetic
+        if (g->complex_weights)
+            launch_pdl(k_ctqw_term<R, 2>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
+                       (const int32_t *)g->d_head, wr, wi, g->n, batch, mk, cg, c, x, tin, tout, acc, first);
+        else
+            launch_pdl(k_ctqw_term<R, 1>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
+                       (const int32_t *)g->d_head, wr, wi, g->n, batch, mk, cg, c, x, tin, tout, acc, first);
+    } else if (index_free && g->kind == HW_GRAPH_TORUS)
         launch_pdl(k_ctqw_term_fam<R, HW_GRAPH_TORUS>, dim3(unsigned(grid)), dim3(256), 0, st, g->n, batch,
                    int(g->dims[0]), int(g->dims[1]), mk, cg, c, x, tin, tout, acc, first);
     else if (index_free && g->kind == HW_GRAPH_HYPERCUBE)
         launch_pdl(k_ctqw_term_fam<R, HW_GRAPH_HYPERCUBE>, dim3(unsigned(grid)), dim3(256), 0, st, g->n, batch,
                    int(g->dims[0]), 0, mk, cg, c, x, tin, tout, acc, first);
     else
-        launch_pdl(k_ctqw_term<R>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
-                   (const int32_t *)g->d_head, g->n, batch, mk, cg, c, x, tin, tout, acc, first);
+        launch_pdl(k_ctqw_term<R, 0>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
+                   (const int32_t *)g->d_head, wr, wi, g->n, batch, mk, cg, c, x, tin, tout, acc, first);
     return hw_cuda(cudaGetLastError(), "k_ctqw_term launch");
 }
 

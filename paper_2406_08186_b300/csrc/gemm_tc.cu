@@ -666,7 +666,7 @@ __global__ void k_scatter_slices(SymSparse Y, double sc, int ns, int ld, void *s
     if (v < Y.n) {
         const double xs = Y.off * sc;
         for (int a = Y.row_ptr[v]; a < Y.row_ptr[v + 1]; ++a)
-            put_slices<FMT>(xs, ns, int64_t(v) * ld + Y.col[a], s0, s1, s2);
+            put_slices<FMT>(Y.w ? xs * Y.w[a] : xs, ns, int64_t(v) * ld + Y.col[a], s0, s1, s2);
     }
     if (v < Y.mk.n) {
         const int m = marked_id(Y.mk, v);

@@ -2,13 +2,15 @@
 // shift as a reversal table, and the vertex-block partition used by the
 // fused coin+shift kernel.  Host code; the result is uploaded once per graph.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "internal.h"
 
 hw_status hw_build_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                              std::vector<int32_t> &rp, std::vector<int32_t> &head,
-                             std::vector<int32_t> &rev)
+                             std::vector<int32_t> &rev, const double *w_re, const double *w_im,
+                             std::vector<double> *wre_out, std::vector<double> *wim_out)
 {
     if (n < 1) return hw_fail(HW_EINVAL, "n must be >= 1 (got %lld)", (long long)n);
     if (n >= (int64_t(1) << 31) - 1) return hw_fail(HW_EUNSUPPORTED, "n >= 2^31 - 1");
@@ -23,6 +25,24 @@ hw_status hw_build_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *c
     rp.resize(n + 1);
     for (int64_t v = 0; v <= n; ++v) rp[v] = int32_t(row_ptr[v]);
     head.assign(col_idx, col_idx + m);
+    if (w_re) {
+        // weights travel with their columns through the row sort
+        wre_out->assign(size_t(m), 0.0);
+        if (w_im) wim_out->assign(size_t(m), 0.0);
+        std::vector<std::pair<int32_t, int64_t>> row;
+        for (int64_t v = 0; v < n; ++v) {
+            row.clear();
+            for (int64_t a = rp[v]; a < rp[v + 1]; ++a) row.emplace_back(col_idx[a], a);
+            std::sort(row.begin(), row.end());
+            for (size_t i = 0; i < row.size(); ++i) {
+                const int64_t a = rp[v] + int64_t(i), src = row[i].second;
+                if (!std::isfinite(w_re[src]) || (w_im && !std::isfinite(w_im[src])))
+                    return hw_fail(HW_EINVAL, "weight of (%lld, %d) is not finite", (long long)v, row[i].first);
+                (*wre_out)[a] = w_re[src];
+                if (w_im) (*wim_out)[a] = w_im[src];
+            }
+        }
+    }
     for (int64_t v = 0; v < n; ++v) {
         int32_t *b = head.data() + rp[v], *e = head.data() + rp[v + 1];
         std::sort(b, e);
@@ -45,6 +65,15 @@ hw_status hw_build_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *c
                                (long long)v, w, w, (long long)v);
             rev[a] = int32_t(p - head.data());
         }
+    }
+    if (w_re) {
+        // W must be Hermitian: arc (w, v) carries the conjugate of arc (v, w)'s weight
+        for (int64_t v = 0; v < n; ++v)
+            for (int32_t a = rp[v]; a < rp[v + 1]; ++a) {
+                const int32_t b = rev[a];
+                if ((*wre_out)[b] != (*wre_out)[a] || (w_im && (*wim_out)[b] != -(*wim_out)[a]))
+                    return hw_fail(HW_EINVAL, "weights not Hermitian at (%lld, %d)", (long long)v, head[a]);
+            }
     }
     return HW_OK;
 }
@@ -148,7 +177,7 @@ extern "C" hw_status hw_graph_structure_host(int64_t n, const int64_t *row_ptr, 
     hw_clear_error();
     if (!kind) return hw_fail(HW_EINVAL, "kind is NULL");
     std::vector<int32_t> rp, head, rev;
-    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, rp, head, rev);
+    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, rp, head, rev, nullptr, nullptr, nullptr, nullptr);
     if (s != HW_OK) return s;
     int64_t d[2];
     hw_detect_family(n, rp, head, kind, d);
@@ -165,8 +194,8 @@ extern "C" hw_status hw_graph_structure(const hw_graph *g, int32_t *kind, int64_
     return HW_OK;
 }
 
-extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
-                                  void *stream, hw_graph **out)
+static hw_status graph_build(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *w_re,
+                             const double *w_im, void *stream, hw_graph **out)
 {
     hw_clear_error();
     if (!out) return hw_fail(HW_EINVAL, "out is NULL");
@@ -174,8 +203,29 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
     hw_graph *g = new (std::nothrow) hw_graph;
     if (!g) return hw_fail(HW_ENOMEM, "host allocation failed");
     std::vector<int32_t> head, rev;
-    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, g->h_row_ptr, head, rev);
+    std::vector<double> wre, wim;
+    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, g->h_row_ptr, head, rev, w_re, w_im, &wre, &wim);
     if (s != HW_OK) { delete g; return s; }
+    g->weighted = w_re != nullptr;
+    g->complex_weights = w_im != nullptr;
+    if (g->weighted) {
+        // row sums of |w| (the infinity norm of W) and the distinct |w| (the
+        // tensor-core slicing test), both host-side
+        g->h_rowabs.assign(size_t(n), 0.0);
+        for (int64_t v = 0; v < n; ++v) {
+            double r = 0.0;
+            for (int32_t a = g->h_row_ptr[v]; a < g->h_row_ptr[v + 1]; ++a)
+                r += g->complex_weights ? std::hypot(wre[a], wim[a]) : std::fabs(wre[a]);
+            g->h_rowabs[v] = r;
+            g->max_rowabs = std::max(g->max_rowabs, r);
+        }
+        if (!g->complex_weights) {
+            for (double x : wre)
+                if (x != 0.0) g->h_wabs.push_back(std::fabs(x));
+            std::sort(g->h_wabs.begin(), g->h_wabs.end());
+            g->h_wabs.erase(std::unique(g->h_wabs.begin(), g->h_wabs.end()), g->h_wabs.end());
+        }
+    }
     g->n = n;
     g->num_arcs = g->h_row_ptr[n];
     g->max_degree = 0;
@@ -192,6 +242,9 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
     for (int32_t d = 1; d <= g->max_degree; ++d) w[d] = 2.0 / double(d);
     std::vector<float> wf(w.size());
     for (size_t d = 0; d < w.size(); ++d) wf[d] = float(w[d]);
+    std::vector<float> wre_f(wre.size()), wim_f(wim.size());
+    for (size_t a = 0; a < wre.size(); ++a) wre_f[a] = float(wre[a]);
+    for (size_t a = 0; a < wim.size(); ++a) wim_f[a] = float(wim[a]);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto fail = [&](hw_status e) { hw_graph_free(g); return e; };
     if ((s = hw_cuda(cudaGetDevice(&g->device), "cudaGetDevice")) != HW_OK) return fail(s);
@@ -229,6 +282,10 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
         cudaMalloc(&g->d_blk, sizeof(int32_t) * g->h_blk.size()) != cudaSuccess ||
         cudaMalloc(&g->d_two_over_d, sizeof(double) * (g->max_degree + 1)) != cudaSuccess ||
         cudaMalloc(&g->d_two_over_d_f, sizeof(float) * (g->max_degree + 1)) != cudaSuccess ||
+        (g->weighted && (cudaMalloc(&g->d_wre, sizeof(double) * std::max<int64_t>(g->num_arcs, 1)) != cudaSuccess ||
+                         cudaMalloc(&g->d_wre_f, sizeof(float) * std::max<int64_t>(g->num_arcs, 1)) != cudaSuccess)) ||
+        (g->complex_weights && (cudaMalloc(&g->d_wim, sizeof(double) * std::max<int64_t>(g->num_arcs, 1)) != cudaSuccess ||
+                                cudaMalloc(&g->d_wim_f, sizeof(float) * std::max<int64_t>(g->num_arcs, 1)) != cudaSuccess)) ||
         cudaHostAlloc(&g->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer(&g->d_err, g->h_err, 0) != cudaSuccess) {
         cudaGetLastError();
@@ -252,11 +309,37 @@ extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32
                                      cudaMemcpyHostToDevice, st), "upload weights")) != HW_OK ||
         (s = hw_cuda(cudaMemcpyAsync(g->d_two_over_d_f, wf.data(), sizeof(float) * wf.size(),
                                      cudaMemcpyHostToDevice, st), "upload weights (float)")) != HW_OK ||
+        (g->weighted && g->num_arcs &&
+         ((s = hw_cuda(cudaMemcpyAsync(g->d_wre, wre.data(), sizeof(double) * g->num_arcs, cudaMemcpyHostToDevice, st),
+                       "upload edge weights")) != HW_OK ||
+          (s = hw_cuda(cudaMemcpyAsync(g->d_wre_f, wre_f.data(), sizeof(float) * g->num_arcs, cudaMemcpyHostToDevice, st),
+                       "upload edge weights (float)")) != HW_OK)) ||
+        (g->complex_weights && g->num_arcs &&
+         ((s = hw_cuda(cudaMemcpyAsync(g->d_wim, wim.data(), sizeof(double) * g->num_arcs, cudaMemcpyHostToDevice, st),
+                       "upload edge weights (imaginary)")) != HW_OK ||
+          (s = hw_cuda(cudaMemcpyAsync(g->d_wim_f, wim_f.data(), sizeof(float) * g->num_arcs, cudaMemcpyHostToDevice, st),
+                       "upload edge weights (imaginary, float)")) != HW_OK)) ||
         (s = hw_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) != HW_OK)
         return fail(s);
     *g->h_err = 0;
     *out = g;
     return HW_OK;
+}
+
+extern "C" hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                  void *stream, hw_graph **out)
+{
+    return graph_build(n, row_ptr, col_idx, nullptr, nullptr, stream, out);
+}
+
+extern "C" hw_status hw_graph_csr_weighted(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                           const double *w_re, const double *w_im, void *stream, hw_graph **out)
+{
+    if (!w_re) {
+        hw_clear_error();
+        return hw_fail(HW_EINVAL, "w_re is NULL (use hw_graph_csr for an unweighted graph)");
+    }
+    return graph_build(n, row_ptr, col_idx, w_re, w_im, stream, out);
 }
 
 extern "C" hw_status hw_graph_free(hw_graph *g)
@@ -272,6 +355,10 @@ extern "C" hw_status hw_graph_free(hw_graph *g)
     cudaFree(g->d_blk);
     cudaFree(g->d_two_over_d);
     cudaFree(g->d_two_over_d_f);
+    cudaFree(g->d_wre);
+    cudaFree(g->d_wim);
+    cudaFree(g->d_wre_f);
+    cudaFree(g->d_wim_f);
     if (g->h_err) cudaFreeHost(g->h_err);
     cudaGetLastError();
     delete g;
@@ -297,7 +384,7 @@ extern "C" hw_status hw_graph_arcs_host(int64_t n, const int64_t *row_ptr, const
 {
     hw_clear_error();
     std::vector<int32_t> rp, head, rev;
-    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, rp, head, rev);
+    hw_status s = hw_build_arcs_host(n, row_ptr, col_idx, rp, head, rev, nullptr, nullptr, nullptr, nullptr);
     if (s != HW_OK) return s;
     if (row_ptr_out) std::memcpy(row_ptr_out, rp.data(), sizeof(int32_t) * rp.size());
     if (head_out) std::memcpy(head_out, head.data(), sizeof(int32_t) * head.size());

@@ -38,6 +38,14 @@ struct hw_graph {
     // edge-major (persE[j n + v]); nullptr otherwise
     int32_t *d_pers = nullptr;       // [num_arcs]
     int32_t *d_persE = nullptr;      // [num_arcs]
+    // weighted adjacency W (hw_graph_csr_weighted), arc-aligned with d_head;
+    // imaginary parts only for a complex Hermitian W
+    bool weighted = false, complex_weights = false;
+    double *d_wre = nullptr, *d_wim = nullptr;
+    float *d_wre_f = nullptr, *d_wim_f = nullptr;
+    std::vector<double> h_rowabs;    // sum over row v of |w|
+    double max_rowabs = 0.0;
+    std::vector<double> h_wabs;      // distinct nonzero |w| (real W)
     int32_t *d_blk = nullptr;        // [nblk+1] first vertex of each block
     double *d_two_over_d = nullptr;  // [max_degree+1], 2/d (0 for d = 0): the Grover weight
     float *d_two_over_d_f = nullptr; // the same rounded to float
@@ -59,9 +67,12 @@ void hw_clear_error();
 
 // ---- host graph construction (graph.cpp)
 // Sorted rows, reversal table and block partition, all on the host.
+// Sorted rows, reversal table and (w_re != NULL) the weights permuted with
+// their columns and checked to be finite and Hermitian.
 hw_status hw_build_arcs_host(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                              std::vector<int32_t> &rp, std::vector<int32_t> &head,
-                             std::vector<int32_t> &rev);
+                             std::vector<int32_t> &rev, const double *w_re, const double *w_im,
+                             std::vector<double> *wre_out, std::vector<double> *wim_out);
 void hw_partition_blocks(const std::vector<int32_t> &rp, int tile_arcs, int tile_verts,
                          std::vector<int32_t> &blk);
 // family of a sorted arc basis (exact comparison of every row)
@@ -153,11 +164,13 @@ void free_marked(MarkedList &m, cudaStream_t st);
 
 // tensor-core Taylor powers (gemm_tc.cu): Q_k = Q_{k-1} Y / k on tcgen05 from
 // split-bf16 operands, accU += sign Q_k in double
-// Y = off on every arc of the CSR (row_ptr, col) plus diag on the marked
-// vertices' diagonal: the sparse symmetric matrix whose powers are taken
+// Y = off (times w[a] when w is not NULL) on every arc a of the CSR (row_ptr,
+// col) plus diag on the marked vertices' diagonal: the sparse symmetric
+// matrix whose powers are taken
 struct SymSparse {
     const int32_t *row_ptr;
     const int32_t *col;
+    const double *w;
     int n;
     double off;
     MarkedList mk;

@@ -678,6 +678,7 @@ extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *
     if (job->kind == HW_JOB_COINED && (!g->d_revE || g->min_degree != g->max_degree || g->max_degree < 1))
         return hw_fail(HW_EUNSUPPORTED, "served coined jobs need a regular graph");
     if (g->n >= (int64_t(1) << 30)) return hw_fail(HW_EUNSUPPORTED, "graph too large to serve");
+    if (g->weighted) return hw_fail(HW_EUNSUPPORTED, "served jobs take unweighted graphs");
     Job J;
     J.id = s->next_id++;
     J.spec = *job;

@@ -85,3 +85,25 @@ def test_invalid_graphs_rejected(case):
         hw.hw_graph_arcs_host(n, rp, col)
     assert e.value.status == hw.HW_EINVAL
     assert hw.hw_last_error()
+
+
+def test_weights_must_be_hermitian_and_finite():
+    # host-side validation runs before any device call
+    import math
+    n, eu, ev = synth.cycle(6)
+    rp, col, w = synth.weighted_csr(n, eu, ev, synth.edge_weights(eu.size, seed=1, complex_phase=True))
+    bad = w.copy()
+    bad[0] = np.conj(bad[0]) * 1.5       # breaks W[v][u] == conj(W[u][v])
+    with pytest.raises(hw.HWError) as e:
+        hw.hw_graph_csr_weighted(n, rp, col, bad, stream=0)
+    assert e.value.status == hw.HW_EINVAL and "Hermitian" in e.value.message
+    bad = w.copy()
+    bad[2] = complex(math.inf, 0.0)
+    with pytest.raises(hw.HWError) as e:
+        hw.hw_graph_csr_weighted(n, rp, col, bad, stream=0)
+    assert e.value.status == hw.HW_EINVAL and "finite" in e.value.message
+    rbad = w.real.copy()
+    rbad[3] += 0.5                       # real W must be symmetric
+    with pytest.raises(hw.HWError) as e:
+        hw.hw_graph_csr_weighted(n, rp, col, rbad, stream=0)
+    assert e.value.status == hw.HW_EINVAL
