@@ -780,6 +780,7 @@ struct EmArgs {
     int64_t n;
     int32_t d;
     int32_t L1, L2;          // torus addressing: rows, columns
+    int32_t grid2d;          // torus addressing: block row y = blockIdx.y is torus row x
     double two_over_d;
     float two_over_d_f;
     MarkedList mk;
@@ -797,24 +798,37 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
     using V = typename Cx<R>::T;
     const V *__restrict__ in = static_cast<const V *>(a.in);
     V *__restrict__ out = static_cast<V *>(a.out);
-    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t n = a.n;
+    // 32-bit indices: every edge-major index j n + v is below the arc count < 2^31
+    const int n = int(a.n);
+    int v;
+    bool live;
     V p[D];
     int r[D];
-    if (v < n) {   // targets depend on the graph only: before the wait
-        if constexpr (ADDR == kAddrTable) {
+    if constexpr (ADDR == kAddrTable) {
+        v = int(blockIdx.x * blockDim.x + threadIdx.x);
+        live = v < n;
+        if (live) {   // targets depend on the graph only: before the wait
 #pragma unroll
             for (int j = 0; j < D; ++j) r[j] = __ldg(a.revE + j * n + v);
+        }
+    } else {
+        static_assert(D == 4, "torus addressing is for degree 4");
+        if (a.grid2d) {   // no division: the block row is the torus row
+            const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
+            v = int(blockIdx.y) * a.L2 + int(y);
+            live = y < uint32_t(a.L2);
+            if (live) torus_targets<ADDR>(TorusVertex(blockIdx.y, y, n, a.L1, a.L2), n, r);
         } else {
-            static_assert(D == 4, "torus addressing is for degree 4");
-            torus_targets<ADDR>(v, n, a.L1, a.L2, r);
+            v = int(blockIdx.x * blockDim.x + threadIdx.x);
+            live = v < n;
+            if (live) torus_targets<ADDR>(TorusVertex(int64_t(v), n, a.L1, a.L2), n, r);
         }
     }
     pdl_wait();
-    if (v < n) {
+    if (live) {
 #pragma unroll
         for (int j = 0; j < D; ++j) p[j] = in[j * n + v];
-        const int mi = find_marked(a.mk, int(v));
+        const int mi = find_marked(a.mk, v);
         if (mi >= 0) {
             if (a.rec_part && a.rec_slot >= 0) {
                 double acc = 0.0;
@@ -1045,7 +1059,8 @@ hw_status launch_layout(const hw_graph *g, hw_dtype dt, const void *in, void *ou
 template <typename R, int COIN>
 static void launch_em(int d, int addr, const EmArgs &a, cudaStream_t st)
 {
-    const dim3 grid(unsigned((a.n + kThreads - 1) / kThreads));
+    dim3 grid(unsigned((a.n + kThreads - 1) / kThreads));
+    if (a.grid2d) grid = dim3(unsigned((a.L2 + kThreads - 1) / kThreads), unsigned(a.L1));
     switch (d) {
     case 1: launch_pdl(k_coined_em<R, 1, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
     case 2: launch_pdl(k_coined_em<R, 2, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
@@ -1083,12 +1098,16 @@ hw_status launch_coined_step_em(const hw_graph *g, hw_dtype dt, hw_coin coin, co
     a.d = g->max_degree;
     a.L1 = int32_t(g->dims[0]);
     a.L2 = int32_t(g->dims[1]);
+    a.grid2d = 0;
     a.two_over_d = 2.0 / double(g->max_degree);
     a.two_over_d_f = float(2.0 / double(g->max_degree));
     a.mk = s.marked;
     int addr = kAddrTable;
-    if (s.index_free && g->kind == HW_GRAPH_TORUS)
+    if (s.index_free && g->kind == HW_GRAPH_TORUS) {
         addr = (s.shift == kShiftPersistent) ? kAddrTorusPS : kAddrTorusFF;
+        // a block row per torus row when rows are long enough to fill blocks
+        a.grid2d = (a.L2 >= kThreads / 2 && a.L1 <= 65535) ? 1 : 0;
+    }
     else if (s.index_free && g->kind == HW_GRAPH_HYPERCUBE && a.d > 8)
         addr = kAddrCube;
     if (dt == HW_C128) {

@@ -109,7 +109,7 @@ __global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *
 // ascending order (the order of the CSR row), so the sums are bit-identical
 // to k_ctqw_term's, without the row_ptr and head reads.
 template <typename R, int FAM>
-__global__ void k_ctqw_term_fam(int64_t n, int batch, int L1, int L2, MarkedList mk, R cg, R coef,
+__global__ void k_ctqw_term_fam(int64_t n, int batch, int L1, int L2, int grid2d, MarkedList mk, R cg, R coef,
                                 const void *x_, const void *tin_, void *tout_, void *acc_, int first)
 {
     using V = typename Cx3<R>::T;
@@ -117,9 +117,11 @@ __global__ void k_ctqw_term_fam(int64_t n, int batch, int L1, int L2, MarkedList
     const V *__restrict__ tin = static_cast<const V *>(tin_);
     V *__restrict__ tout = static_cast<V *>(tout_);
     V *__restrict__ acc = static_cast<V *>(acc_);
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    // torus, one column: a block row per torus row (grid2d), no division
+    const uint32_t y2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = grid2d ? int64_t(blockIdx.y) * L2 + y2 : int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     pdl_wait();   // t_in and acc come from the previous term
-    if (i >= n * batch) {
+    if (grid2d ? y2 >= uint32_t(L2) : i >= n * batch) {
         pdl_trigger();
         return;
     }
@@ -129,7 +131,7 @@ __global__ void k_ctqw_term_fam(int64_t n, int batch, int L1, int L2, MarkedList
     R sx, sy;
     if constexpr (FAM == HW_GRAPH_TORUS) {
         int w[4];
-        TorusVertex(v, n, L1, L2).sorted(w);
+        (grid2d ? TorusVertex(blockIdx.y, y2, n, L1, L2) : TorusVertex(v, n, L1, L2)).sorted(w);
         V q[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) q[j] = tin[int64_t(w[j]) * batch + b];
@@ -182,11 +184,16 @@ hw_status launch_term(const hw_graph *g, bool index_free, int batch, const Marke
             launch_pdl(k_ctqw_term<R, 1>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
                        (const int32_t *)g->d_head, wr, wi, g->n, batch, mk, cg, c, x, tin, tout, acc, first);
     } else if (index_free && g->kind == HW_GRAPH_TORUS)
-        launch_pdl(k_ctqw_term_fam<R, HW_GRAPH_TORUS>, dim3(unsigned(grid)), dim3(256), 0, st, g->n, batch,
-                   int(g->dims[0]), int(g->dims[1]), mk, cg, c, x, tin, tout, acc, first);
+    {
+        const int L1 = int(g->dims[0]), L2 = int(g->dims[1]);
+        const int g2 = (batch == 1 && L2 >= 128 && L1 <= 65535) ? 1 : 0;
+        const dim3 gd = g2 ? dim3(unsigned((L2 + 255) / 256), unsigned(L1)) : dim3(unsigned(grid));
+        launch_pdl(k_ctqw_term_fam<R, HW_GRAPH_TORUS>, gd, dim3(256), 0, st, g->n, batch, L1, L2, g2, mk, cg, c, x,
+                   tin, tout, acc, first);
+    }
     else if (index_free && g->kind == HW_GRAPH_HYPERCUBE)
         launch_pdl(k_ctqw_term_fam<R, HW_GRAPH_HYPERCUBE>, dim3(unsigned(grid)), dim3(256), 0, st, g->n, batch,
-                   int(g->dims[0]), 0, mk, cg, c, x, tin, tout, acc, first);
+                   int(g->dims[0]), 0, 0, mk, cg, c, x, tin, tout, acc, first);
     else
         launch_pdl(k_ctqw_term<R, 0>, dim3(unsigned(grid)), dim3(256), 0, st, (const int32_t *)g->d_row_ptr,
                    (const int32_t *)g->d_head, wr, wi, g->n, batch, mk, cg, c, x, tin, tout, acc, first);

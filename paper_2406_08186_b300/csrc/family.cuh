@@ -40,7 +40,13 @@ struct TorusVertex {
     int w[4];              // neighbour labels by direction
     __device__ __forceinline__ TorusVertex(int64_t v, int64_t n, int L1, int L2)
     {
-        const uint32_t x = uint32_t(v) / uint32_t(L2), y = uint32_t(v) - x * uint32_t(L2);
+        const uint32_t x = uint32_t(v) / uint32_t(L2);
+        init(x, uint32_t(v) - x * uint32_t(L2), n, L1, L2);
+    }
+    // from the coordinates (v = x L2 + y), e.g. a launch with a block row per torus row
+    __device__ __forceinline__ TorusVertex(uint32_t x, uint32_t y, int64_t n, int L1, int L2) { init(x, y, n, L1, L2); }
+    __device__ __forceinline__ void init(uint32_t x, uint32_t y, int64_t n, int L1, int L2)
+    {
         x0 = x == 0;
         xl = x == uint32_t(L1 - 1);
         y0 = y == 0;
@@ -49,7 +55,7 @@ struct TorusVertex {
         xp = x == uint32_t(L1 - 2);
         ys = y == 1;
         yp = y == uint32_t(L2 - 2);
-        const int sv = int(v), sn = int(n);
+        const int sv = int(x * uint32_t(L2) + y), sn = int(n);
         w[0] = x0 ? sv + (sn - L2) : sv - L2;
         w[1] = y0 ? sv + (L2 - 1) : sv - 1;
         w[2] = yl ? sv - (L2 - 1) : sv + 1;
@@ -86,11 +92,10 @@ struct TorusVertex {
     }
 };
 
-// r[j] for the four arc positions of torus vertex v
+// r[j] for the four arc positions of torus vertex tv
 template <int ADDR>
-__device__ __forceinline__ void torus_targets(int64_t v, int64_t n, int L1, int L2, int r[4])
+__device__ __forceinline__ void torus_targets(const TorusVertex &tv, int64_t n, int r[4])
 {
-    const TorusVertex tv(v, n, L1, L2);
     const int sn = int(n);
     if (tv.deep_interior()) {
         // positions up 0, left 1, right 2, down 3 at v and at every neighbour

@@ -37,9 +37,10 @@ static bool check_torus(int L1, int L2)
     }
     for (int v = 0; v < n; ++v) {
         int ff[4], ps[4], srt[4];
-        torus_targets<kAddrTorusFF>(v, n, L1, L2, ff);
-        torus_targets<kAddrTorusPS>(v, n, L1, L2, ps);
-        TorusVertex(v, n, L1, L2).sorted(srt);
+        torus_targets<kAddrTorusFF>(TorusVertex(int64_t(v), n, L1, L2), n, ff);
+        // the coordinate form (launches with a block row per torus row)
+        torus_targets<kAddrTorusPS>(TorusVertex(uint32_t(v / L2), uint32_t(v % L2), n, L1, L2), n, ps);
+        TorusVertex(int64_t(v), n, L1, L2).sorted(srt);
         const int xv = v / L2, yv = v % L2;
         for (int j = 0; j < 4; ++j) {
             ++checked;

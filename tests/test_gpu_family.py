@@ -44,7 +44,7 @@ def _evolve(hw, G, psi0, steps, dt, coin=0, marked=(), addressing=0, shift=0, re
     return out.cpu(), prob.cpu().numpy(), None if rec is None else rec.cpu()
 
 
-TORI = [(3, 3), (3, 5), (7, 4), (33, 65), (130, 257), (1024, 1024)]
+TORI = [(3, 3), (3, 5), (7, 4), (33, 65), (130, 257), (37, 300), (1024, 1024)]
 
 
 @pytest.mark.parametrize("L1,L2", TORI)
