@@ -47,10 +47,11 @@ UNIT = "arc-updates/s"
 # dram__bytes_write.sum), keyed by the SHA-1 of the kernel source they were
 # measured on; a changed kernel reports null until it is measured again.
 TRAFFIC = {
-    # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free), one
-    # launch, cold L2 (profiles/coined_step_c{128,64}_torus1024.md)
-    ("c128", "4d4787c45ce968546a5a6f94f2728daed7ba1f2c"): 67124480 + 17122816,
-    ("c64", "4d4787c45ce968546a5a6f94f2728daed7ba1f2c"): 33565184 + 208640,
+    # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
+    # block row per torus row), one launch, cold L2
+    # (profiles/coined_step_c{128,64}_torus1024.md)
+    ("c128", "e31de75859cae73e01c333118d7a2f1ac274f1dd"): 67126528 + 17821952,
+    ("c64", "e31de75859cae73e01c333118d7a2f1ac274f1dd"): 33566720 + 209664,
 }
 
 
@@ -326,7 +327,7 @@ def run_ours(args):
                      "kernel": "k_coined_em<double,4,grover,%s>" % ("torus" if index_free else "table"),
                      "achieved": ops128 / per_launch128, "peak": fp64_peak, "unit": "FP64 op/s",
                      "frac": ops128 / per_launch128 / fp64_peak,
-                     "peak_source": "hw_measure_fp64 (FMA chains on this GPU); nominal 0.625e12",
+                     "peak_source": "hw_measure_fp64 (register-blocked GEMM loop on this GPU); nominal 0.625e12",
                      "ops_per_launch": ops128, "launch_us": per_launch128 * 1e6,
                      "traffic": TRAFFIC.get(("c128", src_hash)),
                      "hbm": {"achieved": ach128, "peak": peak, "unit": "GB/s", "frac": ach128 / peak,
