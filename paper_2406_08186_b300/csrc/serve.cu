@@ -32,6 +32,7 @@
 #include <map>
 #include <vector>
 
+#include "family.cuh"
 #include "internal.h"
 
 namespace {
@@ -41,6 +42,8 @@ constexpr int kTileVertices = 1024;   // CTQW tiles
 constexpr int kServeTileArcs = 1024;  // coined tiles: whole vertices, at most this many arcs
 constexpr int kMaxServeMarked = 4;
 constexpr int kServeMaxDeg = 32;           // series degree bound (hw_ctqw_plan gives m <= 30)
+// a CTQW job's coefficient tables: c_k and cg_k for k <= kServeMaxDeg, double then float
+constexpr size_t kCoefBytes = ((2 * (kServeMaxDeg + 1) * (sizeof(double) + sizeof(float))) + 255) & ~size_t(255);
 constexpr int kLocalBytes = 3 * 8192 * 8;  // shared memory of a local CTQW job: state and two terms
 constexpr int kLocalThreads = 512;
 constexpr int kLocalCtas = 64;             // local jobs advanced at once (each CTA takes one SM's memory)
@@ -63,9 +66,11 @@ struct SJob {
     double tau;
     // CTQW term k = 1..m: t_k = (-(cg_k) s_y - c_k q_y, cg_k s_x + c_k q_x) with
     // c_k = tau / k, cg_k = c_k gamma (s the neighbour sum of t_{k-1}, q its
-    // own entry on a marked vertex), in both precisions (set on the host)
-    double cd[kServeMaxDeg + 1], cgd[kServeMaxDeg + 1];
-    float cf[kServeMaxDeg + 1], cgf[kServeMaxDeg + 1];
+    // own entry on a marked vertex), in both precisions: tables in the job's
+    // device memory, written once at admission (the job table itself stays
+    // small, since it is uploaded whenever the resident set changes)
+    const double *cd, *cgd;
+    const float *cf, *cgf;
     int32_t kind;            // 0 coined, 1 CTQW
     int32_t dt;              // HW_C64 / HW_C128
     int32_t d;               // coined: the graph's (regular) degree
@@ -74,7 +79,8 @@ struct SJob {
     int32_t n_marked;
     int32_t marked[kMaxServeMarked];
     int32_t local;           // CTQW job run by one CTA from shared memory
-    int32_t pad;
+    int32_t fam;             // coined: hw_graph_kind of the graph (positions from labels when not generic)
+    int32_t fdim0, fdim1;    // torus L1, L2 / hypercube k
 };
 
 struct Tile {
@@ -161,13 +167,17 @@ __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
     for (int i = 0; i < kMaxServeMarked; ++i) mk[i] = (i < nm) ? Jg.marked[i] : -1;
     double *rec = Jg.rec;
     const R f = grover_weight(Jg, R(0));
+    const bool torus = D == 4 && Jg.fam == HW_GRAPH_TORUS;   // uniform across the tile
     for (int v = v0 + int(threadIdx.x); v < v1; v += blockDim.x) {
         V p[D];
         int r[D];
+        if constexpr (D == 4) {
+            if (torus) torus_targets<kAddrTorusFF>(TorusVertex(int64_t(v), n, Jg.fdim0, Jg.fdim1), n, r);
+        }
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             p[j] = in[j * n + v];
-            r[j] = revE[j * n + v];
+            if (!torus) r[j] = revE[j * n + v];
         }
         int mi = -1;
 #pragma unroll
@@ -215,6 +225,7 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
     const int32_t *__restrict__ revE = Jg.revE;
     const int64_t n = Jg.n;
     const int d = Jg.d;
+    const bool cube = Jg.fam == HW_GRAPH_HYPERCUBE;   // uniform across the tile
     const int nm = Jg.n_marked;
     int mk[kMaxServeMarked];
 #pragma unroll
@@ -235,12 +246,13 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
                 }
                 rec[(w - 1) * nm + mi] = acc;
             }
+            CubeWalk cw(v, d);
             for (int j = 0; j < d; ++j) {
                 const V p = in[j * n + v];
                 V c;
                 c.x = -p.x;
                 c.y = -p.y;
-                out[revE[j * n + v]] = c;
+                out[cube ? cw.target(cw.next_bit(), n) : revE[j * n + v]] = c;
             }
             continue;
         }
@@ -252,13 +264,14 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
             sx += p.x;
             sy += p.y;
         }
+        CubeWalk cw(v, d);
 #pragma unroll 4
         for (int j = 0; j < d; ++j) {
             const V p = in[j * n + v];
             V c;
             c.x = fma(f, sx, -p.x);
             c.y = fma(f, sy, -p.y);
-            out[revE[j * n + v]] = c;
+            out[cube ? cw.target(cw.next_bit(), n) : revE[j * n + v]] = c;
         }
     }
 }
@@ -515,6 +528,7 @@ struct hw_server {
     char *host_base = nullptr;
     Arena dev_arena, host_arena;
     SJob *d_jobs = nullptr, *h_jobs = nullptr;       // device table + pinned mirror
+    char *h_coef = nullptr;                           // pinned staging of each slot's CTQW coefficients
     Tile *d_tiles = nullptr, *h_tiles = nullptr;
     int *d_ntiles = nullptr, *h_ntiles = nullptr;
     int *d_local = nullptr, *h_local = nullptr;       // slots of the resident local CTQW jobs
@@ -606,6 +620,7 @@ extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int
         (st = hw_cuda(cudaHostAlloc(&s->host_base, size_t(host_bytes), cudaHostAllocDefault), "cudaHostAlloc(results)")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_jobs, sizeof(SJob) * max_jobs), "cudaMalloc(job table)")) != HW_OK ||
         (st = hw_cuda(cudaHostAlloc(&s->h_jobs, sizeof(SJob) * max_jobs, cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
+        (st = hw_cuda(cudaHostAlloc(&s->h_coef, kCoefBytes * max_jobs, cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_tiles, sizeof(Tile) * s->max_tiles), "cudaMalloc(tiles)")) != HW_OK ||
         (st = hw_cuda(cudaHostAlloc(&s->h_tiles, sizeof(Tile) * s->max_tiles, cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_ntiles, sizeof(int)), "cudaMalloc")) != HW_OK ||
@@ -645,6 +660,7 @@ extern "C" hw_status hw_server_destroy(hw_server *s)
     cudaFreeHost(s->host_base);
     cudaFree(s->d_jobs);
     cudaFreeHost(s->h_jobs);
+    if (s->h_coef) cudaFreeHost(s->h_coef);
     cudaFree(s->d_tiles);
     cudaFreeHost(s->h_tiles);
     cudaFree(s->d_ntiles);
@@ -711,7 +727,7 @@ extern "C" hw_status hw_server_submit(hw_server *s, const hw_job *job, int64_t *
     const size_t rec = job->n_marked ? ((size_t(job->steps) * job->n_marked * 8 + 255) & ~size_t(255)) : 0;
     const size_t prob = (size_t(J.n) * 8 + 255) & ~size_t(255);
     J.dev_bytes = ((job->kind == HW_JOB_COINED || J.local) ? 2 : 4) * state + rec + prob +
-                  ((size_t(job->steps) * 8 + 255) & ~size_t(255));
+                  ((size_t(job->steps) * 8 + 255) & ~size_t(255)) + (job->kind == HW_JOB_CTQW ? kCoefBytes : 0);
     J.host_bytes = prob + ((size_t(job->steps) * 8 + 255) & ~size_t(255));
     if (J.dev_bytes > s->dev_arena.size() || J.host_bytes > s->host_arena.size())
         return hw_fail(HW_ENOMEM, "job needs %zu device bytes; the serving arena holds %zu", J.dev_bytes,
@@ -788,11 +804,27 @@ static hw_status admit(hw_server *s, Job &J)
     D.two_over_d_f = float(D.two_over_d);
     D.gamma = J.spec.gamma;
     D.tau = J.spec.time / double(J.q);
-    for (int k = 1; k <= J.m && k <= kServeMaxDeg; ++k) {
-        D.cd[k] = D.tau / double(k);
-        D.cgd[k] = D.cd[k] * D.gamma;
-        D.cf[k] = float(D.cd[k]);
-        D.cgf[k] = float(D.cgd[k]);
+    if (J.spec.kind == HW_JOB_CTQW) {
+        // staged in the slot's pinned block: the slot is rewritten only by a
+        // later admission, after this job's kernels (which follow the copy)
+        char *cdev = dev + J.dev_bytes - kCoefBytes;
+        char *ch = s->h_coef + kCoefBytes * size_t(J.slot);
+        double *hd = reinterpret_cast<double *>(ch);
+        float *hf = reinterpret_cast<float *>(ch + 2 * (kServeMaxDeg + 1) * sizeof(double));
+        std::memset(ch, 0, kCoefBytes);
+        for (int k = 1; k <= J.m && k <= kServeMaxDeg; ++k) {
+            hd[k] = D.tau / double(k);
+            hd[kServeMaxDeg + 1 + k] = hd[k] * D.gamma;
+            hf[k] = float(hd[k]);
+            hf[kServeMaxDeg + 1 + k] = float(hd[kServeMaxDeg + 1 + k]);
+        }
+        const hw_status cs = hw_cuda(cudaMemcpyAsync(cdev, ch, kCoefBytes, cudaMemcpyHostToDevice, s->st),
+                                     "upload coefficients");
+        if (cs != HW_OK) return cs;
+        D.cd = reinterpret_cast<const double *>(cdev);
+        D.cgd = D.cd + (kServeMaxDeg + 1);
+        D.cf = reinterpret_cast<const float *>(cdev + 2 * (kServeMaxDeg + 1) * sizeof(double));
+        D.cgf = D.cf + (kServeMaxDeg + 1);
     }
     D.kind = J.spec.kind;
     D.dt = J.spec.dt;
@@ -802,6 +834,9 @@ static hw_status admit(hw_server *s, Job &J)
     D.n_marked = J.spec.n_marked;
     for (int i = 0; i < J.spec.n_marked; ++i) D.marked[i] = J.marked[i];
     D.local = J.local ? 1 : 0;
+    D.fam = g->kind;
+    D.fdim0 = int32_t(g->dims[0]);
+    D.fdim1 = int32_t(g->dims[1]);
     // uniform start over the basis: arcs (coined) or vertices (CTQW)
     const double amp = 1.0 / std::sqrt(double(J.dim));
     const int grid = int(std::min<int64_t>(148 * 16, (J.dim + 255) / 256));
