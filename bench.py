@@ -145,6 +145,22 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def rank_max(x, dist=None, device="cuda"):
+    """The largest x over all ranks (the slowest rank's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, world, t_max):
+    """Whole-job throughput of `world` independent replicas: every rank's units
+    over the slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 def cpu_baseline(n, eu, ev, m, budget_s=12.0):
     """The FP64 oracle, untuned, on the host cores: walk steps of the same search."""
     import oracle
@@ -297,16 +313,9 @@ def run_ours(args):
         t_e2e += e0.elapsed_time(e1) / 1e3
     barrier()
 
-    def allmax(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    t128, t64, t_e2e = allmax(t128), allmax(t64), allmax(t_e2e)
+    t128, t64, t_e2e = rank_max(t128, dist), rank_max(t64, dist), rank_max(t_e2e, dist)
     work = arcs * WALK_STEPS * args.steps * world
-    value = work / t128
+    value = replica_value(arcs * WALK_STEPS * args.steps, world, t128)
     per_launch128 = ev128 / (args.steps * WALK_STEPS)
     per_launch64 = ev64 / (args.steps * WALK_STEPS)
     bytes128 = coin_shift_bytes(arcs, 16, index_free)
