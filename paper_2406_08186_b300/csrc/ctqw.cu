@@ -12,10 +12,12 @@
 //
 // hw_ctqw_evolve applies U `steps` times (ping-pong) and records the
 // probability on the marked vertices after each application.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "fpconv.cuh"
@@ -384,6 +386,153 @@ __global__ void __launch_bounds__(128) k_apply_sym_blocks(const void *U_, const 
     pdl_trigger();
 }
 
+// The same block pass, complex64, as a persistent kernel fed by TMA: each CTA
+// walks the blocks b = blockIdx.x, + gridDim.x, ... with two 32 KB stages, the
+// next block's 64 x 64 tile arriving (one cp.async.bulk.tensor, zero fill
+// past the matrix edge) while the current one is summed.  Rows are summed
+// starting from column r (row r), so the 64 threads of a row pass touch 64
+// different columns of the dense tile at each step.
+constexpr int kSymStages = 2;
+constexpr uint64_t kSymWaitNs = 2000000000ull;   // bounded stage waits (2 s)
+
+__device__ __forceinline__ uint32_t sym_smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool sym_wait(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 0) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kSymWaitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void sym_block_ij(int b, int nb, int &I, int &J)
+{
+    I = 0;
+    while (b >= nb - I) { b -= nb - I; ++I; }
+    J = I + b;
+}
+
+// one thread: the tile of upper block b into the stage, completion on bar
+__device__ __forceinline__ void sym_issue(const CUtensorMap *map, int b, int nb, uint32_t dst, uint32_t bar)
+{
+    int I, J;
+    sym_block_ij(b, nb, I, J);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSymB * kSymB * 8)
+                 : "memory");
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(dst), "l"(map), "r"(J * kSymB), "r"(I * kSymB), "r"(bar)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(128) k_apply_sym_tma(const __grid_constant__ CUtensorMap mapU, const void *x_,
+                                                       int n, int nb, int nblocks, void *prow_, void *pcol_,
+                                                       int *err)
+{
+    extern __shared__ __align__(128) unsigned char sym_tma_smem[];
+    float2(*tile)[kSymB][kSymB] = reinterpret_cast<float2(*)[kSymB][kSymB]>(sym_tma_smem);   // [stage][row][col]
+    __shared__ float2 sx[2][kSymB];
+    __shared__ __align__(8) uint64_t bars[kSymStages];
+    __shared__ int failed;
+    const float2 *__restrict__ x = static_cast<const float2 *>(x_);
+    float2 *__restrict__ prow = static_cast<float2 *>(prow_);
+    float2 *__restrict__ pcol = static_cast<float2 *>(pcol_);
+    const int t = threadIdx.x;
+    if (t == 0) {
+        failed = 0;
+        for (int k = 0; k < kSymStages; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sym_smem_addr(&bars[k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // U does not change between applications: the first tiles load before the wait
+        for (int k = 0; k < kSymStages; ++k) {
+            const int b = blockIdx.x + k * gridDim.x;
+            if (b < nblocks) sym_issue(&mapU, b, nb, sym_smem_addr(&tile[k][0][0]), sym_smem_addr(&bars[k]));
+        }
+    }
+    __syncthreads();
+    pdl_wait();   // x is the previous application's output; the partials are free again
+    int k = 0;
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x, ++k) {
+        const int stage = k % kSymStages;
+        int I, J;
+        sym_block_ij(b, nb, I, J);
+        const int r0 = I * kSymB, c0 = J * kSymB;
+        {
+            const int w = t / kSymB, q = t % kSymB;   // sx[0] = x_J (rows), sx[1] = x_I (columns)
+            const int g = (w ? r0 : c0) + q;
+            sx[w][q] = (g < n) ? x[g] : make_float2(0.f, 0.f);
+        }
+        if (t == 0 && !sym_wait(sym_smem_addr(&bars[stage]), uint32_t((k / kSymStages) & 1))) {
+            failed = 1;
+            atomicExch(err, 1);
+        }
+        __syncthreads();
+        if (failed) break;   // uniform: the stage never filled
+        float2(*sU)[kSymB] = tile[stage];
+        // four independent chains per thread (entries s*16 + c of the rotated
+        // order), added in a fixed order at the end
+        float ax[4] = {0.f, 0.f, 0.f, 0.f}, ay[4] = {0.f, 0.f, 0.f, 0.f};
+        if (t < kSymB) {               // row t: sum over c of U[t][c] x_J[c], from column t on
+#pragma unroll
+            for (int c = 0; c < kSymB / 4; ++c) {
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    const int cc = (c + 16 * s4 + t) & (kSymB - 1);
+                    const float2 u = sU[t][cc], q = sx[0][cc];
+                    ax[s4] = fmaf(u.x, q.x, fmaf(-u.y, q.y, ax[s4]));
+                    ay[s4] = fmaf(u.x, q.y, fmaf(u.y, q.x, ay[s4]));
+                }
+            }
+            prow[(int64_t(I) * nb + J) * kSymB + t] =
+                make_float2((ax[0] + ax[1]) + (ax[2] + ax[3]), (ay[0] + ay[1]) + (ay[2] + ay[3]));
+        } else if (I != J) {           // column c: sum over r of U[r][c] x_I[r]
+            const int c = t - kSymB;
+#pragma unroll
+            for (int r = 0; r < kSymB / 4; ++r) {
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    const float2 u = sU[r + 16 * s4][c], q = sx[1][r + 16 * s4];
+                    ax[s4] = fmaf(u.x, q.x, fmaf(-u.y, q.y, ax[s4]));
+                    ay[s4] = fmaf(u.x, q.y, fmaf(u.y, q.x, ay[s4]));
+                }
+            }
+            pcol[(int64_t(J) * nb + I) * kSymB + c] =
+                make_float2((ax[0] + ax[1]) + (ax[2] + ax[3]), (ay[0] + ay[1]) + (ay[2] + ay[3]));
+        }
+        __syncthreads();   // the stage and sx are read: refill the stage
+        if (t == 0) {
+            const int bn = b + kSymStages * gridDim.x;
+            // order the generic reads of the stage before the async-proxy refill
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (bn < nblocks) sym_issue(&mapU, bn, nb, sym_smem_addr(&tile[stage][0][0]), sym_smem_addr(&bars[stage]));
+        }
+    }
+    // on a failed wait, wait (bounded) for every stage still in flight, so no
+    // bulk copy writes this CTA's shared memory after it exits
+    if (failed && t == 0) {
+        for (int kk = k; kk < k + kSymStages; ++kk) {
+            const int64_t bk = int64_t(blockIdx.x) + int64_t(kk) * gridDim.x;
+            if (bk < nblocks) sym_wait(sym_smem_addr(&bars[kk % kSymStages]), uint32_t((kk / kSymStages) & 1));
+        }
+    }
+    pdl_trigger();
+}
+
 // 8 threads per vertex: thread s adds the partials of blocks s, s+8, ... in
 // order, then a fixed shuffle tree combines the 8 sums
 template <typename R>
@@ -425,13 +574,35 @@ __global__ void __launch_bounds__(256) k_apply_sym_reduce(const void *prow_, con
     pdl_trigger();
 }
 
+// complex64 with a tensor map of U (map != NULL): the persistent TMA kernel
 template <typename R>
 hw_status launch_apply_sym(const void *U, const void *x, void *y, int n, void *prow, void *pcol,
-                           const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st)
+                           const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st,
+                           const CUtensorMap *map = nullptr, int *err = nullptr)
 {
     using V = typename Cx2<R>::T;
     const int nb = (n + kSymB - 1) / kSymB;
     const int blocks = nb * (nb + 1) / 2;
+    if (map && sizeof(V) == 8) {
+        static int grid = 0;   // resident CTAs (per process; the device is one B300)
+        const size_t tsmem = sizeof(float2) * kSymStages * kSymB * kSymB;
+        if (!grid) {
+            cudaError_t e = cudaFuncSetAttribute(k_apply_sym_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
+            if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym_tma)");
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_sym_tma, 128, tsmem);
+            if (e != cudaSuccess) return hw_cuda(e, "occupancy (k_apply_sym_tma)");
+            grid = sms * std::max(per, 1);
+        }
+        cudaError_t e = launch_pdl(k_apply_sym_tma, dim3(std::min(grid, blocks)), dim3(128), tsmem, st, *map, x, n, nb,
+                                   blocks, prow, pcol, err);
+        if (e != cudaSuccess) return hw_cuda(e, "k_apply_sym_tma launch");
+        e = launch_pdl(k_apply_sym_reduce<R>, dim3((n * 8 + 255) / 256), dim3(256), 0, st, (const void *)prow,
+                       (const void *)pcol, n, nb, y, mk, rec_part, rec_slot);
+        return hw_cuda(e, "k_apply_sym_reduce launch");
+    }
     const size_t smem = sizeof(V) * (kSymB * (kSymB + 1) + 2 * kSymB);
     cudaError_t e = cudaFuncSetAttribute(k_apply_sym_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym_blocks)");
@@ -642,11 +813,36 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     return hw_cuda(cudaGetLastError(), "pack U");
 }
 
+// Zero-copy word that the TMA-fed application sets when a bounded stage wait
+// runs out of time; hw_ctqw_evolve reports it (HW_ETIMEDOUT) at its next call.
+static int *g_apply_err_h = nullptr, *g_apply_err_d = nullptr;
+static std::mutex g_apply_err_mu;
+
+static hw_status apply_error_word(int **dev)
+{
+    std::lock_guard<std::mutex> lk(g_apply_err_mu);
+    if (!g_apply_err_h) {
+        if (cudaHostAlloc(&g_apply_err_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&g_apply_err_d, g_apply_err_h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            g_apply_err_h = nullptr;
+            return hw_fail(HW_ENOMEM, "host allocation of the error word failed");
+        }
+        *g_apply_err_h = 0;
+    }
+    *dev = g_apply_err_d;
+    return HW_OK;
+}
+
 extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32_t batch, int64_t steps,
                                     const void *psi_in, void *psi_out, const int32_t *marked,
                                     int32_t n_marked, double *record, const hw_opts *opts, void *stream)
 {
     hw_clear_error();
+    if (g_apply_err_h && *reinterpret_cast<volatile int *>(g_apply_err_h)) {
+        *g_apply_err_h = 0;
+        return hw_fail(HW_ETIMEDOUT, "a device-side wait of an earlier hw_ctqw_evolve call ran out of time");
+    }
     if (!U || !psi_in || !psi_out) return hw_fail(HW_EINVAL, "NULL buffer");
     if (dt != HW_C64 && dt != HW_C128) return hw_fail(HW_EINVAL, "unknown dtype");
     if (n < 1 || n > (int64_t(1) << 30)) return hw_fail(HW_EINVAL, "bad n");
@@ -677,6 +873,13 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     // the symmetric path halves the bytes read; complex128 is bound by FP64
     // arithmetic, which both paths share, so it keeps the dense path
     const bool sym = opts && opts->u_symmetric && batch == 1 && dt == HW_C64;
+    // the TMA-fed block pass: a tensor map of U (16-byte aligned, even n)
+    CUtensorMap umap;
+    const bool tma = sym && (uintptr_t(U) % 16) == 0 && n % 2 == 0 && tc_gemm_available() &&
+                     make_map_u64(&umap, U, n, n, n, kSymB, kSymB) == HW_OK;
+    hw_clear_error();
+    int *derr = nullptr;
+    if (tma && (s = apply_error_word(&derr)) != HW_OK) return s;
     const int nb = int((n + kSymB - 1) / kSymB);
     const size_t part_bytes = sym ? size_t(nb) * nb * kSymB * esz : 0;   // one array of block partials
     DevBuf tmp(st), recbuf(st);
@@ -706,7 +909,8 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
         const int64_t slot = (slots && k % stride == 0) ? k / stride - 1 : -1;
         if (sym)
             s = (dt == HW_C128) ? launch_apply_sym<double>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st)
-                                : launch_apply_sym<float>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st);
+                                : launch_apply_sym<float>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st,
+                                                          tma ? &umap : nullptr, derr);
         else
             s = (dt == HW_C128) ? launch_apply<double>(U, src, dst, int(n), batch, mk, rec_part, slot, st)
                                 : launch_apply<float>(U, src, dst, int(n), batch, mk, rec_part, slot, st);

@@ -241,3 +241,30 @@ def test_symmetric_apply_matches_dense_apply_and_oracle(hw, dt, n_bits, steps):
         assert np.sum(np.abs(np.abs(outs[1][0]) ** 2 - np.abs(ref) ** 2)) <= 1e-3
         assert np.max(np.abs(outs[1][1] - rr)) <= 1e-4
     G.free()
+
+
+@pytest.mark.parametrize("name,g,gamma,marked", [
+    # even n, not a multiple of the 64-vertex blocks: the TMA-fed pass, zero-filled edge tiles
+    ("reg3_778", synth.random_regular(778, 3, seed=4), 1 / 3, [5, 700]),
+    # odd n: the shared-memory pass without a tensor map
+    ("er_999", synth.erdos_renyi(1000, 0.006, seed=6), 0.3, [10]),
+])
+def test_symmetric_apply_ragged_sizes(hw, name, g, gamma, marked):
+    import torch
+    n = g[0]
+    marked = [m for m in marked if m < n]
+    G, U = gpu_expm(hw, g, gamma, marked, 0.25, dt=1)
+    x = torch.from_numpy(synth.random_state(n, seed=3)).to("cuda", torch.complex64)
+    outs = []
+    for sym in (0, 1):
+        y = torch.empty_like(x)
+        rec = torch.empty(60, dtype=torch.float64, device="cuda")
+        hw.hw_ctqw_evolve(U, n, hw.HW_C64, 1, 60, x, y, marked, rec, opts={"u_symmetric": sym})
+        outs.append((y.cpu().numpy().astype(np.complex128), rec.cpu().numpy()))
+    ar = oracle.Arcs(*g)
+    ref, rr = oracle.ctqw_evolve(ar, gamma, synth.random_state(n, seed=3), 0.25, 60, marked=marked, record=True)
+    for y, rec in outs:
+        assert np.sum(np.abs(np.abs(y) ** 2 - np.abs(ref) ** 2)) <= 1e-3
+        assert np.max(np.abs(rec - rr)) <= 1e-4
+    assert np.max(np.abs(outs[1][0] - outs[0][0])) <= 1e-5
+    G.free()
