@@ -959,11 +959,13 @@ static void launch_lanes(int d, const RegArgs &a, cudaStream_t st)
 
 static hw_status upload_twiddles()
 {
-    static bool done = false;   // per process; the table is the same for every device
-    static int dev_done = -1;
+    // once per device (the constant bank is per device); the table is the same for all
+    static std::mutex mu;
+    static std::vector<int> done;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (done && dev == dev_done) return HW_OK;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return HW_OK;
     std::vector<double2> tw(kTwMax * (kTwMax + 1) / 2);
     for (int d = 1; d <= kTwMax; ++d)
         for (int r = 0; r < d; ++r) {
@@ -977,7 +979,7 @@ static hw_status upload_twiddles()
     if (s == HW_OK)
         s = hw_cuda(cudaMemcpyToSymbol(c_twf, twf.data(), sizeof(float2) * twf.size()),
                     "cudaMemcpyToSymbol(twiddles, float)");
-    if (s == HW_OK) { done = true; dev_done = dev; }
+    if (s == HW_OK) done.push_back(dev);
     return s;
 }
 

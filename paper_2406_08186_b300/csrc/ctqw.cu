@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -584,17 +585,27 @@ hw_status launch_apply_sym(const void *U, const void *x, void *y, int n, void *p
     const int nb = (n + kSymB - 1) / kSymB;
     const int blocks = nb * (nb + 1) / 2;
     if (map && sizeof(V) == 8) {
-        static int grid = 0;   // resident CTAs (per process; the device is one B300)
+        // resident CTAs per device (the shared-memory attribute is set per device too)
+        static std::mutex mu;
+        static std::map<int, int> grids;
         const size_t tsmem = sizeof(float2) * kSymStages * kSymB * kSymB;
-        if (!grid) {
-            cudaError_t e = cudaFuncSetAttribute(k_apply_sym_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
-            if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym_tma)");
-            int dev = 0, sms = 0, per = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_sym_tma, 128, tsmem);
-            if (e != cudaSuccess) return hw_cuda(e, "occupancy (k_apply_sym_tma)");
-            grid = sms * std::max(per, 1);
+        int dev = 0, grid = 0;
+        cudaGetDevice(&dev);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = grids.find(dev);
+            if (it != grids.end()) {
+                grid = it->second;
+            } else {
+                cudaError_t e =
+                    cudaFuncSetAttribute(k_apply_sym_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
+                if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym_tma)");
+                int sms = 0, per = 0;
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_sym_tma, 128, tsmem);
+                if (e != cudaSuccess) return hw_cuda(e, "occupancy (k_apply_sym_tma)");
+                grid = grids[dev] = sms * std::max(per, 1);
+            }
         }
         cudaError_t e = launch_pdl(k_apply_sym_tma, dim3(std::min(grid, blocks)), dim3(128), tsmem, st, *map, x, n, nb,
                                    blocks, prow, pcol, err);
