@@ -17,6 +17,7 @@
 
 #include "family.cuh"
 #include "internal.h"
+#include "sum4.cuh"
 
 namespace {
 
@@ -840,9 +841,18 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
 #pragma unroll
             for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(-p[j].x, -p[j].y);
         } else if (COIN == HW_COIN_GROVER) {
-            R sx = p[0].x, sy = p[0].y;
+            R sx, sy;
+            if constexpr (D == 4 && sizeof(R) == 8) {
+                // complex128, degree 4: each component's sum rounded once, by
+                // integer operations (the FP64 unit bounds this kernel)
+                sx = sum4::sum4_rn(p[0].x, p[1].x, p[2].x, p[3].x);
+                sy = sum4::sum4_rn(p[0].y, p[1].y, p[2].y, p[3].y);
+            } else {
+                sx = p[0].x;
+                sy = p[0].y;
 #pragma unroll
-            for (int j = 1; j < D; ++j) { sx += p[j].x; sy += p[j].y; }
+                for (int j = 1; j < D; ++j) { sx += p[j].x; sy += p[j].y; }
+            }
             const R f = em_weight<R>(a);
 #pragma unroll
             for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
