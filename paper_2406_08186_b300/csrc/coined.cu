@@ -904,13 +904,21 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
                 out[r] = mkv<V, R>(-p.x, -p.y);
             }
         } else {
-            const V p0 = in[v];
-            R sx = p0.x, sy = p0.y;
+            R sx, sy;
+            if constexpr (sizeof(R) == 8) {
+                // complex128: groups of four rows summed by integer operations
+                // (sum4.cuh), the group sums added in double
+                sum4::grouped_sum2(d, [&](int j) { return in[j * n + v]; }, sx, sy);
+            } else {
+                const V p0 = in[v];
+                sx = p0.x;
+                sy = p0.y;
 #pragma unroll 4
-            for (int j = 1; j < d; ++j) {
-                const V p = in[j * n + v];
-                sx += p.x;
-                sy += p.y;
+                for (int j = 1; j < d; ++j) {
+                    const V p = in[j * n + v];
+                    sx += p.x;
+                    sy += p.y;
+                }
             }
             const R f = em_weight<R>(a);
             CubeWalk cw(v, d);

@@ -15,6 +15,7 @@
 
 #include "family.cuh"
 #include "internal.h"
+#include "sum4.cuh"
 
 namespace {
 
@@ -76,7 +77,15 @@ __global__ void k_ctqw_term(const int32_t *__restrict__ row_ptr, const int32_t *
     R sx = 0, sy = 0;
     int a = row_ptr[v];
     const int e = row_ptr[v + 1];
-    if constexpr (WT == 0) {
+    if (WT == 0 && sizeof(R) == 8 && e - a >= 1 && e - a <= 4) {
+        // complex128, up to four neighbours: their sum rounded once by integer
+        // operations (sum4.cuh); larger degrees keep the double additions,
+        // which measured faster there (the gathers, not the FP64 unit, bound them)
+        double gx, gy;
+        sum4::grouped_sum2(e - a, [&](int j) { return tin[int64_t(head[a + j]) * batch + b]; }, gx, gy);
+        sx = R(gx);
+        sy = R(gy);
+    } else if constexpr (WT == 0) {
         if (a < e) {
             const V q = tin[int64_t(head[a]) * batch + b];
             sx = q.x;
@@ -135,23 +144,37 @@ __global__ void k_ctqw_term_fam(int64_t n, int batch, int L1, int L2, int grid2d
         V q[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) q[j] = tin[int64_t(w[j]) * batch + b];
-        sx = q[0].x;
-        sy = q[0].y;
+        if constexpr (sizeof(R) == 8) {
+            sum4::grouped_sum2(4, [&](int j) { return q[j]; }, sx, sy);
+        } else {
+            sx = q[0].x;
+            sy = q[0].y;
 #pragma unroll
-        for (int j = 1; j < 4; ++j) {
-            sx += q[j].x;
-            sy += q[j].y;
+            for (int j = 1; j < 4; ++j) {
+                sx += q[j].x;
+                sy += q[j].y;
+            }
         }
     } else {
         CubeWalk cw(v, L1);   // L1 = k >= 1
-        const V q0 = tin[int64_t(uint32_t(v) ^ (1u << cw.next_bit())) * batch + b];
-        sx = q0.x;
-        sy = q0.y;
+        if (sizeof(R) == 8 && L1 <= 4) {
+            // as the CSR kernel: up to four neighbours summed once by integer
+            // operations; the walk yields them in the order grouped_sum2 asks for
+            double gx, gy;
+            sum4::grouped_sum2(L1, [&](int) { return tin[int64_t(uint32_t(v) ^ (1u << cw.next_bit())) * batch + b]; },
+                               gx, gy);
+            sx = R(gx);
+            sy = R(gy);
+        } else {
+            const V q0 = tin[int64_t(uint32_t(v) ^ (1u << cw.next_bit())) * batch + b];
+            sx = q0.x;
+            sy = q0.y;
 #pragma unroll 4
-        for (int j = 1; j < L1; ++j) {
-            const V q = tin[int64_t(uint32_t(v) ^ (1u << cw.next_bit())) * batch + b];
-            sx += q.x;
-            sy += q.y;
+            for (int j = 1; j < L1; ++j) {
+                const V q = tin[int64_t(uint32_t(v) ^ (1u << cw.next_bit())) * batch + b];
+                sx += q.x;
+                sy += q.y;
+            }
         }
     }
     term_tail<R, V>(sx, sy, mk, int(v), cg, coef, tin, x, tout, acc, i, first);

@@ -34,6 +34,7 @@
 
 #include "family.cuh"
 #include "internal.h"
+#include "sum4.cuh"
 
 namespace {
 
@@ -199,11 +200,17 @@ __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
             }
             continue;
         }
-        R sx = p[0].x, sy = p[0].y;
+        R sx, sy;
+        if constexpr (sizeof(R) == 8) {   // complex128: integer group sums (sum4.cuh)
+            sum4::grouped_sum2(D, [&](int j) { return p[j]; }, sx, sy);
+        } else {
+            sx = p[0].x;
+            sy = p[0].y;
 #pragma unroll
-        for (int j = 1; j < D; ++j) {
-            sx += p[j].x;
-            sy += p[j].y;
+            for (int j = 1; j < D; ++j) {
+                sx += p[j].x;
+                sy += p[j].y;
+            }
         }
 #pragma unroll
         for (int j = 0; j < D; ++j) {
@@ -256,13 +263,19 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
             }
             continue;
         }
-        const V p0 = in[v];
-        R sx = p0.x, sy = p0.y;
+        R sx, sy;
+        if constexpr (sizeof(R) == 8) {   // complex128: integer group sums (sum4.cuh)
+            sum4::grouped_sum2(d, [&](int j) { return in[j * n + v]; }, sx, sy);
+        } else {
+            const V p0 = in[v];
+            sx = p0.x;
+            sy = p0.y;
 #pragma unroll 4
-        for (int j = 1; j < d; ++j) {
-            const V p = in[j * n + v];
-            sx += p.x;
-            sy += p.y;
+            for (int j = 1; j < d; ++j) {
+                const V p = in[j * n + v];
+                sx += p.x;
+                sy += p.y;
+            }
         }
         CubeWalk cw(v, d);
 #pragma unroll 4

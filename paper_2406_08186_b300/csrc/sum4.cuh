@@ -74,7 +74,7 @@ HW_HD uint64_t join(uint32_t hi, uint32_t lo) { return (static_cast<uint64_t>(hi
 // the sequential sum, kept out of line so that the compiler does not compute
 // it (on the FP64 unit) alongside the integer path on every call
 #if defined(__CUDACC__)
-__device__ __noinline__ double sum4_seq_dev(double x0, double x1, double x2, double x3)
+static __device__ __noinline__ double sum4_seq_dev(double x0, double x1, double x2, double x3)
 {
     return ((x0 + x1) + x2) + x3;
 }
@@ -162,6 +162,52 @@ HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
             return fpconv::from_bits64(sign | (static_cast<uint64_t>(B) << 52) | (join(rh, rl) & 0xFFFFFFFFFFFFFull));
     }
     return sum4_seq(x0, x1, x2, x3);
+}
+
+// componentwise sums of the complex terms t(0) .. t(count-1), count >= 1
+// (t returns a type with double .x, .y, and is called once per term, in
+// order): groups of four consecutive terms summed by sum4_rn (a short last
+// group padded with -0, which leaves any sum unchanged), the group sums added
+// in order in double.  The next group's terms are fetched before the current
+// group is summed, so its loads overlap the integer work.
+template <typename F>
+HW_HD void grouped_sum2(int count, F t, double &sx, double &sy)
+{
+    double cx[4], cy[4], nx[4], ny[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (u < count) {
+            const auto p = t(u);
+            cx[u] = p.x;
+            cy[u] = p.y;
+        } else {
+            cx[u] = -0.0;
+            cy[u] = -0.0;
+        }
+    }
+    sx = 0.0;
+    sy = 0.0;
+    for (int j0 = 0; j0 < count; j0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j0 + 4 + u < count) {
+                const auto p = t(j0 + 4 + u);
+                nx[u] = p.x;
+                ny[u] = p.y;
+            } else {
+                nx[u] = -0.0;
+                ny[u] = -0.0;
+            }
+        }
+        const double gx = sum4_rn(cx[0], cx[1], cx[2], cx[3]), gy = sum4_rn(cy[0], cy[1], cy[2], cy[3]);
+        sx = (j0 == 0) ? gx : sx + gx;
+        sy = (j0 == 0) ? gy : sy + gy;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            cx[u] = nx[u];
+            cy[u] = ny[u];
+        }
+    }
 }
 
 }  // namespace sum4
