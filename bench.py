@@ -48,10 +48,10 @@ UNIT = "arc-updates/s"
 # measured on; a changed kernel reports null until it is measured again.
 TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
-    # block row per torus row), one launch, cold L2
-    # (profiles/coined_step_c{128,64}_torus1024.md)
-    ("c128", "e31de75859cae73e01c333118d7a2f1ac274f1dd"): 67126528 + 17821952,
-    ("c64", "e31de75859cae73e01c333118d7a2f1ac274f1dd"): 33566720 + 209664,
+    # block row per torus row, complex128 sums by integer operations), one
+    # launch, cold L2 (profiles/coined_step_c{128,64}_torus1024.md)
+    ("c128", "afba5da1ccb17d2dd4ad5aa0d38f193b201952a1"): 67132928 + 17300736,
+    ("c64", "afba5da1ccb17d2dd4ad5aa0d38f193b201952a1"): 33566720 + 226304,
 }
 
 
