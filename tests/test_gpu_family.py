@@ -196,3 +196,29 @@ def test_sparse_ctqw_index_free(hw, name, g, dt):
         else:
             assert np.sum(np.abs(np.abs(got) ** 2 - np.abs(ref) ** 2)) <= TOL64_L1
     G.free()
+
+
+def test_complex128_sums_on_every_path_of_the_integer_sum(hw):
+    # amplitudes spanning many binades inside one vertex (the sequential
+    # fallback), subnormals, exact zeros and cancelling pairs, next to
+    # ordinary ones (the integer path): the degree-4 coin against the oracle,
+    # and the index-free and table kernels bit for bit
+    L1, L2 = 24, 40
+    g = synth.torus_rect(L1, L2)
+    ar = oracle.Arcs(*g)
+    G = _graph(hw, g)
+    psi0 = synth.random_state(ar.num_arcs, seed=17)
+    rng = np.random.default_rng(5)
+    scale = 10.0 ** rng.integers(-40, 3, size=ar.num_arcs)
+    psi0 = psi0 * scale
+    psi0[::7] = 0.0
+    psi0[1::11] = 5e-320 + 0j                          # subnormal real parts
+    psi0[3::13] = -psi0[2::13][: psi0[3::13].size]     # cancelling neighbours in a block
+    psi0 = psi0 / np.sqrt(np.sum(np.abs(psi0) ** 2))
+    ref = oracle.coined_evolve(ar, psi0, 9, 0, [3, 500])
+    a = _evolve(hw, G, psi0, 9, hw.HW_C128, 0, [3, 500], addressing=0)
+    b = _evolve(hw, G, psi0, 9, hw.HW_C128, 0, [3, 500], addressing=1)
+    torch = _torch()
+    assert torch.equal(a[0], b[0])
+    assert np.max(np.abs(a[0].numpy() - ref)) <= TOL128
+    G.free()
