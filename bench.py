@@ -50,8 +50,8 @@ TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
     # block row per torus row, complex128 sums by integer operations), one
     # launch, cold L2 (profiles/coined_step_c{128,64}_torus1024.md)
-    ("c128", "afba5da1ccb17d2dd4ad5aa0d38f193b201952a1"): 67132928 + 17300736,
-    ("c64", "afba5da1ccb17d2dd4ad5aa0d38f193b201952a1"): 33566720 + 226304,
+    ("c128", "220ff63a044596522f8ed4396b4cd22b2f5c86b1"): 67133184 + 18286592,
+    ("c64", "220ff63a044596522f8ed4396b4cd22b2f5c86b1"): 33569024 + 228864,
 }
 
 

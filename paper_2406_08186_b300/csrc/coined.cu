@@ -576,6 +576,7 @@ struct RingArgs {
     int *err;                // zero-copy host word: set on a wait timeout
     int64_t rec_slot;
     int64_t n;
+    int64_t arcs;            // row_ptr[n]
     int32_t batch;
     int32_t rowbytes;
     MarkedList mk;
@@ -608,14 +609,15 @@ __device__ __forceinline__ bool ring_wait(uint32_t bar, uint32_t parity)
     }
 }
 
-// issued by one lane: stage the rows of vertex v into a slot (or just arrive
-// when they do not fit, or v is past the warp's range)
-__device__ __forceinline__ void ring_issue(const RingArgs &a, int64_t v, int64_t vend, uint32_t slot, uint32_t bar)
+// issued by one lane: stage the rows of the vertex with arc range [s, e) into
+// a slot (or just arrive when they do not fit, or when in_range is false: the
+// vertex is past the warp's range)
+__device__ __forceinline__ void ring_issue(const RingArgs &a, bool in_range, int s, int e, uint32_t slot,
+                                           uint32_t bar)
 {
     uint32_t bytes = 0;
     const char *src = nullptr;
-    if (v < vend) {
-        const int s = a.row_ptr[v], e = a.row_ptr[v + 1];
+    if (in_range) {
         const int64_t b = int64_t(e - s) * a.rowbytes;
         if (b > 0 && b <= kSlotBytes) {
             bytes = uint32_t(b);
@@ -656,21 +658,39 @@ __global__ void __launch_bounds__(kRingWarps * 32) k_coined_ring(RingArgs a)
     const int BV = a.rowbytes / int(sizeof(T));       // 16-byte (or 8-byte) vectors per row
     const int B = a.batch;
 
+    // rp[i] = row_ptr[v + i] for the current vertex v (a window over the
+    // vertices being processed and staged; entries past n are not used), and
+    // rev_c = the lane's reversal entry of v's block.  Both are loaded one
+    // iteration ahead, so no iteration waits on a global load before its
+    // stores: every fourth vertex's reversal entries and every 32nd vertex's
+    // offsets miss the caches.
+    constexpr int kAhead = kRingSlots - 1;   // vertices staged ahead of the current one
+    int rp[kAhead + 2];
+#pragma unroll
+    for (int i = 0; i < kAhead + 2; ++i) rp[i] = a.row_ptr[vbeg + i <= a.n ? vbeg + i : a.n];
+    int rev_c = (vbeg < vend && rp[0] + lane < rp[1]) ? __ldg(a.rev + rp[0] + lane) : 0;
     if (lane == 0)
-        for (int k = 0; k < kRingSlots - 1; ++k)
-            ring_issue(a, vbeg + k, vend, ring_s + k * kSlotBytes, smem_addr(&bars[warp][k]));
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k)
+            ring_issue(a, vbeg + k < vend, rp[k], rp[k + 1], ring_s + k * kSlotBytes, smem_addr(&bars[warp][k]));
     bool ok = true;
     int64_t waited = 0;     // slots consumed so far (phase bookkeeping for the drain)
     for (int64_t v = vbeg; v < vend && ok; ++v) {
         const int64_t k = v - vbeg;
         const int slot = int(k % kRingSlots);
-        // keep kRingSlots-1 vertices in flight: refill the slot freed last iteration
+        // keep kAhead vertices in flight: refill the slot freed last iteration
         if (lane == 0) {
-            const int nxt = int((k + kRingSlots - 1) % kRingSlots);
-            ring_issue(a, v + kRingSlots - 1, vend, ring_s + nxt * kSlotBytes, smem_addr(&bars[warp][nxt]));
+            const int nxt = int((k + kAhead) % kRingSlots);
+            ring_issue(a, v + kAhead < vend, rp[kAhead], rp[kAhead + 1], ring_s + nxt * kSlotBytes,
+                       smem_addr(&bars[warp][nxt]));
         }
-        const int s = a.row_ptr[v], e = a.row_ptr[v + 1], d = e - s;
-        if (lane < d) rev_s[warp][lane] = __ldg(a.rev + s + lane);
+        const int s = rp[0], e = rp[1], d = e - s;
+        rev_s[warp][lane] = rev_c;   // meaningful for lanes < d
+        // the next iteration's window entry and reversal entries (its block starts at e)
+#pragma unroll
+        for (int i = 0; i < kAhead + 1; ++i) rp[i] = rp[i + 1];
+        rp[kAhead + 1] = a.row_ptr[v + kAhead + 2 <= a.n ? v + kAhead + 2 : a.n];
+        rev_c = (int64_t(e) + lane < a.arcs) ? __ldg(a.rev + e + lane) : 0;
         __syncwarp();
         if (!ring_wait(smem_addr(&bars[warp][slot]), uint32_t((k / kRingSlots) & 1))) {
             if (lane == 0) atomicExch(a.err, 1);
@@ -1208,6 +1228,7 @@ static hw_status launch_shape(const hw_graph *g, hw_dtype dt, int batch, const R
     r.err = g->d_err;
     r.rec_slot = a.rec_slot;
     r.n = a.n;
+    r.arcs = g->num_arcs;
     r.batch = batch;
     r.rowbytes = batch * int(cplx_bytes(dt));
     r.mk = a.mk;
