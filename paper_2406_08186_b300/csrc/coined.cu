@@ -953,6 +953,56 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
     pdl_trigger();
 }
 
+// Grover on the hypercube Q_K, degree K known at compile time: a thread per
+// vertex loads its K rows into registers at once and writes the K outputs
+// from them, so each row is read once (k_coined_em_rt reads the rows twice).
+// The arithmetic is k_coined_em_rt's: the same sums in the same order.
+template <typename R, int K>
+__global__ void __launch_bounds__(kThreads) k_coined_em_cube(EmArgs a)
+{
+    using V = typename Cx<R>::T;
+    const V *__restrict__ in = static_cast<const V *>(a.in);
+    V *__restrict__ out = static_cast<V *>(a.out);
+    const int v = int(blockIdx.x) * int(blockDim.x) + int(threadIdx.x);
+    const int n = int(a.n);   // K n < 2^31: the arc count fits the 32-bit device indices
+    pdl_wait();
+    if (v < n) {
+        V p[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) p[j] = in[j * n + v];
+        const int mi = find_marked(a.mk, v);
+        CubeWalk cw(v, K);
+        if (mi >= 0) {
+            if (a.rec_part && a.rec_slot >= 0) {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) acc += double(p[j].x) * double(p[j].x) + double(p[j].y) * double(p[j].y);
+                a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j) out[cw.target(cw.next_bit(), n)] = mkv<V, R>(-p[j].x, -p[j].y);
+        } else {
+            R sx, sy;
+            if constexpr (sizeof(R) == 8) {
+                sum4::grouped_sum2_fixed<K>(p, sx, sy);
+            } else {
+                sx = p[0].x;
+                sy = p[0].y;
+#pragma unroll
+                for (int j = 1; j < K; ++j) {
+                    sx += p[j].x;
+                    sy += p[j].y;
+                }
+            }
+            const R f = em_weight<R>(a);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                out[cw.target(cw.next_bit(), n)] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
+        }
+    }
+    pdl_trigger();
+}
+
 // arc-major [n][d] <-> edge-major [d][n]: element e of the source, read in order
 template <typename V, bool TO_EDGE>
 __global__ void k_layout(const V *__restrict__ in, V *__restrict__ out, int64_t n, int d)
@@ -1072,12 +1122,16 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
 
 // The edge-major path serves every regular graph except complex64 walks of
 // degree 9..16, where full lane groups of the arc-major k_coined_lanes were
-// measured faster (2^16-vertex hypercube: 8.2 vs 10.5 us per step); complex128
-// above degree 8 and complex64 above 16 use the two-pass k_coined_em_rt
-// (2^20-vertex hypercube: 180 vs 409 us complex128, 89 vs 254 us complex64).
+// measured faster than the two-pass k_coined_em_rt (2^16-vertex hypercube: 8.2
+// vs 10.5 us per step), and the hypercube Q_16 is excepted from that: with
+// index-free addressing it takes k_coined_em_cube (4.4 us), and through the
+// table k_coined_em_rt, so that both addressings keep the same arithmetic.
+// The two-pass kernel against the arc-major ones on the 2^20-vertex
+// hypercube: 180 vs 409 us complex128, 89 vs 254 us complex64.
 bool coined_em_supported(const hw_graph *g, hw_coin coin, hw_dtype dt)
 {
     if (!g->d_revE || (coin == HW_COIN_FOURIER && g->max_degree > 8)) return false;
+    if (g->kind == HW_GRAPH_HYPERCUBE && g->max_degree == 16) return true;
     return !(dt == HW_C64 && g->max_degree >= 9 && g->max_degree <= 16);
 }
 
@@ -1094,6 +1148,42 @@ hw_status launch_layout(const hw_graph *g, hw_dtype dt, const void *in, void *ou
         else k_layout<float2, false><<<grid, 256, 0, st>>>(static_cast<const float2 *>(in), static_cast<float2 *>(out), g->n, d);
     }
     return hw_cuda(cudaGetLastError(), "k_layout launch");
+}
+
+// Which hypercube degrees take k_coined_em_cube (rows in registers) rather
+// than the two-pass k_coined_em_rt, from per-step times on Q_12 .. Q_20:
+// complex64 from degree 16 (Q_16 4.4 vs 7.9 us, Q_20 52.9 vs 68.8 us; the
+// arc-major lane groups stay faster below 16), complex128 up to degree 16
+// (Q_16 11.3 vs 14.5 us); above 16 the 80+ registers of complex128 rows leave
+// too few warps per SM and the two passes win (Q_20 159 vs 165 us).
+template <typename R> constexpr bool cube_regs_kernel(int d)
+{
+    return sizeof(R) == 8 ? (d >= 9 && d <= 16) : (d >= 16 && d <= 20);
+}
+
+template <typename R>
+static void launch_cube(int d, dim3 grid, const EmArgs &a, cudaStream_t st)
+{
+    if constexpr (sizeof(R) == 8) {
+        switch (d) {
+        case 9: launch_pdl(k_coined_em_cube<R, 9>, grid, dim3(kThreads), 0, st, a); break;
+        case 10: launch_pdl(k_coined_em_cube<R, 10>, grid, dim3(kThreads), 0, st, a); break;
+        case 11: launch_pdl(k_coined_em_cube<R, 11>, grid, dim3(kThreads), 0, st, a); break;
+        case 12: launch_pdl(k_coined_em_cube<R, 12>, grid, dim3(kThreads), 0, st, a); break;
+        case 13: launch_pdl(k_coined_em_cube<R, 13>, grid, dim3(kThreads), 0, st, a); break;
+        case 14: launch_pdl(k_coined_em_cube<R, 14>, grid, dim3(kThreads), 0, st, a); break;
+        case 15: launch_pdl(k_coined_em_cube<R, 15>, grid, dim3(kThreads), 0, st, a); break;
+        default: launch_pdl(k_coined_em_cube<R, 16>, grid, dim3(kThreads), 0, st, a); break;
+        }
+    } else {
+        switch (d) {
+        case 16: launch_pdl(k_coined_em_cube<R, 16>, grid, dim3(kThreads), 0, st, a); break;
+        case 17: launch_pdl(k_coined_em_cube<R, 17>, grid, dim3(kThreads), 0, st, a); break;
+        case 18: launch_pdl(k_coined_em_cube<R, 18>, grid, dim3(kThreads), 0, st, a); break;
+        case 19: launch_pdl(k_coined_em_cube<R, 19>, grid, dim3(kThreads), 0, st, a); break;
+        default: launch_pdl(k_coined_em_cube<R, 20>, grid, dim3(kThreads), 0, st, a); break;
+        }
+    }
 }
 
 template <typename R, int COIN>
@@ -1115,8 +1205,12 @@ static void launch_em(int d, int addr, const EmArgs &a, cudaStream_t st)
     case 7: launch_pdl(k_coined_em<R, 7, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
     case 8: launch_pdl(k_coined_em<R, 8, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
     default:   // Grover only
-        if (addr == kAddrCube) launch_pdl(k_coined_em_rt<R, kAddrCube>, grid, dim3(kThreads), 0, st, a);
-        else launch_pdl(k_coined_em_rt<R, kAddrTable>, grid, dim3(kThreads), 0, st, a);
+        if (addr == kAddrCube && cube_regs_kernel<R>(d))
+            launch_cube<R>(d, grid, a, st);
+        else if (addr == kAddrCube)
+            launch_pdl(k_coined_em_rt<R, kAddrCube>, grid, dim3(kThreads), 0, st, a);
+        else
+            launch_pdl(k_coined_em_rt<R, kAddrTable>, grid, dim3(kThreads), 0, st, a);
         break;
     }
 }

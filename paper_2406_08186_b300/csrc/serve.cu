@@ -151,9 +151,10 @@ __device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
 // One coined step of the tile's vertices in the edge-major layout E[j][v]
 // (thread per vertex, degree D known at compile time): the job's pointers and
 // marked vertices are read once per tile, each thread loads its vertex's D
-// arcs (D row segments across the warp) and reversal entries before any
-// arithmetic.  The Grover sum runs in arc order from arc 0, one FMA per
-// component, as in the single-walk kernels.
+// arcs (D row segments across the warp) and reversal entries (none on a
+// recognised torus or hypercube: positions from the label) before any
+// arithmetic.  The Grover sum is the single-walk kernels': in arc order from
+// arc 0 (complex128: integer group sums), one FMA per component.
 template <typename R, int D>
 __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
 {
@@ -169,6 +170,7 @@ __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
     double *rec = Jg.rec;
     const R f = grover_weight(Jg, R(0));
     const bool torus = D == 4 && Jg.fam == HW_GRAPH_TORUS;   // uniform across the tile
+    const bool cube = Jg.fam == HW_GRAPH_HYPERCUBE;
     for (int v = v0 + int(threadIdx.x); v < v1; v += blockDim.x) {
         V p[D];
         int r[D];
@@ -178,8 +180,10 @@ __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             p[j] = in[j * n + v];
-            if (!torus) r[j] = revE[j * n + v];
+            if (!torus && !cube) r[j] = revE[j * n + v];
         }
+        // hypercube: each output's position is computed where it is stored
+        CubeWalk cw(v, D);
         int mi = -1;
 #pragma unroll
         for (int i = 0; i < kMaxServeMarked; ++i)
@@ -196,13 +200,13 @@ __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
                 V c;
                 c.x = -p[j].x;
                 c.y = -p[j].y;
-                out[r[j]] = c;
+                out[cube ? cw.target(cw.next_bit(), n) : r[j]] = c;
             }
             continue;
         }
         R sx, sy;
         if constexpr (sizeof(R) == 8) {   // complex128: integer group sums (sum4.cuh)
-            sum4::grouped_sum2(D, [&](int j) { return p[j]; }, sx, sy);
+            sum4::grouped_sum2_fixed<D>(p, sx, sy);
         } else {
             sx = p[0].x;
             sy = p[0].y;
@@ -217,7 +221,7 @@ __device__ void serve_coined_em(const SJob &Jg, int64_t w, int v0, int v1)
             V c;
             c.x = fma(f, sx, -p[j].x);
             c.y = fma(f, sy, -p[j].y);
-            out[r[j]] = c;
+            out[cube ? cw.target(cw.next_bit(), n) : r[j]] = c;
         }
     }
 }
@@ -285,6 +289,37 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
             c.x = fma(f, sx, -p.x);
             c.y = fma(f, sy, -p.y);
             out[cube ? cw.target(cw.next_bit(), n) : revE[j * n + v]] = c;
+        }
+    }
+}
+
+// Hypercube degrees whose rows are held in registers (serve_coined_em<R, d>)
+// rather than read twice: complex64 16..20, where the single-walk
+// k_coined_em_cube was measured faster than the two-pass kernel, and
+// complex128 9..12 (that kernel wins up to 16, but here every path shares one
+// kernel's registers, and 13..16 complex128 rows push it into spills).
+template <typename R> __device__ __forceinline__ bool serve_cube_regs(int d)
+{
+    return sizeof(R) == 8 ? (d >= 9 && d <= 12) : (d >= 16 && d <= 20);
+}
+
+template <typename R>
+__device__ void serve_coined_cube(const SJob &J, int64_t w, int v0, int v1)
+{
+    if constexpr (sizeof(R) == 8) {
+        switch (J.d) {
+        case 9: serve_coined_em<R, 9>(J, w, v0, v1); break;
+        case 10: serve_coined_em<R, 10>(J, w, v0, v1); break;
+        case 11: serve_coined_em<R, 11>(J, w, v0, v1); break;
+        default: serve_coined_em<R, 12>(J, w, v0, v1); break;
+        }
+    } else {
+        switch (J.d) {
+        case 16: serve_coined_em<R, 16>(J, w, v0, v1); break;
+        case 17: serve_coined_em<R, 17>(J, w, v0, v1); break;
+        case 18: serve_coined_em<R, 18>(J, w, v0, v1); break;
+        case 19: serve_coined_em<R, 19>(J, w, v0, v1); break;
+        default: serve_coined_em<R, 20>(J, w, v0, v1); break;
         }
     }
 }
@@ -401,16 +436,21 @@ k_serve_step(const SJob *__restrict__ jobs, const Tile *__restrict__ tiles, cons
         const int64_t local = now - J.start_tick;
         if (local < 0 || local >= J.total_subs) continue;   // uniform over the CTA
         if (J.kind == 0) {
-            // coined, edge-major: unrolled for the common degrees, two passes otherwise
+            // coined, edge-major: unrolled for the common degrees and for the
+            // hypercube degrees where rows held in registers beat two passes,
+            // two passes otherwise
+            const bool cube = J.fam == HW_GRAPH_HYPERCUBE;
             if (J.dt == HW_C128) {
                 if (J.d == 3) serve_coined_em<double, 3>(J, local, tl.v0, tl.v1);
                 else if (J.d == 4) serve_coined_em<double, 4>(J, local, tl.v0, tl.v1);
                 else if (J.d == 8) serve_coined_em<double, 8>(J, local, tl.v0, tl.v1);
+                else if (cube && serve_cube_regs<double>(J.d)) serve_coined_cube<double>(J, local, tl.v0, tl.v1);
                 else serve_coined_em_rt<double>(J, local, tl.v0, tl.v1);
             } else {
                 if (J.d == 3) serve_coined_em<float, 3>(J, local, tl.v0, tl.v1);
                 else if (J.d == 4) serve_coined_em<float, 4>(J, local, tl.v0, tl.v1);
                 else if (J.d == 8) serve_coined_em<float, 8>(J, local, tl.v0, tl.v1);
+                else if (cube && serve_cube_regs<float>(J.d)) serve_coined_cube<float>(J, local, tl.v0, tl.v1);
                 else serve_coined_em_rt<float>(J, local, tl.v0, tl.v1);
             }
         } else {

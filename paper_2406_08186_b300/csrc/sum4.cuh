@@ -210,4 +210,24 @@ HW_HD void grouped_sum2(int count, F t, double &sx, double &sy)
     }
 }
 
+// grouped_sum2 over K terms already held in an array (K known at compile
+// time): the same groups, padding and order of additions, so both give the
+// same bits
+template <int K, typename V>
+HW_HD void grouped_sum2_fixed(const V (&p)[K], double &sx, double &sy)
+{
+#pragma unroll
+    for (int j0 = 0; j0 < K; j0 += 4) {
+        double gx[4], gy[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            gx[u] = (j0 + u < K) ? double(p[j0 + u < K ? j0 + u : 0].x) : -0.0;
+            gy[u] = (j0 + u < K) ? double(p[j0 + u < K ? j0 + u : 0].y) : -0.0;
+        }
+        const double x = sum4_rn(gx[0], gx[1], gx[2], gx[3]), y = sum4_rn(gy[0], gy[1], gy[2], gy[3]);
+        sx = (j0 == 0) ? x : sx + x;
+        sy = (j0 == 0) ? y : sy + y;
+    }
+}
+
 }  // namespace sum4

@@ -147,7 +147,10 @@ def test_persistent_shift_needs_a_torus(hw):
         G.free()
 
 
-@pytest.mark.parametrize("k", [9, 12, 17])
+# degrees 9..16 complex128 and 16..20 complex64 take the register-resident
+# hypercube kernel with index-free addressing and the two-pass kernel through
+# the table; other (degree, precision) pairs the two-pass or arc-major kernels
+@pytest.mark.parametrize("k", [9, 12, 16, 17])
 @pytest.mark.parametrize("dt", [1, 2])
 def test_hypercube_index_free_bit_identical_and_matches_oracle(hw, k, dt):
     g = synth.hypercube(k)
@@ -160,11 +163,15 @@ def test_hypercube_index_free_bit_identical_and_matches_oracle(hw, k, dt):
     b = _evolve(hw, G, psi0, steps, dt, 0, marked, addressing=1, record=True)
     torch = _torch()
     assert torch.equal(a[0], b[0]) and torch.equal(a[2], b[2])
-    if dt == hw.HW_C128 and k <= 12:
+    if (dt == hw.HW_C128 and k <= 12) or k == 16:
         ar = oracle.Arcs(*g)
         ref, rec_ref = oracle.coined_evolve(ar, psi0, steps, 0, marked, record=True)
-        assert np.max(np.abs(a[0].numpy() - ref)) <= TOL128
-        assert np.max(np.abs(a[2].numpy() - rec_ref)) <= TOL128
+        if dt == hw.HW_C128:
+            assert np.max(np.abs(a[0].numpy() - ref)) <= TOL128
+            assert np.max(np.abs(a[2].numpy() - rec_ref)) <= TOL128
+        else:
+            assert np.sum(np.abs(a[1] - oracle.prob_coined(ar, ref))) <= TOL64_L1
+            assert np.max(np.abs(a[2].numpy() - rec_ref)) <= 1e-5
     G.free()
 
 
