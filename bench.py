@@ -432,6 +432,7 @@ def run_workload_ctqw(args):
     peak, src = measured_peaks()
     res = {"workload": "hypercube12_ctqw", "n": n, "marked": m, "gamma": 1 / 12, "dt": 0.1,
            "applications": 2000}
+    fp64 = hw.hw_measure_fp64()
     for dt, name in ((hw.HW_C128, "c128"), (hw.HW_C64, "c64")):
         cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
         U = torch.empty((n, n), dtype=cdt, device="cuda")
@@ -464,6 +465,19 @@ def run_workload_ctqw(args):
                      "apply_us": t_ev / 2000 * 1e6, "apply_gbs": apply_bytes / (t_ev / 2000) / 1e9,
                      "apply_frac_hbm": apply_bytes / (t_ev / 2000) / 1e9 / peak,
                      "p_m_max": float(rec.max().item())}
+        if dt == hw.HW_C128:
+            # dense complex128 application: three real FMAs per element (the 3M
+            # form), bound by the FP64 pipe
+            fmas = 3.0 * n * n
+            res[name]["apply_fp64_fma_per_s"] = fmas / (t_ev / 2000)
+            res[name]["apply_fp64_frac"] = fmas / (t_ev / 2000) / fp64
+            res[name]["fp64_peak_fma_per_s"] = fp64
+            # Taylor powers: FP64 GEMM tiles of 64 x 64 on and above the diagonal
+            # only (the powers of the real symmetric Y are symmetric)
+            nb = (n + 63) // 64
+            expm_fmas = (deg - 1) * (nb * (nb + 1) // 2) * 64 * 64 * n
+            res[name]["expm_fp64_fma_per_s"] = expm_fmas / t_exp
+            res[name]["expm_fp64_frac"] = expm_fmas / t_exp / fp64
     res["peak_hbm"] = peak
     print(json.dumps(res), flush=True)
 

@@ -41,6 +41,8 @@ struct GemmArgs {
     double scale;     // C *= scale before the epilogue
     double *acc;      // EPI_TAYLOR: acc += sign * C
     double sign;
+    int sym_out;      // C is symmetric (a product of commuting symmetric matrices): only the
+                      // tiles on and above the diagonal are computed, each written to both places
 };
 
 __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g)
@@ -50,7 +52,18 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g)
     const int n = g.n;
     const int t = threadIdx.x;
     const int ty = t / 16, tx = t % 16;
-    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    int bi = blockIdx.y, bj = blockIdx.x;
+    if (g.sym_out) {   // blockIdx.x numbers the upper tiles row by row
+        const int nb = (n + BN - 1) / BN;
+        int rem = blockIdx.x;
+        bi = 0;
+        while (rem >= nb - bi) {
+            rem -= nb - bi;
+            ++bi;
+        }
+        bj = bi + rem;
+    }
+    const int i0 = bi * BM, j0 = bj * BN;
     double acc[4][4] = {};
     for (int pass = 0; pass < (g.A2 ? 2 : 1); ++pass) {
         const double *A = pass ? g.A2 : g.A1;
@@ -95,13 +108,20 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g)
             const double c = acc[i][j] * g.scale;
             g.out[o] = c;
             if (g.epi == EPI_TAYLOR) g.acc[o] += g.sign * c;
+            if (g.sym_out && bi != bj) {   // the mirror element (j, i) of a tile above the diagonal
+                const int64_t mo = int64_t(gj) * n + gi;
+                g.out[mo] = c;
+                if (g.epi == EPI_TAYLOR) g.acc[mo] += g.sign * c;
+            }
         }
     }
 }
 
 hw_status dgemm(const GemmArgs &a, cudaStream_t st)
 {
-    dim3 grid((a.n + BN - 1) / BN, (a.n + BM - 1) / BM);
+    const int nb = (a.n + BN - 1) / BN;
+    dim3 grid(nb, (a.n + BM - 1) / BM);
+    if (a.sym_out) grid = dim3(unsigned(int64_t(nb) * (nb + 1) / 2), 1);
     k_dgemm<<<grid, 256, 0, st>>>(a);
     return hw_cuda(cudaGetLastError(), "k_dgemm launch");
 }
@@ -300,6 +320,83 @@ hw_status launch_apply(const void *U, const void *x, void *y, int n, int batch, 
 {
     if (batch == 1) return launch_apply_bt<R, 1>(U, x, y, n, batch, mk, rec_part, rec_slot, st);
     return launch_apply_bt<R, 4>(U, x, y, n, batch, mk, rec_part, rec_slot, st);
+}
+
+// ------------------------------------------------------------ apply U, complex128, three real products
+// y = U x for one complex128 state with three real multiply-adds per element
+// instead of four (the 3M form of a complex product): with U = A + iB and
+// x = p + iq, P1 = A p, P2 = B q, P3 = (A + B)(p + q), and
+// y = (P1 - P2) + i (P3 - P1 - P2).  S = A + B is formed once per call
+// (k_sum_plane), p + q once per staged chunk of x.  The FP64 pipe bounds the
+// four-product kernel, so a quarter of its work goes; the bytes read grow from
+// 16 to 24 per element (U and S).
+__global__ void k_sum_plane(const double2 *__restrict__ U, double *__restrict__ S, int64_t count)
+{
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < count; e += int64_t(gridDim.x) * blockDim.x) {
+        const double2 u = U[e];
+        S[e] = u.x + u.y;
+    }
+}
+
+__global__ void __launch_bounds__(kApplyThreads)
+k_apply_3m(const double2 *__restrict__ U, const double *__restrict__ S, const double2 *__restrict__ x,
+           double2 *__restrict__ y, int n, MarkedList mk, double *rec_part, int64_t rec_slot)
+{
+    extern __shared__ unsigned char smem_raw[];
+    double2 *xs = reinterpret_cast<double2 *>(smem_raw);
+    double *ss = reinterpret_cast<double *>(xs + kApplyChunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (kApplyThreads / 32) + warp;
+    pdl_wait();   // x is the previous application's output
+    double p1 = 0, p2 = 0, p3 = 0;
+    for (int c0 = 0; c0 < n; c0 += kApplyChunk) {
+        const int cn = min(kApplyChunk, n - c0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cn; j += kApplyThreads) {
+            const double2 q = x[c0 + j];
+            xs[j] = q;
+            ss[j] = q.x + q.y;
+        }
+        __syncthreads();
+        if (i < n) {
+            const double2 *Ui = U + int64_t(i) * n + c0;
+            const double *Si = S + int64_t(i) * n + c0;
+            for (int j = lane; j < cn; j += 32) {
+                const double2 u = Ui[j], q = xs[j];
+                p1 = fma(u.x, q.x, p1);
+                p2 = fma(u.y, q.y, p2);
+                p3 = fma(Si[j], ss[j], p3);
+            }
+        }
+    }
+    if (i < n) {
+        for (int o = 16; o > 0; o >>= 1) {
+            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+            p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+            p3 += __shfl_xor_sync(0xffffffffu, p3, o);
+        }
+        if (lane == 0) {
+            const double ox = p1 - p2, oy = (p3 - p1) - p2;
+            y[i] = make_double2(ox, oy);
+            if (rec_part && rec_slot >= 0) {
+                const int mi = marked_find(mk, i);
+                if (mi >= 0) rec_part[rec_slot * mk.n + mi] = ox * ox + oy * oy;
+            }
+        }
+    }
+    pdl_trigger();
+}
+
+hw_status launch_apply_3m(const void *U, const double *S, const void *x, void *y, int n, const MarkedList &mk,
+                          double *rec_part, int64_t rec_slot, cudaStream_t st)
+{
+    const int grid = (n + kApplyThreads / 32 - 1) / (kApplyThreads / 32);
+    const size_t smem = (sizeof(double2) + sizeof(double)) * kApplyChunk;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_3m, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_3m)");
+    launch_pdl(k_apply_3m, dim3(grid), dim3(kApplyThreads), smem, st, static_cast<const double2 *>(U), S,
+               static_cast<const double2 *>(x), static_cast<double2 *>(y), n, mk, rec_part, rec_slot);
+    return hw_cuda(cudaGetLastError(), "k_apply_3m launch");
 }
 
 // ------------------------------------------------------------ apply a symmetric U
@@ -795,6 +892,7 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
             a.scale = 1.0 / double(k);
             a.acc = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
             a.sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;
+            a.sym_out = 1;   // Q_k = Y^k / k! with Y real symmetric
             if ((s = dgemm(a, st)) != HW_OK) return s;
             Qk = dst;
             dst = (dst == Q.as<double>()) ? Qn.as<double>() : Q.as<double>();
@@ -808,6 +906,7 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
         a.A2 = Im.as<double>(); a.B2 = Im.as<double>();
         a.sigma = -1.0;
         a.n = n; a.epi = EPI_STORE; a.out = Q.as<double>(); a.scale = 1.0;
+        a.sym_out = 1;   // Re^2 - Im^2 is symmetric for symmetric Re, Im
         if ((s = dgemm(a, st)) != HW_OK) return s;                     // Re Re - Im Im
         GemmArgs b{};
         b.A1 = Re.as<double>(); b.B1 = Im.as<double>();
@@ -893,8 +992,18 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     if (tma && (s = apply_error_word(&derr)) != HW_OK) return s;
     const int nb = int((n + kSymB - 1) / kSymB);
     const size_t part_bytes = sym ? size_t(nb) * nb * kSymB * esz : 0;   // one array of block partials
-    DevBuf tmp(st), recbuf(st);
+    // complex128, one state, dense U: the three-product form with S = Re U + Im U
+    const bool three = !sym && dt == HW_C128 && batch == 1;
+    DevBuf tmp(st), recbuf(st), splane(st);
     if ((s = tmp.get(bytes + 2 * part_bytes + 256, "scratch allocation (state scratch)")) != HW_OK) return s;
+    if (three) {
+        if ((s = splane.get(size_t(n) * size_t(n) * sizeof(double), "scratch allocation (Re U + Im U)")) != HW_OK)
+            return s;
+        const int64_t count = n * n;
+        const int g = int(std::min<int64_t>(148 * 8, (count + 255) / 256));
+        k_sum_plane<<<g, 256, 0, st>>>(static_cast<const double2 *>(U), splane.as<double>(), count);
+        if ((s = hw_cuda(cudaGetLastError(), "k_sum_plane launch")) != HW_OK) return s;
+    }
     void *prow = static_cast<char *>(tmp.p) + ((bytes + 255) & ~size_t(255));
     void *pcol = static_cast<char *>(prow) + part_bytes;
     double *rec_part = nullptr;
@@ -922,6 +1031,8 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
             s = (dt == HW_C128) ? launch_apply_sym<double>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st)
                                 : launch_apply_sym<float>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st,
                                                           tma ? &umap : nullptr, derr);
+        else if (three)
+            s = launch_apply_3m(U, splane.as<double>(), src, dst, int(n), mk, rec_part, slot, st);
         else
             s = (dt == HW_C128) ? launch_apply<double>(U, src, dst, int(n), batch, mk, rec_part, slot, st)
                                 : launch_apply<float>(U, src, dst, int(n), batch, mk, rec_part, slot, st);
