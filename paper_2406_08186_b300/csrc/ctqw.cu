@@ -327,9 +327,17 @@ hw_status launch_apply(const void *U, const void *x, void *y, int n, int batch, 
 // instead of four (the 3M form of a complex product): with U = A + iB and
 // x = p + iq, P1 = A p, P2 = B q, P3 = (A + B)(p + q), and
 // y = (P1 - P2) + i (P3 - P1 - P2).  S = A + B is formed once per call
-// (k_sum_plane), p + q once per staged chunk of x.  The FP64 pipe bounds the
+// (k_sum_plane), p + q by the application that writes x.  The FP64 pipe bounds the
 // four-product kernel, so a quarter of its work goes; the bytes read grow from
 // 16 to 24 per element (U and S).
+// Four warps (rows) per CTA and 1024 staged columns (24 KB), so that up to
+// seven CTAs share an SM: n = 4096 gives 1024 CTAs, 6.9 per SM, and the SMs
+// with one CTA more than the others wait 1/7 instead of 1/4 of the time
+// (eight rows per CTA and 48 KB gave 3.5 per SM, four at most).
+constexpr int k3mThreads = 128;
+constexpr int k3mChunk = 1024;
+
+// S[e] = Re U[e] + Im U[e] (also used for the start state's p + q)
 __global__ void k_sum_plane(const double2 *__restrict__ U, double *__restrict__ S, int64_t count)
 {
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < count; e += int64_t(gridDim.x) * blockDim.x) {
@@ -338,30 +346,49 @@ __global__ void k_sum_plane(const double2 *__restrict__ U, double *__restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(kApplyThreads)
+__global__ void __launch_bounds__(k3mThreads, 7)
 k_apply_3m(const double2 *__restrict__ U, const double *__restrict__ S, const double2 *__restrict__ x,
-           double2 *__restrict__ y, int n, MarkedList mk, double *rec_part, int64_t rec_slot)
+           const double *__restrict__ xsum, double2 *__restrict__ y, double *__restrict__ ysum, int n,
+           MarkedList mk, double *rec_part, int64_t rec_slot)
 {
     extern __shared__ unsigned char smem_raw[];
     double2 *xs = reinterpret_cast<double2 *>(smem_raw);
-    double *ss = reinterpret_cast<double *>(xs + kApplyChunk);
+    double *ss = reinterpret_cast<double *>(xs + k3mChunk);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (kApplyThreads / 32) + warp;
+    const int i = blockIdx.x * (k3mThreads / 32) + warp;
     pdl_wait();   // x is the previous application's output
     double p1 = 0, p2 = 0, p3 = 0;
-    for (int c0 = 0; c0 < n; c0 += kApplyChunk) {
-        const int cn = min(kApplyChunk, n - c0);
+    for (int c0 = 0; c0 < n; c0 += k3mChunk) {
+        const int cn = min(k3mChunk, n - c0);
         __syncthreads();
-        for (int j = threadIdx.x; j < cn; j += kApplyThreads) {
-            const double2 q = x[c0 + j];
-            xs[j] = q;
-            ss[j] = q.x + q.y;
+        for (int j = threadIdx.x; j < cn; j += k3mThreads) {
+            xs[j] = x[c0 + j];
+            ss[j] = xsum[c0 + j];
         }
         __syncthreads();
         if (i < n) {
             const double2 *Ui = U + int64_t(i) * n + c0;
             const double *Si = S + int64_t(i) * n + c0;
-            for (int j = lane; j < cn; j += 32) {
+            // four columns per lane in flight (each lane still adds its
+            // columns in increasing order)
+            int j = lane;
+            for (; j + 96 < cn; j += 128) {
+                double2 u[4];
+                double sv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    u[q] = Ui[j + 32 * q];
+                    sv[q] = Si[j + 32 * q];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double2 xq = xs[j + 32 * q];
+                    p1 = fma(u[q].x, xq.x, p1);
+                    p2 = fma(u[q].y, xq.y, p2);
+                    p3 = fma(sv[q], ss[j + 32 * q], p3);
+                }
+            }
+            for (; j < cn; j += 32) {
                 const double2 u = Ui[j], q = xs[j];
                 p1 = fma(u.x, q.x, p1);
                 p2 = fma(u.y, q.y, p2);
@@ -378,6 +405,7 @@ k_apply_3m(const double2 *__restrict__ U, const double *__restrict__ S, const do
         if (lane == 0) {
             const double ox = p1 - p2, oy = (p3 - p1) - p2;
             y[i] = make_double2(ox, oy);
+            ysum[i] = ox + oy;   // the next application's p + q
             if (rec_part && rec_slot >= 0) {
                 const int mi = marked_find(mk, i);
                 if (mi >= 0) rec_part[rec_slot * mk.n + mi] = ox * ox + oy * oy;
@@ -387,15 +415,15 @@ k_apply_3m(const double2 *__restrict__ U, const double *__restrict__ S, const do
     pdl_trigger();
 }
 
-hw_status launch_apply_3m(const void *U, const double *S, const void *x, void *y, int n, const MarkedList &mk,
-                          double *rec_part, int64_t rec_slot, cudaStream_t st)
+hw_status launch_apply_3m(const void *U, const double *S, const void *x, const double *xsum, void *y, double *ysum,
+                          int n, const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st)
 {
-    const int grid = (n + kApplyThreads / 32 - 1) / (kApplyThreads / 32);
-    const size_t smem = (sizeof(double2) + sizeof(double)) * kApplyChunk;
+    const int grid = (n + k3mThreads / 32 - 1) / (k3mThreads / 32);
+    const size_t smem = (sizeof(double2) + sizeof(double)) * k3mChunk;
     cudaError_t e = cudaFuncSetAttribute(k_apply_3m, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_3m)");
-    launch_pdl(k_apply_3m, dim3(grid), dim3(kApplyThreads), smem, st, static_cast<const double2 *>(U), S,
-               static_cast<const double2 *>(x), static_cast<double2 *>(y), n, mk, rec_part, rec_slot);
+    launch_pdl(k_apply_3m, dim3(grid), dim3(k3mThreads), smem, st, static_cast<const double2 *>(U), S,
+               static_cast<const double2 *>(x), xsum, static_cast<double2 *>(y), ysum, n, mk, rec_part, rec_slot);
     return hw_cuda(cudaGetLastError(), "k_apply_3m launch");
 }
 
@@ -997,13 +1025,16 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     DevBuf tmp(st), recbuf(st), splane(st);
     if ((s = tmp.get(bytes + 2 * part_bytes + 256, "scratch allocation (state scratch)")) != HW_OK) return s;
     if (three) {
-        if ((s = splane.get(size_t(n) * size_t(n) * sizeof(double), "scratch allocation (Re U + Im U)")) != HW_OK)
+        // S, then Re x + Im x of the two state buffers
+        if ((s = splane.get((size_t(n) * size_t(n) + 2 * size_t(n)) * sizeof(double),
+                            "scratch allocation (Re U + Im U)")) != HW_OK)
             return s;
         const int64_t count = n * n;
         const int g = int(std::min<int64_t>(148 * 8, (count + 255) / 256));
         k_sum_plane<<<g, 256, 0, st>>>(static_cast<const double2 *>(U), splane.as<double>(), count);
         if ((s = hw_cuda(cudaGetLastError(), "k_sum_plane launch")) != HW_OK) return s;
     }
+    double *xsum = three ? splane.as<double>() + n * n : nullptr, *ysum = three ? xsum + n : nullptr;
     void *prow = static_cast<char *>(tmp.p) + ((bytes + 255) & ~size_t(255));
     void *pcol = static_cast<char *>(prow) + part_bytes;
     double *rec_part = nullptr;
@@ -1024,6 +1055,10 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
             return s;
         src = T;
     }
+    if (three) {
+        k_sum_plane<<<int((n + 255) / 256), 256, 0, st>>>(static_cast<const double2 *>(src), xsum, n);
+        if ((s = hw_cuda(cudaGetLastError(), "k_sum_plane launch")) != HW_OK) return s;
+    }
     for (int64_t k = 1; k <= steps; ++k) {
         void *dst = ((steps - k) % 2 == 0) ? P : T;
         const int64_t slot = (slots && k % stride == 0) ? k / stride - 1 : -1;
@@ -1031,8 +1066,10 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
             s = (dt == HW_C128) ? launch_apply_sym<double>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st)
                                 : launch_apply_sym<float>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st,
                                                           tma ? &umap : nullptr, derr);
-        else if (three)
-            s = launch_apply_3m(U, splane.as<double>(), src, dst, int(n), mk, rec_part, slot, st);
+        else if (three) {
+            s = launch_apply_3m(U, splane.as<double>(), src, xsum, dst, ysum, int(n), mk, rec_part, slot, st);
+            std::swap(xsum, ysum);
+        }
         else
             s = (dt == HW_C128) ? launch_apply<double>(U, src, dst, int(n), batch, mk, rec_part, slot, st)
                                 : launch_apply<float>(U, src, dst, int(n), batch, mk, rec_part, slot, st);
