@@ -156,6 +156,32 @@ def test_evolve_matches_oracle_and_hamming_reduction(hw):
     G.free()
 
 
+@pytest.mark.parametrize("name,g,marked", [
+    # one state, complex128: the three-product application; n past one and two
+    # 1024-column chunks and off the 4-row CTA grid, and tiny graphs
+    ("reg3_1500", synth.random_regular(1500, 3, seed=8), [3, 1499]),
+    ("er_2047", synth.erdos_renyi(2051, 0.003, seed=5), [-1]),   # isolated vertices dropped: n = 2047
+    ("path3", synth.path(3), [1]),
+    ("K2", synth.complete(2), []),
+])
+def test_evolve_three_product_sizes(hw, name, g, marked):
+    n = g[0]
+    marked = [m % n for m in marked]
+    G, U = gpu_expm(hw, g, 0.35, marked, 0.2)
+    psi0 = synth.random_state(n, seed=n)
+    steps = 25
+    psi, rec, prob, norm = gpu_evolve(hw, U, psi0, steps, marked, record=bool(marked))
+    ar = oracle.Arcs(*g)
+    if marked:
+        ref, rr = oracle.ctqw_evolve(ar, 0.35, psi0, 0.2, steps, marked=marked, record=True)
+        assert np.max(np.abs(rec - rr)) <= TOL128
+    else:
+        ref = oracle.ctqw_evolve(ar, 0.35, psi0, 0.2, steps, marked=marked)
+    assert np.max(np.abs(psi - ref)) <= TOL128
+    assert abs(norm[0] - np.sum(np.abs(psi0) ** 2)) < 1e-12
+    G.free()
+
+
 def test_evolve_batched_and_in_place(hw):
     import torch
     g = synth.erdos_renyi(200, 0.05, seed=2)
