@@ -50,8 +50,8 @@ TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
     # block row per torus row, complex128 sums by integer operations), one
     # launch, cold L2 (profiles/coined_step_c{128,64}_torus1024.md)
-    ("c128", "220ff63a044596522f8ed4396b4cd22b2f5c86b1"): 67133184 + 18286592,
-    ("c64", "220ff63a044596522f8ed4396b4cd22b2f5c86b1"): 33569024 + 228864,
+    ("c128", "f3e939a0195c9aadbd698cdcad55487394a0ca95"): 67132416 + 17325824,
+    ("c64", "f3e939a0195c9aadbd698cdcad55487394a0ca95"): 33566464 + 195840,
 }
 
 
