@@ -366,7 +366,10 @@ hw_status hw_ctqw_evolve_sparse(const hw_graph *g, double gamma, const int32_t *
  * states on the device, and each hw_server_run round advances every resident
  * job by K sub-steps (a coined step, or one series term of e^{-iH dt}) with
  * one multi-job kernel launch per sub-step, K launches replayed as one CUDA
- * graph.  Each job starts from the uniform state over its basis (all arcs for
+ * graph.  CTQW jobs whose state and two series terms fit one CTA's shared
+ * memory advance instead by whole walk steps in a kernel beside that graph,
+ * between 1 and K steps per round, as many as keep its time close to the
+ * graph's (measured on earlier rounds).  Each job starts from the uniform state over its basis (all arcs for
  * a coined walk, all vertices for a CTQW) and returns its probabilities
  * (Sec. 3.1 / 3.2, summed in double) and, with marked vertices, the total
  * marked probability after every step.  A job's result does not depend on

@@ -17,8 +17,12 @@
 // memory (complex64 up to 8192 vertices, complex128 up to 4096) is "local":
 // a CTA of its own (k_serve_local, launched beside k_serve_step in every
 // sub-step of the graph) keeps the state and the series terms in shared
-// memory and advances the job by a whole walk step per sub-step, with block
-// barriers between the Taylor terms instead of one launch per term.
+// memory and advances the job by whole walk steps, with block barriers
+// between the Taylor terms instead of one launch per term.  It runs beside the
+// round's graph, on a second stream, L steps per round: L follows the
+// measured times of the two branches, so that the local jobs (which advance
+// whole steps) do not hold back the tiled CTQW jobs (which advance one term
+// per sub-step) and are not held back by a round of idle sub-steps either.
 //
 // Each job's arithmetic depends only on its own data and a fixed per-vertex
 // order, so its result is the same alone and in any mix.
@@ -39,7 +43,10 @@
 namespace {
 
 constexpr int kServeThreads = 256;
-constexpr int kTileVertices = 1024;   // CTQW tiles
+// CTQW tiles: 16 KiB of a job's four state-sized buffers each, one or two
+// vertices per thread (a term's neighbour gathers are latency-bound, so small
+// jobs need many CTAs)
+constexpr int kTileVerticesC64 = 512, kTileVerticesC128 = 256;
 constexpr int kServeTileArcs = 1024;  // coined tiles: whole vertices, at most this many arcs
 constexpr int kMaxServeMarked = 4;
 constexpr int kServeMaxDeg = 32;           // series degree bound (hw_ctqw_plan gives m <= 30)
@@ -121,7 +128,9 @@ __device__ void serve_ctqw(const SJob &J, int64_t ls, int v)
     V *__restrict__ tout = static_cast<V *>(J.T[k & 1]);
     V *__restrict__ acc = static_cast<V *>(J.X[1 - cur]);
     R sx = 0, sy = 0;
-    for (int a = J.row_ptr[v]; a < J.row_ptr[v + 1]; ++a) {
+    const int a0 = J.row_ptr[v], a1 = J.row_ptr[v + 1];
+#pragma unroll 4
+    for (int a = a0; a < a1; ++a) {
         const V q = tin[J.head[a]];
         sx += q.x;
         sy += q.y;
@@ -400,23 +409,24 @@ __device__ void serve_ctqw_local(const SJob &J, int64_t w0, int ns, unsigned cha
     for (int v = threadIdx.x; v < n; v += blockDim.x) out[v] = acc[v];
 }
 
-// K sub-steps (walk steps) of every resident local CTQW job, a CTA per job;
-// this kernel runs beside the K tiled sub-step kernels of a round.
-__global__ void __launch_bounds__(kLocalThreads)
+// Up to L walk steps of every resident local CTQW job, a CTA per job;
+// prog[slot] counts the steps a job has done (the host keeps the same count).
+__global__ void __launch_bounds__(kLocalThreads, 1)
 k_serve_local(const SJob *__restrict__ jobs, const int *__restrict__ local, const int *__restrict__ nlocal,
-              const int64_t *__restrict__ tick, int K)
+              int64_t *__restrict__ prog, int L)
 {
     extern __shared__ __align__(16) unsigned char lsmem[];
     const int nl = *nlocal;
-    const int64_t now = *tick;
     for (int i = blockIdx.x; i < nl; i += gridDim.x) {
-        const SJob &J = jobs[local[i]];
-        const int64_t w0 = std::max<int64_t>(0, now - J.start_tick);
-        const int64_t w1 = std::min<int64_t>(J.total_subs, now + K - J.start_tick);
+        const int slot = local[i];
+        const SJob &J = jobs[slot];
+        const int64_t w0 = prog[slot];
+        const int64_t w1 = std::min<int64_t>(J.total_subs, w0 + L);
         if (w1 <= w0) continue;   // uniform over the CTA
         if (J.dt == HW_C128) serve_ctqw_local<double>(J, w0, int(w1 - w0), lsmem);
         else serve_ctqw_local<float>(J, w0, int(w1 - w0), lsmem);
-        __syncthreads();   // the next job reuses the shared memory
+        __syncthreads();   // every thread has read prog[slot]; the next job reuses the shared memory
+        if (threadIdx.x == 0) prog[slot] = w1;
     }
 }
 
@@ -561,6 +571,7 @@ struct Job {
     int32_t m = 1, q = 1;
     size_t dev_bytes = 0, host_bytes = 0;
     bool local = false;         // CTQW job run from shared memory by k_serve_local
+    int64_t lprog = 0;          // local job: walk steps launched so far
     cudaEvent_t done_ev = nullptr;
     double t_submit = 0, t_done = 0;
 };
@@ -586,8 +597,13 @@ struct hw_server {
     int *d_ntiles = nullptr, *h_ntiles = nullptr;
     int *d_local = nullptr, *h_local = nullptr;       // slots of the resident local CTQW jobs
     int *d_nlocal = nullptr, *h_nlocal = nullptr;
-    cudaStream_t st2 = nullptr;                       // second branch of the captured sub-step
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaStream_t st2 = nullptr;                       // the local CTQW jobs' branch of a round
+    int64_t *d_lprog = nullptr;                       // steps done by the local job in each slot
+    int L = 1;                                        // local steps per round
+    static constexpr int kTimeSets = 8;               // rounds of branch timings in flight
+    cudaEvent_t tev[kTimeSets][4] = {};               // graph start/end, local start/end
+    bool tlocal[kTimeSets] = {};
+    int64_t round_no = 0;
     int64_t *d_tick = nullptr;
     int64_t tick = 0;
     int max_tiles = 0;
@@ -619,18 +635,12 @@ static hw_status server_capture(hw_server *s)
         if (g) cudaGraphDestroy(g);
         return st;
     }
-    // a round: the K tiled sub-steps (chained by programmatic dependent
-    // launch) beside one launch that advances the local CTQW jobs by K steps,
-    // then the tick
-    cudaEventRecord(s->fork_ev, s->st);
-    cudaStreamWaitEvent(s->st2, s->fork_ev, 0);
-    k_serve_local<<<kLocalCtas, kLocalThreads, kLocalBytes, s->st2>>>(s->d_jobs, s->d_local, s->d_nlocal, s->d_tick,
-                                                                      s->K);
-    cudaEventRecord(s->join_ev, s->st2);
+    // the graph of a round: the K tiled sub-steps (chained by programmatic
+    // dependent launch), then the tick; the local CTQW jobs run beside it
+    // (hw_server_run)
     for (int k = 0; k < s->K; ++k)
         launch_pdl(k_serve_step, dim3(sms * 6), dim3(kServeThreads), smem, s->st, (const SJob *)s->d_jobs,
                    (const Tile *)s->d_tiles, (const int *)s->d_ntiles, (const int64_t *)s->d_tick, k);
-    cudaStreamWaitEvent(s->st, s->join_ev, 0);
     k_serve_tick<<<1, 1, 0, s->st>>>(s->d_tick, s->K);
     st = hw_cuda(cudaStreamEndCapture(s->st, &g), "end capture");
     if (st != HW_OK) return st;
@@ -653,10 +663,11 @@ extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int
     if (!s) return hw_fail(HW_ENOMEM, "host allocation failed");
     s->max_jobs = max_jobs;
     s->K = substeps_per_round;
-    // Every full tile owns at least 16 KiB of arena (two complex64 states of a
-    // 1024-arc coined tile with degree <= 32 holds >= 993 arcs; four of a
-    // 1024-vertex CTQW tile) and each job has at most one partial tile, so this
-    // bounds the tiles of any resident set.
+    // Every full tile owns at least 15000 bytes of arena (two complex64 states
+    // of a 1024-arc coined tile with degree <= 32 holds >= 993 arcs; four of a
+    // 512-vertex complex64 or 256-vertex complex128 CTQW tile, 16 KiB) and each
+    // job has at most one partial tile, so this bounds the tiles of any
+    // resident set.
     s->max_tiles = int(std::min<int64_t>(int64_t(1) << 30, arena_bytes / 15000 + max_jobs));
     auto fail = [&](hw_status e) { hw_server_destroy(s); return e; };
     hw_status st;
@@ -665,10 +676,12 @@ extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int
     if ((st = hw_cuda(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking), "cudaStreamCreate")) != HW_OK)
         return fail(st);
     s->own_stream = true;
-    if ((st = hw_cuda(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking), "cudaStreamCreate")) != HW_OK ||
-        (st = hw_cuda(cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming), "event")) != HW_OK ||
-        (st = hw_cuda(cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming), "event")) != HW_OK)
+    if ((st = hw_cuda(cudaStreamCreateWithFlags(&s->st2, cudaStreamNonBlocking), "cudaStreamCreate")) != HW_OK)
         return fail(st);
+    for (int r = 0; r < hw_server::kTimeSets; ++r)
+        for (int e = 0; e < 4; ++e)
+            if ((st = hw_cuda(cudaEventCreate(&s->tev[r][e]), "event")) != HW_OK) return fail(st);
+    s->L = substeps_per_round;
     if ((st = hw_cuda(cudaMalloc(&s->dev_base, size_t(arena_bytes)), "cudaMalloc(serving arena)")) != HW_OK ||
         (st = hw_cuda(cudaHostAlloc(&s->host_base, size_t(host_bytes), cudaHostAllocDefault), "cudaHostAlloc(results)")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_jobs, sizeof(SJob) * max_jobs), "cudaMalloc(job table)")) != HW_OK ||
@@ -680,6 +693,7 @@ extern "C" hw_status hw_server_create(int64_t arena_bytes, int32_t max_jobs, int
         (st = hw_cuda(cudaHostAlloc(&s->h_ntiles, sizeof(int), cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_tick, sizeof(int64_t)), "cudaMalloc")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_local, sizeof(int) * max_jobs), "cudaMalloc(local jobs)")) != HW_OK ||
+        (st = hw_cuda(cudaMalloc(&s->d_lprog, sizeof(int64_t) * max_jobs), "cudaMalloc(local progress)")) != HW_OK ||
         (st = hw_cuda(cudaHostAlloc(&s->h_local, sizeof(int) * max_jobs, cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
         (st = hw_cuda(cudaMalloc(&s->d_nlocal, sizeof(int)), "cudaMalloc")) != HW_OK ||
         (st = hw_cuda(cudaHostAlloc(&s->h_nlocal, sizeof(int), cudaHostAllocDefault), "cudaHostAlloc")) != HW_OK ||
@@ -705,6 +719,7 @@ extern "C" hw_status hw_server_destroy(hw_server *s)
     hw_clear_error();
     if (!s) return HW_OK;
     if (s->st) cudaStreamSynchronize(s->st);
+    if (s->st2) cudaStreamSynchronize(s->st2);
     for (auto &kv : s->jobs)
         if (kv.second.done_ev) cudaEventDestroy(kv.second.done_ev);
     if (s->graph) cudaGraphExecDestroy(s->graph);
@@ -720,11 +735,13 @@ extern "C" hw_status hw_server_destroy(hw_server *s)
     cudaFreeHost(s->h_ntiles);
     cudaFree(s->d_tick);
     cudaFree(s->d_local);
+    cudaFree(s->d_lprog);
     cudaFreeHost(s->h_local);
     cudaFree(s->d_nlocal);
     cudaFreeHost(s->h_nlocal);
-    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
-    if (s->join_ev) cudaEventDestroy(s->join_ev);
+    for (int r = 0; r < hw_server::kTimeSets; ++r)
+        for (int e = 0; e < 4; ++e)
+            if (s->tev[r][e]) cudaEventDestroy(s->tev[r][e]);
     if (s->st2) cudaStreamDestroy(s->st2);
     if (s->own_stream && s->st) cudaStreamDestroy(s->st);
     cudaGetLastError();
@@ -804,7 +821,7 @@ static hw_status rebuild_tiles(hw_server *s)
         // coined: a vertex per thread, and at least kServeTileArcs arcs per tile
         const int64_t step = (J.spec.kind == HW_JOB_COINED)
                                  ? std::max<int64_t>(kServeThreads, kServeTileArcs / J.spec.graph->max_degree)
-                                 : kTileVertices;
+                                 : (J.spec.dt == HW_C128 ? kTileVerticesC128 : kTileVerticesC64);
         for (int64_t v0 = 0; v0 < J.n; v0 += step) {
             if (nt >= s->max_tiles) return hw_fail(HW_EUNSUPPORTED, "tile list overflow (%d tiles)", nt);
             Tile t;
@@ -896,6 +913,11 @@ static hw_status admit(hw_server *s, Job &J)
     if (J.spec.dt == HW_C128) k_fill<double2><<<grid, 256, 0, s->st>>>(static_cast<double2 *>(D.X[0]), J.dim, amp);
     else k_fill<float2><<<grid, 256, 0, s->st>>>(static_cast<float2 *>(D.X[0]), J.dim, amp);
     J.end_tick = s->tick + J.total_subs;
+    if (J.local) {
+        J.lprog = 0;
+        const hw_status ps = hw_cuda(cudaMemsetAsync(s->d_lprog + J.slot, 0, sizeof(int64_t), s->st), "memset progress");
+        if (ps != HW_OK) return ps;
+    }
     J.state = RESIDENT;
     s->resident.push_back(J.id);
     s->table_dirty = true;
@@ -952,6 +974,71 @@ static hw_status retire(hw_server *s, Job &J)
     return HW_OK;
 }
 
+// Local steps per round from the branch times of a finished round: the local
+// branch should take about as long as the graph beside it.  With no tiled
+// work the sub-steps are idle launches, and L stays at K.
+static void pace_local(hw_server *s)
+{
+    if (*s->h_ntiles == 0) {
+        s->L = s->K;
+        return;
+    }
+    const int64_t r = s->round_no - hw_server::kTimeSets / 2;
+    if (r < 0) return;
+    const int set = int(r % hw_server::kTimeSets);
+    if (!s->tlocal[set] || cudaEventQuery(s->tev[set][1]) != cudaSuccess ||
+        cudaEventQuery(s->tev[set][3]) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    float tg = 0.f, tl = 0.f;
+    if (cudaEventElapsedTime(&tg, s->tev[set][0], s->tev[set][1]) != cudaSuccess ||
+        cudaEventElapsedTime(&tl, s->tev[set][2], s->tev[set][3]) != cudaSuccess || tl <= 0.f) {
+        cudaGetLastError();
+        return;
+    }
+    const double want = double(s->L) * tg / tl;   // the L that matches the two branches
+    if (tl > 1.25f * tg) s->L = std::max(1, int(want));
+    else if (tl < 0.8f * tg) s->L = std::min(s->K, std::max(s->L + 1, int(want)));
+}
+
+// One round: the graph (K tiled sub-steps and the tick) on the server stream
+// and, beside it on the second stream, L steps of every local CTQW job; the
+// server stream then waits for both, so the next round's table updates and
+// retirements follow them.  Branch times are recorded for pace_local.
+static hw_status launch_round(hw_server *s)
+{
+    pace_local(s);
+    const int set = int(s->round_no % hw_server::kTimeSets);
+    cudaEvent_t *ev = s->tev[set];
+    const bool local = *s->h_nlocal > 0;
+    hw_status st;
+    if ((st = hw_cuda(cudaEventRecord(ev[0], s->st), "event record")) != HW_OK) return st;
+    if (local) {
+        if ((st = hw_cuda(cudaStreamWaitEvent(s->st2, ev[0], 0), "stream wait")) != HW_OK ||
+            (st = hw_cuda(cudaEventRecord(ev[2], s->st2), "event record")) != HW_OK)
+            return st;
+        k_serve_local<<<kLocalCtas, kLocalThreads, kLocalBytes, s->st2>>>(s->d_jobs, s->d_local, s->d_nlocal,
+                                                                          s->d_lprog, s->L);
+        if ((st = hw_cuda(cudaGetLastError(), "k_serve_local launch")) != HW_OK ||
+            (st = hw_cuda(cudaEventRecord(ev[3], s->st2), "event record")) != HW_OK)
+            return st;
+    }
+    if ((st = hw_cuda(cudaGraphLaunch(s->graph, s->st), "cudaGraphLaunch")) != HW_OK ||
+        (st = hw_cuda(cudaEventRecord(ev[1], s->st), "event record")) != HW_OK)
+        return st;
+    if (local && (st = hw_cuda(cudaStreamWaitEvent(s->st, ev[3], 0), "stream wait")) != HW_OK) return st;
+    s->tlocal[set] = local;
+    ++s->round_no;
+    s->tick += s->K;
+    // the host's copy of every local job's progress (the kernel does the same)
+    for (int64_t id : s->resident) {
+        Job &J = s->jobs[id];
+        if (J.local) J.lprog = std::min<int64_t>(J.spec.steps, J.lprog + s->L);
+    }
+    return HW_OK;
+}
+
 extern "C" hw_status hw_server_run(hw_server *s, int32_t *n_completed)
 {
     hw_clear_error();
@@ -969,7 +1056,7 @@ extern "C" hw_status hw_server_run(hw_server *s, int32_t *n_completed)
     // 1. retire jobs whose last sub-step has been launched
     for (size_t i = 0; i < s->resident.size();) {
         Job &J = s->jobs[s->resident[i]];
-        if (J.end_tick <= s->tick) {
+        if (J.local ? J.lprog >= J.spec.steps : J.end_tick <= s->tick) {
             if ((st = retire(s, J)) != HW_OK) return st;
             s->free_slots.push_back(J.slot);
             s->resident.erase(s->resident.begin() + i);
@@ -1021,8 +1108,7 @@ extern "C" hw_status hw_server_run(hw_server *s, int32_t *n_completed)
             s->table_dirty = false;
             s->upload_pending = true;
         }
-        if ((st = hw_cuda(cudaGraphLaunch(s->graph, s->st), "cudaGraphLaunch")) != HW_OK) return st;
-        s->tick += s->K;
+        if ((st = launch_round(s)) != HW_OK) return st;
     }
     if (n_completed) *n_completed = done;
     return HW_OK;
