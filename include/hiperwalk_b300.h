@@ -29,6 +29,10 @@
  *   - Batched buffers are batch-innermost: element (i, b) is at i*batch + b.
  *   - No call waits without bound: device-side waits carry a time limit and
  *     report HW_ETIMEDOUT.
+ *   - Host threads: calls may run concurrently from several threads, also on
+ *     the same graph (its per-graph caches are locked), but a graph must not
+ *     be freed while another call uses it, and one server (hw_server_*) is
+ *     driven by one thread at a time.
  */
 #ifndef HIPERWALK_B300_H
 #define HIPERWALK_B300_H
