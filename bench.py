@@ -607,7 +607,7 @@ def run_workload_sampled(args):
         torch.cuda.synchronize()
         t_s = e[0].elapsed_time(e[1]) / 1e3 / args.steps
         t_p = e[1].elapsed_time(e[2]) / 1e3 / args.steps
-        curve, k, pmax = hw.success_curve(prob.cpu().numpy(), [m])
+        curve, k, pmax = hw.success_curve(prob, [m])
         res[name] = {"samples": R, "value": G.num_arcs * steps_total / t_s, "ms_sampled": t_s * 1e3,
                      "ms_plain_evolve": t_p * 1e3, "overhead": t_s / t_p - 1.0,
                      "best_sample_step": k * 100, "best_p_m": pmax}

@@ -295,6 +295,32 @@ hw_status hw_ctqw_sample(const void *U, int64_t n, hw_dtype dt, int32_t batch, i
                          const hw_opts *opts, void *stream);
 
 /*
+ * hw_success_curve -- the success probability of a search at sampled times
+ * and the sample where it peaks.  Sec. 3 provides search by walks with marked
+ * vertices, evaluated with simulate(range=...) and probability_distribution
+ * (Sec. 3.1, 3.2); Sec. 5 plans the success probability and the optimal
+ * running time as outputs.  With prob_out of hw_coined_sample or
+ * hw_ctqw_sample:
+ *   curve[r][b] = sum_{m in M} prob[r][m][b]   (summed in double, ids ascending)
+ *   argmax[b]   = the first r with the largest curve[r][b] (the optimal
+ *                 running time is start + argmax * stride); NaN entries never
+ *                 count; -1 when R = 0 or every entry is NaN
+ *   max[b]      = curve[argmax[b]][b] (NaN when argmax[b] = -1)
+ *   prob        DEVICE double[R][n][batch] (may be NULL when R = 0)
+ *   R, n, batch samples (>= 0), vertices (>= 1), states per sample (>= 1)
+ *   marked      HOST int32[n_marked], n_marked >= 1, ids in [0, n), no repeats
+ *   curve_out   DEVICE double[R][batch], must not overlap prob
+ *   argmax_out  DEVICE int64[batch] or NULL;  max_out DEVICE double[batch] or NULL
+ * Buffers are caller-owned and 8-byte aligned.  Up to 16 marked ids travel
+ * with the launch; longer lists are uploaded to stream-ordered scratch, which
+ * synchronises the stream once.
+ * Errors: HW_EINVAL, HW_ENOMEM, HW_ECUDA.
+ */
+hw_status hw_success_curve(const double *prob, int64_t R, int64_t n, int32_t batch, const int32_t *marked,
+                           int32_t n_marked, double *curve_out, int64_t *argmax_out, double *max_out,
+                           void *stream);
+
+/*
  * hw_probability -- per-vertex probabilities, summed in double precision.
  *   g != NULL: coined walk, p_v = sum_{w in N(v)} |<v,w|psi>|^2 (Sec. 3.2);
  *              psi is DEVICE [num_arcs][batch]; n is ignored.
@@ -319,11 +345,17 @@ hw_status hw_probability(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batc
  * device that loads the library until the process exits).
  *   Arguments, layouts and results as hw_probability.
  *   Limit: batch <= 64 when norm_out != NULL (HW_EINVAL otherwise).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the one array, so
- * calls whose work overlaps on the GPU (different streams, no ordering) race
- * on it and must be serialised by the caller.
+ * The array is device memory of the library's module: it is committed when
+ * the module is loaded on a device, which with CUDA's lazy module loading
+ * can be this entry point's first call there.  That first call also looks up
+ * the array's device address (cudaGetSymbolAddress) with the device current.
+ * So make one call per device at start-up, before the memory budget is
+ * reserved and before any stream capture; later calls allocate nothing.  The
+ * address is cached per device for the life of the process: resetting a
+ * device (cudaDeviceReset) while the library is loaded is not supported.
+ * All calls on a device share the one array, so calls whose work overlaps on
+ * the GPU (different streams, no ordering) race on it and must be serialised
+ * by the caller.
  * Errors: HW_EINVAL, HW_EUNSUPPORTED (device index >= 64), HW_ECUDA.
  */
 hw_status hw_probability_noalloc(const hw_graph *g, int64_t n, hw_dtype dt, int32_t batch,

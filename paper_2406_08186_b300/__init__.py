@@ -34,7 +34,7 @@ EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free"
            "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_trim_scratch", "hw_last_error",
            "hw_version", "hw_coined_sample", "hw_ctqw_sample", "hw_graph_structure",
            "hw_graph_structure_host", "hw_measure_fp64", "hw_measure_l2",
-           "hw_graph_csr_weighted")
+           "hw_graph_csr_weighted", "hw_success_curve")
 
 
 class HWError(RuntimeError):
@@ -100,6 +100,8 @@ def lib():
         L.hw_coined_sample.restype = st
         L.hw_ctqw_sample.argtypes = [P, i64, st, i32, i64, i64, i64, P, P, P, ctypes.POINTER(hw_opts), P]
         L.hw_ctqw_sample.restype = st
+        L.hw_success_curve.argtypes = [P, i64, i64, i32, P, i32, P, P, P, P]
+        L.hw_success_curve.restype = st
         L.hw_probability.argtypes = [P, i64, st, i32, P, P, P, P]
         L.hw_probability.restype = st
         L.hw_probability_noalloc.argtypes = [P, i64, st, i32, P, P, P, P]
@@ -378,15 +380,30 @@ def sample_count(start: int, end: int, stride: int) -> int:
     return max(0, (end - start + stride - 1) // stride)
 
 
-def success_curve(prob, marked):
-    """Success probability of a search at each sample (the sum over the marked
-    vertices of the per-vertex probabilities, prob shaped [samples][n]) and the
-    sample where it peaks: (curve, index of the maximum, maximum).  Host only."""
-    import numpy as np
-    p = np.asarray(prob, dtype=np.float64)
-    curve = p[:, np.asarray(list(marked), dtype=np.int64)].sum(axis=1)
-    k = int(np.argmax(curve)) if curve.size else -1
-    return curve, k, (float(curve[k]) if curve.size else 0.0)
+def hw_success_curve(prob, marked, curve_out, argmax_out=None, max_out=None, stream=None):
+    """Success probability of a search per sample, curve[r][b] = sum over the
+    marked vertices of prob[r][m][b], and the first sample where it peaks
+    (device tensors: prob float64 [R][n] or [R][n][batch], curve_out float64
+    [R] or [R][batch], argmax_out int64 [batch], max_out float64 [batch])."""
+    R, n = int(prob.shape[0]), int(prob.shape[1])
+    batch = int(prob.shape[2]) if prob.dim() == 3 else 1
+    m, nm = _host_i32(marked)
+    _check(lib().hw_success_curve(_dev(prob, "float64"), R, n, batch,
+                                  None if m is None else m.ctypes.data_as(ctypes.c_void_p), nm,
+                                  _dev(curve_out, "float64"), _dev(argmax_out, "int64"),
+                                  _dev(max_out, "float64"), _stream(stream)))
+
+
+def success_curve(prob, marked, stream=None):
+    """(curve, sample index of the maximum, maximum) of a single-state search from
+    its sampled probabilities prob [R][n] (a float64 CUDA tensor), computed by
+    hw_success_curve; the two scalars are read back (the call synchronises)."""
+    import torch
+    curve = torch.empty(prob.shape[0], dtype=torch.float64, device=prob.device)
+    k = torch.empty(1, dtype=torch.int64, device=prob.device)
+    mx = torch.empty(1, dtype=torch.float64, device=prob.device)
+    hw_success_curve(prob, marked, curve, k, mx, stream=stream)
+    return curve, int(k.item()), float(mx.item())
 
 
 def hw_probability(g, n: int, dt: int, batch: int, psi, prob_out=None, norm_out=None, stream=None):

@@ -162,6 +162,112 @@ hw_status launch_probability(const hw_graph *g, int64_t n, hw_dtype dt, int batc
     return s;
 }
 
+// ---------------------------------------------------------------- search analysis
+// The success probability of a search at sampled times (the paper's search
+// use of simulate(range=...) and probability_distribution, Sec. 3, and the
+// success probability / optimal running time of Sec. 5):
+//   curve[r][b] = sum_{m in M} prob[r][m][b]   (marked ids ascending)
+// and, per column b, the first sample r at which the curve is largest.
+namespace {
+
+__global__ void k_success_curve(const double *__restrict__ prob, int64_t R, int64_t n, int batch,
+                                MarkedList mk, double *__restrict__ curve)
+{
+    const int64_t total = R * batch;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        int64_t b = 0;
+        const int64_t r = (batch == 1) ? i : idx_div(i, batch, b);
+        const double *row = prob + r * n * batch + b;
+        double s = 0.0;
+        for (int k = 0; k < mk.n; ++k) s += row[int64_t(marked_id(mk, k)) * batch];
+        curve[i] = s;
+    }
+}
+
+constexpr int kArgmaxThreads = 256;
+
+// (value, sample) pairs: a pair with r < 0 holds nothing; otherwise the larger
+// value wins and equal values go to the earlier sample.  NaN entries are
+// skipped when the pairs are formed, so they never win.
+__device__ __forceinline__ bool curve_better(double v, int64_t r, double bv, int64_t br)
+{
+    if (r < 0) return false;
+    if (br < 0) return true;
+    return v > bv || (v == bv && r < br);
+}
+
+// one CTA per column: strided scan, then a fixed tree over the threads
+__global__ void __launch_bounds__(kArgmaxThreads)
+k_curve_argmax(const double *__restrict__ curve, int64_t R, int batch, int64_t *__restrict__ argmax,
+               double *__restrict__ maxv)
+{
+    __shared__ double sv[kArgmaxThreads];
+    __shared__ int64_t sr[kArgmaxThreads];
+    const int b = blockIdx.x;
+    double bv = 0.0;
+    int64_t br = -1;
+    for (int64_t r = threadIdx.x; r < R; r += kArgmaxThreads) {
+        const double v = curve[r * batch + b];
+        if (v == v && curve_better(v, r, bv, br)) { bv = v; br = r; }
+    }
+    sv[threadIdx.x] = bv;
+    sr[threadIdx.x] = br;
+    __syncthreads();
+    for (int o = kArgmaxThreads / 2; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o && curve_better(sv[threadIdx.x + o], sr[threadIdx.x + o], sv[threadIdx.x],
+                                                 sr[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + o];
+            sr[threadIdx.x] = sr[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (argmax) argmax[b] = sr[0];
+        if (maxv) maxv[b] = sr[0] < 0 ? __longlong_as_double(0x7ff8000000000000LL) : sv[0];
+    }
+}
+
+}  // namespace
+
+extern "C" hw_status hw_success_curve(const double *prob, int64_t R, int64_t n, int32_t batch,
+                                      const int32_t *marked, int32_t n_marked, double *curve_out,
+                                      int64_t *argmax_out, double *max_out, void *stream)
+{
+    hw_clear_error();
+    if (R < 0) return hw_fail(HW_EINVAL, "R must be >= 0");
+    if (n < 1) return hw_fail(HW_EINVAL, "n must be >= 1");
+    if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
+    if (n_marked < 1 || !marked) return hw_fail(HW_EINVAL, "the success curve needs at least one marked vertex");
+    if (!curve_out) return hw_fail(HW_EINVAL, "curve_out is NULL");
+    if (R > 0 && !prob) return hw_fail(HW_EINVAL, "prob is NULL");
+    if (((uintptr_t)prob | (uintptr_t)curve_out | (uintptr_t)argmax_out | (uintptr_t)max_out) % 8)
+        return hw_fail(HW_EINVAL, "buffers must be 8-byte aligned");
+    if (R > 0) {
+        const char *p0 = reinterpret_cast<const char *>(prob);
+        const char *c0 = reinterpret_cast<const char *>(curve_out);
+        const size_t pb = sizeof(double) * size_t(R) * size_t(n) * size_t(batch);
+        const size_t cb = sizeof(double) * size_t(R) * size_t(batch);
+        if (p0 < c0 + cb && c0 < p0 + pb) return hw_fail(HW_EINVAL, "curve_out overlaps prob");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MarkedList mk;
+    hw_status s = make_marked(marked, n_marked, n, st, &mk);
+    if (s != HW_OK) return s;
+    if (R > 0) {
+        const int64_t total = R * batch;
+        const int64_t grid = std::min<int64_t>(148 * 8, std::max<int64_t>(1, (total + 255) / 256));
+        k_success_curve<<<grid, 256, 0, st>>>(prob, R, n, batch, mk, curve_out);
+        s = hw_cuda(cudaGetLastError(), "k_success_curve launch");
+    }
+    if (s == HW_OK && (argmax_out || max_out)) {
+        k_curve_argmax<<<batch, kArgmaxThreads, 0, st>>>(curve_out, R, batch, argmax_out, max_out);
+        s = hw_cuda(cudaGetLastError(), "k_curve_argmax launch");
+    }
+    free_marked(mk, st);
+    return s;
+}
+
 // ---------------------------------------------------------------- no allocation
 // hw_probability for callers that cannot allocate device memory during a
 // call: programs that run under a fixed, pre-reserved memory budget (a

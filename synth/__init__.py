@@ -210,14 +210,21 @@ def adjacency_csr(n: int, eu: np.ndarray, ev: np.ndarray, scramble_seed: int | N
     """
     tails = np.concatenate([eu, ev])
     heads = np.concatenate([ev, eu])
-    if scramble_seed is None:
-        key = np.arange(tails.size)
-    else:
-        key = splitmix64(scramble_seed, tails.size)
-    order = np.lexsort((key, tails))
+    order = _row_order(tails, scramble_seed)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(tails, minlength=n), out=row_ptr[1:])
     return row_ptr, heads[order].astype(np.int32)
+
+
+def _row_order(tails: np.ndarray, scramble_seed):
+    """Permutation grouping the entries by tail; inside a row, the order of the
+    top 32 bits of SplitMix64(scramble_seed) draws (ties by position), or the
+    given order when scramble_seed is None.  One sort of a packed 64-bit key
+    (tails < 2^31)."""
+    if scramble_seed is None:
+        return np.argsort(tails, kind="stable")
+    key = (tails.astype(np.uint64) << np.uint64(32)) | (splitmix64(scramble_seed, tails.size) >> np.uint64(32))
+    return np.argsort(key, kind="stable")
 
 
 def edge_weights(count: int, seed: int, complex_phase: bool = False) -> np.ndarray:
@@ -237,11 +244,7 @@ def weighted_csr(n: int, eu: np.ndarray, ev: np.ndarray, we: np.ndarray, scrambl
     tails = np.concatenate([eu, ev])
     heads = np.concatenate([ev, eu])
     vals = np.concatenate([we, np.conj(we)])
-    if scramble_seed is None:
-        key = np.arange(tails.size)
-    else:
-        key = splitmix64(scramble_seed, tails.size)
-    order = np.lexsort((key, tails))
+    order = _row_order(tails, scramble_seed)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(tails, minlength=n), out=row_ptr[1:])
     return row_ptr, heads[order].astype(np.int32), vals[order]
@@ -278,6 +281,46 @@ def gaussian_states(dim: int, batch: int, seed: int) -> np.ndarray:
         z = complex_gaussian(seed, dim, b * dim)
         out[:, b] = z / np.sqrt(np.sum(np.abs(z) ** 2))
     return out
+
+
+def gaussian_states_device(dim: int, batch: int, seed: int, dtype=None, device="cuda"):
+    """``gaussian_states`` drawn on a torch device: the same SplitMix64 streams
+    (bit-exact 64-bit integer arithmetic), Box-Muller and per-column
+    normalisation in float64 with the device's math functions, then cast to
+    ``dtype`` (default complex128).  The device's log, sqrt, sin and cos and its
+    summation order may differ from the host's in the last bit, so columns
+    agree with ``gaussian_states`` to a few float64 ulps, not bit for bit.
+    Returns a [dim, batch] tensor (batch innermost), one column drawn at a time."""
+    import torch
+    dtype = torch.complex128 if dtype is None else dtype
+    out = torch.empty((dim, batch), dtype=dtype, device=device)
+    golden = _as_i64(0x9E3779B97F4A7C15)
+    m1, m2 = _as_i64(0xBF58476D1CE4E5B9), _as_i64(0x94D049BB133111EB)
+    s0 = _as_i64(seed & 0xFFFFFFFFFFFFFFFF)
+
+    def lsr(z, k):   # logical right shift of 64-bit patterns held in int64
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    for b in range(batch):
+        k = torch.arange(2 * b * dim + 1, 2 * (b + 1) * dim + 1, dtype=torch.int64, device=device)
+        z = s0 + k * golden                      # wraps mod 2^64 like the uint64 form
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        u = lsr(z, 11).to(torch.float64) * (2.0 ** -53)
+        u1, u2 = u[0::2], u[1::2]
+        r = torch.sqrt(-2.0 * torch.log1p(-u1))
+        th = 2.0 * math.pi * u2
+        col = torch.complex(r * torch.cos(th), r * torch.sin(th))
+        col = col / torch.sqrt(torch.sum(col.real * col.real + col.imag * col.imag))
+        out[:, b] = col.to(dtype)
+    return out
+
+
+def _as_i64(x: int) -> int:
+    """The int64 value with the bit pattern of the unsigned 64-bit x."""
+    x &= 0xFFFFFFFFFFFFFFFF
+    return x - (1 << 64) if x >= (1 << 63) else x
 
 
 def random_state(dim: int, seed: int) -> np.ndarray:

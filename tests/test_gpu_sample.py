@@ -75,9 +75,20 @@ def test_coined_samples_batched_and_probabilities_only(hw):
     G.free()
 
 
-def test_complete_graph_search_curve(hw):
+def _search_curve_kn(N, steps):
     # K_N with one mark from the uniform state: the class amplitudes (al, be, ga)
     # of arcs (m,u), (u,m), (u,u') follow a 3-term recursion; p_m = (N-1) |al|^2
+    al = be = ga = 1.0 / math.sqrt(N * (N - 1))
+    ref = []
+    for _ in range(steps):
+        mu = (be + (N - 2) * ga) / (N - 1)
+        al, be, ga = 2 * mu - be, -al, 2 * mu - ga
+        ref.append((N - 1) * al * al)
+    return np.array(ref)
+
+
+def test_complete_graph_search_curve(hw):
+    # the success curve and its peak from the device, against the closed form
     import torch
     N, steps = 40, 50
     g = synth.complete(N)
@@ -87,17 +98,81 @@ def test_complete_graph_search_curve(hw):
     x = torch.full((ar_arcs,), 1 / math.sqrt(ar_arcs), dtype=torch.complex128, device="cuda")
     prob = torch.empty((steps, N), dtype=torch.float64, device="cuda")
     hw.hw_coined_sample(G, 0, [m], 2, 1, 1, steps + 1, 1, x, None, prob)
-    torch.cuda.synchronize()
-    curve, k, pmax = hw.success_curve(prob.cpu().numpy(), [m])
-    al = be = ga = 1.0 / math.sqrt(N * (N - 1))
-    ref = []
-    for _ in range(steps):
-        mu = (be + (N - 2) * ga) / (N - 1)
-        al, be, ga = 2 * mu - be, -al, 2 * mu - ga
-        ref.append((N - 1) * al * al)
-    assert np.max(np.abs(curve - np.array(ref))) < 1e-12
-    assert k == int(np.argmax(ref)) and abs(pmax - max(ref)) < 1e-12
+    curve, k, pmax = hw.success_curve(prob, [m])
+    ref = _search_curve_kn(N, steps)
+    assert np.max(np.abs(curve.cpu().numpy() - ref)) < 1e-12
+    assert k == int(np.argmax(ref)) and abs(pmax - ref.max()) < 1e-12
     G.free()
+
+
+def test_success_curve_matches_oracle_record(hw):
+    # two marks, two states per sample: the curve of every column against the
+    # marked-probability record of the oracle's walk, and the peak against
+    # the record's (unique) maximum
+    import torch
+    g = synth.torus(16)
+    G = _graph(hw, g)
+    ar = oracle.Arcs(*g)
+    marked = [37, 200]
+    B, start, end, stride = 2, 3, 90, 3
+    psi0 = np.stack([synth.random_state(ar.num_arcs, seed=s) for s in (11, 12)], axis=1)
+    x = torch.from_numpy(np.ascontiguousarray(psi0)).cuda()
+    R = hw.sample_count(start, end, stride)
+    prob = torch.empty((R, g[0], B), dtype=torch.float64, device="cuda")
+    hw.hw_coined_sample(G, 0, marked, 2, B, start, end, stride, x, None, prob)
+    curve = torch.empty((R, B), dtype=torch.float64, device="cuda")
+    kmax = torch.empty(B, dtype=torch.int64, device="cuda")
+    vmax = torch.empty(B, dtype=torch.float64, device="cuda")
+    hw.hw_success_curve(prob, marked, curve, kmax, vmax)
+    torch.cuda.synchronize()
+    for b in range(B):
+        _, rec = oracle.coined_evolve(ar, psi0[:, b], end, marked=marked, record=True)
+        ref = rec[start - 1:end - 1:stride]       # rec[t-1] = marked probability after step t
+        got = curve[:, b].cpu().numpy()
+        assert np.max(np.abs(got - ref)) < 1e-12
+        assert int(kmax[b]) == int(np.argmax(ref))
+        assert abs(float(vmax[b]) - ref.max()) < 1e-12
+    G.free()
+
+
+def test_success_curve_edge_cases(hw):
+    import torch
+    dev = "cuda"
+    # ties go to the earliest sample; NaN entries never win (sums of dyadic
+    # values, so every sum below is exact)
+    prob = torch.tensor([[[0.25], [0.125]], [[0.375], [0.0]], [[float("nan")], [0.5]], [[0.125], [0.25]]],
+                        dtype=torch.float64, device=dev)            # [R=4][n=2][batch=1]
+    curve = torch.empty((4, 1), dtype=torch.float64, device=dev)
+    k = torch.empty(1, dtype=torch.int64, device=dev)
+    v = torch.empty(1, dtype=torch.float64, device=dev)
+    hw.hw_success_curve(prob, [0, 1], curve, k, v)
+    c = curve[:, 0].cpu().numpy()
+    assert c[0] == 0.375 and c[1] == 0.375 and math.isnan(c[2]) and c[3] == 0.375
+    assert int(k) == 0 and float(v) == 0.375
+    # only NaN: no maximum
+    hw.hw_success_curve(prob[2:3], [0], curve[:1], k, v)
+    assert int(k) == -1 and math.isnan(float(v))
+    # no samples: argmax -1, maximum NaN
+    empty = torch.empty((0, 2), dtype=torch.float64, device=dev)
+    hw.hw_success_curve(empty, [1], torch.empty(0, dtype=torch.float64, device=dev), k, v)
+    assert int(k) == -1 and math.isnan(float(v))
+    # more marks than travel with the launch (> 16): the list goes to the device
+    R, n = 7, 300
+    p = torch.rand((R, n), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(3))
+    marks = list(range(5, 300, 9))
+    cv = torch.empty(R, dtype=torch.float64, device=dev)
+    hw.hw_success_curve(p, marks, cv, k, v)
+    pn = p.cpu().numpy()
+    ref = pn[:, marks].sum(axis=1)
+    assert np.max(np.abs(cv.cpu().numpy() - ref)) < 1e-13
+    assert int(k) == int(np.argmax(ref))
+    # argument checks
+    for bad in ([], [n], [3, 3]):
+        with pytest.raises(hw.HWError) as e:
+            hw.hw_success_curve(p, bad, cv, k, v)
+        assert e.value.status == hw.HW_EINVAL
+    with pytest.raises(hw.HWError):
+        hw.hw_success_curve(p, [1], p.view(-1)[:R])      # curve inside prob
 
 
 def test_ctqw_samples(hw):

@@ -67,7 +67,7 @@ def _plain(hw, G, kind, dt, steps, marked, gamma=0.0, t=0.0):
     return prob.cpu().numpy(), None if rec is None else rec.cpu().numpy()
 
 
-DEGREE = {"torus": 4, "Q9": 9, "reg3": 3, "reg8": 8, "t": 4, "torus72": 4}
+DEGREE = {"torus": 4, "Q9": 9, "reg3": 3, "reg8": 8, "t": 4, "torus72": 4, "Q12": 12, "reg8k": 8, "torus96": 4}
 
 
 def _mix(hw):
@@ -138,6 +138,35 @@ def test_served_coined_matches_oracle(hw):
     assert np.max(np.abs(prob - oracle.prob_coined(ar, ref))) <= 1e-12
     assert np.max(np.abs(rec - rr)) <= 1e-12
     G.free()
+
+
+def test_served_ctqw_matches_oracle(hw):
+    # both CTQW branches of the server against the FP64 oracle, with marks and
+    # the marked-probability record: shared-memory ("local") jobs, complex128
+    # on 4096 vertices and complex64 on 8192; tiled jobs (one launch per
+    # series term), complex128 on 5184 vertices and complex64 on 9216
+    gs = {"Q12": synth.hypercube(12), "reg8k": synth.random_regular(8192, 8, seed=5),
+          "torus72": synth.torus(72), "torus96": synth.torus(96)}
+    graphs = {k: _graph(hw, g) for k, g in gs.items()}
+    jobs = [("Q12", hw.HW_JOB_CTQW, 2, 25, [4077, 9]),
+            ("reg8k", hw.HW_JOB_CTQW, 1, 40, [3]),
+            ("torus72", hw.HW_JOB_CTQW, 2, 15, [100, 5000]),
+            ("torus96", hw.HW_JOB_CTQW, 1, 20, [1, 4000, 9000])]
+    served = _serve(hw, graphs, jobs)
+    for (gname, kind, dt, steps, marked), (prob, rec, _) in zip(jobs, served):
+        ar = oracle.Arcs(*gs[gname])
+        n = gs[gname][0]
+        ref, rr = oracle.ctqw_evolve(ar, 1.0 / DEGREE[gname], np.full(n, 1 / np.sqrt(n), dtype=np.complex128),
+                                     0.1, steps, marked=marked, record=True)
+        p_ref = np.abs(ref) ** 2
+        if dt == 2:
+            assert np.max(np.abs(prob - p_ref)) <= 1e-12, gname
+            assert np.max(np.abs(rec - rr)) <= 1e-12, gname
+        else:
+            assert np.sum(np.abs(prob - p_ref)) <= 1e-3, gname
+            assert np.max(np.abs(rec - rr)) <= 1e-4, gname
+    for G in graphs.values():
+        G.free()
 
 
 def test_admission_waits_for_arena_memory(hw):

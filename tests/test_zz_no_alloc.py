@@ -58,6 +58,26 @@ def test_noalloc_matches_hw_probability_vertex_states(hw):
         assert np.max(np.abs(nm - n_ref)) <= TOL
 
 
+def test_noalloc_fills_the_whole_scratch_array(hw):
+    # the largest partial count (1184 row chunks) times the largest batch (64)
+    # writes every slot of the built-in array, the last one included
+    import torch
+    n, batch = 1184 * 4096 + 1, 64
+    gen = torch.Generator(device="cuda").manual_seed(31)
+    psi = torch.randn(n * batch, dtype=torch.complex128, device="cuda", generator=gen)
+    n_ref = torch.empty(batch, dtype=torch.float64, device="cuda")
+    hw.hw_probability(None, n, hw.HW_C128, batch, psi, None, n_ref)
+    for _ in range(2):
+        nm = torch.full((batch,), float("nan"), dtype=torch.float64, device="cuda")
+        hw.hw_probability_noalloc(None, n, hw.HW_C128, batch, psi, None, nm)
+        torch.cuda.synchronize()
+        # both reductions run the same fixed order, so they agree far below
+        # the bar; the sums are about 2n, so the bar is relative
+        assert np.max(np.abs(nm.cpu().numpy() - n_ref.cpu().numpy()) / n_ref.cpu().numpy()) <= TOL
+    del psi
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_rejects_batch_over_limit(hw):
     import torch
     n = 64
