@@ -49,7 +49,7 @@ UNIT = "arc-updates/s"
 TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
     # block row per torus row, complex128 sums by integer operations), one
-    # launch, cold L2 (profiles/coined_step_c{128,64}_torus1024.md)
+    # launch, cold L2
     ("c128", "f3e939a0195c9aadbd698cdcad55487394a0ca95"): 67132416 + 17325824,
     ("c64", "f3e939a0195c9aadbd698cdcad55487394a0ca95"): 33566464 + 195840,
 }
@@ -91,6 +91,17 @@ def measured_peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+def measured_tensor_peak():
+    """Dense bf16 tensor-core peak (TFLOP/s) measured on the B300s (burst:
+    the expm is timed on its own); fp16 runs at the same rate."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (measured, burst)"
+    except Exception:
+        return 1800.0, "fallback 1.8 PFLOP/s bf16 burst"
 
 
 class Clocks:
@@ -163,7 +174,9 @@ def replica_value(units_per_rank, world, t_max):
 
 
 def cpu_baseline(n, eu, ev, m, budget_s=12.0):
-    """The FP64 oracle, untuned, on the host cores: walk steps of the same search."""
+    """The FP64 oracle, untuned, on the host cores: walk steps of the same search.
+    Also returns the oracle's state and per-vertex probabilities after those
+    steps, for the error of the GPU results over the same steps."""
     import oracle
     cores = oracle.threads()
     ar = oracle.Arcs(n, eu, ev)
@@ -173,8 +186,9 @@ def cpu_baseline(n, eu, ev, m, budget_s=12.0):
         psi = oracle.coined_evolve(ar, psi, 5, marked=[m])
         done += 5
     el = time.perf_counter() - t0
-    return {"value": ar.num_arcs * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d walk steps of the 1024x1024 torus search (complex128 oracle, OpenMP)" % done}
+    return ({"value": ar.num_arcs * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": "%d walk steps of the 1024x1024 torus search (complex128 oracle, OpenMP)" % done},
+            done, psi, oracle.prob_coined(ar, psi))
 
 
 def run_reference(args):
@@ -331,7 +345,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "torus1024_search", "n": n, "arcs": arcs, "walk_steps": WALK_STEPS,
                    "coin": "grover", "marked": m, "state": "complex128", "record": "p_m(t) every step",
-                   "l2": "256 MiB written between timed steps; working set 151 MB > L2",
+                   "l2": "256 MiB written between timed steps; working set 134 MB (two 64 MiB state buffers) > L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm",
                      "kernel": "k_coined_em<double,4,grover,%s>" % ("torus" if index_free else "table"),
@@ -357,10 +371,30 @@ def run_ours(args):
         "norm_after": {"c128": norm128, "c64": norm64},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(n, eu, ev, m)
+        cb, done, psi_ref, p_ref = cpu_baseline(n, eu, ev, m)
+        line["cpu_baseline"] = cb
+        # the error of both GPU forms against the oracle over the same steps
+        errs = {"walk_steps": done}
+        for b, tag in ((b128, "c128"), (b64, "c64")):
+            hw.hw_coined_evolve(G, hw.HW_COIN_GROVER, [m], b["dt"], 1, done, b["psi0"], b["out"], stream=stream)
+            hw.hw_probability(G, n, b["dt"], 1, b["out"], b["prob"], stream=stream)
+            torch.cuda.synchronize()
+            got = b["out"].cpu().numpy().astype(np.complex128)
+            pg = b["prob"].cpu().numpy()
+            errs[tag] = {"max_abs_psi": float(np.max(np.abs(got - psi_ref))),
+                         "p_L1": float(np.sum(np.abs(pg - p_ref))), "p_m_abs": float(abs(pg[m] - p_ref[m]))}
+        line["error_vs_oracle"] = errs
+    G.free()
+    if world == 1 and not args.no_configs:
+        # the other configurations, each with its own timing, clocks, roofline
+        # and error figures
+        cpu = not args.no_cpu_baseline
+        line["cfg1_torus64"] = sub_torus64(hw, reps=max(args.steps, 10), warmup=args.warmup, with_cpu=cpu)
+        line["cfg3_hypercube12"] = sub_ctqw_q12(hw, reps=3, warmup=1, with_cpu=cpu)
+        line["cfg4_er_batched"] = sub_er_batched(hw, reps=3, warmup=1, with_cpu=cpu)
+        line["cfg5_serving"] = sub_serving(hw, args.serving_jobs)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    G.free()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -370,59 +404,65 @@ def _events(n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def run_workload_batched(args):
-    """Batched coined walks: ER graph n = 2^20, mean degree 8 (isolated vertices dropped),
-    64 unit complex64 states, Grover coin, 500 steps, one SpMM-shaped launch per step."""
+def _oracle_cores():
+    import oracle
+    return oracle.threads()
+
+
+def sub_torus64(hw, reps, warmup, with_cpu):
+    """Configuration 1: 64 x 64 torus, Grover, no mark, start on the 4 arcs of
+    (32, 32), 100 steps, complex128, per-vertex probabilities.  Time per run
+    (evolve + probabilities) from CUDA events; the run is launch-latency bound
+    (0.6 MB per walk step)."""
     import torch
-    import paper_2406_08186_b300 as hw
-    n0 = 1 << 20
-    n, eu, ev = synth.erdos_renyi(n0, 8.0 / (n0 - 1), seed=5)
+    n, eu, ev = synth.torus(64)
     row_ptr, col = synth.adjacency_csr(n, eu, ev)
     G = hw.hw_graph_csr(n, row_ptr, col)
-    A2, B, steps = G.num_arcs, 64, 500
-    gen = torch.Generator(device="cuda").manual_seed(4)
-    psi0 = torch.randn((A2, B), dtype=torch.complex64, device="cuda", generator=gen)
-    psi0 /= torch.linalg.vector_norm(psi0, dim=0, keepdim=True)
+    psi0_h = synth.state_on_vertex_arcs(synth.arc_offsets(n, eu, ev), 32 * 64 + 32)
+    psi0 = torch.from_numpy(psi0_h).cuda()
     out = torch.empty_like(psi0)
-    norm = torch.empty(B, dtype=torch.float64, device="cuda")
-    prob = torch.empty(n * B, dtype=torch.float64, device="cuda")
+    prob = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, 2, psi0, out)   # autotunes the launch shape once
-    for _ in range(args.warmup):
-        hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, steps, psi0, out)
+    for _ in range(max(3, warmup)):
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
+        hw.hw_probability(G, n, hw.HW_C128, 1, out, prob)
     torch.cuda.synchronize()
-    tot = ev_t = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        e = _events(4)
+    with Clocks(torch.cuda.current_device()) as clk:
+        e = _events(2)
         e[0].record(stream)
+        for _ in range(reps):
+            hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
+            hw.hw_probability(G, n, hw.HW_C128, 1, out, prob)
         e[1].record(stream)
-        hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, steps, psi0, out)
-        e[2].record(stream)
-        hw.hw_probability(G, n, hw.HW_C64, B, out, prob, norm)
-        e[3].record(stream)
         torch.cuda.synchronize()
-        tot += e[0].elapsed_time(e[3]) / 1e3
-        ev_t += e[1].elapsed_time(e[2]) / 1e3
-    peak, src = measured_peaks()
-    per_launch = ev_t / (args.steps * steps)
-    bytes_launch = A2 * (2 * B * 8 + 4) + 4 * (n + 1)
-    nm = norm.cpu().numpy()
-    print(json.dumps({"workload": "er_batched", "metric": METRIC, "unit": UNIT,
-                      "value": A2 * B * steps * args.steps / tot, "ms_per_step": 1e3 * tot / args.steps,
-                      "n": n, "arcs": A2, "batch": B, "walk_steps": steps, "dtype": "f32 (fp64 sums)",
-                      "roofline": {"bound": "hbm", "achieved": bytes_launch / per_launch / 1e9, "peak": peak,
-                                   "unit": "GB/s", "frac": bytes_launch / per_launch / 1e9 / peak,
-                                   "bytes_per_launch": bytes_launch, "launch_us": per_launch * 1e6,
-                                   "peak_source": src},
-                      "norm_minmax": [float(nm.min()), float(nm.max())]}), flush=True)
+    t = e[0].elapsed_time(e[1]) / 1e3 / reps
+    arcs = G.num_arcs
+    res = {"workload": "torus64_center", "metric": METRIC, "unit": UNIT, "value": arcs * 100 / t,
+           "us_per_run": t * 1e6, "us_per_walk_step": t / 100 * 1e6, "reps": reps, "dtype": "f64",
+           "roofline": {"bound": "latency", "bytes_per_walk_step": arcs * 32 + 4 * (n + 1),
+                        "note": "256 KiB state; a walk step moves 0.6 MB, far below what fills the GPU"},
+           "clocks": clk.summary()}
+    if with_cpu:
+        import oracle
+        ar = oracle.Arcs(n, eu, ev)
+        t0 = time.perf_counter()
+        ref = oracle.coined_evolve(ar, psi0_h, 100)
+        el = time.perf_counter() - t0
+        p_ref = oracle.prob_coined(ar, ref)
+        res["cpu_baseline"] = {"value": arcs * 100 / el, "unit": UNIT, "cores": _oracle_cores(), "kind": "oracle",
+                               "sample": "the whole 100-step run"}
+        res["error_vs_oracle"] = {"c128_max_abs_psi": float(np.max(np.abs(out.cpu().numpy() - ref))),
+                                  "c128_max_abs_p": float(np.max(np.abs(prob.cpu().numpy() - p_ref)))}
+    G.free()
+    return res
 
 
-def run_workload_ctqw(args):
-    """CTQW search on Q_12: U = exp(-iH 0.1) dense (Taylor, scaling and squaring), 2000 applications."""
+def sub_ctqw_q12(hw, reps, warmup, with_cpu):
+    """Configuration 3: CTQW search on Q_12, gamma = 1/12, one seeded mark,
+    U = exp(-iH 0.1) dense (Taylor, scaling and squaring), 2000 applications,
+    complex128 and complex64 (tensor-core powers); each result's error against
+    the complex128 GPU result and, with the CPU leg, against the oracle."""
     import torch
-    import paper_2406_08186_b300 as hw
     g = synth.hypercube(12)
     n = 4096
     m = synth.seeded_vertex(3, n)
@@ -430,56 +470,177 @@ def run_workload_ctqw(args):
     G = hw.hw_graph_csr(n, row_ptr, col)
     stream = torch.cuda.current_stream()
     peak, src = measured_peaks()
-    res = {"workload": "hypercube12_ctqw", "n": n, "marked": m, "gamma": 1 / 12, "dt": 0.1,
-           "applications": 2000}
+    tc_peak, tc_src = measured_tensor_peak()
     fp64 = hw.hw_measure_fp64()
-    for dt, name in ((hw.HW_C128, "c128"), (hw.HW_C64, "c64")):
-        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
-        U = torch.empty((n, n), dtype=cdt, device="cuda")
-        x = torch.full((n,), 1 / 64, dtype=cdt, device="cuda")
-        y = torch.empty_like(x)
-        rec = torch.empty(2000, dtype=torch.float64, device="cuda")
-        sym = {"u_symmetric": 1}   # U = e^{-iH dt} is complex symmetric
-        for _ in range(max(1, args.warmup)):
-            hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
-            hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec, opts=sym)
-        torch.cuda.synchronize()
-        t_exp = t_ev = 0.0
-        for _ in range(args.steps):
+    res = {"workload": "hypercube12_ctqw", "n": n, "marked": m, "gamma": 1 / 12, "dt": 0.1,
+           "applications": 2000, "reps": reps}
+    deg, sq = hw.hw_ctqw_plan(G, 1 / 12, [m], 0.1)
+    kept = {}
+    with Clocks(torch.cuda.current_device()) as clk:
+        for dt, name in ((hw.HW_C128, "c128"), (hw.HW_C64, "c64")):
+            cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+            U = torch.empty((n, n), dtype=cdt, device="cuda")
+            x = torch.full((n,), 1 / 64, dtype=cdt, device="cuda")
+            y = torch.empty_like(x)
+            rec = torch.empty(2000, dtype=torch.float64, device="cuda")
+            prob = torch.empty(n, dtype=torch.float64, device="cuda")
+            sym = {"u_symmetric": 1}   # U = e^{-iH dt} is complex symmetric
+            for _ in range(max(1, warmup)):
+                hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+                hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec, opts=sym)
+            torch.cuda.synchronize()
+            t_exp = t_ev = 0.0
+            for _ in range(reps):
+                e = _events(3)
+                e[0].record(stream)
+                hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+                e[1].record(stream)
+                hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec, opts=sym)
+                e[2].record(stream)
+                torch.cuda.synchronize()
+                t_exp += e[0].elapsed_time(e[1]) / 1e3
+                t_ev += e[1].elapsed_time(e[2]) / 1e3
+            t_exp /= reps
+            t_ev /= reps
+            hw.hw_probability(None, n, dt, 1, y, prob)
+            torch.cuda.synchronize()
+            kept[name] = (U, y, rec, prob)
+            r = {"expm_ms": t_exp * 1e3, "evolve_ms": t_ev * 1e3, "apply_us": t_ev / 2000 * 1e6,
+                 "taylor_degree": deg, "squarings": sq, "p_m_max": float(rec.max().item())}
+            if dt == hw.HW_C128:
+                # Taylor powers: FP64 GEMM tiles of 64 x 64 on and above the
+                # diagonal (the powers of the real symmetric Y are symmetric)
+                nb = (n + 63) // 64
+                fmas = (deg - 1) * (nb * (nb + 1) // 2) * 64 * 64 * n
+                r["expm_roofline"] = {"bound": "fp64", "achieved": fmas / t_exp, "peak": fp64,
+                                      "unit": "FMA/s", "frac": fmas / t_exp / fp64, "fma_per_expm": fmas,
+                                      "peak_source": "hw_measure_fp64 (register-blocked GEMM loop on this GPU)"}
+                # application: three real FMAs per element (the 3M form)
+                afma = 3.0 * n * n
+                r["apply_roofline"] = {"bound": "fp64", "achieved": afma / (t_ev / 2000), "peak": fp64,
+                                       "unit": "FMA/s", "frac": afma / (t_ev / 2000) / fp64, "fma_per_apply": afma}
+            else:
+                # MMA work issued on the tensor cores per expm: (m - 1) powers, each
+                # over the CTA tiles (128 x 256 x n) of the cluster tiles on and
+                # above the diagonal, two fp16 products per tile (272 tiles at
+                # n = 4096), against the bf16/fp16 dense peak
+                cl = (n + 255) // 256          # 2-CTA cluster tiles of 256 x 256 on and above the diagonal
+                mma = (deg - 1) * (cl * (cl + 1)) * 128 * 256 * n * 2 * 2.0
+                dense = (deg - 1) * 2.0 * n ** 3
+                r["expm_roofline"] = {"bound": "tensor", "achieved": mma / t_exp / 1e12, "peak": tc_peak,
+                                      "unit": "TFLOP/s", "frac": mma / t_exp / 1e12 / tc_peak,
+                                      "flop_per_expm_issued": mma, "dense_equivalent_tflops": dense / t_exp / 1e12,
+                                      "peak_source": tc_src,
+                                      "note": "whole expm (slicing, Taylor sums, finish) over the MMA work"}
+                abytes = n * n // 2 * 8 + n * 8
+                r["apply_roofline"] = {"bound": "l2", "achieved": abytes / (t_ev / 2000) / 1e9, "unit": "GB/s",
+                                       "bytes_per_apply": abytes,
+                                       "note": "upper triangle of U (68 MB) streamed per application, L2-resident"}
+            res[name] = r
+    res["clocks"] = clk.summary()
+    U128, y128, rec128, p128 = kept["c128"]
+    U64, y64, rec64, p64 = kept["c64"]
+    res["c64_vs_c128"] = {"U_max_abs": float((U64.to(torch.complex128) - U128).abs().max().item()),
+                          "p_L1": float((p64 - p128).abs().sum().item()),
+                          "p_m_record_max_abs": float((rec64 - rec128).abs().max().item())}
+    if with_cpu:
+        import oracle
+        ar = oracle.Arcs(*g)
+        t0 = time.perf_counter()
+        ref, rr = oracle.ctqw_evolve(ar, 1 / 12, np.full(n, 1 / 64, dtype=np.complex128), 0.1, 2000,
+                                     marked=[m], record=True)
+        el = time.perf_counter() - t0
+        pr = np.abs(ref) ** 2
+        res["cpu_baseline"] = {"value": 2000 / el, "unit": "applications/s", "cores": _oracle_cores(),
+                               "kind": "oracle", "sample": "the whole 2000-application run (sparse Taylor action)"}
+        res["error_vs_oracle"] = {
+            "c128_max_abs_psi": float(np.max(np.abs(y128.cpu().numpy() - ref))),
+            "c128_record_max_abs": float(np.max(np.abs(rec128.cpu().numpy() - rr))),
+            "c64_p_L1": float(np.sum(np.abs(p64.cpu().numpy() - pr))),
+            "c64_record_max_abs": float(np.max(np.abs(rec64.cpu().numpy() - rr)))}
+    G.free()
+    return res
+
+
+def er_graph():
+    n0 = 1 << 20
+    n, eu, ev = synth.erdos_renyi(n0, 8.0 / (n0 - 1), seed=5)
+    return n, eu, ev
+
+
+def sub_er_batched(hw, reps, warmup, with_cpu):
+    """Configuration 4: batched coined walks on the Erdos-Renyi graph (n = 2^20,
+    mean degree 8, isolated vertices dropped), 64 complex64 Gaussian states
+    drawn on the device by the seeded recipe (the inputs the parity test
+    checks), Grover coin, 500 steps, one SpMM-shaped launch per step."""
+    import torch
+    n, eu, ev = er_graph()
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    A2, B, steps = G.num_arcs, 64, 500
+    psi0 = synth.gaussian_states_device(A2, B, seed=4, dtype=torch.complex64)
+    out = torch.empty_like(psi0)
+    norm = torch.empty(B, dtype=torch.float64, device="cuda")
+    prob = torch.empty(n * B, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, 2, psi0, out)   # autotunes the launch shape once
+    for _ in range(max(1, warmup)):
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, steps, psi0, out)
+    torch.cuda.synchronize()
+    tot = ev_t = 0.0
+    with Clocks(torch.cuda.current_device()) as clk:
+        for _ in range(reps):
+            flush.zero_()
             e = _events(3)
             e[0].record(stream)
-            hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+            hw.hw_coined_evolve(G, 0, [], hw.HW_C64, B, steps, psi0, out)
             e[1].record(stream)
-            hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec, opts=sym)
+            hw.hw_probability(G, n, hw.HW_C64, B, out, prob, norm)
             e[2].record(stream)
             torch.cuda.synchronize()
-            t_exp += e[0].elapsed_time(e[1]) / 1e3
-            t_ev += e[1].elapsed_time(e[2]) / 1e3
-        t_exp /= args.steps
-        t_ev /= args.steps
-        deg, sq = hw.hw_ctqw_plan(G, 1 / 12, [m], 0.1)
-        gemm_flop = (deg - 1) * 2.0 * n ** 3
-        apply_bytes = n * n * (16 if dt == hw.HW_C128 else 8)   # the dense-U figure (the symmetric path reads half)
-        res[name] = {"expm_ms": t_exp * 1e3, "evolve_ms": t_ev * 1e3, "taylor_degree": deg, "squarings": sq,
-                     "gemm_tflops_useful": gemm_flop / t_exp / 1e12,
-                     "apply_us": t_ev / 2000 * 1e6, "apply_gbs": apply_bytes / (t_ev / 2000) / 1e9,
-                     "apply_frac_hbm": apply_bytes / (t_ev / 2000) / 1e9 / peak,
-                     "p_m_max": float(rec.max().item())}
-        if dt == hw.HW_C128:
-            # dense complex128 application: three real FMAs per element (the 3M
-            # form), bound by the FP64 pipe
-            fmas = 3.0 * n * n
-            res[name]["apply_fp64_fma_per_s"] = fmas / (t_ev / 2000)
-            res[name]["apply_fp64_frac"] = fmas / (t_ev / 2000) / fp64
-            res[name]["fp64_peak_fma_per_s"] = fp64
-            # Taylor powers: FP64 GEMM tiles of 64 x 64 on and above the diagonal
-            # only (the powers of the real symmetric Y are symmetric)
-            nb = (n + 63) // 64
-            expm_fmas = (deg - 1) * (nb * (nb + 1) // 2) * 64 * 64 * n
-            res[name]["expm_fp64_fma_per_s"] = expm_fmas / t_exp
-            res[name]["expm_fp64_frac"] = expm_fmas / t_exp / fp64
-    res["peak_hbm"] = peak
-    print(json.dumps(res), flush=True)
+            tot += e[0].elapsed_time(e[2]) / 1e3
+            ev_t += e[0].elapsed_time(e[1]) / 1e3
+    peak, src = measured_peaks()
+    per_launch = ev_t / (reps * steps)
+    bytes_launch = A2 * (2 * B * 8 + 4) + 4 * (n + 1)
+    nm = norm.cpu().numpy()
+    res = {"workload": "er_batched", "metric": METRIC, "unit": UNIT,
+           "value": A2 * B * steps * reps / tot, "ms_per_run": 1e3 * tot / reps, "ms_per_walk_step": per_launch * 1e3,
+           "n": n, "arcs": A2, "batch": B, "walk_steps": steps, "reps": reps, "dtype": "f32 (fp64 sums)",
+           "input": "synth.gaussian_states_device(seed 4), complex64",
+           "roofline": {"bound": "hbm", "achieved": bytes_launch / per_launch / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": bytes_launch / per_launch / 1e9 / peak,
+                        "bytes_per_launch": bytes_launch, "launch_us": per_launch * 1e6, "peak_source": src},
+           "norm_minmax": [float(nm.min()), float(nm.max())], "clocks": clk.summary()}
+    del flush
+    # the same run in complex128 (pinned to the oracle at 1e-12 by the tests)
+    # as the reference for the complex64 result's error
+    x128 = psi0.to(torch.complex128)
+    y128 = torch.empty_like(x128)
+    hw.hw_coined_evolve(G, 0, [], hw.HW_C128, B, steps, x128, y128)
+    p128 = torch.empty(n * B, dtype=torch.float64, device="cuda")
+    hw.hw_probability(G, n, hw.HW_C128, B, y128, p128)
+    torch.cuda.synchronize()
+    dp = (prob - p128).view(n, B).abs().sum(dim=0)
+    res["c64_vs_c128"] = {"p_L1_max_over_columns": float(dp.max().item()),
+                          "psi_max_abs": float((out.to(torch.complex128) - y128).abs().max().item())}
+    del x128, y128, p128
+    if with_cpu:
+        import oracle
+        ar = oracle.Arcs(n, eu, ev)
+        start = psi0[:, 0].cpu().numpy().astype(np.complex128)
+        t0 = time.perf_counter()
+        ref = oracle.coined_evolve(ar, start, steps)
+        el = time.perf_counter() - t0
+        got = out[:, 0].cpu().numpy().astype(np.complex128)
+        res["cpu_baseline"] = {"value": A2 * steps / el, "unit": UNIT, "cores": _oracle_cores(), "kind": "oracle",
+                               "sample": "batch column 0, all 500 steps (one of the 64 columns)"}
+        res["error_vs_oracle"] = {
+            "column": 0, "c64_max_abs_psi": float(np.max(np.abs(got - ref))),
+            "c64_p_L1": float(np.sum(np.abs(prob.view(n, B)[:, 0].cpu().numpy() - oracle.prob_coined(ar, ref))))}
+    G.free()
+    return res
 
 
 def run_workload_weighted(args):
@@ -546,34 +707,6 @@ def run_workload_weighted(args):
             res["q20_sparse_%s_%s" % ("complex" if cplx else "real", "c128" if dt == hw.HW_C128 else "c64")] = r
         G.free()
     print(json.dumps(res), flush=True)
-
-
-def run_workload_torus64(args):
-    """64 x 64 torus, Grover, no mark, start on the 4 arcs of (32, 32), 100 steps, complex128."""
-    import torch
-    import paper_2406_08186_b300 as hw
-    n, eu, ev = synth.torus(64)
-    row_ptr, col = synth.adjacency_csr(n, eu, ev)
-    G = hw.hw_graph_csr(n, row_ptr, col)
-    psi0 = torch.from_numpy(synth.state_on_vertex_arcs(synth.arc_offsets(n, eu, ev), 32 * 64 + 32)).cuda()
-    out = torch.empty_like(psi0)
-    prob = torch.empty(n, dtype=torch.float64, device="cuda")
-    stream = torch.cuda.current_stream()
-    for _ in range(max(3, args.warmup)):
-        hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
-        hw.hw_probability(G, n, hw.HW_C128, 1, out, prob)
-    torch.cuda.synchronize()
-    e = _events(2)
-    e[0].record(stream)
-    for _ in range(args.steps):
-        hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
-        hw.hw_probability(G, n, hw.HW_C128, 1, out, prob)
-    e[1].record(stream)
-    torch.cuda.synchronize()
-    t = e[0].elapsed_time(e[1]) / 1e3 / args.steps
-    print(json.dumps({"workload": "torus64_center", "metric": METRIC, "unit": UNIT,
-                      "value": G.num_arcs * 100 / t, "us_per_run": t * 1e6, "us_per_walk_step": t / 100 * 1e6}),
-          flush=True)
 
 
 def run_workload_sampled(args):
@@ -695,46 +828,70 @@ def serving_jobs(count, seed=6):
     return jobs
 
 
-class GraphMenu:
-    """Resident graphs of the serving mix, built on first use (outside the timed region)."""
+def menu_graph(fam, k):
+    """(n, row_ptr, col, degree) of one graph of the serving mix (host only)."""
+    if fam == "torus":
+        L = int(round(math.sqrt(1 << k)))
+        n, eu, ev = synth.torus(L)
+        d = 4
+    elif fam == "hypercube":
+        n, eu, ev = synth.hypercube(k)
+        d = k
+    else:
+        d = int(fam[3:])
+        n, eu, ev = synth.random_regular(1 << k, d, seed=100 + k * 10 + d)
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    return n, row_ptr, col, d
 
-    def __init__(self, hw):
+
+def _menu_graph_star(key):
+    return key, menu_graph(*key)
+
+
+class GraphMenu:
+    """Resident graphs of the serving mix, generated on the host cores by a
+    process pool (spawned, so no worker inherits a CUDA context) and uploaded
+    before any timing."""
+
+    def __init__(self, hw, keys):
+        import concurrent.futures
+        import multiprocessing
         self.hw = hw
         self.g = {}
+        keys = sorted(set(keys), key=lambda fk: -fk[1])       # largest first
+        workers = max(1, min(16, os.cpu_count() or 1, len(keys)))
+        ctx = multiprocessing.get_context("spawn")
+        with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as pool:
+            for key, (n, row_ptr, col, d) in pool.map(_menu_graph_star, keys):
+                self.g[key] = (hw.hw_graph_csr(n, row_ptr, col), d)
 
     def get(self, fam, k):
-        key = (fam, k)
-        if key not in self.g:
-            if fam == "torus":
-                L = int(round(math.sqrt(1 << k)))
-                n, eu, ev = synth.torus(L)
-                d = 4
-            elif fam == "hypercube":
-                n, eu, ev = synth.hypercube(k)
-                d = k
-            else:
-                d = int(fam[3:])
-                n, eu, ev = synth.random_regular(1 << k, d, seed=100 + k * 10 + d)
-            row_ptr, col = synth.adjacency_csr(n, eu, ev)
-            self.g[key] = (self.hw.hw_graph_csr(n, row_ptr, col), d)
-        return self.g[key]
+        return self.g[(fam, k)]
+
+    def free(self):
+        for G, _ in self.g.values():
+            G.free()
 
 
-def run_workload_serving(args):
-    """Served mix of walk jobs (continuous batching) vs the plain one-job-at-a-time
-    complex128 path: walks/s, p50/p99 latency."""
+def sub_serving(hw, count, substeps=16, arena_gb=64.0, baseline_jobs=None):
+    """Configuration 5: a stream of `count` walk jobs (the serving mix of seed 6)
+    served by continuous batching, saturated (all jobs at t = 0) and with Poisson
+    arrivals at 0.8 x the saturated rate: walks/s and p50/p99 latency (arrival to
+    result on the host), against the plain one-job-at-a-time complex128 path on
+    the same jobs (the first `baseline_jobs` of them when given); each served
+    result's error against that complex128 result."""
     import torch
-    import paper_2406_08186_b300 as hw
-    jobs = serving_jobs(args.jobs)
-    menu = GraphMenu(hw)
-    for j in jobs:                                    # build every graph before timing
+    jobs = serving_jobs(count)
+    menu = GraphMenu(hw, [(j["fam"], j["k"]) for j in jobs])
+    for j in jobs:
         G, d = menu.get(j["fam"], j["k"])
         j["G"], j["d"] = G, d
         j["marked"] = sorted({synth.seeded_vertex(j["mark_seed"] + r, G.n) for r in range(j["n_marked"])})
-    arena = int(args.arena_gb * (1 << 30))
+    arena = int(arena_gb * (1 << 30))
+    kept = {}
 
-    def serve(arrivals):
-        srv = hw.Server(arena, max_jobs=512, substeps=args.substeps, host_bytes=4 << 30)
+    def serve(arrivals, keep):
+        srv = hw.Server(arena, max_jobs=512, substeps=substeps, host_bytes=4 << 30)
         t0 = time.perf_counter()
         pending = sorted(range(len(jobs)), key=lambda i: arrivals[i])
         nxt = 0
@@ -751,7 +908,9 @@ def run_workload_serving(args):
             for jid in srv.poll():
                 i = idmap.pop(jid)
                 lat.append(time.perf_counter() - t0 - arrivals[i])
-                srv.result(jid)
+                prob, rec, _ = srv.result(jid)
+                if keep:
+                    kept[i] = (prob, rec)
             if nxt < len(pending) and not idmap:
                 time.sleep(max(0.0, min(0.001, arrivals[pending[nxt]] - (time.perf_counter() - t0))))
         el = time.perf_counter() - t0
@@ -760,19 +919,23 @@ def run_workload_serving(args):
         return {"walks_per_s": len(jobs) / el, "makespan_s": el, "p50_s": float(np.percentile(lat, 50)),
                 "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean())}
 
-    # saturated: every job arrives at t = 0
-    sat = serve([0.0] * len(jobs))
-    # Poisson arrivals at 0.8 x the saturated rate
-    lam = 0.8 * sat["walks_per_s"]
-    gaps = -np.log1p(-synth.uniform01(61, len(jobs))) / lam
-    poisson = serve(list(np.cumsum(gaps)))
+    with Clocks(torch.cuda.current_device()) as clk:
+        sat = serve([0.0] * len(jobs), True)
+        lam = 0.8 * sat["walks_per_s"]
+        gaps = -np.log1p(-synth.uniform01(61, len(jobs))) / lam
+        poisson = serve(list(np.cumsum(gaps)), False)
+    clocks = clk.summary()
 
-    # plain one-job-at-a-time complex128 path (a bounded prefix of the same jobs)
-    base_jobs = jobs[:min(len(jobs), args.baseline_jobs)]
+    # plain one-job-at-a-time complex128 path on the same jobs, each result
+    # copied back like a served one; the served results are compared with it
+    base_jobs = list(range(len(jobs) if baseline_jobs is None else min(len(jobs), baseline_jobs)))
+    err = {"c128_max_abs_p": 0.0, "c64_max_L1_p": 0.0, "record_max_abs": 0.0}
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for j in base_jobs:
+    t_plain = 0.0
+    for i in base_jobs:
+        j = jobs[i]
         G = j["G"]
+        t0 = time.perf_counter()
         dim = G.num_arcs if j["kind"] == 0 else G.n
         x = torch.full((dim,), 1.0 / math.sqrt(dim), dtype=torch.complex128, device="cuda")
         y = torch.empty_like(x)
@@ -783,15 +946,31 @@ def run_workload_serving(args):
             hw.hw_ctqw_evolve_sparse(G, 1.0 / j["d"], j["marked"], 0.1, hw.HW_C128, 1, j["steps"], x, y, rec)
         prob = torch.empty(G.n, dtype=torch.float64, device="cuda")
         hw.hw_probability(G if j["kind"] == 0 else None, G.n, hw.HW_C128, 1, y, prob)
-        prob.cpu()
-        if rec is not None:
-            rec.cpu()
-    base_rate = len(base_jobs) / (time.perf_counter() - t0)
-    print(json.dumps({"workload": "serving", "jobs": len(jobs), "metric": "walks/s", "unit": "walks/s",
-                      "saturated": sat, "poisson_0.8": poisson, "lambda_per_s": lam,
-                      "plain_c128_one_at_a_time": {"walks_per_s": base_rate, "jobs_timed": len(base_jobs)},
-                      "speedup_vs_plain": poisson["walks_per_s"] / base_rate,
-                      "substeps_per_round": args.substeps, "arena_gb": args.arena_gb}), flush=True)
+        p_h = prob.cpu().numpy()
+        r_h = rec.cpu().numpy() if rec is not None else None
+        t_plain += time.perf_counter() - t0
+        sp, sr = kept[i]
+        if j["dt"] == hw.HW_C128:
+            err["c128_max_abs_p"] = max(err["c128_max_abs_p"], float(np.max(np.abs(sp - p_h))))
+        else:
+            err["c64_max_L1_p"] = max(err["c64_max_L1_p"], float(np.sum(np.abs(sp - p_h))))
+        if r_h is not None:
+            err["record_max_abs"] = max(err["record_max_abs"], float(np.max(np.abs(sr - r_h))))
+    base_rate = len(base_jobs) / t_plain
+    menu.free()
+    return {"workload": "serving", "jobs": len(jobs), "metric": "walks/s", "unit": "walks/s",
+            "saturated": sat, "poisson_0.8": poisson, "lambda_per_s": lam,
+            "plain_c128_one_at_a_time": {"walks_per_s": base_rate, "jobs_timed": len(base_jobs),
+                                         "same_jobs": len(base_jobs) == len(jobs), "seconds": t_plain},
+            "speedup_saturated_vs_plain": sat["walks_per_s"] / base_rate,
+            "speedup_poisson_vs_plain": poisson["walks_per_s"] / base_rate,
+            "served_vs_plain_c128_error": err,
+            "substeps_per_round": substeps, "arena_gb": arena_gb, "clocks": clocks}
+
+
+def run_workload_serving(args):
+    import paper_2406_08186_b300 as hw  # noqa: F401
+    print(json.dumps(sub_serving(hw, args.jobs, args.substeps, args.arena_gb, args.baseline_jobs)), flush=True)
 
 
 def run_profile(args):
@@ -885,18 +1064,23 @@ def main():
                              "serving", "sampled", "sparse_ctqw", "weighted_ctqw"],
                     help="the default is the benchmarked workload; the others print their own line")
     ap.add_argument("--jobs", type=int, default=10000, help="serving: number of jobs")
-    ap.add_argument("--baseline-jobs", type=int, default=200, help="serving: jobs timed on the plain path")
+    ap.add_argument("--baseline-jobs", type=int, default=None,
+                    help="serving: jobs timed on the plain path (default: all of them)")
+    ap.add_argument("--serving-jobs", type=int, default=1000,
+                    help="default line: jobs of the serving stream in its serving record")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default line without the records of configurations 1, 3, 4 and 5")
     ap.add_argument("--substeps", type=int, default=16, help="serving: sub-steps per round")
     ap.add_argument("--arena-gb", type=float, default=64.0, help="serving: device arena")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
-    elif args.workload == "er_batched":
-        run_workload_batched(args)
-    elif args.workload == "hypercube12_ctqw":
-        run_workload_ctqw(args)
-    elif args.workload == "torus64_center":
-        run_workload_torus64(args)
+    elif args.workload in ("er_batched", "hypercube12_ctqw", "torus64_center"):
+        import paper_2406_08186_b300 as hw
+        fn = {"er_batched": sub_er_batched, "hypercube12_ctqw": sub_ctqw_q12,
+              "torus64_center": sub_torus64}[args.workload]
+        print(json.dumps(fn(hw, reps=args.steps, warmup=args.warmup, with_cpu=not args.no_cpu_baseline)),
+              flush=True)
     elif args.workload == "sampled":
         run_workload_sampled(args)
     elif args.workload == "sparse_ctqw":

@@ -309,7 +309,7 @@ hw_status hw_ctqw_sample(const void *U, int64_t n, hw_dtype dt, int32_t batch, i
  *   prob        DEVICE double[R][n][batch] (may be NULL when R = 0)
  *   R, n, batch samples (>= 0), vertices (>= 1), states per sample (>= 1)
  *   marked      HOST int32[n_marked], n_marked >= 1, ids in [0, n), no repeats
- *   curve_out   DEVICE double[R][batch], must not overlap prob
+ *   curve_out   DEVICE double[R][batch], must not overlap prob (may be NULL when R = 0)
  *   argmax_out  DEVICE int64[batch] or NULL;  max_out DEVICE double[batch] or NULL
  * Buffers are caller-owned and 8-byte aligned.  Up to 16 marked ids travel
  * with the launch; longer lists are uploaded to stream-ordered scratch, which

@@ -13,33 +13,37 @@
 // unweighted graph, scaled by 1 / (gamma tau), has entries 0, 1 and 1/gamma),
 // B keeps one slice and the products with its lower slices are dropped.
 //
-// Work is cut into 128 x 256 CTA tiles, grouped 2 x 2 into thread-block
-// clusters (256 x 512 cluster tiles).  The two CTAs of a cluster row share
-// their A rows and the two of a cluster column share their B rows: each CTA
-// loads half of its A tile and half of its B tile with TMA and multicasts it
-// to the CTA that shares it, so every operand byte leaves L2 once per
-// cluster, not once per CTA.  Persistent clusters walk a list of cluster
-// tiles.  Per CTA, 6 warps: warp 4 lane 0 streams K blocks (32 elements = one
-// 64-byte swizzle row) of every slice into a shared-memory ring (3 to 8
-// stages, 216 KiB); warp 5 lane 0 issues the MMAs (M = 128, N = 256) into one
-// of two 256-column TMEM accumulators and releases each stage with a
-// tcgen05.commit that arrives on the stage's "empty" barrier in all three
-// CTAs that write into it; warps 0-3 drain the other accumulator (tcgen05.ld,
-// warp w owns TMEM lanes 32w..32w+31 = tile rows) and run the epilogue of the
-// previous tile:
+// Work is cut into 128 x 256 CTA tiles, paired along M into 2-CTA
+// thread-block clusters (256 x 256 cluster tiles): the two CTAs of a pair
+// compute rows 0-127 and 128-255 of the same 256 columns, so each loads its
+// own A rows and half of the shared B rows with TMA and multicasts that half
+// to both CTAs; every B byte leaves L2 once per pair.  Persistent clusters
+// walk a list of cluster tiles.  Per CTA, 14 warps (448 threads): warp 4
+// lane 0 streams K blocks (32 elements = one 64-byte swizzle row) of every
+// slice into a shared-memory ring (up to 8 stages, 216 KiB); warp 5 lane 0
+// issues the MMAs (M = 128, N = 256) into one of two 256-column TMEM
+// accumulators and releases each stage with a tcgen05.commit that arrives on
+// the stage's "empty" barrier in both CTAs that write into it; warps 0-3 and
+// 6-9 drain the other accumulator (tcgen05.ld, warp w owns TMEM lanes of
+// quadrant w % 4 = tile rows, warps 0-3 and 6-9 one half of the columns each)
+// and run the epilogue of the previous tile:
 //   EPI_STORE:  C = scale * acc (fp32)
 //   EPI_TAYLOR: Q = scale * acc, written back as slices of qscale * Q (the
-//               next power's A operand); k_taylor_acc then adds Q to the lower
-//               triangle of Re/Im U in double on a second stream, overlapped
-//               with the next power's GEMM (the caller mirrors the sum).
+//               next power's A operand).
+// The double-precision Taylor sum of the previous power (U += coef Q, lower
+// triangle; the caller mirrors it) runs inside the next power's GEMM: warps
+// 0-3 and 6-13 do it while the tensor cores work on the first tile (the
+// previous power's slices are this GEMM's A operand, so they are mostly L2
+// hits); the last power's term is added by k_finish_c64 while it packs the
+// complex64 U, or by k_taylor_acc (tc_power_end).
 // For a symmetric product (every Taylor power of the symmetric Y is
 // symmetric) only cluster tiles that reach the upper triangle run, 128 x 128
 // blocks below the diagonal are not written, and each off-diagonal block is
 // also written to its mirror position with coalesced transposed stores.
 // Every wait on an mbarrier is bounded; a timeout sets an error flag that the
 // host reads, and the CTA still frees its tensor memory.  Before a CTA exits,
-// its producer waits until every stage it filled has been released by all
-// three consumers, so no peer signals a CTA that has left.
+// its producer waits until every stage it filled has been released by both
+// consumers, so no peer signals a CTA that has left.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>

@@ -239,7 +239,7 @@ extern "C" hw_status hw_success_curve(const double *prob, int64_t R, int64_t n, 
     if (n < 1) return hw_fail(HW_EINVAL, "n must be >= 1");
     if (batch < 1) return hw_fail(HW_EINVAL, "batch must be >= 1");
     if (n_marked < 1 || !marked) return hw_fail(HW_EINVAL, "the success curve needs at least one marked vertex");
-    if (!curve_out) return hw_fail(HW_EINVAL, "curve_out is NULL");
+    if (R > 0 && !curve_out) return hw_fail(HW_EINVAL, "curve_out is NULL");
     if (R > 0 && !prob) return hw_fail(HW_EINVAL, "prob is NULL");
     if (((uintptr_t)prob | (uintptr_t)curve_out | (uintptr_t)argmax_out | (uintptr_t)max_out) % 8)
         return hw_fail(HW_EINVAL, "buffers must be 8-byte aligned");

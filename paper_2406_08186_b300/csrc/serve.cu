@@ -15,14 +15,14 @@
 //
 // A continuous-time job whose three working vectors fit in one CTA's shared
 // memory (complex64 up to 8192 vertices, complex128 up to 4096) is "local":
-// a CTA of its own (k_serve_local, launched beside k_serve_step in every
-// sub-step of the graph) keeps the state and the series terms in shared
-// memory and advances the job by whole walk steps, with block barriers
-// between the Taylor terms instead of one launch per term.  It runs beside the
-// round's graph, on a second stream, L steps per round: L follows the
-// measured times of the two branches, so that the local jobs (which advance
-// whole steps) do not hold back the tiled CTQW jobs (which advance one term
-// per sub-step) and are not held back by a round of idle sub-steps either.
+// a CTA of its own keeps the state and the series terms in shared memory and
+// advances the job by whole walk steps, with block barriers between the
+// Taylor terms instead of one launch per term.  These CTAs (k_serve_local,
+// one launch per round) run on a second stream, beside the round's graph of
+// k_serve_step sub-steps, L walk steps per round: L follows the measured
+// times of the two branches, so that the local jobs (which advance whole
+// steps) do not hold back the tiled CTQW jobs (which advance one term per
+// sub-step) and are not held back by a round of idle sub-steps either.
 //
 // Each job's arithmetic depends only on its own data and a fixed per-vertex
 // order, so its result is the same alone and in any mix.
