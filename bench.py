@@ -457,11 +457,29 @@ def sub_torus64(hw, reps, warmup, with_cpu):
     return res
 
 
+def sparse_power_figures(n, deg_graph, m_deg, esz, n_marked):
+    """Algorithmic bytes and FP64 operations of the sparse Taylor powers of one
+    expm (m_deg powers Q_k = Y Q_{k-1} / k of an n x n dense Q, Y with deg_graph
+    neighbours per row): per power Q_{k-1} read once (its gathered rows are L2
+    hits), Q_k written, U's real or imaginary plane read and written in double.
+    complex128 FP64 operations per element: the neighbour groups of four are
+    summed by integer operations, their ceil(d/4) - 1 sums added in double, one
+    multiply, one add into U (plus one FMA on marked rows)."""
+    nn = n * n
+    bytes_power = 2 * nn * esz + 2 * nn * 8
+    fp64_power = nn * ((deg_graph + 3) // 4 - 1 + 2) + n_marked * n
+    return m_deg * bytes_power, m_deg * fp64_power
+
+
 def sub_ctqw_q12(hw, reps, warmup, with_cpu):
     """Configuration 3: CTQW search on Q_12, gamma = 1/12, one seeded mark,
     U = exp(-iH 0.1) dense (Taylor, scaling and squaring), 2000 applications,
-    complex128 and complex64 (tensor-core powers); each result's error against
-    the complex128 GPU result and, with the CPU leg, against the oracle."""
+    complex128 and complex64.  Both forms of the Taylor powers are timed: sparse
+    x dense products with the graph (the default for complex128) and dense
+    GEMMs (FP64 for complex128; tcgen05 tensor cores for complex64, its
+    default).  Each result's
+    error against the complex128 GPU result and, with the CPU leg, against the
+    oracle."""
     import torch
     g = synth.hypercube(12)
     n = 4096
@@ -476,73 +494,98 @@ def sub_ctqw_q12(hw, reps, warmup, with_cpu):
            "applications": 2000, "reps": reps}
     deg, sq = hw.hw_ctqw_plan(G, 1 / 12, [m], 0.1)
     kept = {}
+
+    def time_expm(dt, U, opts, count):
+        e = _events(2)
+        e[0].record(stream)
+        for _ in range(count):
+            hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U, opts=opts)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]) / 1e3 / count
+
     with Clocks(torch.cuda.current_device()) as clk:
         for dt, name in ((hw.HW_C128, "c128"), (hw.HW_C64, "c64")):
             cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+            esz = 8 if dt == hw.HW_C128 else 4
             U = torch.empty((n, n), dtype=cdt, device="cuda")
+            Ud = torch.empty_like(U)
+            Us = torch.empty_like(U)
             x = torch.full((n,), 1 / 64, dtype=cdt, device="cuda")
             y = torch.empty_like(x)
             rec = torch.empty(2000, dtype=torch.float64, device="cuda")
             prob = torch.empty(n, dtype=torch.float64, device="cuda")
             sym = {"u_symmetric": 1}   # U = e^{-iH dt} is complex symmetric
+            dense, sparse = {"taylor_powers": 1}, {"taylor_powers": 2}
             for _ in range(max(1, warmup)):
                 hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
+                hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, Ud, opts=dense)
+                hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, Us, opts=sparse)
                 hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec, opts=sym)
             torch.cuda.synchronize()
-            t_exp = t_ev = 0.0
+            t_exp = time_expm(dt, U, None, max(reps, 10))
+            t_dense = time_expm(dt, Ud, dense, reps if dt == hw.HW_C128 else max(reps, 10))
+            t_sparse = time_expm(dt, Us, sparse, max(reps, 10))
+            e = _events(2)
+            e[0].record(stream)
             for _ in range(reps):
-                e = _events(3)
-                e[0].record(stream)
-                hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U)
-                e[1].record(stream)
                 hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec, opts=sym)
-                e[2].record(stream)
-                torch.cuda.synchronize()
-                t_exp += e[0].elapsed_time(e[1]) / 1e3
-                t_ev += e[1].elapsed_time(e[2]) / 1e3
-            t_exp /= reps
-            t_ev /= reps
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            t_ev = e[0].elapsed_time(e[1]) / 1e3 / reps
             hw.hw_probability(None, n, dt, 1, y, prob)
             torch.cuda.synchronize()
-            kept[name] = (U, y, rec, prob)
+            kept[name] = (U, Ud, Us, y, rec, prob)
+            sp_bytes, sp_ops = sparse_power_figures(n, 12, deg, esz, 1)
             r = {"expm_ms": t_exp * 1e3, "evolve_ms": t_ev * 1e3, "apply_us": t_ev / 2000 * 1e6,
-                 "taylor_degree": deg, "squarings": sq, "p_m_max": float(rec.max().item())}
+                 "taylor_degree": deg, "squarings": sq, "p_m_max": float(rec.max().item()),
+                 "expm_default_form": "sparse x dense" if dt == hw.HW_C128 else "tensor-core GEMMs",
+                 "expm_sparse": {"ms": t_sparse * 1e3,
+                                 "roofline": {"bound": "hbm", "achieved": sp_bytes / t_sparse / 1e9, "peak": peak,
+                                              "unit": "GB/s", "frac": sp_bytes / t_sparse / 1e9 / peak,
+                                              "bytes_per_expm": sp_bytes, "peak_source": src,
+                                              "note": "whole expm (identity init, powers, pack) over the powers' "
+                                                      "compulsory bytes; the neighbour gathers are L2 reads"}},
+                 "expm_dense": {"ms": t_dense * 1e3}}
             if dt == hw.HW_C128:
-                # Taylor powers: FP64 GEMM tiles of 64 x 64 on and above the
-                # diagonal (the powers of the real symmetric Y are symmetric)
+                r["expm_sparse"]["roofline"]["fp64"] = {"achieved": sp_ops / t_sparse, "peak": fp64, "unit": "op/s",
+                                                        "frac": sp_ops / t_sparse / fp64, "ops_per_expm": sp_ops}
+                # dense form: FP64 GEMM tiles of 64 x 64 on and above the diagonal
+                # (the powers of the real symmetric Y are symmetric)
                 nb = (n + 63) // 64
                 fmas = (deg - 1) * (nb * (nb + 1) // 2) * 64 * 64 * n
-                r["expm_roofline"] = {"bound": "fp64", "achieved": fmas / t_exp, "peak": fp64,
-                                      "unit": "FMA/s", "frac": fmas / t_exp / fp64, "fma_per_expm": fmas,
-                                      "peak_source": "hw_measure_fp64 (register-blocked GEMM loop on this GPU)"}
+                r["expm_dense"]["roofline"] = {"bound": "fp64", "achieved": fmas / t_dense, "peak": fp64,
+                                               "unit": "FMA/s", "frac": fmas / t_dense / fp64, "fma_per_expm": fmas,
+                                               "peak_source": "hw_measure_fp64 (register-blocked GEMM loop on this GPU)"}
                 # application: three real FMAs per element (the 3M form)
                 afma = 3.0 * n * n
                 r["apply_roofline"] = {"bound": "fp64", "achieved": afma / (t_ev / 2000), "peak": fp64,
                                        "unit": "FMA/s", "frac": afma / (t_ev / 2000) / fp64, "fma_per_apply": afma}
             else:
-                # MMA work issued on the tensor cores per expm: (m - 1) powers, each
-                # over the CTA tiles (128 x 256 x n) of the cluster tiles on and
-                # above the diagonal, two fp16 products per tile (272 tiles at
-                # n = 4096), against the bf16/fp16 dense peak
+                # dense form on the tensor cores: (m - 1) powers, each over the CTA
+                # tiles (128 x 256 x n) of the cluster tiles on and above the
+                # diagonal, two fp16 products per tile (272 tiles at n = 4096)
                 cl = (n + 255) // 256          # 2-CTA cluster tiles of 256 x 256 on and above the diagonal
                 mma = (deg - 1) * (cl * (cl + 1)) * 128 * 256 * n * 2 * 2.0
-                dense = (deg - 1) * 2.0 * n ** 3
-                r["expm_roofline"] = {"bound": "tensor", "achieved": mma / t_exp / 1e12, "peak": tc_peak,
-                                      "unit": "TFLOP/s", "frac": mma / t_exp / 1e12 / tc_peak,
-                                      "flop_per_expm_issued": mma, "dense_equivalent_tflops": dense / t_exp / 1e12,
-                                      "peak_source": tc_src,
-                                      "note": "whole expm (slicing, Taylor sums, finish) over the MMA work"}
+                r["expm_dense"]["roofline"] = {"bound": "tensor", "achieved": mma / t_dense / 1e12, "peak": tc_peak,
+                                               "unit": "TFLOP/s", "frac": mma / t_dense / 1e12 / tc_peak,
+                                               "flop_per_expm_issued": mma,
+                                               "dense_equivalent_tflops": (deg - 1) * 2.0 * n ** 3 / t_dense / 1e12,
+                                               "peak_source": tc_src,
+                                               "note": "whole expm (slicing, Taylor sums, finish) over the MMA work"}
                 abytes = n * n // 2 * 8 + n * 8
                 r["apply_roofline"] = {"bound": "l2", "achieved": abytes / (t_ev / 2000) / 1e9, "unit": "GB/s",
                                        "bytes_per_apply": abytes,
                                        "note": "upper triangle of U (68 MB) streamed per application, L2-resident"}
             res[name] = r
     res["clocks"] = clk.summary()
-    U128, y128, rec128, p128 = kept["c128"]
-    U64, y64, rec64, p64 = kept["c64"]
+    U128, U128d, U128s, y128, rec128, p128 = kept["c128"]
+    U64, U64d, U64s, y64, rec64, p64 = kept["c64"]
     res["c64_vs_c128"] = {"U_max_abs": float((U64.to(torch.complex128) - U128).abs().max().item()),
+                          "U_sparse_max_abs": float((U64s.to(torch.complex128) - U128).abs().max().item()),
                           "p_L1": float((p64 - p128).abs().sum().item()),
                           "p_m_record_max_abs": float((rec64 - rec128).abs().max().item())}
+    res["c128_sparse_vs_dense_U_max_abs"] = float((U128s - U128d).abs().max().item())
     if with_cpu:
         import oracle
         ar = oracle.Arcs(*g)

@@ -88,7 +88,20 @@ typedef struct hw_opts {
                                   S|v,w> = |w,v> (default); 1 = persistent, S|v,w> = |w,u> with
                                   u - w = w - v, the walker keeping its direction (graphs that
                                   hw_graph_structure recognises as a torus only, else HW_EINVAL) */
-    int32_t reserved[2];
+    int32_t launch_mode;       /* hw_coined_evolve, batch 1, Grover, regular graph of degree 2..8:
+                                  0 = default: when the walk is small (up to 16384 arcs in
+                                  complex128, 24576 in complex64) every step runs in one
+                                  launch, the state held in the shared memory of one
+                                  thread-block cluster; 1 = one launch per step.  Both give
+                                  bit-identical results. */
+    int32_t taylor_powers;     /* hw_ctqw_expm: how the powers Y^k / k! of Y = H time / 2^s are
+                                  formed.  1 = dense n^3 products: FP64 GEMMs for HW_C128,
+                                  the tensor cores (opts->gemm_mode) for HW_C64; 2 = sparse x
+                                  dense products with the graph (row v of Y Q gathers the rows
+                                  of v's neighbours; Y has d << n entries per row), in double
+                                  for HW_C128 and in float for HW_C64; 0 = default: 2 for
+                                  HW_C128, 1 for HW_C64.  The Taylor sum is in double and the
+                                  squarings are dense FP64 GEMMs either way. */
 } hw_opts;
 
 /* Fill `opts` with the defaults. */

@@ -49,7 +49,7 @@ class hw_opts(ctypes.Structure):
                 ("taylor_squarings", ctypes.c_int32), ("gemm_mode", ctypes.c_int32),
                 ("u_symmetric", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("addressing", ctypes.c_int32), ("shift", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("launch_mode", ctypes.c_int32), ("taylor_powers", ctypes.c_int32)]
 
 
 class hw_job(ctypes.Structure):

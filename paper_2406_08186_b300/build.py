@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhiperwalk_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
-SOURCES = ["api.cpp", "graph.cpp", "coined.cu", "prob.cu", "ctqw.cu", "ctqw_sparse.cu", "gemm_tc.cu", "serve.cu", "measure.cu"]
+SOURCES = ["api.cpp", "graph.cpp", "coined.cu", "coined_cluster.cu", "prob.cu", "ctqw.cu", "ctqw_sparse.cu", "gemm_tc.cu", "serve.cu", "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3,-Wall",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -110,6 +110,8 @@ extern "C" void hw_opts_init(hw_opts *o)
     o->u_symmetric = 0;
     o->addressing = 0;
     o->shift = 0;
+    o->launch_mode = 0;
+    o->taylor_powers = 0;
 }
 
 hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaStream_t st,
@@ -206,6 +208,8 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
     const int stride = opts ? opts->record_stride : 1;
     if (stride < 1) return hw_fail(HW_EINVAL, "record_stride must be >= 1");
     if (opts && (opts->tile < 0 || opts->tile > 14)) return hw_fail(HW_EINVAL, "tile must be 0..14");
+    const int launch_mode = opts ? opts->launch_mode : 0;
+    if (launch_mode != 0 && launch_mode != 1) return hw_fail(HW_EINVAL, "launch_mode must be 0 or 1");
     int shift = kShiftFlipFlop;
     bool index_free = false;
     if (hw_status so = coined_opts(g, opts, &shift, &index_free); so != HW_OK) return so;
@@ -261,6 +265,16 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
         }
     }
 
+    if (batch == 1 && launch_mode == 0 && coined_cluster_supported(g, coin, dt)) {
+        // small regular graph: every step in one launch, the state held in
+        // the shared memory of one thread-block cluster; the kernel records
+        // the marked probability after every stride-th step itself
+        if ((s = launch_coined_cluster(g, dt, psi_in, psi_out, steps, mk, rec_part, stride,
+                                       shift_table(g, shift), st)) != HW_OK)
+            return s;
+        if (slots && n_marked > 1) return launch_record_finalize(rec_part, n_marked, slots, batch, record, st);
+        return HW_OK;
+    }
     if (batch == 1 && coined_em_supported(g, coin, dt)) {
         // regular graph: the steps run in the edge-major layout between two
         // scratch buffers; the state is transposed in and out once

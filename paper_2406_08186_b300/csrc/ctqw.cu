@@ -23,6 +23,7 @@
 
 #include "fpconv.cuh"
 #include "internal.h"
+#include "sum4.cuh"
 
 namespace {
 
@@ -208,6 +209,208 @@ __global__ void k_pack_u(int64_t total, const double *__restrict__ re, const dou
         V u;
         pack1(u, re[e], im[e]);
         U[e] = u;
+    }
+}
+
+// ------------------------------------------------------------ sparse Taylor powers
+// Q_k = Y Q_{k-1} / k with Y = tau H: row v of Q_k combines the rows of v's
+// neighbours w (weight -gamma tau W_vw) and, for a marked v, its own row
+// (weight -tau).  Y has d << n entries per row, so this is a sparse x dense
+// product: it runs as a gather of rows, not as an n^3 GEMM.  A thread owns one
+// column c of a CTA's kSpRows rows, reads Q_{k-1}[w][c] for each neighbour
+// (coalesced over the CTA's 256 columns), writes Q_k[v][c] and adds
+// sign Q_k[v][c] to U's real or imaginary plane in double.  Blocks run row
+// block by row block inside one 256-column slab before the next slab, so the
+// rows gathered by the CTAs in flight (a slab is n x 256 values) stay in L2.
+// complex128: Q in double, an unweighted row's neighbour sum in groups of
+// four rounded once (sum4.cuh), then one multiply by -gamma tau / k; weighted
+// rows take one FMA per neighbour.  complex64: Q in float, the sums and
+// products in float, the accumulation into U in double.
+constexpr int kSpRows = 8;       // rows per CTA
+constexpr int kSpCols = 256;     // columns per CTA, one per thread
+constexpr int kSpGather = 16;    // neighbour values held in registers at once
+
+struct SparsePow {
+    const int32_t *row_ptr, *head;
+    const double *w;             // arc weights (weighted W) or nullptr
+    const float *wf;             // the same in float
+    int n;
+    double off, diag;            // -gamma tau / k, -tau / k
+    float offf, diagf;
+    MarkedList mk;
+    const void *Qp;              // Q_{k-1}, n x n
+    void *Qn;                    // Q_k
+    double *acc;                 // Re U or Im U, n x n
+    int neg;                     // acc -= Q_k instead of +=
+};
+
+__device__ __forceinline__ double sp_weight(const SparsePow &a, int e, double) { return __ldg(a.w + e); }
+__device__ __forceinline__ float sp_weight(const SparsePow &a, int e, float) { return __ldg(a.wf + e); }
+__device__ __forceinline__ double sp_off(const SparsePow &a, double) { return a.off; }
+__device__ __forceinline__ float sp_off(const SparsePow &a, float) { return a.offf; }
+__device__ __forceinline__ double sp_diag(const SparsePow &a, double) { return a.diag; }
+__device__ __forceinline__ float sp_diag(const SparsePow &a, float) { return a.diagf; }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return fpconv::f32_to_f64(x); }
+
+// VEC adjacent columns per thread, moved as one vector (16 bytes)
+template <typename T, int VEC> struct SpVec;
+template <> struct SpVec<double, 2> { using V = double2; };
+template <> struct SpVec<float, 4> { using V = float4; };
+template <> struct SpVec<double, 1> { using V = double; };
+template <> struct SpVec<float, 1> { using V = float; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ void sp_load(T (&x)[VEC], const T *p)
+{
+    const typename SpVec<T, VEC>::V v = *reinterpret_cast<const typename SpVec<T, VEC>::V *>(p);
+    const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) x[k] = e[k];
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void sp_store(T *p, const T (&x)[VEC])
+{
+    typename SpVec<T, VEC>::V v;
+    T *e = reinterpret_cast<T *>(&v);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) e[k] = x[k];
+    *reinterpret_cast<typename SpVec<T, VEC>::V *>(p) = v;
+}
+
+// neighbour sum of one column, terms x[0..deg) with deg <= kSpGather:
+// complex128 unweighted in grouped_sum1's groups of four and order, with
+// constant indices so that x stays in registers; otherwise sequential from 0
+template <typename T, bool WEIGHTED, int VEC>
+__device__ __forceinline__ T sp_sum(const SparsePow &a, int e0, int deg, const T (&x)[kSpGather][VEC], int k)
+{
+    T sum = 0;
+    if constexpr (WEIGHTED) {
+#pragma unroll
+        for (int j = 0; j < kSpGather; ++j)
+            if (j < deg) sum = fma(sp_weight(a, e0 + j, T(0)), x[j][k], sum);
+    } else if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int g0 = 0; g0 < kSpGather; g0 += 4) {
+            if (g0 < deg) {
+                const double q = sum4::sum4_rn(x[g0][k], g0 + 1 < deg ? x[g0 + 1][k] : -0.0,
+                                               g0 + 2 < deg ? x[g0 + 2][k] : -0.0, g0 + 3 < deg ? x[g0 + 3][k] : -0.0);
+                sum = (g0 == 0) ? q : sum + q;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kSpGather; ++j)
+            if (j < deg) sum += x[j][k];
+    }
+    return sum;
+}
+
+// the same sums for any degree, four neighbours at a time
+template <typename T, bool WEIGHTED, int VEC>
+__device__ __forceinline__ void sp_sum_long(const SparsePow &a, const T *Qp, int64_t n, int c0, int e0, int deg,
+                                            T (&sum)[VEC])
+{
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) sum[k] = 0;
+    for (int g0 = 0; g0 < deg; g0 += 4) {
+        T x[4][VEC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (g0 + u < deg) sp_load<T, VEC>(x[u], Qp + int64_t(__ldg(a.head + e0 + g0 + u)) * n + c0);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k)
+                if (g0 + u >= deg) x[u][k] = (sizeof(T) == 8 && !WEIGHTED) ? T(-0.0) : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            if constexpr (WEIGHTED) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (g0 + u < deg) sum[k] = fma(sp_weight(a, e0 + g0 + u, T(0)), x[u][k], sum[k]);
+            } else if constexpr (sizeof(T) == 8) {
+                const double q = sum4::sum4_rn(x[0][k], x[1][k], x[2][k], x[3][k]);
+                sum[k] = (g0 == 0) ? q : sum[k] + q;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (g0 + u < deg) sum[k] += x[u][k];
+            }
+        }
+    }
+}
+
+template <typename T, bool WEIGHTED, int VEC>
+__global__ void __launch_bounds__(kSpCols) k_taylor_sparse(SparsePow a)
+{
+    const int c0 = (int(blockIdx.y) * kSpCols + int(threadIdx.x)) * VEC;
+    if (c0 >= a.n) return;
+    const T *__restrict__ Qp = static_cast<const T *>(a.Qp);
+    T *__restrict__ Qn = static_cast<T *>(a.Qn);
+    const int64_t n = a.n;
+    const int v0 = int(blockIdx.x) * kSpRows;
+    const int v1 = min(a.n, v0 + kSpRows);
+    for (int v = v0; v < v1; ++v) {
+        const int64_t e = int64_t(v) * n + c0;
+        double u[VEC];   // U's plane, fetched before the gathers so its latency overlaps them
+#pragma unroll
+        for (int k = 0; k < VEC; k += (VEC > 1 ? 2 : 1)) {
+            if constexpr (VEC > 1) {
+                const double2 w2 = *reinterpret_cast<const double2 *>(a.acc + e + k);
+                u[k] = w2.x;
+                u[k + 1] = w2.y;
+            } else {
+                u[k] = a.acc[e + k];
+            }
+        }
+        const int e0 = __ldg(a.row_ptr + v), deg = __ldg(a.row_ptr + v + 1) - e0;
+        T sum[VEC];
+        if (deg <= kSpGather) {
+            T x[kSpGather][VEC];
+#pragma unroll
+            for (int j = 0; j < kSpGather; ++j)
+                if (j < deg) sp_load<T, VEC>(x[j], Qp + int64_t(__ldg(a.head + e0 + j)) * n + c0);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) sum[k] = sp_sum<T, WEIGHTED, VEC>(a, e0, deg, x, k);
+        } else {
+            sp_sum_long<T, WEIGHTED, VEC>(a, Qp, n, c0, e0, deg, sum);
+        }
+        T q[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) q[k] = sp_off(a, T(0)) * sum[k];
+        if (marked_find(a.mk, v) >= 0) {
+            T own[VEC];
+            sp_load<T, VEC>(own, Qp + e);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) q[k] = fma(sp_diag(a, T(0)), own[k], q[k]);
+        }
+        sp_store<T, VEC>(Qn + e, q);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            const double qd = to_f64(q[k]);
+            u[k] = a.neg ? u[k] - qd : u[k] + qd;
+        }
+#pragma unroll
+        for (int k = 0; k < VEC; k += (VEC > 1 ? 2 : 1)) {
+            if constexpr (VEC > 1) *reinterpret_cast<double2 *>(a.acc + e + k) = make_double2(u[k], u[k + 1]);
+            else a.acc[e + k] = u[k];
+        }
+    }
+}
+
+// Re U = I, Im U = 0, Q_0 = I
+template <typename T>
+__global__ void k_taylor_identity(int n, double *__restrict__ re, double *__restrict__ im, T *__restrict__ q0)
+{
+    const int64_t total = int64_t(n) * n;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        int64_t j;
+        const int64_t i = idx_div(e, n, j);
+        re[e] = (i == j) ? 1.0 : 0.0;
+        im[e] = 0.0;
+        q0[e] = (i == j) ? T(1) : T(0);
     }
 }
 
@@ -840,17 +1043,74 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     const int64_t nn = int64_t(n) * n;
     const size_t bytes = sizeof(double) * nn;
 
-    const bool use_tc = (dt == HW_C64) && tc_gemm_available();
-    DevBuf Y(st), Q(st), Qn(st), Re(st), Im(st);
+    const int powers = opts ? opts->taylor_powers : 0;
+    if (powers < 0 || powers > 2) return hw_fail(HW_EINVAL, "taylor_powers must be 0, 1 or 2");
+    // default: the measured faster form on the 4096-vertex hypercube search
+    // (complex128: sparse x dense 6.3 ms against 697 ms of FP64 GEMMs;
+    // complex64: tensor-core GEMMs 1.56 ms against 1.93 ms sparse x dense)
+    const bool sparse = powers == 2 || (powers == 0 && (dt == HW_C128 || !tc_gemm_available()));
+    const bool use_tc = !sparse && (dt == HW_C64) && tc_gemm_available();
+    DevBuf Y(st), Q(st), Qn(st), Re(st), Im(st), Qf(st), Qfn(st);
     if ((s = Re.get(bytes, "scratch allocation (ReU)")) != HW_OK || (s = Im.get(bytes, "scratch allocation (ImU)")) != HW_OK)
         return s;
-    if (!use_tc || sq > 0) {
-        // the FP64 powers and the squarings need two n x n work matrices, the FP64 powers also Y
+    if ((!use_tc && !(sparse && dt == HW_C64)) || sq > 0) {
+        // the FP64 powers (dense or sparse) and the squarings need two n x n
+        // double work matrices, the dense FP64 powers also Y
         if ((s = Q.get(bytes, "scratch allocation (Q)")) != HW_OK || (s = Qn.get(bytes, "scratch allocation (Q)")) != HW_OK)
             return s;
     }
     bool packed = false;
-    if (use_tc) {
+    if (sparse) {
+        // T2 + T3 as sparse x dense products: Q_0 = I, Q_k = Y Q_{k-1} / k for
+        // k = 1..m, each added to Re / Im U with the sign of (-i)^k
+        const bool c128 = dt == HW_C128;
+        if (!c128 && ((s = Qf.get(sizeof(float) * nn, "scratch allocation (Q)")) != HW_OK ||
+                      (s = Qfn.get(sizeof(float) * nn, "scratch allocation (Q)")) != HW_OK))
+            return s;
+        void *Qa = c128 ? Q.p : Qf.p, *Qb = c128 ? Qn.p : Qfn.p;
+        if (c128) k_taylor_identity<double><<<ew_grid(nn), 256, 0, st>>>(n, Re.as<double>(), Im.as<double>(), static_cast<double *>(Qa));
+        else k_taylor_identity<float><<<ew_grid(nn), 256, 0, st>>>(n, Re.as<double>(), Im.as<double>(), static_cast<float *>(Qa));
+        if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;
+        // 16-byte column vectors when every row starts on a vector boundary
+        const int vec = c128 ? (n % 2 == 0 ? 2 : 1) : (n % 4 == 0 ? 4 : 1);
+        const dim3 grid((n + kSpRows - 1) / kSpRows, (n + kSpCols * vec - 1) / (kSpCols * vec));
+        for (int k = 1; k <= m_deg; ++k) {
+            SparsePow a;
+            a.row_ptr = g->d_row_ptr;
+            a.head = g->d_head;
+            a.w = g->weighted ? g->d_wre : nullptr;
+            a.wf = g->weighted ? g->d_wre_f : nullptr;
+            a.n = n;
+            a.off = -gamma * tau / double(k);
+            a.diag = -tau / double(k);
+            a.offf = float(a.off);
+            a.diagf = float(a.diag);
+            a.mk = mk;
+            a.Qp = Qa;
+            a.Qn = Qb;
+            a.acc = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
+            a.neg = (k % 4 == 0 || k % 4 == 3) ? 0 : 1;
+            if (c128) {
+                if (vec == 2) {
+                    if (g->weighted) k_taylor_sparse<double, true, 2><<<grid, kSpCols, 0, st>>>(a);
+                    else k_taylor_sparse<double, false, 2><<<grid, kSpCols, 0, st>>>(a);
+                } else {
+                    if (g->weighted) k_taylor_sparse<double, true, 1><<<grid, kSpCols, 0, st>>>(a);
+                    else k_taylor_sparse<double, false, 1><<<grid, kSpCols, 0, st>>>(a);
+                }
+            } else {
+                if (vec == 4) {
+                    if (g->weighted) k_taylor_sparse<float, true, 4><<<grid, kSpCols, 0, st>>>(a);
+                    else k_taylor_sparse<float, false, 4><<<grid, kSpCols, 0, st>>>(a);
+                } else {
+                    if (g->weighted) k_taylor_sparse<float, true, 1><<<grid, kSpCols, 0, st>>>(a);
+                    else k_taylor_sparse<float, false, 1><<<grid, kSpCols, 0, st>>>(a);
+                }
+            }
+            if ((s = hw_cuda(cudaGetLastError(), "k_taylor_sparse launch")) != HW_OK) return s;
+            std::swap(Qa, Qb);
+        }
+    } else if (use_tc) {
         // complex64 path: powers on the tensor cores from 16-bit slices; the
         // series is summed below the diagonal only.
         // T1 + the k = 0, 1 terms: Re U = I, Im U = -Y = gamma tau A + tau sum_m |m><m|

@@ -149,6 +149,11 @@ hw_status launch_coined_step(const hw_graph *g, hw_dtype dt, hw_coin coin, const
                              cudaStream_t st);
 hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coin, int batch,
                                      const CoinedStep &s, int tile, cudaStream_t st);
+// whole walks of small regular graphs in one thread-block cluster (coined_cluster.cu)
+bool coined_cluster_supported(const hw_graph *g, hw_coin coin, hw_dtype dt);
+hw_status launch_coined_cluster(const hw_graph *g, hw_dtype dt, const void *in, void *out, int64_t steps,
+                                const MarkedList &mk, double *rec_part, int64_t stride, const int32_t *shift,
+                                cudaStream_t st);
 hw_status launch_marked_prob(const int32_t *row_ptr, hw_dtype dt, int batch, const void *psi,
                              const MarkedList &marked, double *dst, cudaStream_t st);
 hw_status launch_record_finalize(const double *rec_part, int32_t n_marked, int64_t slots,

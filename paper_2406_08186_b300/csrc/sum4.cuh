@@ -210,6 +210,23 @@ HW_HD void grouped_sum2(int count, F t, double &sx, double &sy)
     }
 }
 
+// the real-valued grouped_sum2: sum of t(0) .. t(count-1) (count >= 1) by
+// groups of four rounded once (sum4_rn, a short last group padded with -0),
+// the group sums added in order in double
+template <typename F>
+HW_HD double grouped_sum1(int count, F t)
+{
+    double s = 0.0;
+    for (int j0 = 0; j0 < count; j0 += 4) {
+        double x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = (j0 + u < count) ? double(t(j0 + u)) : -0.0;
+        const double g = sum4_rn(x[0], x[1], x[2], x[3]);
+        s = (j0 == 0) ? g : s + g;
+    }
+    return s;
+}
+
 // grouped_sum2 over K terms already held in an array (K known at compile
 // time): the same groups, padding and order of additions, so both give the
 // same bits

@@ -1,0 +1,103 @@
+"""Whole coined walks of small regular graphs in one launch (one thread-block
+cluster holding the state in distributed shared memory, Sec. 3.2): against the
+FP64 oracle (complex128 1e-12), bit-identical to the one-launch-per-step path
+(hw_opts.launch_mode = 1), with marks, a strided record, in place, the
+persistent shift, ragged vertex ranges, fewer vertices than CTAs, degrees 2..8
+and the largest size the path takes."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("torus64", synth.torus(64)),                       # configuration 1's graph
+    ("torus7x9", synth.torus_rect(7, 9)),               # 63 vertices: ragged CTA ranges
+    ("cycle5", synth.cycle(5)),                         # degree 2, fewer vertices than CTAs
+    ("Q7", synth.hypercube(7)),                         # degree 7
+    ("reg3", synth.random_regular(1002, 3, seed=4)),
+    ("reg5", synth.random_regular(600, 5, seed=8)),
+    ("reg8", synth.random_regular(2048, 8, seed=6)),    # 16384 arcs: the complex128 size limit
+    ("torus64x96", synth.torus_rect(64, 96)),           # 24576 arcs: the complex64 size limit
+]
+
+
+def _graph(hw, g):
+    row_ptr, col = synth.adjacency_csr(*g)
+    return hw.hw_graph_csr(g[0], row_ptr, col)
+
+
+@pytest.mark.parametrize("name,g", CASES)
+@pytest.mark.parametrize("dt", [2, 1])
+def test_cluster_walk_matches_oracle_and_per_step_path(hw, name, g, dt):
+    import torch
+    n = g[0]
+    G = _graph(hw, g)
+    ar = oracle.Arcs(*g)
+    marked = sorted({1, n // 2, n - 1}) if n > 2 else [1]
+    steps, stride = 37, 3
+    psi0 = synth.random_state(ar.num_arcs, seed=13)
+    cdt = torch.complex128 if dt == 2 else torch.complex64
+    x = torch.from_numpy(psi0).to("cuda", cdt)
+    slots = steps // stride
+    outs, recs = [], []
+    for mode in (0, 1):
+        y = torch.empty_like(x)
+        rec = torch.empty(slots, dtype=torch.float64, device="cuda")
+        hw.hw_coined_evolve(G, 0, marked, dt, 1, steps, x, y, rec, opts={"record_stride": stride, "launch_mode": mode})
+        outs.append(y)
+        recs.append(rec)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(recs[0], recs[1])
+    ref, rr = oracle.coined_evolve(ar, psi0, steps, marked=marked, record=True)
+    got = outs[0].cpu().numpy().astype(np.complex128)
+    if dt == 2:
+        assert np.max(np.abs(got - ref)) <= 1e-12
+        assert np.max(np.abs(recs[0].cpu().numpy() - rr[stride - 1::stride][:slots])) <= 1e-12
+    else:
+        assert np.max(np.abs(got - ref)) <= 1e-5
+        assert np.max(np.abs(recs[0].cpu().numpy() - rr[stride - 1::stride][:slots])) <= 1e-5
+    G.free()
+
+
+def test_cluster_walk_in_place_and_persistent_shift(hw):
+    import torch
+    L1, L2 = 12, 10
+    g = synth.torus_rect(L1, L2)
+    G = _graph(hw, g)
+    ar = oracle.Arcs(*g)
+    psi0 = synth.random_state(ar.num_arcs, seed=3)
+    for shift in (0, 1):
+        x = torch.from_numpy(psi0).cuda()
+        hw.hw_coined_evolve(G, 0, [17], 2, 1, 21, x, x, opts={"shift": shift})   # in place, odd steps
+        ref = oracle.coined_evolve(ar, psi0, 21, marked=[17], persistent_torus=(L1, L2) if shift else None)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(x.cpu().numpy() - ref)) <= 1e-12
+        y = torch.from_numpy(psi0).cuda()
+        hw.hw_coined_evolve(G, 0, [17], 2, 1, 21, y, y, opts={"shift": shift, "launch_mode": 1})
+        torch.cuda.synchronize()
+        assert torch.equal(x, y)
+    G.free()
+
+
+def test_cluster_walk_record_single_mark_and_one_step(hw):
+    import torch
+    g = synth.torus(64)
+    G = _graph(hw, g)
+    ar = oracle.Arcs(*g)
+    psi0 = synth.uniform_state(ar.num_arcs)
+    x = torch.from_numpy(psi0).cuda()
+    for steps in (1, 100):
+        y = torch.empty_like(x)
+        rec = torch.empty(steps, dtype=torch.float64, device="cuda")
+        hw.hw_coined_evolve(G, 0, [2080], 2, 1, steps, x, y, rec)
+        ref, rr = oracle.coined_evolve(ar, psi0, steps, marked=[2080], record=True)
+        torch.cuda.synchronize()
+        assert np.max(np.abs(y.cpu().numpy() - ref)) <= 1e-12
+        assert np.max(np.abs(rec.cpu().numpy() - rr)) <= 1e-12
+    with pytest.raises(hw.HWError):
+        hw.hw_coined_evolve(G, 0, [], 2, 1, 3, x, x, opts={"launch_mode": 2})
+    G.free()

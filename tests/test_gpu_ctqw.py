@@ -1,7 +1,9 @@
 """GPU parity of the continuous-time walk (Sec. 3.1) against the FP64 oracle.
 
-U = e^{-iH dt} from hw_ctqw_expm is compared column by column with the
-oracle's sparse series action, and the evolved states / marked-vertex curves
+U = e^{-iH dt} from hw_ctqw_expm, with its Taylor powers formed both ways
+(sparse x dense products with the graph, the default, and dense n^3 GEMMs:
+FP64 for complex128, tensor cores for complex64), is compared column by
+column with the oracle's sparse series action, and the evolved states / marked-vertex curves
 from hw_ctqw_evolve with the oracle's evolution.  complex128: max-abs <= 1e-12;
 complex64: probability L1 <= 1e-3 after 1000+ applications.
 """
@@ -23,8 +25,13 @@ def _graph(hw, g):
     return hw.hw_graph_csr(n, row_ptr, col)
 
 
-def gpu_expm(hw, g, gamma, marked, t, dt=2, opts=None):
+POWERS = [2, 1]   # hw_opts.taylor_powers: sparse x dense products, dense GEMMs
+
+
+def gpu_expm(hw, g, gamma, marked, t, dt=2, opts=None, powers=2):
     import torch
+    opts = dict(opts or {})
+    opts["taylor_powers"] = powers
     G = _graph(hw, g)
     n = g[0]
     cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
@@ -59,11 +66,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("powers", POWERS)
 @pytest.mark.parametrize("t", [0.1, 1.0, 10.0])
 @pytest.mark.parametrize("name,g,gamma,marked", CASES)
-def test_expm_c128_matches_oracle_columns(hw, name, g, gamma, marked, t):
+def test_expm_c128_matches_oracle_columns(hw, name, g, gamma, marked, t, powers):
     marked = [m for m in marked if m < g[0]]
-    G, U = gpu_expm(hw, g, gamma, marked, t)
+    G, U = gpu_expm(hw, g, gamma, marked, t, powers=powers)
     ar = oracle.Arcs(*g)
     ref = oracle.ctqw_columns(ar, gamma, t, np.arange(g[0]), marked=marked)
     # Each squaring roughly doubles the rounding error already in U, so the
@@ -75,9 +83,10 @@ def test_expm_c128_matches_oracle_columns(hw, name, g, gamma, marked, t):
     G.free()
 
 
-def test_expm_c64_close(hw):
+@pytest.mark.parametrize("powers", POWERS)
+def test_expm_c64_close(hw, powers):
     g = synth.hypercube(7)
-    G, U = gpu_expm(hw, g, 1 / 7, [3], 0.1, dt=1)
+    G, U = gpu_expm(hw, g, 1 / 7, [3], 0.1, dt=1, powers=powers)
     ar = oracle.Arcs(*g)
     ref = oracle.ctqw_columns(ar, 1 / 7, 0.1, np.arange(128), marked=[3])
     assert np.max(np.abs(U.cpu().numpy() - ref)) < 2e-6
@@ -90,11 +99,13 @@ def test_expm_c64_close(hw):
     # gamma = 0.3: Y needs two slices (three products)
     ("er_two_slices", synth.erdos_renyi(1000, 0.006, seed=6), 0.3, [990], 0.25),
 ])
-def test_expm_c64_ragged_multi_tile(hw, name, g, gamma, marked, t):
-    # n not a multiple of the 128 x 256 tiles, several cluster tiles and
-    # mirrored blocks; columns checked against the oracle's action
+@pytest.mark.parametrize("powers", POWERS)
+def test_expm_c64_ragged_multi_tile(hw, name, g, gamma, marked, t, powers):
+    # n not a multiple of the 128 x 256 tiles (or of the sparse kernel's
+    # 8 x 256 blocks), several cluster tiles and mirrored blocks; columns
+    # checked against the oracle's action
     n = g[0]
-    G, U = gpu_expm(hw, g, gamma, marked, t, dt=1)
+    G, U = gpu_expm(hw, g, gamma, marked, t, dt=1, powers=powers)
     ar = oracle.Arcs(*g)
     cols = np.array([0, 1, 130, 257, n // 2, n - 2, n - 1])
     ref = oracle.ctqw_columns(ar, gamma, t, cols, marked=marked)
@@ -106,10 +117,11 @@ def test_expm_c64_ragged_multi_tile(hw, name, g, gamma, marked, t):
     G.free()
 
 
-def test_expm_hypercube_closed_form(hw):
+@pytest.mark.parametrize("powers", POWERS)
+def test_expm_hypercube_closed_form(hw, powers):
     # no marks: U[u, v] = cos(gamma t)^(k-h) (i sin(gamma t))^h, h = Hamming distance
     k, gamma, t = 8, 0.25, 3.0
-    G, U = gpu_expm(hw, synth.hypercube(k), gamma, [], t)
+    G, U = gpu_expm(hw, synth.hypercube(k), gamma, [], t, powers=powers)
     u = np.arange(1 << k)
     h = np.array([bin(x).count("1") for x in range(1 << k)])
     H = h[u[:, None] ^ u[None, :]]
@@ -206,14 +218,15 @@ def test_evolve_batched_and_in_place(hw):
     G.free()
 
 
+@pytest.mark.parametrize("powers", POWERS)
 @pytest.mark.parametrize("dt", [2, 1])
-def test_config3_hypercube12_search_full_size(hw, dt):
+def test_config3_hypercube12_search_full_size(hw, dt, powers):
     # Q_12, gamma = 1/12, one seeded mark, dt = 0.1, uniform start, 2000 applications.
     k, gamma, tstep, steps = 12, 1 / 12, 0.1, 2000
     g = synth.hypercube(k)
     N = 1 << k
     m = synth.seeded_vertex(3, N)
-    G, U = gpu_expm(hw, g, gamma, [m], tstep, dt=dt)
+    G, U = gpu_expm(hw, g, gamma, [m], tstep, dt=dt, powers=powers)
     ar = oracle.Arcs(*g)
     cols = np.array([0, m, 1, 2047, 4095, 1234, 3000, 77])
     refU = oracle.ctqw_columns(ar, gamma, tstep, cols, marked=[m])

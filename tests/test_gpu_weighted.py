@@ -117,13 +117,14 @@ def test_dense_expm_real_weights(hw, name, g, gamma, marked, t):
     w = ar.weights(eu, ev, we)
     cols = np.unique(np.array([0, 1, 130, 257, n // 2, n - 2, n - 1]) % n)
     ref = oracle.ctqw_columns(ar, gamma, t, cols, marked=marked, weights=w)
-    for dt, tol in ((hw.HW_C128, TOL128), (hw.HW_C64, 2e-6)):
-        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
-        U = torch.empty((n, n), dtype=cdt, device="cuda")
-        hw.hw_ctqw_expm(G, gamma, marked, t, dt, U)
-        Uh = U.cpu().numpy()
-        assert np.max(np.abs(Uh[:, cols] - ref)) <= tol, dt
-        assert np.max(np.abs(Uh - Uh.T)) <= tol      # H real symmetric: U symmetric
+    for powers in (2, 1):   # sparse x dense products with W, dense GEMMs
+        for dt, tol in ((hw.HW_C128, TOL128), (hw.HW_C64, 2e-6)):
+            cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+            U = torch.empty((n, n), dtype=cdt, device="cuda")
+            hw.hw_ctqw_expm(G, gamma, marked, t, dt, U, opts={"taylor_powers": powers})
+            Uh = U.cpu().numpy()
+            assert np.max(np.abs(Uh[:, cols] - ref)) <= tol, (dt, powers)
+            assert np.max(np.abs(Uh - Uh.T)) <= tol      # H real symmetric: U symmetric
     G.free()
 
 
