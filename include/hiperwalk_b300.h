@@ -389,6 +389,7 @@ hw_status hw_probability_noalloc(const hw_graph *g, int64_t n, hw_dtype dt, int3
  * Scratch (slices, 3(m+n)k x 2 bytes) comes from the stream-ordered
  * allocator.  The call synchronises `stream` before returning, to report a
  * device-side pipeline timeout as HW_ETIMEDOUT.
+ * A, B and C must be device memory of the current device (HW_EINVAL otherwise).
  * Errors: HW_EINVAL, HW_EUNSUPPORTED (not an sm_103 device), HW_ENOMEM,
  * HW_ECUDA, HW_ETIMEDOUT.
  */

@@ -13,20 +13,18 @@
 // unweighted graph, scaled by 1 / (gamma tau), has entries 0, 1 and 1/gamma),
 // B keeps one slice and the products with its lower slices are dropped.
 //
-// Work is cut into 128 x 256 CTA tiles, paired along M into 2-CTA
-// thread-block clusters (256 x 256 cluster tiles): the two CTAs of a pair
-// compute rows 0-127 and 128-255 of the same 256 columns, so each loads its
-// own A rows and half of the shared B rows with TMA and multicasts that half
-// to both CTAs; every B byte leaves L2 once per pair.  Persistent clusters
-// walk a list of cluster tiles.  Per CTA, 14 warps (448 threads): warp 4
-// lane 0 streams K blocks (32 elements = one 64-byte swizzle row) of every
-// slice into a shared-memory ring (up to 8 stages, 216 KiB); warp 5 lane 0
-// issues the MMAs (M = 128, N = 256) into one of two 256-column TMEM
-// accumulators and releases each stage with a tcgen05.commit that arrives on
-// the stage's "empty" barrier in both CTAs that write into it; warps 0-3 and
-// 6-9 drain the other accumulator (tcgen05.ld, warp w owns TMEM lanes of
-// quadrant w % 4 = tile rows, warps 0-3 and 6-9 one half of the columns each)
-// and run the epilogue of the previous tile:
+// Work is cut into 128 x 256 CTA tiles; persistent CTAs, one per SM, walk a
+// list of tiles.  Each CTA loads its own A rows and all of its B rows with
+// TMA into its own shared memory: the operands of a Taylor power (the previous
+// power's slices and Y's) stay in L2, which serves the repeated B reads.  Per
+// CTA, 14 warps (448 threads): warp 4 lane 0 streams K blocks (32 elements =
+// one 64-byte swizzle row) of every slice into a shared-memory ring (up to 8
+// stages, 216 KiB); warp 5 lane 0 issues the MMAs (M = 128, N = 256) into one
+// of two 256-column TMEM accumulators and releases each stage with a
+// tcgen05.commit on the stage's "empty" barrier; warps 0-3 and 6-9 drain the
+// other accumulator (tcgen05.ld, warp w owns TMEM lanes of quadrant w % 4 =
+// tile rows, warps 0-3 and 6-9 one half of the columns each) and run the
+// epilogue of the previous tile:
 //   EPI_STORE:  C = scale * acc (fp32)
 //   EPI_TAYLOR: Q = scale * acc, written back as slices of qscale * Q (the
 //               next power's A operand).
@@ -42,8 +40,8 @@
 // also written to its mirror position with coalesced transposed stores.
 // Every wait on an mbarrier is bounded; a timeout sets an error flag that the
 // host reads, and the CTA still frees its tensor memory.  Before a CTA exits,
-// its producer waits until every stage it filled has been released by both
-// consumers, so no peer signals a CTA that has left.
+// its producer waits until every stage it filled has been released, so no
+// copy or MMA is in flight when it leaves.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -63,8 +61,6 @@
 namespace {
 
 constexpr int TM = 128, TN = 256, TK = 32;                // CTA tile; K block = one 64-byte swizzle row
-constexpr int kCM = 2, kCN = 1;                           // cluster of kCM x kCN CTAs: rank = i + kCM j
-constexpr int kCluster = kCM * kCN;
 constexpr int kATile = TM * TK * 2;                       // 8 KB per A slice
 constexpr int kBTile = TN * TK * 2;                       // 16 KB per B slice
 constexpr int kRingBytes = 216 * 1024;                    // shared-memory ring
@@ -79,7 +75,7 @@ enum { FMT_BF16 = 0, FMT_F16 = 1 };
 enum { EPI_STORE = 0, EPI_TAYLOR = 1 };
 
 struct TcArgs {
-    const int2 *tiles;       // cluster tiles (P, Q): rows 256 P.., columns 512 Q..
+    const int2 *tiles;       // CTA tiles (P, Q): rows 128 P.., columns 256 Q..
     int m, n, k;
     int epi;
     int sym;                 // skip blocks below the diagonal, mirror the others
@@ -140,27 +136,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// 2D tile load written to the same shared-memory offset of every CTA in mask,
-// each CTA's mbarrier at offset bar receiving the bytes it got
-__device__ __forceinline__ void tma_load_mc(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
-                                            uint16_t mask)
+// 2D tile load into this CTA's shared memory, completing on its mbarrier
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
 
@@ -200,15 +182,6 @@ __device__ __forceinline__ void mma16(uint32_t tmem_d, uint64_t adesc, uint64_t 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// arrives once on the mbarrier at offset bar of every CTA in mask when this
-// thread's earlier MMAs have completed
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(bar), "h"(mask)
                  : "memory");
 }
 
@@ -440,23 +413,21 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
 
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_rank();
-    const int ci = int(rank) % kCM, cj = int(rank) / kCM;     // position in the cluster
-    const int cid = int(blockIdx.x) / kCluster, ncl = int(gridDim.x) / kCluster;
+    const int cid = int(blockIdx.x), ncl = int(gridDim.x);
     const int nkb = (a.k + TK - 1) / TK;
     volatile int *tmo = &timed_out;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_empty[s]), 1 + (kCM - 1) + (kCN - 1));   // this CTA and those sharing its loads
+            mbar_init(smem_u32(&bar_empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&bar_tfull[b]), 1);
             mbar_init(smem_u32(&bar_tempty[b]), 8);  // one arrival per epilogue warp
         }
         timed_out = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");   // visible to the async proxy
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -465,50 +436,39 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    cluster_sync();   // every CTA's barriers are initialised before any peer signals them
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
     if (warp == 4) {
         if (lane == 0) {
-            // producer: this CTA's half of the A tile goes to both CTAs of its
-            // cluster row, its half of the B tile to both CTAs of its column
+            // producer: one TMA box per slice of the A tile (128 rows) and of
+            // the B tile (256 rows) per K block
             const CUtensorMap *mA[3] = {&tA0, &tA1, &tA2};
             const CUtensorMap *mB[3] = {&tB0, &tB1, &tB2};
-            // (with one CTA in a cluster row or column, the CTA loads both halves itself)
-            const uint16_t maskA = uint16_t(kCN == 2 ? (1u << ci) | (1u << (ci + kCM)) : (1u << rank));
-            const uint16_t maskB = uint16_t(kCM == 2 ? 3u << (kCM * cj) : (1u << rank));
-            const int ha0 = (kCN == 2) ? cj : 0, ha1 = (kCN == 2) ? cj + 1 : 2;   // A halves loaded here
-            const int hb0 = (kCM == 2) ? ci : 0, hb1 = (kCM == 2) ? ci + 1 : 2;   // B halves loaded here
             uint32_t g = 0, phase = 0;
             int s = 0;
             for (int t = cid; t < ntiles && !*tmo; t += ncl) {
                 const int2 ct = a.tiles[t];
-                const int rowA = ct.x * kCM * TM + ci * TM;
-                const int rowB = ct.y * kCN * TN + cj * TN;
+                const int rowA = ct.x * TM;
+                const int rowB = ct.y * TN;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (g >= uint32_t(S) && !mbar_wait(smem_u32(&bar_empty[s]), phase ^ 1u)) {
                         *tmo = 1;
                         break;
                     }
                     const uint32_t full = smem_u32(&bar_full[s]);
-                    mbar_expect_tx(full, uint32_t(kStageBytes));   // all bytes landing here, from any CTA
+                    mbar_expect_tx(full, uint32_t(kStageBytes));   // all bytes of the stage's boxes
                     const uint32_t st = base + uint32_t(s * kStageBytes);
 #pragma unroll
-                    for (int i = 0; i < NA; ++i)
-                        for (int h = ha0; h < ha1; ++h)
-                            tma_load_mc(st + uint32_t(i * kATile + h * (kATile / 2)), mA[i], full, kb * TK,
-                                        rowA + h * (TM / 2), maskA);
+                    for (int i = 0; i < NA; ++i) tma_load(st + uint32_t(i * kATile), mA[i], full, kb * TK, rowA);
 #pragma unroll
                     for (int j = 0; j < NB; ++j)
-                        for (int h = hb0; h < hb1; ++h)
-                            tma_load_mc(st + uint32_t(NA * kATile + j * kBTile + h * (kBTile / 2)), mB[j], full,
-                                        kb * TK, rowB + h * (TN / 2), maskB);
+                        tma_load(st + uint32_t(NA * kATile + j * kBTile), mB[j], full, kb * TK, rowB);
                     ++g;
                     if (++s == S) { s = 0; phase ^= 1u; }
                 }
             }
-            // drain: the last fill of every stage released by all three consumers
+            // drain: the last fill of every stage released by the MMAs
             for (uint32_t q = 0; q < uint32_t(S) && q < g; ++q) {
                 const uint32_t last_use = (g - 1 - q) / uint32_t(S);
                 if (!mbar_wait(smem_u32(&bar_empty[q]), last_use & 1u)) *tmo = 1;
@@ -517,10 +477,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
     } else if (warp == 5) {
         if (lane == 0) {
             // MMA issuer: accumulator b = (local tile) & 1
-            // every CTA that writes into this CTA's stages: itself, the other
-            // CTA of its cluster row (A) and of its cluster column (B)
-            const uint16_t maskC = uint16_t((1u << rank) | (kCN == 2 ? 1u << (ci + kCM * (1 - cj)) : 0u) |
-                                            (kCM == 2 ? 1u << ((1 - ci) + kCM * cj) : 0u));
             const uint64_t d0 = smem_desc_sw64(base);
             uint32_t phase = 0, li = 0;
             int s = 0;
@@ -540,7 +496,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
                     }
                     const uint64_t dA = d0 + uint64_t((s * kStageBytes) >> 4);
                     mma_block<FMT, NA, NB>(tacc, dA, dA + uint64_t((NA * kATile) >> 4), kb > 0 ? 1u : 0u);
-                    mma_commit_mc(smem_u32(&bar_empty[s]), maskC);
+                    mma_commit(smem_u32(&bar_empty[s]));
                     if (++s == S) { s = 0; phase ^= 1u; }
                 }
                 mma_commit(smem_u32(&bar_tfull[b]));
@@ -567,8 +523,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int2 ct = a.tiles[t];
-            epilogue_tile<FMT, NA>(a, ct.x * kCM * TM + ci * TM, ct.y * kCN * TN + cj * TN, tmem + uint32_t(b * TN),
-                                   quad, lane, cb, cb + TN / 2);
+            epilogue_tile<FMT, NA>(a, ct.x * TM, ct.y * TN, tmem + uint32_t(b * TN), quad, lane, cb, cb + TN / 2);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0)
@@ -578,7 +533,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
     __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    cluster_sync();   // no CTA leaves while a peer may still write to or signal it
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     if (threadIdx.x == 0 && timed_out) atomicExch(a.err, 1);
@@ -775,8 +729,8 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Slices {
     void *s[3] = {nullptr, nullptr, nullptr};
-    CUtensorMap mapA[3];     // half of an A tile (64 rows), as the multicast loads take it
-    CUtensorMap mapB[3];     // half of a B tile (128 rows)
+    CUtensorMap mapA[3];     // boxes of an A tile (128 rows x one K block)
+    CUtensorMap mapB[3];     // boxes of a B tile (256 rows x one K block)
 };
 
 // three slice planes of a rows x ld 16-bit matrix in one buffer, plus their maps
@@ -784,8 +738,8 @@ hw_status slices_make(Slices &S, uint16_t *buf, int rows, int cols, int ld, int 
 {
     for (int i = 0; i < 3; ++i) {
         S.s[i] = buf + size_t(i) * rows * ld;
-        hw_status st = make_map(&S.mapA[i], S.s[i], rows, cols, ld, fmt, TM / 2);
-        if (st == HW_OK) st = make_map(&S.mapB[i], S.s[i], rows, cols, ld, fmt, TN / 2);
+        hw_status st = make_map(&S.mapA[i], S.s[i], rows, cols, ld, fmt, TM);
+        if (st == HW_OK) st = make_map(&S.mapB[i], S.s[i], rows, cols, ld, fmt, TN);
         if (st != HW_OK) return st;
     }
     return HW_OK;
@@ -804,18 +758,20 @@ const Mode kModes[5] = {
     {FMT_F16, 2},    // 4: fp16 x 2
 };
 
-// cluster tiles (P, Q) of 256 x 512 in 4 x 4 groups; with sym only those with
-// a 128 x 128 block (r, c), r <= c: row blocks 2P, 2P+1, column blocks 4Q..4Q+3
-std::vector<int2> cluster_tiles(int m, int n, bool sym)
+// CTA tiles (P, Q) of 128 x 256, in groups of 8 x 4 (1024 x 1024 elements, so
+// that the CTAs running at once share their A rows and B rows in L2); with
+// sym only those holding a 128 x 128 block (r, c) with r <= c: row block P,
+// column blocks 2Q, 2Q + 1
+std::vector<int2> cta_tiles(int m, int n, bool sym)
 {
-    const int tp = (m + kCM * TM - 1) / (kCM * TM), tq = (n + kCN * TN - 1) / (kCN * TN);
+    const int tp = (m + TM - 1) / TM, tq = (n + TN - 1) / TN;
     std::vector<int2> t;
-    const int G = 4;
-    for (int bp = 0; bp < tp; bp += G)
-        for (int bq = 0; bq < tq; bq += G)
-            for (int p = bp; p < std::min(tp, bp + G); ++p)
-                for (int q = bq; q < std::min(tq, bq + G); ++q)
-                    if (!sym || kCM * p <= 2 * kCN * q + 2 * kCN - 1) t.push_back(make_int2(p, q));
+    const int GP = 8, GQ = 4;
+    for (int bp = 0; bp < tp; bp += GP)
+        for (int bq = 0; bq < tq; bq += GQ)
+            for (int p = bp; p < std::min(tp, bp + GP); ++p)
+                for (int q = bq; q < std::min(tq, bq + GQ); ++q)
+                    if (!sym || TM * p <= TN * q + TN - 1) t.push_back(make_int2(p, q));
     return t;
 }
 
@@ -850,46 +806,34 @@ hw_status launch_tc(int fmt, int na, int nb, const Slices &A, const Slices &B, c
                     cudaStream_t st)
 {
     static std::mutex mu;
-    static std::map<std::pair<TcKernel, int>, int> max_clusters;   // (kernel, device) -> clusters at once
+    static std::map<std::pair<TcKernel, int>, int> max_ctas;   // (kernel, device) -> CTAs at once
     TcKernel kern = tc_kernel(fmt, na, nb);
     if (!kern) return hw_fail(HW_EINVAL, "no tensor-core kernel for %d x %d slices", na, nb);
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = tc_smem_bytes(na, nb);
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int ncl = 0;
+    const int smem = tc_smem_bytes(na, nb);
+    int nctas = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
-        auto it = max_clusters.find({kern, dev});
-        if (it != max_clusters.end()) {
-            ncl = it->second;
+        auto it = max_ctas.find({kern, dev});
+        if (it != max_ctas.end()) {
+            nctas = it->second;
         } else {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 int(cfg.dynamicSmemBytes));
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_tc_gemm)");
-            int sms = 148;
+            int sms = 148, per_sm = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cfg.gridDim = dim3(unsigned(sms / kCluster * kCluster));
-            e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
-            if (e != cudaSuccess) return hw_cuda(e, "cudaOccupancyMaxActiveClusters(k_tc_gemm)");
-            if (ncl < 1) return hw_fail(HW_EUNSUPPORTED, "no cluster of k_tc_gemm fits on this device");
-            max_clusters[{kern, dev}] = ncl;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+            if (e != cudaSuccess) return hw_cuda(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_tc_gemm)");
+            if (per_sm < 1) return hw_fail(HW_EUNSUPPORTED, "k_tc_gemm does not fit on an SM of this device");
+            nctas = per_sm * sms;
+            max_ctas[{kern, dev}] = nctas;
         }
     }
-    // persistent: as many clusters as run at once, each walking the cluster-tile list
-    cfg.gridDim = dim3(unsigned(std::min(ntiles, ncl) * kCluster));
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A.mapA[0], A.mapA[1], A.mapA[2], B.mapB[0], B.mapB[1],
-                                       B.mapB[2], a, ntiles);
-    return hw_cuda(e, "k_tc_gemm launch");
+    // persistent: as many CTAs as run at once, each walking the tile list
+    kern<<<std::min(ntiles, nctas), kThreads, smem, st>>>(A.mapA[0], A.mapA[1], A.mapA[2], B.mapB[0], B.mapB[1],
+                                                          B.mapB[2], a, ntiles);
+    return hw_cuda(cudaGetLastError(), "k_tc_gemm launch");
 }
 
 int row_grid(int64_t rows) { return int(std::min<int64_t>(148 * 16, std::max<int64_t>(rows, 1))); }
@@ -995,7 +939,7 @@ hw_status tc_power_begin(const SymSparse &Y, const double *yvals, int nyvals, do
     p->s_prev = p->sY;
     p->theta = theta;
     p->st = st;
-    const std::vector<int2> tiles = cluster_tiles(n, n, true);
+    const std::vector<int2> tiles = cta_tiles(n, n, true);
     p->ntiles = int(tiles.size());
     const size_t one = size_t(n) * p->ld * 3;     // 16-bit elements per slice buffer (3 planes)
     const size_t tiles_b = sizeof(int2) * tiles.size();
@@ -1128,11 +1072,27 @@ extern "C" hw_status hw_gemm_tc(int64_t m, int64_t n, int64_t k, const float *A,
     if (!A || !B || !C) return hw_fail(HW_EINVAL, "NULL operand");
     if (mode < 1 || mode > 4) return hw_fail(HW_EINVAL, "mode must be 1..4");
     if (!tc_gemm_available()) return hw_fail(HW_EUNSUPPORTED, "needs an sm_103 device");
+    {
+        // the operands must be memory of the current device (not host or peer memory)
+        int dev = -1;
+        hw_status ds = hw_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+        if (ds != HW_OK) return ds;
+        const void *ptrs[3] = {A, B, C};
+        for (const void *q : ptrs) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+                cudaGetLastError();
+                return hw_fail(HW_EINVAL, "operand %p is not device memory", q);
+            }
+            if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+                return hw_fail(HW_EINVAL, "operand %p is not memory of the current device %d", q, dev);
+        }
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Mode &md = kModes[mode];
     const int ld = round_up(int(k), 64);
     const size_t sa = size_t(m) * ld * 3, sb = size_t(n) * ld * 3;
-    const std::vector<int2> tiles = cluster_tiles(int(m), int(n), false);
+    const std::vector<int2> tiles = cta_tiles(int(m), int(n), false);
     const size_t tiles_b = sizeof(int2) * tiles.size();
     void *mem = nullptr;
     hw_status s = hw_cuda(hw_malloc_async(&mem, (sa + sb) * 2 + tiles_b + 256, st), "scratch allocation (slices)");

@@ -59,3 +59,18 @@ def test_split_accuracy(hw, slices, rel):
     ref = A.astype(np.float64) @ B.T.astype(np.float64)
     bound = np.outer(np.linalg.norm(A, axis=1), np.linalg.norm(B, axis=1))
     assert np.max(np.abs(C - ref) / bound) < rel
+
+
+def test_rejects_operands_not_on_the_device(hw):
+    # the tensor-core GEMM takes device memory of the current device only
+    import ctypes
+    import torch
+    m, n, k = 128, 128, 64
+    host = np.zeros((m, k), dtype=np.float32)
+    pinned = torch.zeros((m, k), dtype=torch.float32).pin_memory()
+    dev_b = torch.zeros((n, k), dtype=torch.float32, device="cuda")
+    dev_c = torch.zeros((m, n), dtype=torch.float32, device="cuda")
+    for a_ptr in (host.ctypes.data, pinned.data_ptr()):
+        st = hw.lib().hw_gemm_tc(m, n, k, ctypes.c_void_p(a_ptr), ctypes.c_void_p(dev_b.data_ptr()),
+                                 ctypes.c_void_p(dev_c.data_ptr()), 1, None)
+        assert st == hw.HW_EINVAL
