@@ -427,6 +427,14 @@ def sub_torus64(hw, reps, warmup, with_cpu):
         hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
         hw.hw_probability(G, n, hw.HW_C128, 1, out, prob)
     torch.cuda.synchronize()
+    # enough runs for half a second of timed work, so that the clock sampler
+    # (every 200 ms) sees the timed region
+    e = _events(2)
+    e[0].record(stream)
+    hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    reps = max(reps, int(0.5 / max(e[0].elapsed_time(e[1]) / 1e3, 1e-6)))
     with Clocks(torch.cuda.current_device()) as clk:
         e = _events(2)
         e[0].record(stream)
@@ -439,8 +447,11 @@ def sub_torus64(hw, reps, warmup, with_cpu):
     arcs = G.num_arcs
     res = {"workload": "torus64_center", "metric": METRIC, "unit": UNIT, "value": arcs * 100 / t,
            "us_per_run": t * 1e6, "us_per_walk_step": t / 100 * 1e6, "reps": reps, "dtype": "f64",
-           "roofline": {"bound": "latency", "bytes_per_walk_step": arcs * 32 + 4 * (n + 1),
-                        "note": "256 KiB state; a walk step moves 0.6 MB, far below what fills the GPU"},
+           "roofline": {"bound": "latency", "bytes_per_walk_step": arcs * 32,
+                        "note": "the whole walk in one launch (one 16-CTA thread-block cluster holds the 256 KiB "
+                                "state in shared memory, a hardware cluster barrier per step), then one "
+                                "probability launch; per step the FP64 FMAs of 4096 vertices on the cluster's "
+                                "16 SMs and the barrier set the time"},
            "clocks": clk.summary()}
     if with_cpu:
         import oracle
@@ -1035,6 +1046,46 @@ def run_profile(args):
         print(json.dumps({"profile": args.profile, "steps": args.profile_steps, "tile": args.profile_tile}))
         G.free()
         return
+    if args.profile == "cluster_torus64":
+        # configuration 1: one 100-step run of the 64 x 64 torus (one cluster launch)
+        n, eu, ev = synth.torus(64)
+        row_ptr, col = synth.adjacency_csr(n, eu, ev)
+        G = hw.hw_graph_csr(n, row_ptr, col)
+        psi0 = torch.from_numpy(synth.state_on_vertex_arcs(synth.arc_offsets(n, eu, ev), 32 * 64 + 32)).cuda()
+        out = torch.empty_like(psi0)
+        hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 100, psi0, out)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile}))
+        G.free()
+        return
+    if args.profile.startswith("cube20_"):
+        # the 2^20-vertex hypercube (degree 20), uniform start, one seeded mark, profile_steps steps
+        k = 20
+        n, eu, ev = synth.hypercube(k)
+        row_ptr, col = synth.adjacency_csr(n, eu, ev)
+        G = hw.hw_graph_csr(n, row_ptr, col)
+        dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        x = torch.full((G.num_arcs,), 1.0 / math.sqrt(G.num_arcs), dtype=cdt, device="cuda")
+        y = torch.empty_like(x)
+        hw.hw_coined_evolve(G, 0, [synth.seeded_vertex(3, n)], dt, 1, args.profile_steps, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "steps": args.profile_steps}))
+        G.free()
+        return
+    if args.profile in ("expm_sparse_c128", "expm_sparse_c64"):
+        # the 4096-vertex hypercube CTQW: one expm with the Taylor powers as sparse x dense products
+        n = 4096
+        m = synth.seeded_vertex(3, n)
+        row_ptr, col = synth.adjacency_csr(*synth.hypercube(12))
+        G = hw.hw_graph_csr(n, row_ptr, col)
+        dt = hw.HW_C128 if args.profile.endswith("c128") else hw.HW_C64
+        U = torch.empty((n, n), dtype=torch.complex128 if dt == hw.HW_C128 else torch.complex64, device="cuda")
+        hw.hw_ctqw_expm(G, 1 / 12, [m], 0.1, dt, U, opts={"taylor_powers": 2})
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile}))
+        G.free()
+        return
     if args.profile in ("expm_c64", "apply_c128", "apply_c64", "apply_sym_c64"):
         # the 4096-vertex hypercube CTQW: one expm (11 tensor-core powers) or a few applications
         n = 4096
@@ -1098,7 +1149,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", choices=["coined_c128", "coined_c64", "batched_c64", "expm_c64", "apply_c128",
                                           "apply_c64", "apply_sym_c64", "sparse_torus_c64", "sparse_torus_c128",
-                                          "sparse_cube_c64", "sparse_cube_c128"],
+                                          "sparse_cube_c64", "sparse_cube_c128", "cluster_torus64",
+                                          "cube20_c128", "cube20_c64", "expm_sparse_c128", "expm_sparse_c64"],
                     help="run a few coin+shift launches of the workload and exit (for ncu)")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--profile-tile", type=int, default=10)

@@ -941,11 +941,13 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
                 }
             }
             const R f = em_weight<R>(a);
+            // the rows again, last first: the rows read last by the sum are
+            // the likeliest to be still in L2
             CubeWalk cw(v, d);
 #pragma unroll 4
-            for (int j = 0; j < d; ++j) {
+            for (int j = d - 1; j >= 0; --j) {
                 const V p = in[j * n + v];
-                const int r = (ADDR == kAddrCube) ? cw.target(cw.next_bit(), n) : __ldg(a.revE + j * n + v);
+                const int r = (ADDR == kAddrCube) ? cw.target(cw.prev_bit(), n) : __ldg(a.revE + j * n + v);
                 out[r] = mkv<V, R>(fma(f, sx, -p.x), fma(f, sy, -p.y));
             }
         }

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_coined_cluster(ClusterArgs a)
     const int comp = threadIdx.x & 1;
     for (int64_t t = 1; t <= a.steps; ++t) {
         const R *cur = reinterpret_cast<const R *>((t & 1) ? buf0 : buf1);
+        R *nxt = reinterpret_cast<R *>((t & 1) ? buf1 : buf0);
         const uint32_t nb = (t & 1) ? base1 : base0;
         for (int lv = threadIdx.x >> 1; lv < nv; lv += blockDim.x >> 1) {
             R p[D];
@@ -145,7 +146,10 @@ __global__ void __launch_bounds__(kMaxThreads) k_coined_cluster(ClusterArgs a)
             for (int j = 0; j < D; ++j) {
                 const uint32_t g = tgt[lv * D + j];
                 const R o = marked ? -p[j] : fma(f, sum, -p[j]);
-                st_peer(peer_addr(nb + ((g & 0xFFFFFFu) * 2u + uint32_t(comp)) * uint32_t(sizeof(R)), g >> 24), o);
+                const uint32_t e = (g & 0xFFFFFFu) * 2u + uint32_t(comp);
+                // arcs owned by this CTA take a plain shared-memory store
+                if ((g >> 24) == uint32_t(rank)) nxt[e] = o;
+                else st_peer(peer_addr(nb + e * uint32_t(sizeof(R)), g >> 24), o);
             }
         }
         cluster_barrier();

@@ -145,6 +145,21 @@ struct CubeWalk {
         ++j;
         return b;
     }
+    // the same positions from the last one down: position d - 1 first
+    // (clear bits highest first, then set bits lowest first); a walk uses
+    // either next_bit or prev_bit, not both
+    __device__ __forceinline__ int prev_bit()
+    {
+        int b;
+        if (clr) {
+            b = 31 - __clz(clr);
+            clr ^= 1u << b;
+        } else {
+            b = __ffs(set) - 1;
+            set &= set - 1u;
+        }
+        return b;
+    }
     __device__ __forceinline__ int target(int b, int64_t n) const
     {
         const int rpos = ((v >> b) & 1u) ? (pc - 1) + b - __popc(v & ((1u << b) - 1u)) : __popc(v >> (b + 1));

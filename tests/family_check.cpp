@@ -2,7 +2,7 @@
 // host against brute force: for tori L1 x L2 and hypercubes Q_k, each
 // vertex's neighbours are sorted by label, and the edge-major index of the
 // flip-flop target (w, v) and of the persistent target (w, 2w - v) is found by
-// searching w's sorted list.  The device intrinsics are given host
+// searching w's sorted list; the hypercube walk is also checked in reverse.  The device intrinsics are given host
 // definitions with the same meaning.  Prints "ok <count>" or the first
 // mismatch; exits non-zero on a mismatch.
 #include <algorithm>
@@ -75,6 +75,17 @@ static bool check_cube(int k)
             if ((v ^ (1 << b)) != w || cw.target(b, n) != want) {
                 std::printf("cube k=%d v=%d j=%d: bit %d (w %d/%d) target %d/%d\n", k, v, j, b, v ^ (1 << b), w,
                             cw.target(b, n), want);
+                return false;
+            }
+        }
+        // the reverse walk visits the same positions from the last one down
+        CubeWalk rw(v, k);
+        for (int j = k - 1; j >= 0; --j) {
+            ++checked;
+            const int b = rw.prev_bit();
+            if ((v ^ (1 << b)) != nb[v][j]) {
+                std::printf("cube k=%d v=%d reverse position %d: bit %d (w %d/%d)\n", k, v, j, b, v ^ (1 << b),
+                            nb[v][j]);
                 return false;
             }
         }
