@@ -253,10 +253,11 @@ __device__ __forceinline__ float sp_diag(const SparsePow &a, float) { return a.d
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return fpconv::f32_to_f64(x); }
 
-// VEC adjacent columns per thread, moved as one vector (16 bytes)
+// VEC adjacent columns per thread, moved as one vector
 template <typename T, int VEC> struct SpVec;
 template <> struct SpVec<double, 2> { using V = double2; };
 template <> struct SpVec<float, 4> { using V = float4; };
+template <> struct SpVec<float, 2> { using V = float2; };
 template <> struct SpVec<double, 1> { using V = double; };
 template <> struct SpVec<float, 1> { using V = float; };
 
@@ -1071,8 +1072,9 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
         if (c128) k_taylor_identity<double><<<ew_grid(nn), 256, 0, st>>>(n, Re.as<double>(), Im.as<double>(), static_cast<double *>(Qa));
         else k_taylor_identity<float><<<ew_grid(nn), 256, 0, st>>>(n, Re.as<double>(), Im.as<double>(), static_cast<float *>(Qa));
         if ((s = hw_cuda(cudaGetLastError(), "Taylor init")) != HW_OK) return s;
-        // 16-byte column vectors when every row starts on a vector boundary
-        const int vec = c128 ? (n % 2 == 0 ? 2 : 1) : (n % 4 == 0 ? 4 : 1);
+        // two adjacent columns per thread when every row starts on a pair boundary
+        // (two floats, not four, for complex64: four held 116 registers, two CTAs per SM)
+        const int vec = n % 2 == 0 ? 2 : 1;
         const dim3 grid((n + kSpRows - 1) / kSpRows, (n + kSpCols * vec - 1) / (kSpCols * vec));
         for (int k = 1; k <= m_deg; ++k) {
             SparsePow a;
@@ -1099,9 +1101,9 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
                     else k_taylor_sparse<double, false, 1><<<grid, kSpCols, 0, st>>>(a);
                 }
             } else {
-                if (vec == 4) {
-                    if (g->weighted) k_taylor_sparse<float, true, 4><<<grid, kSpCols, 0, st>>>(a);
-                    else k_taylor_sparse<float, false, 4><<<grid, kSpCols, 0, st>>>(a);
+                if (vec == 2) {
+                    if (g->weighted) k_taylor_sparse<float, true, 2><<<grid, kSpCols, 0, st>>>(a);
+                    else k_taylor_sparse<float, false, 2><<<grid, kSpCols, 0, st>>>(a);
                 } else {
                     if (g->weighted) k_taylor_sparse<float, true, 1><<<grid, kSpCols, 0, st>>>(a);
                     else k_taylor_sparse<float, false, 1><<<grid, kSpCols, 0, st>>>(a);

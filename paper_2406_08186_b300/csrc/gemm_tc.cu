@@ -66,9 +66,10 @@ constexpr int kBTile = TN * TK * 2;                       // 16 KB per B slice
 constexpr int kRingBytes = 216 * 1024;                    // shared-memory ring
 constexpr int kMaxStages = 8;
 constexpr int kSmemSlack = 2048;                          // alignment of the ring base + margin
-constexpr int kAccWarps = 8;                              // warps 6..13: accumulation (6..9 also epilogues)
+constexpr int kAccWarps = 8;                              // warps 6..13: accumulation, then epilogues
 constexpr int kThreads = 192 + 32 * kAccWarps;
 constexpr int kTmemCols = 2 * TN;                         // two accumulators
+constexpr int kEpiWarps = 12;                             // warps 0-3 and 6-13
 constexpr uint64_t kWaitLimitNs = 2000000000ull;          // bounded mbarrier waits (2 s)
 
 enum { FMT_BF16 = 0, FMT_F16 = 1 };
@@ -424,7 +425,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&bar_tfull[b]), 1);
-            mbar_init(smem_u32(&bar_tempty[b]), 8);  // one arrival per epilogue warp
+            mbar_init(smem_u32(&bar_tempty[b]), kEpiWarps);  // one arrival per epilogue warp
         }
         timed_out = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");   // visible to the async proxy
@@ -506,16 +507,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
         // warps 0-3 and 6-13: first the previous power's accumulation (its
         // slices are this GEMM's A operand, so mostly L2 hits), rows spread
         // over all CTAs, while the tensor cores work on the first tile; then
-        // warps 0-3 and 6-9 run the epilogues, warp w on TMEM lane quadrant
-        // w % 4 and half of the tile's columns
+        // the epilogues, warp w on TMEM lane quadrant w % 4 and a third of the
+        // tile's columns (warps 0-3 the first, 6-9 the second, 10-13 the last)
         if (a.accU)
             acc_rows<FMT, NA>(a.n, a.accQ[0], a.accQ[1], a.accQ[2], a.ldq, a.acc_coef, a.accU, int(blockIdx.x),
                               int(gridDim.x), warp < 4 ? int(threadIdx.x) : int(threadIdx.x) - 64,
                               128 + 32 * kAccWarps);
-        const bool epi = warp < 10;
-        const int quad = warp & 3, cb = (warp < 4) ? 0 : TN / 2;
+        // the tile's 256 columns in three parts of 16-column chunks (6, 5, 5)
+        const int quad = warp & 3, third = (warp < 4) ? 0 : (warp < 10 ? 1 : 2);
+        const int cb = third == 0 ? 0 : (third == 1 ? 96 : 176), ce = third == 0 ? 96 : (third == 1 ? 176 : 256);
         uint32_t li = 0;
-        for (int t = cid; t < ntiles && epi; t += ncl, ++li) {
+        for (int t = cid; t < ntiles; t += ncl, ++li) {
             const int b = int(li & 1u);
             if (!mbar_wait(smem_u32(&bar_tfull[b]), (li >> 1) & 1u)) {
                 *tmo = 1;
@@ -523,7 +525,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int2 ct = a.tiles[t];
-            epilogue_tile<FMT, NA>(a, ct.x * TM, ct.y * TN, tmem + uint32_t(b * TN), quad, lane, cb, cb + TN / 2);
+            epilogue_tile<FMT, NA>(a, ct.x * TM, ct.y * TN, tmem + uint32_t(b * TN), quad, lane, cb, ce);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0)

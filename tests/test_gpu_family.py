@@ -229,3 +229,22 @@ def test_complex128_sums_on_every_path_of_the_integer_sum(hw):
     assert torch.equal(a[0], b[0])
     assert np.max(np.abs(a[0].numpy() - ref)) <= TOL128
     G.free()
+
+
+@pytest.mark.parametrize("name,g", [("reg18_1000", synth.random_regular(1000, 18, seed=3)),   # 1000 = 31 x 32 + 8
+                                    ("reg24_777", synth.random_regular(778, 24, seed=5)),
+                                    ("Q18", synth.hypercube(18))])
+def test_complex128_high_degree_two_pass_matches_oracle(hw, name, g):
+    # complex128 Grover of degree 17..24 takes the two-pass kernel (sums, then
+    # the rows again last-first); regular graphs through the table, the
+    # hypercube from its labels
+    G = _graph(hw, g)
+    ar = oracle.Arcs(*g)
+    psi0 = synth.random_state(ar.num_arcs, seed=8)
+    marked = [2, G.n // 3, G.n - 1]
+    steps = 11
+    a = _evolve(hw, G, psi0, steps, hw.HW_C128, 0, marked, addressing=0, record=True)
+    ref, rec_ref = oracle.coined_evolve(ar, psi0, steps, 0, marked, record=True)
+    assert np.max(np.abs(a[0].numpy() - ref)) <= TOL128
+    assert np.max(np.abs(a[2].numpy() - rec_ref)) <= TOL128
+    G.free()
