@@ -955,11 +955,14 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
     pdl_trigger();
 }
 
-// Grover on the hypercube Q_K, degree K known at compile time: a thread per
-// vertex loads its K rows into registers at once and writes the K outputs
-// from them, so each row is read once (k_coined_em_rt reads the rows twice).
-// The arithmetic is k_coined_em_rt's: the same sums in the same order.
-template <typename R, int K>
+// Grover on a regular graph of degree K (K known at compile time): a thread
+// per vertex loads its K rows into registers at once and writes the K
+// outputs from them, so each row is read once (k_coined_em_rt reads the rows
+// twice).  Hypercubes take the targets from the labels (kAddrCube), other
+// graphs (and the tables' addressing of hypercubes) from revE; both give the
+// same bits.  complex128 sums: grouped_sum2_fixed (groups of four, folded
+// four at a time by the integer sum).
+template <typename R, int K, int ADDR>
 __global__ void __launch_bounds__(kThreads) k_coined_em_cube(EmArgs a)
 {
     using V = typename Cx<R>::T;
@@ -974,6 +977,9 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_cube(EmArgs a)
         for (int j = 0; j < K; ++j) p[j] = in[j * n + v];
         const int mi = find_marked(a.mk, v);
         CubeWalk cw(v, K);
+        auto target = [&](int j) {
+            return (ADDR == kAddrCube) ? cw.target(cw.next_bit(), n) : __ldg(a.revE + j * n + v);
+        };
         if (mi >= 0) {
             if (a.rec_part && a.rec_slot >= 0) {
                 double acc = 0.0;
@@ -982,7 +988,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_cube(EmArgs a)
                 a.rec_part[a.rec_slot * a.mk.n + mi] = acc;
             }
 #pragma unroll
-            for (int j = 0; j < K; ++j) out[cw.target(cw.next_bit(), n)] = mkv<V, R>(-p[j].x, -p[j].y);
+            for (int j = 0; j < K; ++j) out[target(j)] = mkv<V, R>(-p[j].x, -p[j].y);
         } else {
             R sx, sy;
             if constexpr (sizeof(R) == 8) {
@@ -998,8 +1004,7 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_cube(EmArgs a)
             }
             const R f = em_weight<R>(a);
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-                out[cw.target(cw.next_bit(), n)] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
+            for (int j = 0; j < K; ++j) out[target(j)] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
         }
     }
     pdl_trigger();
@@ -1152,38 +1157,39 @@ hw_status launch_layout(const hw_graph *g, hw_dtype dt, const void *in, void *ou
     return hw_cuda(cudaGetLastError(), "k_layout launch");
 }
 
-// Which hypercube degrees take k_coined_em_cube (rows in registers) rather
-// than the two-pass k_coined_em_rt, from per-step times on Q_12 .. Q_20:
+// Which degrees take k_coined_em_cube (rows in registers) rather than the
+// two-pass k_coined_em_rt, from per-step times on Q_12 .. Q_20:
 // complex64 from degree 16 (Q_16 4.4 vs 7.9 us, Q_20 52.9 vs 68.8 us; the
 // arc-major lane groups stay faster below 16), complex128 up to degree 16
-// (Q_16 11.3 vs 14.5 us); above 16 the 80+ registers of complex128 rows leave
-// too few warps per SM and the two passes win (Q_20 159 vs 165 us).
+// (Q_16 11.3 vs 14.5 us, 8.7 us with the folded group sums); above 16 the
+// 80+ registers of complex128 rows leave too few warps per SM and the two
+// passes win (Q_20 159 vs 165 us).
 template <typename R> constexpr bool cube_regs_kernel(int d)
 {
     return sizeof(R) == 8 ? (d >= 9 && d <= 16) : (d >= 16 && d <= 20);
 }
 
-template <typename R>
+template <typename R, int ADDR>
 static void launch_cube(int d, dim3 grid, const EmArgs &a, cudaStream_t st)
 {
     if constexpr (sizeof(R) == 8) {
         switch (d) {
-        case 9: launch_pdl(k_coined_em_cube<R, 9>, grid, dim3(kThreads), 0, st, a); break;
-        case 10: launch_pdl(k_coined_em_cube<R, 10>, grid, dim3(kThreads), 0, st, a); break;
-        case 11: launch_pdl(k_coined_em_cube<R, 11>, grid, dim3(kThreads), 0, st, a); break;
-        case 12: launch_pdl(k_coined_em_cube<R, 12>, grid, dim3(kThreads), 0, st, a); break;
-        case 13: launch_pdl(k_coined_em_cube<R, 13>, grid, dim3(kThreads), 0, st, a); break;
-        case 14: launch_pdl(k_coined_em_cube<R, 14>, grid, dim3(kThreads), 0, st, a); break;
-        case 15: launch_pdl(k_coined_em_cube<R, 15>, grid, dim3(kThreads), 0, st, a); break;
-        default: launch_pdl(k_coined_em_cube<R, 16>, grid, dim3(kThreads), 0, st, a); break;
+        case 9: launch_pdl(k_coined_em_cube<R, 9, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 10: launch_pdl(k_coined_em_cube<R, 10, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 11: launch_pdl(k_coined_em_cube<R, 11, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 12: launch_pdl(k_coined_em_cube<R, 12, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 13: launch_pdl(k_coined_em_cube<R, 13, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 14: launch_pdl(k_coined_em_cube<R, 14, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 15: launch_pdl(k_coined_em_cube<R, 15, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        default: launch_pdl(k_coined_em_cube<R, 16, ADDR>, grid, dim3(kThreads), 0, st, a); break;
         }
     } else {
         switch (d) {
-        case 16: launch_pdl(k_coined_em_cube<R, 16>, grid, dim3(kThreads), 0, st, a); break;
-        case 17: launch_pdl(k_coined_em_cube<R, 17>, grid, dim3(kThreads), 0, st, a); break;
-        case 18: launch_pdl(k_coined_em_cube<R, 18>, grid, dim3(kThreads), 0, st, a); break;
-        case 19: launch_pdl(k_coined_em_cube<R, 19>, grid, dim3(kThreads), 0, st, a); break;
-        default: launch_pdl(k_coined_em_cube<R, 20>, grid, dim3(kThreads), 0, st, a); break;
+        case 16: launch_pdl(k_coined_em_cube<R, 16, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 17: launch_pdl(k_coined_em_cube<R, 17, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 18: launch_pdl(k_coined_em_cube<R, 18, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        case 19: launch_pdl(k_coined_em_cube<R, 19, ADDR>, grid, dim3(kThreads), 0, st, a); break;
+        default: launch_pdl(k_coined_em_cube<R, 20, ADDR>, grid, dim3(kThreads), 0, st, a); break;
         }
     }
 }
@@ -1207,8 +1213,10 @@ static void launch_em(int d, int addr, const EmArgs &a, cudaStream_t st)
     case 7: launch_pdl(k_coined_em<R, 7, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
     case 8: launch_pdl(k_coined_em<R, 8, COIN, kAddrTable>, grid, dim3(kThreads), 0, st, a); break;
     default:   // Grover only
-        if (addr == kAddrCube && cube_regs_kernel<R>(d))
-            launch_cube<R>(d, grid, a, st);
+        if (cube_regs_kernel<R>(d) && addr == kAddrCube)
+            launch_cube<R, kAddrCube>(d, grid, a, st);
+        else if (cube_regs_kernel<R>(d))
+            launch_cube<R, kAddrTable>(d, grid, a, st);
         else if (addr == kAddrCube)
             launch_pdl(k_coined_em_rt<R, kAddrCube>, grid, dim3(kThreads), 0, st, a);
         else

@@ -223,7 +223,8 @@ __global__ void k_pack_u(int64_t total, const double *__restrict__ re, const dou
 // block by row block inside one 256-column slab before the next slab, so the
 // rows gathered by the CTAs in flight (a slab is n x 256 values) stay in L2.
 // complex128: Q in double, an unweighted row's neighbour sum in groups of
-// four rounded once (sum4.cuh), then one multiply by -gamma tau / k; weighted
+// four rounded once (sum4.cuh), the group sums added in order, then one
+// multiply by -gamma tau / k; weighted
 // rows take one FMA per neighbour.  complex64: Q in float, the sums and
 // products in float, the accumulation into U in double.
 constexpr int kSpRows = 8;       // rows per CTA
@@ -281,8 +282,9 @@ __device__ __forceinline__ void sp_store(T *p, const T (&x)[VEC])
 }
 
 // neighbour sum of one column, terms x[0..deg) with deg <= kSpGather:
-// complex128 unweighted in grouped_sum1's groups of four and order, with
-// constant indices so that x stays in registers; otherwise sequential from 0
+// complex128 unweighted in groups of four rounded once (sum4_rn, a short last
+// group padded with -0), the group sums added in order; otherwise sequential
+// from 0; constant indices, so that x stays in registers
 template <typename T, bool WEIGHTED, int VEC>
 __device__ __forceinline__ T sp_sum(const SparsePow &a, int e0, int deg, const T (&x)[kSpGather][VEC], int k)
 {
