@@ -848,7 +848,13 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
     pdl_wait();
     if (live) {
 #pragma unroll
-        for (int j = 0; j < D; ++j) p[j] = in[j * n + v];
+        for (int j = 0; j < D; ++j) {
+            // complex128: each row is read once and the two state buffers do
+            // not fit L2, so loads and stores stream (evict first); complex64
+            // states stay in L2 from step to step and keep the default
+            if constexpr (sizeof(R) == 8) p[j] = __ldcs(in + j * n + v);
+            else p[j] = in[j * n + v];
+        }
         const int mi = find_marked(a.mk, v);
         if (mi >= 0) {
             if (a.rec_part && a.rec_slot >= 0) {
@@ -875,7 +881,11 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
             }
             const R f = em_weight<R>(a);
 #pragma unroll
-            for (int j = 0; j < D; ++j) out[r[j]] = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
+            for (int j = 0; j < D; ++j) {
+                const V o = mkv<V, R>(fma(f, sx, -p[j].x), fma(f, sy, -p[j].y));
+                if constexpr (sizeof(R) == 8) __stcs(out + r[j], o);
+                else out[r[j]] = o;
+            }
         } else {
             const R scale = R(1) / sqrt(R(D));
 #pragma unroll
@@ -892,6 +902,33 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
         }
     }
     pdl_trigger();
+}
+
+// an L2 access policy that marks the lines a load brings in as evict-last,
+// and a complex128 load under it
+__device__ __forceinline__ uint64_t l2_evict_last_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ double2 ld_keep(const double2 *p, uint64_t pol)
+{
+    double2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float2 ld_keep(const float2 *p, uint64_t pol)
+{
+    float2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(v.x), "=f"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
 }
 
 // Grover, any degree: thread per vertex, a pass for the sum and a pass (rows
@@ -928,7 +965,10 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
             if constexpr (sizeof(R) == 8) {
                 // complex128: groups of four rows summed by integer operations
                 // (sum4.cuh), the group sums added in double
-                sum4::grouped_sum2(d, [&](int j) { return in[j * n + v]; }, sx, sy);
+                // first reads of the rows marked evict-last in L2: the second
+                // pass reads them again
+                const uint64_t keep = l2_evict_last_policy();
+                sum4::grouped_sum2(d, [&](int j) { return ld_keep(in + j * n + v, keep); }, sx, sy);
             } else {
                 const V p0 = in[v];
                 sx = p0.x;
@@ -946,9 +986,11 @@ __global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
             CubeWalk cw(v, d);
 #pragma unroll 4
             for (int j = d - 1; j >= 0; --j) {
-                const V p = in[j * n + v];
+                // the rows' last use (evict first) and streaming stores, so
+                // that L2 keeps the rows the other warps have still to re-read
+                const V p = __ldcs(in + j * n + v);
                 const int r = (ADDR == kAddrCube) ? cw.target(cw.prev_bit(), n) : __ldg(a.revE + j * n + v);
-                out[r] = mkv<V, R>(fma(f, sx, -p.x), fma(f, sy, -p.y));
+                __stcs(out + r, mkv<V, R>(fma(f, sx, -p.x), fma(f, sy, -p.y)));
             }
         }
     }
