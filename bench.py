@@ -445,9 +445,16 @@ def sub_torus64(hw, reps, warmup, with_cpu):
         torch.cuda.synchronize()
     t = e[0].elapsed_time(e[1]) / 1e3 / reps
     arcs = G.num_arcs
+    # the one-launch walk runs on one 16-CTA cluster: its FP64 ceiling is 16/148
+    # of the GPU's measured FP64 rate (8 FMAs per vertex and step)
+    fp64 = hw.hw_measure_fp64()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fmas = 8.0 * n * 100
     res = {"workload": "torus64_center", "metric": METRIC, "unit": UNIT, "value": arcs * 100 / t,
            "us_per_run": t * 1e6, "us_per_walk_step": t / 100 * 1e6, "reps": reps, "dtype": "f64",
            "roofline": {"bound": "latency", "bytes_per_walk_step": arcs * 32,
+                        "fp64_of_16_sms": {"achieved": fmas / t, "peak": fp64 * 16 / sms, "unit": "FMA/s",
+                                           "frac": fmas / t / (fp64 * 16 / sms), "fma_per_run": fmas},
                         "note": "the whole walk in one launch (one 16-CTA thread-block cluster holds the 256 KiB "
                                 "state in shared memory, a hardware cluster barrier per step), then one "
                                 "probability launch; per step the FP64 FMAs of 4096 vertices on the cluster's "

@@ -83,6 +83,31 @@ def test_cluster_walk_in_place_and_persistent_shift(hw):
     G.free()
 
 
+def test_configuration1_in_one_launch_dihedral_symmetry(hw):
+    # configuration 1: the 64 x 64 torus from the four arcs of (32, 32), 100
+    # steps; besides the oracle, the probabilities are symmetric under the
+    # reflections x -> 64 - x, y -> 64 - y and the swap x <-> y about (32, 32)
+    import torch
+    n, eu, ev = synth.torus(64)
+    G = _graph(hw, (n, eu, ev))
+    psi0 = synth.state_on_vertex_arcs(synth.arc_offsets(n, eu, ev), 32 * 64 + 32)
+    x = torch.from_numpy(psi0).cuda()
+    y = torch.empty_like(x)
+    prob = torch.empty(n, dtype=torch.float64, device="cuda")
+    hw.hw_coined_evolve(G, 0, [], 2, 1, 100, x, y)
+    hw.hw_probability(G, n, 2, 1, y, prob)
+    ar = oracle.Arcs(n, eu, ev)
+    ref = oracle.prob_coined(ar, oracle.coined_evolve(ar, psi0, 100))
+    p = prob.cpu().numpy()
+    assert np.max(np.abs(p - ref)) <= 1e-12
+    P = p.reshape(64, 64)
+    idx = (64 - np.arange(64)) % 64
+    assert np.max(np.abs(P - P[idx, :])) <= 1e-13
+    assert np.max(np.abs(P - P[:, idx])) <= 1e-13
+    assert np.max(np.abs(P - P.T)) <= 1e-13
+    G.free()
+
+
 def test_cluster_walk_record_single_mark_and_one_step(hw):
     import torch
     g = synth.torus(64)
