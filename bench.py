@@ -48,10 +48,10 @@ UNIT = "arc-updates/s"
 # measured on; a changed kernel reports null until it is measured again.
 TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
-    # block row per torus row, complex128 sums by integer operations), one
-    # launch, cold L2
-    ("c128", "f3e939a0195c9aadbd698cdcad55487394a0ca95"): 67132416 + 17325824,
-    ("c64", "f3e939a0195c9aadbd698cdcad55487394a0ca95"): 33566464 + 195840,
+    # block row per torus row, complex128 sums by integer operations and
+    # streaming loads and stores), one launch, cold L2
+    ("c128", "158875b1c12157bb7eb27d9bfe2b0223d7ada1ab"): 67133184 + 16111872,
+    ("c64", "158875b1c12157bb7eb27d9bfe2b0223d7ada1ab"): 33566464 + 326912,
 }
 
 
