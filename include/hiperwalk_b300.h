@@ -255,14 +255,17 @@ hw_status hw_coined_sample(const hw_graph *g, hw_coin coin, const int32_t *marke
  * (Sec. 3.1), dense, by a truncated Taylor series with scaling and squaring:
  * U = (sum_{k<=m} (-i H time/2^s)^k / k!)^(2^s).
  *   U_out    DEVICE [n][n] row-major complex (dt), caller-owned
- *   dt       HW_C128: products in double precision;
- *            HW_C64: products of the powers of H on the tensor cores from
- *            16-bit slices of their operands (opts->gemm_mode, default fp16 x 2)
- *            with fp32 accumulation; Taylor sums and squarings in double;
- *            U rounded to complex64 at the end.
- * Scratch: a few n x n real buffers from the stream-ordered allocator.
- * With HW_C64 the call synchronises `stream` before returning, to report a
- * device-side pipeline timeout of the tensor-core kernel as HW_ETIMEDOUT.
+ *   dt       HW_C128: the powers (H time / 2^s)^k / k! in double precision,
+ *            by default as sparse x dense products with the graph;
+ *            HW_C64: by default the powers on the tensor cores from 16-bit
+ *            slices of their operands (opts->gemm_mode, default fp16 x 2)
+ *            with fp32 accumulation; opts->taylor_powers chooses the other
+ *            form (dense FP64 GEMMs for HW_C128, sparse x dense products in
+ *            float for HW_C64).  Taylor sums and squarings in double; U
+ *            rounded to complex64 at the end for HW_C64.
+ * Scratch: four or five n x n real buffers from the stream-ordered allocator.
+ * On the tensor-core path the call synchronises `stream` before returning,
+ * to report a device-side pipeline timeout of that kernel as HW_ETIMEDOUT.
  * Errors: HW_EINVAL, HW_EUNSUPPORTED (n > 32768), HW_ENOMEM, HW_ECUDA,
  * HW_ETIMEDOUT.
  */

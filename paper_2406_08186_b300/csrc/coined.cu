@@ -15,6 +15,7 @@
 #include <mutex>
 #include <vector>
 
+#include "cache_hints.cuh"
 #include "family.cuh"
 #include "internal.h"
 #include "sum4.cuh"
@@ -902,33 +903,6 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
         }
     }
     pdl_trigger();
-}
-
-// an L2 access policy that marks the lines a load brings in as evict-last,
-// and a complex128 load under it
-__device__ __forceinline__ uint64_t l2_evict_last_policy()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ double2 ld_keep(const double2 *p, uint64_t pol)
-{
-    double2 v;
-    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
-                 : "=d"(v.x), "=d"(v.y)
-                 : "l"(p), "l"(pol));
-    return v;
-}
-
-__device__ __forceinline__ float2 ld_keep(const float2 *p, uint64_t pol)
-{
-    float2 v;
-    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
-                 : "=f"(v.x), "=f"(v.y)
-                 : "l"(p), "l"(pol));
-    return v;
 }
 
 // Grover, any degree: thread per vertex, a pass for the sum and a pass (rows

@@ -36,6 +36,7 @@
 #include <map>
 #include <vector>
 
+#include "cache_hints.cuh"
 #include "family.cuh"
 #include "internal.h"
 #include "sum4.cuh"
@@ -278,7 +279,9 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
         }
         R sx, sy;
         if constexpr (sizeof(R) == 8) {   // complex128: integer group sums (sum4.cuh)
-            sum4::grouped_sum2(d, [&](int j) { return in[j * n + v]; }, sx, sy);
+            // the rows are read again below: keep them in L2
+            const uint64_t keep = l2_evict_last_policy();
+            sum4::grouped_sum2(d, [&](int j) { return ld_keep(in + j * n + v, keep); }, sx, sy);
         } else {
             const V p0 = in[v];
             sx = p0.x;
@@ -291,13 +294,26 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
             }
         }
         CubeWalk cw(v, d);
+        if constexpr (sizeof(R) == 8) {
+            // complex128: the rows again, last first and as their last use,
+            // with streaming stores (the plain path's k_coined_em_rt does the same)
 #pragma unroll 4
-        for (int j = 0; j < d; ++j) {
-            const V p = in[j * n + v];
-            V c;
-            c.x = fma(f, sx, -p.x);
-            c.y = fma(f, sy, -p.y);
-            out[cube ? cw.target(cw.next_bit(), n) : revE[j * n + v]] = c;
+            for (int j = d - 1; j >= 0; --j) {
+                const V p = __ldcs(in + j * n + v);
+                V c;
+                c.x = fma(f, sx, -p.x);
+                c.y = fma(f, sy, -p.y);
+                __stcs(out + (cube ? cw.target(cw.prev_bit(), n) : revE[j * n + v]), c);
+            }
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < d; ++j) {
+                const V p = in[j * n + v];
+                V c;
+                c.x = fma(f, sx, -p.x);
+                c.y = fma(f, sy, -p.y);
+                out[cube ? cw.target(cw.next_bit(), n) : revE[j * n + v]] = c;
+            }
         }
     }
 }
