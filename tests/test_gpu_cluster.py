@@ -126,3 +126,27 @@ def test_cluster_walk_record_single_mark_and_one_step(hw):
     with pytest.raises(hw.HWError):
         hw.hw_coined_evolve(G, 0, [], 2, 1, 3, x, x, opts={"launch_mode": 2})
     G.free()
+
+
+def test_cluster_walk_long_marked_list(hw):
+    # more marked vertices than travel with the launch (> 16): the list is
+    # searched in device memory; records of every marked vertex summed
+    import torch
+    g = synth.torus(32)
+    G = _graph(hw, g)
+    ar = oracle.Arcs(*g)
+    marked = list(range(3, 1024, 47))            # 22 vertices
+    psi0 = synth.random_state(ar.num_arcs, seed=21)
+    x = torch.from_numpy(psi0).cuda()
+    outs = []
+    for mode in (0, 1):
+        y = torch.empty_like(x)
+        rec = torch.empty(30, dtype=torch.float64, device="cuda")
+        hw.hw_coined_evolve(G, 0, marked, 2, 1, 30, x, y, rec, opts={"launch_mode": mode})
+        outs.append((y, rec))
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    ref, rr = oracle.coined_evolve(ar, psi0, 30, marked=marked, record=True)
+    assert np.max(np.abs(outs[0][0].cpu().numpy() - ref)) <= 1e-12
+    assert np.max(np.abs(outs[0][1].cpu().numpy() - rr)) <= 1e-12
+    G.free()
