@@ -142,10 +142,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_coined_cluster(ClusterArgs a)
                     for (int j = 1; j < D; ++j) sum += p[j];
                 }
             }
+            // marked: fma(0, 0, -p) = -p, one FMA per output either way (a
+            // select against a separate -p would negate every row on the FP64 pipe)
+            const R fv = marked ? R(0) : f;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const uint32_t g = tgt[lv * D + j];
-                const R o = marked ? -p[j] : fma(f, sum, -p[j]);
+                const R o = fma(fv, sum, -p[j]);
                 const uint32_t e = (g & 0xFFFFFFu) * 2u + uint32_t(comp);
                 // arcs owned by this CTA take a plain shared-memory store
                 if ((g >> 24) == uint32_t(rank)) nxt[e] = o;

@@ -169,44 +169,41 @@ HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
 // order): groups of four consecutive terms summed by sum4_rn (a short last
 // group padded with -0, which leaves any sum unchanged), the group sums
 // added in order in double.  The next group's terms are fetched before the
-// current group is summed, so its loads overlap the integer work.
+// current group is summed, so its loads overlap the integer work; the first
+// group's sum starts the total (no addition to 0.0 on the FP64 unit).
+template <typename F>
+HW_HD void load_group(int j0, int count, F &t, double (&x)[4], double (&y)[4])
+{
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (j0 + u < count) {
+            const auto p = t(j0 + u);
+            x[u] = p.x;
+            y[u] = p.y;
+        } else {
+            x[u] = -0.0;
+            y[u] = -0.0;
+        }
+    }
+}
+
 template <typename F>
 HW_HD void grouped_sum2(int count, F t, double &sx, double &sy)
 {
     double cx[4], cy[4], nx[4], ny[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        if (u < count) {
-            const auto p = t(u);
-            cx[u] = p.x;
-            cy[u] = p.y;
-        } else {
-            cx[u] = -0.0;
-            cy[u] = -0.0;
-        }
-    }
-    sx = 0.0;
-    sy = 0.0;
-    for (int j0 = 0; j0 < count; j0 += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (j0 + 4 + u < count) {
-                const auto p = t(j0 + 4 + u);
-                nx[u] = p.x;
-                ny[u] = p.y;
-            } else {
-                nx[u] = -0.0;
-                ny[u] = -0.0;
-            }
-        }
-        const double gx = sum4_rn(cx[0], cx[1], cx[2], cx[3]), gy = sum4_rn(cy[0], cy[1], cy[2], cy[3]);
-        sx = (j0 == 0) ? gx : sx + gx;
-        sy = (j0 == 0) ? gy : sy + gy;
+    load_group(0, count, t, cx, cy);
+    load_group(4, count, t, nx, ny);
+    sx = sum4_rn(cx[0], cx[1], cx[2], cx[3]);
+    sy = sum4_rn(cy[0], cy[1], cy[2], cy[3]);
+    for (int j0 = 4; j0 < count; j0 += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             cx[u] = nx[u];
             cy[u] = ny[u];
         }
+        load_group(j0 + 4, count, t, nx, ny);
+        sx += sum4_rn(cx[0], cx[1], cx[2], cx[3]);
+        sy += sum4_rn(cy[0], cy[1], cy[2], cy[3]);
     }
 }
 
