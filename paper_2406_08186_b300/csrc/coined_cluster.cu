@@ -6,13 +6,26 @@
 // thread-block cluster of up to 16 CTAs keeps the whole state in the
 // distributed shared memory of its CTAs and runs every step in one launch:
 // CTA c owns a contiguous range of vertices and their arcs (arc-major, as in
-// the basis), in two buffers at the same shared-memory offsets in every CTA.
-// A step reads the owned arcs from the current buffer, applies the coin
+// the basis), in three buffers at the same shared-memory offsets in every
+// CTA.  Step t reads the owned arcs from buffer (t-1) mod 3, applies the coin
 // (Grover, -I on marked vertices) and stores each output at its shifted arc
-// (reversal or persistent table) in the next buffer of the CTA that owns that
-// arc, with st.shared::cluster; the hardware cluster barrier (release /
-// acquire) then separates the steps, so no wait in this kernel is a software
-// spin.  The state enters from and leaves to global memory once per call.
+// (reversal or persistent table) in buffer t mod 3 of the CTA that owns that
+// arc: a plain shared-memory store when that is this CTA, else st.async,
+// which also counts the bytes on the owner's mbarrier t mod 3.  A CTA then
+// waits only for the bytes its own arcs receive from other CTAs (known from
+// the table), not for the whole cluster.
+//
+// Why three buffers and no other handshake: a shift moves the walker from v
+// to the head w of its arc, and the reverse arc (w, v) exists, so CTA c
+// stores into CTA r exactly when r stores into c.  When c starts step t it
+// has received r's outputs of step t-1, which r stores only after the CTA
+// barrier that ends its step t-2, i.e. after r has read buffer (t-3) mod 3 =
+// t mod 3 for the last time; and r cannot run ahead of c by more than one
+// step, so each mbarrier only ever counts the bytes of one step.  Every wait
+// is bounded (a timeout sets the graph's error word and ends the walk), and a
+// hardware cluster barrier before exit keeps every CTA's shared memory alive
+// while a peer may still address it.  The state enters from and leaves to
+// global memory once per call.
 //
 // The coin arithmetic is the edge-major kernels' (a sequential sum from arc
 // 0, for complex128 degree 4 the integer four-term sum rounded once, then one
@@ -47,7 +60,10 @@ struct ClusterArgs {
     double w;                 // 2/d
     float wf;
     MarkedList mk;
+    int *err;                 // set when a bounded wait runs out of time
 };
+
+constexpr uint64_t kWaitNs = 2000000000ull;   // bounded mbarrier waits (2 s)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -76,60 +92,132 @@ __device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank)
     return r;
 }
 
-__device__ __forceinline__ void st_peer(uint32_t addr, double v)
+// st.async: store to a peer CTA's shared memory and count the bytes on the
+// peer's mbarrier (both addresses in the shared::cluster window)
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t bar)
 {
-    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+                 "l"(__double_as_longlong(v)), "r"(bar)
+                 : "memory");
 }
 
-__device__ __forceinline__ void st_peer(uint32_t addr, float v)
+__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar)
 {
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// the one local arrival of a phase, announcing the bytes peers will deliver
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// true once the phase with this parity has completed (acquire at cluster
+// scope: the peers' st.async data is visible after it); false after kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 0) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > kWaitNs) return false;
+        }
+    }
 }
 
 template <typename R> __device__ __forceinline__ R weight(const ClusterArgs &a);
 template <> __device__ __forceinline__ double weight<double>(const ClusterArgs &a) { return a.w; }
 template <> __device__ __forceinline__ float weight<float>(const ClusterArgs &a) { return a.wf; }
 
-// Shared memory of a CTA: buffer 0, buffer 1 (vpc D amplitudes each), then the
-// packed target of every owned arc: (owner rank << 24) | arc index in the owner.
+// Shared memory of a CTA: buffers 0, 1, 2, each two planes (real parts,
+// imaginary parts) of D rows of vpc values, arc position j of local vertex lv
+// at row j, column lv; then the packed target of every owned arc, in the same
+// [j][lv] order: (owner rank << 24) | (position in the owner's list) vpc +
+// (local vertex in the owner); three mbarriers (static shared memory, same
+// offset in every CTA).  A warp works on 32 consecutive vertices and one
+// component, so its loads are one row segment, and where the shift keeps
+// neighbours together (the torus and the hypercube) its stores are too.
 template <typename R, int D>
-__global__ void __launch_bounds__(kMaxThreads) k_coined_cluster(ClusterArgs a)
+__global__ void __launch_bounds__(kMaxThreads, 1) k_coined_cluster(ClusterArgs a)
 {
     using V = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int cap = a.vpc * D;
-    V *buf0 = reinterpret_cast<V *>(smem);
-    V *buf1 = buf0 + cap;
-    uint32_t *tgt = reinterpret_cast<uint32_t *>(buf1 + cap);
+    __shared__ __align__(8) uint64_t bars[3];
+    __shared__ int s_local;
+    const int vpc = a.vpc;
+    const int plane = vpc * D;                 // values per component plane
+    R *buf0 = reinterpret_cast<R *>(smem);     // buffer b starts at buf0 + 2 b plane
+    uint32_t *tgt = reinterpret_cast<uint32_t *>(buf0 + 6 * plane);
     const int rank = int(cta_rank());
-    const int v0 = rank * a.vpc;
-    const int nv = max(0, min(a.n, v0 + a.vpc) - v0);
+    const int v0 = rank * vpc;
+    const int nv = max(0, min(a.n, v0 + vpc) - v0);
     const int arcs = nv * D;
     const V *in = static_cast<const V *>(a.in);
-    for (int i = threadIdx.x; i < arcs; i += blockDim.x) {
-        const int t = __ldg(a.shift + v0 * D + i);   // global arc receiving arc v0 D + i
-        const int r = (t / D) / a.vpc;
-        tgt[i] = (uint32_t(r) << 24) | uint32_t(t - r * cap);
-        buf0[i] = in[v0 * D + i];
+    const uint32_t bar0 = smem_addr(&bars[0]);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(bar0 + 8u * b, 1);
+        // the initialised barriers are visible to the peers' st.async
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_local = 0;
     }
-    // every CTA of the cluster is running and has its targets before any
-    // peer stores into its buffers
+    __syncthreads();
+    int local = 0;
+    for (int i = threadIdx.x; i < arcs; i += blockDim.x) {
+        const int lv = i / D, j = i - lv * D;
+        const int t = __ldg(a.shift + v0 * D + i);   // global arc receiving arc v0 D + i
+        const int tw = t / D, r = tw / vpc;
+        tgt[j * vpc + lv] = (uint32_t(r) << 24) | uint32_t((t - tw * D) * vpc + (tw - r * vpc));
+        local += (r == rank);
+        const V x = in[v0 * D + i];
+        buf0[j * vpc + lv] = x.x;
+        buf0[plane + j * vpc + lv] = x.y;
+    }
+    if (local) atomicAdd(&s_local, local);
+    // every CTA of the cluster is running, has its targets and its barriers
+    // before any peer stores into its buffers
     cluster_barrier();
-    const uint32_t base0 = smem_addr(buf0), base1 = smem_addr(buf1);
+    // the shift is a permutation, so as many owned arcs receive from this CTA
+    // as owned arcs send to it; the rest arrive from peers, two components each
+    const uint32_t in_bytes = uint32_t(arcs - s_local) * 2u * uint32_t(sizeof(R));
+    const uint32_t base0 = smem_addr(buf0), bufbytes = uint32_t(2 * plane) * uint32_t(sizeof(R));
     const R f = weight<R>(a);
-    // two threads per vertex: thread 2i takes the real parts of vertex i's
-    // arcs, thread 2i + 1 the imaginary parts (the two components of the
-    // Grover coin are independent sums), so each step has twice the warps to
-    // hide the shared-memory, FP64 and cluster-store latencies
-    const int comp = threadIdx.x & 1;
+    // the two components of the Grover coin are independent sums: the first
+    // half of the threads takes the real parts, the second the imaginary
+    // parts (blockDim.x is a multiple of 64, so a warp holds one component),
+    // which doubles the warps that hide the shared-memory, FP64 and
+    // cluster-store latencies
+    const int half = int(blockDim.x >> 1);
+    const int comp = int(threadIdx.x) >= half ? 1 : 0;
+    const int lane_v = int(threadIdx.x) - comp * half;
+    int cb = 0, nb = 1;        // buffers read and written by step t
+    uint32_t phase = 0;        // parity of each mbarrier's current phase
     for (int64_t t = 1; t <= a.steps; ++t) {
-        const R *cur = reinterpret_cast<const R *>((t & 1) ? buf0 : buf1);
-        R *nxt = reinterpret_cast<R *>((t & 1) ? buf1 : buf0);
-        const uint32_t nb = (t & 1) ? base1 : base0;
-        for (int lv = threadIdx.x >> 1; lv < nv; lv += blockDim.x >> 1) {
+        const R *cur = buf0 + (2 * cb + comp) * plane;
+        R *nxt = buf0 + 2 * nb * plane;
+        const uint32_t nbase = base0 + uint32_t(nb) * bufbytes, bar = bar0 + 8u * uint32_t(nb);
+        if (threadIdx.x == 0) mbar_expect(bar, in_bytes);
+        for (int lv = lane_v; lv < nv; lv += half) {
             R p[D];
 #pragma unroll
-            for (int j = 0; j < D; ++j) p[j] = cur[2 * (lv * D + j) + comp];
+            for (int j = 0; j < D; ++j) p[j] = cur[j * vpc + lv];
             // a marked vertex's coin block is -I
             const bool marked = marked_find(a.mk, v0 + lv) >= 0;
             R sum = 0;
@@ -147,34 +235,51 @@ __global__ void __launch_bounds__(kMaxThreads) k_coined_cluster(ClusterArgs a)
             const R fv = marked ? R(0) : f;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const uint32_t g = tgt[lv * D + j];
+                const uint32_t g = tgt[j * vpc + lv];
                 const R o = fma(fv, sum, -p[j]);
-                const uint32_t e = (g & 0xFFFFFFu) * 2u + uint32_t(comp);
+                const uint32_t e = uint32_t(comp * plane) + (g & 0xFFFFFFu);
+                const uint32_t r = g >> 24;
                 // arcs owned by this CTA take a plain shared-memory store
-                if ((g >> 24) == uint32_t(rank)) nxt[e] = o;
-                else st_peer(peer_addr(nb + e * uint32_t(sizeof(R)), g >> 24), o);
+                if (r == uint32_t(rank)) nxt[e] = o;
+                else st_async(peer_addr(nbase + e * uint32_t(sizeof(R)), r), o, peer_addr(bar, r));
             }
         }
-        cluster_barrier();
+        const bool got = mbar_wait(bar, (phase >> nb) & 1u);
+        phase ^= 1u << nb;
+        // the local stores are visible, and every thread has read buffer cb
+        if (__syncthreads_or(!got)) {
+            if (threadIdx.x == 0) atomicExch(a.err, 1);
+            break;
+        }
         if (a.rec_part && t % a.stride == 0) {
             // marked probability after step t, from the owning CTA's buffer
-            const V *now = (t & 1) ? buf1 : buf0;
+            const R *now = buf0 + 2 * nb * plane;
             for (int i = threadIdx.x; i < a.mk.n; i += blockDim.x) {
                 const int lv = marked_id(a.mk, i) - v0;
                 if (lv < 0 || lv >= nv) continue;
                 double acc = 0.0;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    const V q = now[lv * D + j];
-                    acc += double(q.x) * double(q.x) + double(q.y) * double(q.y);
+                    const double x = now[j * vpc + lv], y = now[plane + j * vpc + lv];
+                    acc += x * x + y * y;
                 }
                 a.rec_part[(t / a.stride - 1) * a.mk.n + i] = acc;
             }
         }
+        cb = nb;
+        nb = (nb == 2) ? 0 : nb + 1;
     }
-    const V *fin = (a.steps & 1) ? buf1 : buf0;
+    const R *fin = buf0 + 2 * cb * plane;
     V *out = static_cast<V *>(a.out);
-    for (int i = threadIdx.x; i < arcs; i += blockDim.x) out[v0 * D + i] = fin[i];
+    for (int i = threadIdx.x; i < arcs; i += blockDim.x) {
+        const int lv = i / D, j = i - lv * D;
+        V x;
+        x.x = fin[j * vpc + lv];
+        x.y = fin[plane + j * vpc + lv];
+        out[v0 * D + i] = x;
+    }
+    // no CTA leaves while a peer may still address its shared memory
+    cluster_barrier();
 }
 
 template <typename R, int D>
@@ -264,7 +369,7 @@ size_t cluster_smem(const hw_graph *g, hw_dtype dt, int ctas, int *vpc)
 {
     const int d = g->max_degree;
     *vpc = int((g->n + ctas - 1) / ctas);
-    return size_t(*vpc) * d * (2 * cplx_bytes(dt) + sizeof(uint32_t));
+    return size_t(*vpc) * d * (3 * cplx_bytes(dt) + sizeof(uint32_t));
 }
 
 }  // namespace
@@ -305,7 +410,9 @@ hw_status launch_coined_cluster(const hw_graph *g, hw_dtype dt, const void *in, 
     a.w = w;
     a.wf = float(w);
     a.mk = mk;
-    const int threads = std::min(kMaxThreads, std::max(32, (2 * vpc + 31) / 32 * 32));
+    a.err = g->d_err;
+    // two threads per vertex, a multiple of 64 so that each warp holds one component
+    const int threads = std::min(kMaxThreads, std::max(64, (2 * vpc + 63) / 64 * 64));
     const cudaError_t e = (dt == HW_C128) ? launch_deg<double>(g->max_degree, a, ctas, threads, smem, st)
                                           : launch_deg<float>(g->max_degree, a, ctas, threads, smem, st);
     return hw_cuda(e, "k_coined_cluster launch");
