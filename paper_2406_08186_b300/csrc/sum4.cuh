@@ -20,6 +20,13 @@
 // 32-bit leading-zero counts: measured on this GPU, variable 64-bit shifts and
 // 64-bit leading-zero counts issue on the FP64 pipe, which would defeat the
 // purpose.  The header compiles as plain C++ for the host check.
+//
+// Three forms compute the same function and return the same bits for every
+// input: sum4_rn_cases (one branch per case), sum4_rn (an early return for
+// four zeros, a select-only path for the common case, sum4_rn_cases for the
+// rest) and sum4_rn_flat (selects throughout).  Which is fastest depends on
+// the kernel: measured, the four-arc kernels take sum4_rn and the loops over
+// groups of a long vertex take sum4_rn_flat.
 #pragma once
 
 #include <cstdint>
@@ -88,7 +95,9 @@ HW_HD double sum4_seq(double x0, double x1, double x2, double x3)
 #endif
 }
 
-HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
+// The method with one branch per case: the fast path below returns the
+// common case itself and hands every other input to this form.
+HW_HD double sum4_rn_cases(double x0, double x1, double x2, double x3)
 {
     const double xs[4] = {x0, x1, x2, x3};
     uint32_t hi[4], lo[4];
@@ -164,13 +173,158 @@ HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
     return sum4_seq(x0, x1, x2, x3);
 }
 
+#if defined(__CUDACC__)
+static __device__ __noinline__ double sum4_cases_dev(double x0, double x1, double x2, double x3)
+{
+    return sum4_rn_cases(x0, x1, x2, x3);
+}
+#endif
+
+HW_HD uint32_t lo32(uint64_t v) { return static_cast<uint32_t>(v); }
+HW_HD uint32_t hi32(uint64_t v) { return static_cast<uint32_t>(v >> 32); }
+
+// The same function with a fast path: all four addends zero returns at once
+// (a state with real amplitudes has all-zero imaginary sums); otherwise the
+// four addends are aligned independently, summed as a tree (the negative ones
+// as one's complements plus their count) and rounded with selects only, so a
+// warp whose lanes see different signs and rounding cases runs one stream.
+// Inputs outside that path (infinite, NaN or subnormal addends, a spread of
+// more than 8 binades, a sum below 2^53 units of the grid, which includes an
+// exact cancellation, or a result outside the normal range) take
+// sum4_rn_cases, out of line.
+HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
+{
+    const double xs[4] = {x0, x1, x2, x3};
+    uint32_t hi[4], lo[4];
+    int e[4];
+    bool nz[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint64_t u = fpconv::bits64(xs[i]);
+        hi[i] = hi32(u);
+        lo[i] = lo32(u);
+        e[i] = static_cast<int>((hi[i] >> 20) & 0x7ff);
+        nz[i] = ((hi[i] << 1) | lo[i]) != 0;
+    }
+    if (!(nz[0] || nz[1] || nz[2] || nz[3])) {
+        // a sum of zeros is -0 only when every addend is -0
+        const uint32_t allneg = (hi[0] & hi[1] & hi[2] & hi[3]) >> 31;
+        return fpconv::from_bits64(static_cast<uint64_t>(allneg) << 63);
+    }
+    const int E01 = e[0] > e[1] ? e[0] : e[1], E23 = e[2] > e[3] ? e[2] : e[3];
+    const int E = E01 > E23 ? E01 : E23;
+    bool rare = false;
+    uint32_t nneg = 0;
+    uint64_t a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int sft = E - e[i];
+        rare = rare || e[i] == 0x7ff || (nz[i] && (e[i] == 0 || sft > 8));
+        // 53-bit significand (zero for a zero addend) placed at 2^(8 - sft)
+        uint32_t mh = (hi[i] & 0xFFFFFu) | (nz[i] ? 0x100000u : 0u), ml = lo[i];
+        shl64(mh, ml, (8 - sft) & 31);
+        const uint32_t neg = hi[i] >> 31, m = 0u - neg;   // all ones for a negative addend
+        nneg += neg;
+        a[i] = join(mh ^ m, ml ^ m);                      // -x = ~x + 1: the +1s are nneg
+    }
+    // signed 64-bit sum on the grid 2^(E - 1083), |sum| < 2^63 (integer adds)
+    const uint64_t t = (a[0] + a[1]) + (a[2] + a[3]) + nneg;
+    const uint32_t sgn = hi32(t) >> 31;
+    const uint64_t mag = (t ^ (0ull - sgn)) + sgn;
+    const uint32_t th = hi32(mag), tl = lo32(mag);
+    const int lz = th ? clz32(th) : 32 + clz32(tl);
+    const int sh = 11 - lz;                           // bits below the kept 53
+    rare = rare || sh <= 0;
+    // round to nearest even: add half a unit of the last kept bit less one,
+    // plus that bit, then drop the sh low bits
+    const uint32_t inc = ((1u << ((sh - 1) & 31)) - 1u) + ((tl >> (sh & 31)) & 1u);
+    const uint64_t r = mag + inc;
+    uint32_t kh = hi32(r), kl = lo32(r);
+    shr64(kh, kl, sh & 31);
+    const uint32_t carry = kh >> 21;                  // the rounding carried to 2^53
+    const int B = E - 8 + sh + static_cast<int>(carry);
+    rare = rare || B < 1 || B > 0x7fe;
+    if (rare) {
+#if defined(__CUDA_ARCH__)
+        return sum4_cases_dev(x0, x1, x2, x3);
+#else
+        return sum4_rn_cases(x0, x1, x2, x3);
+#endif
+    }
+    // (B - 1 - carry) 2^52 + kept: the implicit bit (2^52, or 2^53 after a
+    // carry) lands in the exponent field
+    return fpconv::from_bits64((static_cast<uint64_t>(sgn) << 63) +
+                               (static_cast<uint64_t>(static_cast<uint32_t>(B - 1 - static_cast<int>(carry))) << 52) +
+                               join(kh, kl));
+}
+
+// The same function with every step as a select (no early return for zeros
+// either) up to the fallback to the sequential sum: used where the terms are
+// general complex amplitudes, summed in a loop of groups, so that the code a
+// group inlines stays short.
+HW_HD double sum4_rn_flat(double x0, double x1, double x2, double x3)
+{
+    const double xs[4] = {x0, x1, x2, x3};
+    uint32_t hi[4], lo[4];
+    int e[4];
+    bool nz[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint64_t u = fpconv::bits64(xs[i]);
+        hi[i] = hi32(u);
+        lo[i] = lo32(u);
+        e[i] = static_cast<int>((hi[i] >> 20) & 0x7ff);
+        nz[i] = ((hi[i] << 1) | lo[i]) != 0;
+    }
+    const int E01 = e[0] > e[1] ? e[0] : e[1], E23 = e[2] > e[3] ? e[2] : e[3];
+    const int E = E01 > E23 ? E01 : E23;
+    bool special = false;
+    uint32_t nneg = 0;
+    uint64_t a[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int sft = E - e[i];
+        special = special || e[i] == 0x7ff || (nz[i] && (e[i] == 0 || sft > 8));
+        uint32_t mh = (hi[i] & 0xFFFFFu) | (nz[i] ? 0x100000u : 0u), ml = lo[i];
+        shl64(mh, ml, (8 - sft) & 31);
+        const uint32_t neg = hi[i] >> 31, m = 0u - neg;
+        nneg += neg;
+        a[i] = join(mh ^ m, ml ^ m);
+    }
+    const uint64_t t = (a[0] + a[1]) + (a[2] + a[3]) + nneg;
+    const uint32_t sgn = hi32(t) >> 31;
+    const uint64_t mag = (t ^ (0ull - sgn)) + sgn;
+    const uint32_t th = hi32(mag), tl = lo32(mag);
+    const int lz = th ? clz32(th) : 32 + clz32(tl);
+    const int sh = 11 - lz;
+    // sh > 0: round to nearest even; sh <= 0: exact, shifted up
+    const int sr = sh > 0 ? sh : 0, sl = sh > 0 ? 0 : -sh;
+    const uint32_t inc = sr ? ((1u << ((sr - 1) & 31)) - 1u) + ((tl >> sr) & 1u) : 0u;
+    const uint64_t r = mag + inc;
+    uint32_t kh = hi32(r), kl = lo32(r);
+    shr64(kh, kl, sr);
+    shl64_wide(kh, kl, sl);
+    const uint32_t carry = kh >> 21;
+    const int B = E - 8 + sh + static_cast<int>(carry);
+    const uint64_t bits = (static_cast<uint64_t>(sgn) << 63) +
+                          (static_cast<uint64_t>(static_cast<uint32_t>(B - 1 - static_cast<int>(carry))) << 52) +
+                          join(kh, kl);
+    const bool allzero = !(nz[0] || nz[1] || nz[2] || nz[3]);
+    const bool cancel = mag == 0;
+    const bool ok = allzero || (!special && (cancel || (B >= 1 && B <= 0x7fe)));
+    if (!ok) return sum4_seq(x0, x1, x2, x3);
+    const uint32_t allneg = (hi[0] & hi[1] & hi[2] & hi[3]) >> 31;
+    return fpconv::from_bits64(allzero ? (static_cast<uint64_t>(allneg) << 63) : cancel ? 0ull : bits);
+}
+
 // componentwise sums of the complex terms t(0) .. t(count-1), count >= 1
 // (t returns a type with double .x, .y, and is called once per term, in
 // order): groups of four consecutive terms summed by sum4_rn (a short last
 // group padded with -0, which leaves any sum unchanged), the group sums
 // added in order in double.  The next group's terms are fetched before the
 // current group is summed, so its loads overlap the integer work; the first
-// group's sum starts the total (no addition to 0.0 on the FP64 unit).
+// group's sum starts the total (no addition to 0.0 on the FP64 unit).  The
+// groups take sum4_rn_flat (same results as sum4_rn).
 template <typename F>
 HW_HD void load_group(int j0, int count, F &t, double (&x)[4], double (&y)[4])
 {
@@ -193,8 +347,8 @@ HW_HD void grouped_sum2(int count, F t, double &sx, double &sy)
     double cx[4], cy[4], nx[4], ny[4];
     load_group(0, count, t, cx, cy);
     load_group(4, count, t, nx, ny);
-    sx = sum4_rn(cx[0], cx[1], cx[2], cx[3]);
-    sy = sum4_rn(cy[0], cy[1], cy[2], cy[3]);
+    sx = sum4_rn_flat(cx[0], cx[1], cx[2], cx[3]);
+    sy = sum4_rn_flat(cy[0], cy[1], cy[2], cy[3]);
     for (int j0 = 4; j0 < count; j0 += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -202,8 +356,8 @@ HW_HD void grouped_sum2(int count, F t, double &sx, double &sy)
             cy[u] = ny[u];
         }
         load_group(j0 + 4, count, t, nx, ny);
-        sx += sum4_rn(cx[0], cx[1], cx[2], cx[3]);
-        sy += sum4_rn(cy[0], cy[1], cy[2], cy[3]);
+        sx += sum4_rn_flat(cx[0], cx[1], cx[2], cx[3]);
+        sy += sum4_rn_flat(cy[0], cy[1], cy[2], cy[3]);
     }
 }
 

@@ -1,5 +1,6 @@
-"""The four-term sum of the complex128 Grover coin (sum4.cuh), built for the
-host, against exact rational arithmetic: when the addends lie within 8 binades
+"""The four-term sum of the complex128 Grover coin (sum4.cuh; its three forms
+sum4_rn, sum4_rn_flat and sum4_rn_cases), built for the host, against exact
+rational arithmetic: when the addends lie within 8 binades
 of the largest (and are normal, the result normal) it must equal the exact sum
 rounded once to the nearest double (ties to even) -- Python's float() of a
 Fraction rounds that way; otherwise it must equal the sequential double sum
@@ -66,8 +67,9 @@ def test_sum4_correctly_rounded(tmp_path):
     text = "\n".join(" ".join("%016x" % _bits(x) for x in c) for c in cases) + "\n"
     out = subprocess.run([str(exe)], input=text, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0
-    got = [int(h, 16) for h in out.stdout.split()]
-    assert len(got) == len(cases)
+    words = [int(h, 16) for h in out.stdout.split()]
+    assert len(words) == 3 * len(cases)
+    got = [tuple(words[3 * i:3 * i + 3]) for i in range(len(cases))]
     exact_seen = 0
     for c, g in zip(cases, got):
         if _exact_path(c):
@@ -86,5 +88,5 @@ def test_sum4_correctly_rounded(tmp_path):
                 exact_seen += 1
         else:
             want_bits = _bits(((c[0] + c[1]) + c[2]) + c[3])
-        assert g == want_bits, (c, hex(g), hex(want_bits))
+        assert g == (want_bits,) * 3, (c, [hex(x) for x in g], hex(want_bits))
     assert exact_seen > 20000
