@@ -50,8 +50,8 @@ TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
     # block row per torus row, complex128 sums by integer operations and
     # streaming loads and stores), one launch, cold L2
-    ("c128", "158875b1c12157bb7eb27d9bfe2b0223d7ada1ab"): 67133184 + 16111872,
-    ("c64", "158875b1c12157bb7eb27d9bfe2b0223d7ada1ab"): 33566464 + 326912,
+    ("c128", "63463a7da7537292070fa3be1bf53f45f95a5359"): 67132416 + 16863232,
+    ("c64", "63463a7da7537292070fa3be1bf53f45f95a5359"): 33566976 + 268288,
 }
 
 
@@ -462,9 +462,10 @@ def sub_torus64(hw, reps, warmup, with_cpu):
                         "fp64_of_16_sms": {"achieved": fmas / t, "peak": fp64 * 16 / sms, "unit": "FMA/s",
                                            "frac": fmas / t / (fp64 * 16 / sms), "fma_per_run": fmas},
                         "note": "the whole walk in one launch (one 16-CTA thread-block cluster holds the 256 KiB "
-                                "state in shared memory, a hardware cluster barrier per step), then one "
-                                "probability launch; per step the FP64 FMAs of 4096 vertices on the cluster's "
-                                "16 SMs and the barrier set the time"},
+                                "state in shared memory; outputs owned by other CTAs go by st.async, counted on "
+                                "the owner's mbarrier, and each CTA waits only for its own incoming bytes), then "
+                                "one probability launch; per step the integer four-term sums and the FP64 FMAs "
+                                "of 4096 vertices on the cluster's 16 SMs and the cross-CTA latency set the time"},
            "clocks": clk.summary()}
     if with_cpu:
         import oracle
