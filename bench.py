@@ -598,10 +598,10 @@ def sub_ctqw_q12(hw, reps, warmup, with_cpu):
                 r["apply_roofline"] = {"bound": "fp64", "achieved": afma / (t_ev / 2000), "peak": fp64,
                                        "unit": "FMA/s", "frac": afma / (t_ev / 2000) / fp64, "fma_per_apply": afma}
             else:
-                # dense form on the tensor cores: (m - 1) powers, each over the CTA
-                # tiles (128 x 256 x n) of the cluster tiles on and above the
-                # diagonal, two fp16 products per tile (272 tiles at n = 4096)
-                cl = (n + 255) // 256          # 2-CTA cluster tiles of 256 x 256 on and above the diagonal
+                # dense form on the tensor cores: (m - 1) powers, each over the
+                # 256 x 256 tiles of CTA pairs on and above the diagonal (136 at
+                # n = 4096), two fp16 products per tile
+                cl = (n + 255) // 256          # pair tiles per side
                 mma = (deg - 1) * (cl * (cl + 1)) * 128 * 256 * n * 2 * 2.0
                 r["expm_dense"]["roofline"] = {"bound": "tensor", "achieved": mma / t_dense / 1e12, "peak": tc_peak,
                                                "unit": "TFLOP/s", "frac": mma / t_dense / 1e12 / tc_peak,

@@ -102,6 +102,11 @@ typedef struct hw_opts {
                                   for HW_C128 and in float for HW_C64; 0 = default: 2 for
                                   HW_C128, 1 for HW_C64.  The Taylor sum is in double and the
                                   squarings are dense FP64 GEMMs either way. */
+    int32_t gemm_tiles;        /* hw_ctqw_expm, HW_C64 tensor-core powers: 0 = default (2 when
+                                  the device runs thread-block clusters of two CTAs, else 1);
+                                  1 = one CTA per 128 x 256 output tile; 2 = the two CTAs of a
+                                  cluster share a 256 x 256 tile as one pair MMA (each loads
+                                  its own A rows and half of the B rows). */
 } hw_opts;
 
 /* Fill `opts` with the defaults. */

@@ -49,7 +49,8 @@ class hw_opts(ctypes.Structure):
                 ("taylor_squarings", ctypes.c_int32), ("gemm_mode", ctypes.c_int32),
                 ("u_symmetric", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("addressing", ctypes.c_int32), ("shift", ctypes.c_int32),
-                ("launch_mode", ctypes.c_int32), ("taylor_powers", ctypes.c_int32)]
+                ("launch_mode", ctypes.c_int32), ("taylor_powers", ctypes.c_int32),
+                ("gemm_tiles", ctypes.c_int32)]
 
 
 class hw_job(ctypes.Structure):

@@ -112,6 +112,7 @@ extern "C" void hw_opts_init(hw_opts *o)
     o->shift = 0;
     o->launch_mode = 0;
     o->taylor_powers = 0;
+    o->gemm_tiles = 0;
 }
 
 hw_status make_marked(const int32_t *marked, int32_t n_marked, int64_t n, cudaStream_t st,

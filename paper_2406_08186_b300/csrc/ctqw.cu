@@ -1143,7 +1143,9 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
             }
         }
         const SymSparse ys{g->d_row_ptr, g->d_head, g->d_wre, n, -gamma * tau, mk, -tau};
-        if ((s = tc_power_begin(ys, yvals.data(), int(yvals.size()), theta, gmode, st, &tp)) != HW_OK) return s;
+        if ((s = tc_power_begin(ys, yvals.data(), int(yvals.size()), theta, gmode, opts ? opts->gemm_tiles : 0, st,
+                                &tp)) != HW_OK)
+            return s;
         for (int k = 2; k <= m_deg && s == HW_OK; ++k) {
             double *accU = (k % 2 == 0) ? Re.as<double>() : Im.as<double>();
             const double sign = (k % 4 == 0 || k % 4 == 3) ? 1.0 : -1.0;

@@ -13,6 +13,11 @@
 // unweighted graph, scaled by 1 / (gamma tau), has entries 0, 1 and 1/gamma),
 // B keeps one slice and the products with its lower slices are dropped.
 //
+// Two forms.  The Taylor powers run on CTA pairs by default (k_tc_gemm_pair,
+// below: 256 x 256 tiles, one pair MMA per K step, 64-element K blocks); the
+// form described next, one CTA per tile, serves hw_gemm_tc and
+// hw_opts.gemm_tiles = 1.
+//
 // Work is cut into 128 x 256 CTA tiles; persistent CTAs, one per SM, walk a
 // list of tiles.  Each CTA loads its own A rows and all of its B rows with
 // TMA into its own shared memory: the operands of a Taylor power (the previous
@@ -160,6 +165,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr)
     return d;
 }
 
+// The same for 128-byte rows (64 16-bit elements, 128-byte swizzle): 8-row
+// groups 1024 bytes apart; the pair kernel's K blocks
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= uint64_t((addr & 0x3FFFFu) >> 4);      // start address
+    d |= uint64_t(1) << 16;                      // leading offset (unused when swizzled)
+    d |= uint64_t(1024 >> 4) << 32;              // stride offset between 8-row groups
+    d |= uint64_t(1) << 46;                      // descriptor version
+    d |= uint64_t(2) << 61;                      // 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor: 16-bit A and B (bf16 = 1, fp16 = 0), fp32 accumulator,
 // both K-major, M = TM, N = TN.
 template <int FMT>
@@ -183,6 +201,69 @@ __device__ __forceinline__ void mma16(uint32_t tmem_d, uint64_t adesc, uint64_t 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// ---- CTA-pair forms (cta_group::2): the two CTAs of a cluster of 2 share
+// one 256 x 256 tile; every tcgen05 instruction of the pair kernel takes the
+// pair form.  Addresses of barriers are in the shared::cluster window: the
+// CTA's own (a shared::cta address) or the peer's (mapa).
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// every thread of both CTAs: what each did before is visible to both after
+__device__ __forceinline__ void pair_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// 2D tile load into this CTA's shared memory, its bytes counted on an
+// mbarrier of either CTA of the pair (the leader's)
+__device__ __forceinline__ void tma_load_pair(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// M = 256 (128 rows from each CTA's shared memory, at the same offsets), N = TN
+// (TN / 2 rows of B from each CTA); each CTA's TMEM receives its 128 rows
+template <int FMT>
+__device__ __forceinline__ constexpr uint32_t idesc_pair()
+{
+    return (1u << 4) | (uint32_t(FMT == FMT_BF16 ? 1 : 0) << 7) | (uint32_t(FMT == FMT_BF16 ? 1 : 0) << 10) |
+           (uint32_t(TN >> 3) << 17) | (uint32_t((2 * TM) >> 4) << 24);
+}
+
+template <int FMT>
+__device__ __forceinline__ void mma16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc_pair<FMT>()), "r"(acc)
+        : "memory");
+}
+
+// arrive on one mbarrier (either CTA) when the pair's earlier MMAs are done
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
 
@@ -540,6 +621,191 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
     if (threadIdx.x == 0 && timed_out) atomicExch(a.err, 1);
 }
 
+// The same GEMM with 256 x 256 tiles, each computed by the two CTAs of a
+// cluster as one pair MMA (M = 256): CTA r of the pair loads rows 128 r.. of
+// the tile's A rows and rows 128 r.. of its B rows, so per unit of tensor work
+// each CTA loads a quarter fewer bytes (A with two slices, B with one), and
+// K blocks are 64 elements (whole 128-byte rows, 128-byte swizzle).  The even CTA
+// (the leader) issues the MMAs; both CTAs' loads count on the leader's "full"
+// barrier; the leader's commits arrive on the "empty" and "accumulator full"
+// barriers of both CTAs (one commit each); both CTAs' epilogue warps arrive on
+// the leader's "accumulator empty" barrier.  Tiles (P, Q) cover rows 256 P..,
+// columns 256 Q..; everything else (ring, epilogues, accumulation, bounded
+// waits, drain) is as in k_tc_gemm.
+template <int FMT, int NA, int NB>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_gemm_pair(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+               const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+               const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, TcArgs a,
+               int ntiles)
+{
+    constexpr int TKP = 64;                                    // K block: one 128-byte swizzle row
+    constexpr int kATileP = TM * TKP * 2;                      // 16 KB per A slice
+    constexpr int kBHalf = (TN / 2) * TKP * 2;                 // TN / 2 rows of B per CTA: 16 KB
+    constexpr int kStageBytes = NA * kATileP + NB * kBHalf;
+    constexpr int S = (kRingBytes / kStageBytes < kMaxStages) ? kRingBytes / kStageBytes : kMaxStages;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full[kMaxStages], bar_empty[kMaxStages], bar_tfull[2], bar_tempty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int timed_out;
+
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int pid = int(blockIdx.x) >> 1, npair = int(gridDim.x) >> 1;
+    const int nkb = (a.k + TKP - 1) / TKP;
+    volatile int *tmo = &timed_out;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bar_tfull[b]), 1);
+            mbar_init(smem_u32(&bar_tempty[b]), 2 * kEpiWarps);   // epilogue warps of both CTAs
+        }
+        timed_out = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_slot)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    // both CTAs' barriers are initialised and their TMEM allocated before
+    // either CTA signals the other
+    pair_barrier();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer (both CTAs): this CTA's A rows and half of the B rows
+            const CUtensorMap *mA[3] = {&tA0, &tA1, &tA2};
+            const CUtensorMap *mB[3] = {&tB0, &tB1, &tB2};
+            uint32_t g = 0, phase = 0;
+            int s = 0;
+            for (int t = pid; t < ntiles && !*tmo; t += npair) {
+                const int2 ct = a.tiles[t];
+                const int rowA = ct.x * 2 * TM + int(rank) * TM;
+                const int rowB = ct.y * TN + int(rank) * (TN / 2);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (g >= uint32_t(S) && !mbar_wait(smem_u32(&bar_empty[s]), phase ^ 1u)) {
+                        *tmo = 1;
+                        break;
+                    }
+                    const uint32_t full_own = smem_u32(&bar_full[s]);
+                    if (leader) mbar_expect_tx(full_own, uint32_t(2 * kStageBytes));   // both CTAs' boxes
+                    const uint32_t full = leader ? full_own : peer_addr(full_own, 0);
+                    const uint32_t st = base + uint32_t(s * kStageBytes);
+#pragma unroll
+                    for (int i = 0; i < NA; ++i) tma_load_pair(st + uint32_t(i * kATileP), mA[i], full, kb * TKP, rowA);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        tma_load_pair(st + uint32_t(NA * kATileP + j * kBHalf), mB[j], full, kb * TKP, rowB);
+                    ++g;
+                    if (++s == S) { s = 0; phase ^= 1u; }
+                }
+            }
+            // drain: the last fill of every stage released by the pair's MMAs
+            for (uint32_t q = 0; q < uint32_t(S) && q < g; ++q) {
+                const uint32_t last_use = (g - 1 - q) / uint32_t(S);
+                if (!mbar_wait(smem_u32(&bar_empty[q]), last_use & 1u)) *tmo = 1;
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0 && leader) {
+            // MMA issuer (leader): accumulator b = (local tile) & 1, in both CTAs' TMEM
+            const uint64_t d0 = smem_desc_sw128(base);
+            uint32_t phase = 0, li = 0;
+            int s = 0;
+            for (int t = pid; t < ntiles && !*tmo; t += npair, ++li) {
+                const int b = int(li & 1u);
+                const uint32_t ub = li >> 1;
+                if (ub > 0 && !mbar_wait(smem_u32(&bar_tempty[b]), (ub & 1u) ^ 1u)) {
+                    *tmo = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tacc = tmem + uint32_t(b * TN);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(smem_u32(&bar_full[s]), phase)) {
+                        *tmo = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t dA = d0 + uint64_t((s * kStageBytes) >> 4);
+                    const uint64_t dB = dA + uint64_t((NA * kATileP) >> 4);
+                    // K steps of 16 elements: 32 bytes further along the swizzled row
+#pragma unroll
+                    for (int kk = 0; kk < TKP / 16; ++kk) {
+#pragma unroll
+                        for (int d = NA - 1; d >= 0; --d) {
+#pragma unroll
+                            for (int i = d; i >= 0; --i) {
+                                const int j = d - i;
+                                if (j < NB) {
+                                    const uint64_t ad = dA + uint64_t((i * kATileP) >> 4) + uint64_t(2 * kk);
+                                    const uint64_t bd = dB + uint64_t((j * kBHalf) >> 4) + uint64_t(2 * kk);
+                                    const bool first = (kk == 0 && d == NA - 1 && i == d);
+                                    mma16_pair<FMT>(tacc, ad, bd, (first && kb == 0) ? 0u : 1u);
+                                }
+                            }
+                        }
+                    }
+                    const uint32_t e = smem_u32(&bar_empty[s]);
+                    mma_commit_pair(e);
+                    mma_commit_pair(peer_addr(e, 1));
+                    if (++s == S) { s = 0; phase ^= 1u; }
+                }
+                const uint32_t tf = smem_u32(&bar_tfull[b]);
+                mma_commit_pair(tf);
+                mma_commit_pair(peer_addr(tf, 1));
+            }
+        }
+    } else {
+        if (a.accU)
+            acc_rows<FMT, NA>(a.n, a.accQ[0], a.accQ[1], a.accQ[2], a.ldq, a.acc_coef, a.accU, int(blockIdx.x),
+                              int(gridDim.x), warp < 4 ? int(threadIdx.x) : int(threadIdx.x) - 64,
+                              128 + 32 * kAccWarps);
+        const int quad = warp & 3, third = (warp < 4) ? 0 : (warp < 10 ? 1 : 2);
+        const int cb = third == 0 ? 0 : (third == 1 ? 96 : 176), ce = third == 0 ? 96 : (third == 1 ? 176 : 256);
+        uint32_t li = 0;
+        for (int t = pid; t < ntiles; t += npair, ++li) {
+            const int b = int(li & 1u);
+            if (!mbar_wait(smem_u32(&bar_tfull[b]), (li >> 1) & 1u)) {
+                *tmo = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int2 ct = a.tiles[t];
+            epilogue_tile<FMT, NA>(a, ct.x * 2 * TM + int(rank) * TM, ct.y * TN, tmem + uint32_t(b * TN), quad, lane,
+                                   cb, ce);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t te = smem_u32(&bar_tempty[b]);
+                if (leader)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(te) : "memory");
+                else
+                    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(peer_addr(te, 0))
+                                 : "memory");
+            }
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    // no CTA frees its TMEM or leaves while the pair's MMAs or the peer's
+    // arrivals may still reach it
+    pair_barrier();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    if (threadIdx.x == 0 && timed_out) atomicExch(a.err, 1);
+}
+
 // largest |x| of a matrix as float bits (non-negative floats order like their bits);
 // blocks stride over rows, threads over columns
 template <typename T>
@@ -711,18 +977,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
     return fn;
 }
 
-// 2D 16-bit map over a [rows][cols] slice with row stride ld: box TK x box_rows, 64-byte swizzle
-hw_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int fmt, int box_rows)
+// 2D 16-bit map over a [rows][cols] slice with row stride ld: box TK x box_rows
+// with 64-byte swizzle, or (wide) 64 x box_rows with 128-byte swizzle
+hw_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int fmt, int box_rows,
+                   bool wide = false)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
     if (!enc) return hw_fail(HW_ECUDA, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
     cuuint64_t strides[1] = {cuuint64_t(ld) * 2};
-    cuuint32_t box[2] = {TK, cuuint32_t(box_rows)};
+    cuuint32_t box[2] = {wide ? 64u : cuuint32_t(TK), cuuint32_t(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(map, fmt == FMT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
                      const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     wide ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return hw_fail(HW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
     return HW_OK;
 }
@@ -733,6 +1002,7 @@ struct Slices {
     void *s[3] = {nullptr, nullptr, nullptr};
     CUtensorMap mapA[3];     // boxes of an A tile (128 rows x one K block)
     CUtensorMap mapB[3];     // boxes of a B tile (256 rows x one K block)
+    CUtensorMap mapP[3];     // the pair kernel's boxes (128 rows x 64 columns, 128-byte swizzle)
 };
 
 // three slice planes of a rows x ld 16-bit matrix in one buffer, plus their maps
@@ -742,6 +1012,7 @@ hw_status slices_make(Slices &S, uint16_t *buf, int rows, int cols, int ld, int 
         S.s[i] = buf + size_t(i) * rows * ld;
         hw_status st = make_map(&S.mapA[i], S.s[i], rows, cols, ld, fmt, TM);
         if (st == HW_OK) st = make_map(&S.mapB[i], S.s[i], rows, cols, ld, fmt, TN);
+        if (st == HW_OK) st = make_map(&S.mapP[i], S.s[i], rows, cols, ld, fmt, TM, true);
         if (st != HW_OK) return st;
     }
     return HW_OK;
@@ -774,6 +1045,21 @@ std::vector<int2> cta_tiles(int m, int n, bool sym)
             for (int p = bp; p < std::min(tp, bp + GP); ++p)
                 for (int q = bq; q < std::min(tq, bq + GQ); ++q)
                     if (!sym || TM * p <= TN * q + TN - 1) t.push_back(make_int2(p, q));
+    return t;
+}
+
+// pair tiles (P, Q) of 256 x 256, in groups of 4 x 4 (1024 x 1024 elements);
+// with sym only those holding a 128 x 128 block (r, c) with r <= c, i.e. P <= Q
+std::vector<int2> pair_tiles(int m, int n, bool sym)
+{
+    const int tp = (m + 2 * TM - 1) / (2 * TM), tq = (n + TN - 1) / TN;
+    std::vector<int2> t;
+    const int GP = 4, GQ = 4;
+    for (int bp = 0; bp < tp; bp += GP)
+        for (int bq = 0; bq < tq; bq += GQ)
+            for (int p = bp; p < std::min(tp, bp + GP); ++p)
+                for (int q = bq; q < std::min(tq, bq + GQ); ++q)
+                    if (!sym || 2 * TM * p <= TN * q + TN - 1) t.push_back(make_int2(p, q));
     return t;
 }
 
@@ -838,6 +1124,82 @@ hw_status launch_tc(int fmt, int na, int nb, const Slices &A, const Slices &B, c
     return hw_cuda(cudaGetLastError(), "k_tc_gemm launch");
 }
 
+int tc_pair_smem_bytes(int na, int nb)
+{
+    const int stage = (na + nb) * TM * 64 * 2;   // 64-element K blocks, 128 rows of A and of B per slice
+    return std::min(kMaxStages, kRingBytes / stage) * stage + kSmemSlack;
+}
+
+TcKernel tc_kernel_pair(int fmt, int na, int nb)
+{
+    if (fmt == FMT_F16) {
+        if (na == 2 && nb == 2) return k_tc_gemm_pair<FMT_F16, 2, 2>;
+        if (na == 2 && nb == 1) return k_tc_gemm_pair<FMT_F16, 2, 1>;
+        return nullptr;
+    }
+    if (na == 1 && nb == 1) return k_tc_gemm_pair<FMT_BF16, 1, 1>;
+    if (na == 2 && nb == 2) return k_tc_gemm_pair<FMT_BF16, 2, 2>;
+    if (na == 2 && nb == 1) return k_tc_gemm_pair<FMT_BF16, 2, 1>;
+    if (na == 3 && nb == 3) return k_tc_gemm_pair<FMT_BF16, 3, 3>;
+    if (na == 3 && nb == 1) return k_tc_gemm_pair<FMT_BF16, 3, 1>;
+    return nullptr;
+}
+
+cudaLaunchConfig_t pair_config(int ctas, int smem, cudaStream_t st, cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// CTA pairs the device runs at once with this kernel (0: none), cached per (kernel, device)
+int tc_pairs(int fmt, int na, int nb)
+{
+    static std::mutex mu;
+    static std::map<std::pair<TcKernel, int>, int> pairs;
+    TcKernel kern = tc_kernel_pair(fmt, na, nb);
+    if (!kern) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 0; }
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pairs.find({kern, dev});
+    if (it != pairs.end()) return it->second;
+    const int smem = tc_pair_smem_bytes(na, nb);
+    int nclusters = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess) {
+        cudaLaunchAttribute at[1];
+        const cudaLaunchConfig_t cfg = pair_config(2, smem, nullptr, at);
+        if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) nclusters = 0;
+    }
+    cudaGetLastError();
+    pairs[{kern, dev}] = nclusters;
+    return nclusters;
+}
+
+// the pair form: tiles from pair_tiles, B boxes of TN / 2 rows (the A maps' box)
+hw_status launch_tc_pair(int fmt, int na, int nb, const Slices &A, const Slices &B, const TcArgs &a, int ntiles,
+                         cudaStream_t st)
+{
+    TcKernel kern = tc_kernel_pair(fmt, na, nb);
+    const int npairs = tc_pairs(fmt, na, nb);
+    if (!kern || npairs < 1) return hw_fail(HW_EUNSUPPORTED, "no CTA-pair tensor-core kernel runs here");
+    const int smem = tc_pair_smem_bytes(na, nb);
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = pair_config(2 * std::min(ntiles, npairs), smem, st, at);
+    return hw_cuda(cudaLaunchKernelEx(&cfg, kern, A.mapP[0], A.mapP[1], A.mapP[2], B.mapP[0], B.mapP[1],
+                                      B.mapP[2], a, ntiles),
+                   "k_tc_gemm_pair launch");
+}
+
 int row_grid(int64_t rows) { return int(std::min<int64_t>(148 * 16, std::max<int64_t>(rows, 1))); }
 
 hw_status read_err_flag(int *d_err, cudaStream_t st)
@@ -877,6 +1239,7 @@ struct TcPower {
     Slices Y, Q[2];
     int2 *d_tiles = nullptr;
     int ntiles = 0;
+    bool pair = false;       // 256 x 256 tiles on CTA pairs (k_tc_gemm_pair)
     int cur = 0;
     int *err = nullptr;
     double sY = 1, s_prev = 1, theta = 0;
@@ -918,12 +1281,13 @@ bool tc_gemm_available()
 // infinity norm (all host-known).  Y is sliced at the scale 1 / min(yvals)
 // when that makes every entry exact in one slice, else at the power of two
 // that maps max(yvals) into [1/2, 1].
-hw_status tc_power_begin(const SymSparse &Y, const double *yvals, int nyvals, double theta, int mode,
+hw_status tc_power_begin(const SymSparse &Y, const double *yvals, int nyvals, double theta, int mode, int tiles_mode,
                          cudaStream_t st, TcPower **out)
 {
     const int n = Y.n;
     *out = nullptr;
     if (mode < 0 || mode > 4) return hw_fail(HW_EINVAL, "gemm precision mode %d", mode);
+    if (tiles_mode < 0 || tiles_mode > 2) return hw_fail(HW_EINVAL, "gemm_tiles must be 0..2");
     TcPower *p = new (std::nothrow) TcPower;
     if (!p) return hw_fail(HW_ENOMEM, "host allocation failed");
     p->n = n;
@@ -941,7 +1305,14 @@ hw_status tc_power_begin(const SymSparse &Y, const double *yvals, int nyvals, do
     p->s_prev = p->sY;
     p->theta = theta;
     p->st = st;
-    const std::vector<int2> tiles = cta_tiles(n, n, true);
+    // pairs by default where the device co-schedules them
+    const bool pairs_here = tc_pairs(p->md.fmt, p->md.ns, p->nb) > 0;
+    if (tiles_mode == 2 && !pairs_here) {
+        delete p;
+        return hw_fail(HW_EUNSUPPORTED, "gemm_tiles = 2: this device runs no CTA pair of the kernel");
+    }
+    p->pair = tiles_mode == 2 || (tiles_mode == 0 && pairs_here);
+    const std::vector<int2> tiles = p->pair ? pair_tiles(n, n, true) : cta_tiles(n, n, true);
     p->ntiles = int(tiles.size());
     const size_t one = size_t(n) * p->ld * 3;     // 16-bit elements per slice buffer (3 planes)
     const size_t tiles_b = sizeof(int2) * tiles.size();
@@ -1020,7 +1391,8 @@ hw_status tc_power_step(TcPower *p, int k, double *accU, double sign)
         a.acc_coef = p->pend_coef;
         a.accU = p->pend_accU;
     }
-    hw_status s = launch_tc(p->md.fmt, p->md.ns, p->nb, A, p->Y, a, p->ntiles, p->st);
+    hw_status s = p->pair ? launch_tc_pair(p->md.fmt, p->md.ns, p->nb, A, p->Y, a, p->ntiles, p->st)
+                          : launch_tc(p->md.fmt, p->md.ns, p->nb, A, p->Y, a, p->ntiles, p->st);
     p->pend_accU = accU;
     p->pend_coef = sign / s_k;
     p->pend_buf = nxt;

@@ -39,6 +39,19 @@ def test_version_and_opts():
     assert "sm_103a" in hw.hw_version()
     o = hw.hw_opts_init()
     assert (o.record_stride, o.taylor_degree, o.taylor_squarings, o.gemm_mode, o.tile) == (1, 0, -1, 0, 0)
+    assert (o.u_symmetric, o.addressing, o.shift, o.launch_mode, o.taylor_powers, o.gemm_tiles) == (0,) * 6
+
+
+def test_opts_struct_matches_header():
+    # hw_opts_init writes sizeof(hw_opts) bytes: the binding's struct must
+    # carry the header's fields, in order, all int32
+    import re
+    text = open(os.path.join(ROOT, "include", "hiperwalk_b300.h")).read()
+    body = text[text.index("typedef struct hw_opts {"):text.index("} hw_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"int32_t\s+(\w+)\s*;", body)
+    assert [f for f, _ in hw.hw_opts._fields_] == fields
+    assert ctypes.sizeof(hw.hw_opts) == 4 * len(fields)
 
 
 def _graphs():

@@ -117,6 +117,32 @@ def test_expm_c64_ragged_multi_tile(hw, name, g, gamma, marked, t, powers):
     G.free()
 
 
+@pytest.mark.parametrize("name,g,gamma,marked,t", [
+    ("reg3_exact", synth.random_regular(778, 3, seed=4), 1 / 3, [5, 700], 0.4),   # n not a multiple of 256
+    ("er_two_slices", synth.erdos_renyi(1000, 0.006, seed=6), 0.3, [990], 0.25),
+    ("Q12", synth.hypercube(12), 1 / 12, [1234], 0.1),                           # configuration 3's graph
+])
+@pytest.mark.parametrize("mode", [0, 2, 3])
+def test_expm_c64_pair_tiles_match_single_tiles(hw, name, g, gamma, marked, t, mode):
+    # the tensor-core powers on CTA pairs (256 x 256 tiles, hw_opts.gemm_tiles
+    # = 2) and on single CTAs (128 x 256, = 1) run the same MMAs in the same
+    # order per output element: U agrees bit for bit, in every precision mode
+    # (fp16 x 2; bf16 x 2; bf16 x 3), and matches the oracle's columns
+    n = g[0]
+    Us = []
+    for tiles in (1, 2):
+        G, U = gpu_expm(hw, g, gamma, marked, t, dt=1, powers=1, opts={"gemm_tiles": tiles, "gemm_mode": mode})
+        Us.append(U)
+        G.free()
+    import torch
+    assert torch.equal(Us[0], Us[1])
+    ar = oracle.Arcs(*g)
+    cols = np.array([0, 1, 255, 256, n // 2, n - 1])
+    ref = oracle.ctqw_columns(ar, gamma, t, cols, marked=marked)
+    tol = 2e-6 if mode != 2 else 2e-3   # bf16 x 2 keeps about 16 bits
+    assert np.max(np.abs(Us[1].cpu().numpy()[:, cols] - ref)) < tol
+
+
 @pytest.mark.parametrize("powers", POWERS)
 def test_expm_hypercube_closed_form(hw, powers):
     # no marks: U[u, v] = cos(gamma t)^(k-h) (i sin(gamma t))^h, h = Hamming distance
