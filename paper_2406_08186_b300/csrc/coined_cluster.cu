@@ -282,12 +282,32 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_coined_cluster(ClusterArgs a
     cluster_barrier();
 }
 
+// the kernel attributes (shared-memory limit kSmemLimit, non-portable
+// cluster size), set once per kernel and device: a walk of 100 steps takes
+// about 90 us, and two driver calls per launch are a visible part of that
+std::mutex g_attr_mu;
+
+template <typename R, int D>
+cudaError_t set_attributes_once()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return e != cudaSuccess ? e : cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (done[dev]) return cudaSuccess;
+    auto kern = k_coined_cluster<R, D>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
 template <typename R, int D>
 cudaError_t launch_one(const ClusterArgs &a, int ctas, int threads, size_t smem, cudaStream_t st)
 {
     auto kern = k_coined_cluster<R, D>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e == cudaSuccess && ctas > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = set_attributes_once<R, D>();
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
@@ -336,7 +356,8 @@ int cluster_ctas(size_t smem)
         const size_t probe = cls ? size_t(kSmemLimit) : size_t(100 * 1024);
         for (int c : {16, 8}) {
             auto kern = k_coined_cluster<double, 4>;
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(probe)) != cudaSuccess ||
+            // the attribute at the kernels' fixed limit (>= probe), as launches set it
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess ||
                 (c > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
                 cudaGetLastError();
                 continue;

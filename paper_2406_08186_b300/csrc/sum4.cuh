@@ -23,7 +23,7 @@
 //
 // Three forms compute the same function and return the same bits for every
 // input: sum4_rn_cases (one branch per case), sum4_rn (an early return for
-// four zeros, a select-only path for the common case, sum4_rn_cases for the
+// four zeros, a select-only path for the common case, short branches for the
 // rest) and sum4_rn_flat (selects throughout).  Which is fastest depends on
 // the kernel: measured, the four-arc kernels take sum4_rn and the loops over
 // groups of a long vertex take sum4_rn_flat.
@@ -95,8 +95,8 @@ HW_HD double sum4_seq(double x0, double x1, double x2, double x3)
 #endif
 }
 
-// The method with one branch per case: the fast path below returns the
-// common case itself and hands every other input to this form.
+// The method with one branch per case, the plainest statement of it (host
+// checks compare the other two forms with it and with rational arithmetic).
 HW_HD double sum4_rn_cases(double x0, double x1, double x2, double x3)
 {
     const double xs[4] = {x0, x1, x2, x3};
@@ -173,13 +173,6 @@ HW_HD double sum4_rn_cases(double x0, double x1, double x2, double x3)
     return sum4_seq(x0, x1, x2, x3);
 }
 
-#if defined(__CUDACC__)
-static __device__ __noinline__ double sum4_cases_dev(double x0, double x1, double x2, double x3)
-{
-    return sum4_rn_cases(x0, x1, x2, x3);
-}
-#endif
-
 HW_HD uint32_t lo32(uint64_t v) { return static_cast<uint32_t>(v); }
 HW_HD uint32_t hi32(uint64_t v) { return static_cast<uint32_t>(v >> 32); }
 
@@ -188,10 +181,11 @@ HW_HD uint32_t hi32(uint64_t v) { return static_cast<uint32_t>(v >> 32); }
 // four addends are aligned independently, summed as a tree (the negative ones
 // as one's complements plus their count) and rounded with selects only, so a
 // warp whose lanes see different signs and rounding cases runs one stream.
-// Inputs outside that path (infinite, NaN or subnormal addends, a spread of
-// more than 8 binades, a sum below 2^53 units of the grid, which includes an
-// exact cancellation, or a result outside the normal range) take
-// sum4_rn_cases, out of line.
+// The other cases branch off without recomputing anything: infinite, NaN or
+// subnormal addends, a spread of more than 8 binades and a result outside the
+// normal range take the sequential sum (out of line); an exact cancellation
+// returns +0; a sum that cancelled down to fewer than 54 bits is exact and is
+// shifted up instead of rounded.
 HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
 {
     const double xs[4] = {x0, x1, x2, x3};
@@ -213,13 +207,13 @@ HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
     }
     const int E01 = e[0] > e[1] ? e[0] : e[1], E23 = e[2] > e[3] ? e[2] : e[3];
     const int E = E01 > E23 ? E01 : E23;
-    bool rare = false;
+    bool special = false;
     uint32_t nneg = 0;
     uint64_t a[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int sft = E - e[i];
-        rare = rare || e[i] == 0x7ff || (nz[i] && (e[i] == 0 || sft > 8));
+        special = special || e[i] == 0x7ff || (nz[i] && (e[i] == 0 || sft > 8));
         // 53-bit significand (zero for a zero addend) placed at 2^(8 - sft)
         uint32_t mh = (hi[i] & 0xFFFFFu) | (nz[i] ? 0x100000u : 0u), ml = lo[i];
         shl64(mh, ml, (8 - sft) & 31);
@@ -234,23 +228,24 @@ HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
     const uint32_t th = hi32(mag), tl = lo32(mag);
     const int lz = th ? clz32(th) : 32 + clz32(tl);
     const int sh = 11 - lz;                           // bits below the kept 53
-    rare = rare || sh <= 0;
     // round to nearest even: add half a unit of the last kept bit less one,
     // plus that bit, then drop the sh low bits
     const uint32_t inc = ((1u << ((sh - 1) & 31)) - 1u) + ((tl >> (sh & 31)) & 1u);
     const uint64_t r = mag + inc;
     uint32_t kh = hi32(r), kl = lo32(r);
     shr64(kh, kl, sh & 31);
-    const uint32_t carry = kh >> 21;                  // the rounding carried to 2^53
-    const int B = E - 8 + sh + static_cast<int>(carry);
-    rare = rare || B < 1 || B > 0x7fe;
-    if (rare) {
-#if defined(__CUDA_ARCH__)
-        return sum4_cases_dev(x0, x1, x2, x3);
-#else
-        return sum4_rn_cases(x0, x1, x2, x3);
-#endif
+    uint32_t carry = kh >> 21;                        // the rounding carried to 2^53
+    if (special || sh <= 0) {
+        if (special) return sum4_seq(x0, x1, x2, x3);
+        if (mag == 0) return 0.0;                     // exact cancellation: +0 when rounding to nearest
+        // at most 53 significant bits: exact, shifted up to the leading bit
+        kh = th;
+        kl = tl;
+        shl64_wide(kh, kl, -sh);
+        carry = 0;
     }
+    const int B = E - 8 + sh + static_cast<int>(carry);
+    if (B < 1 || B > 0x7fe) return sum4_seq(x0, x1, x2, x3);
     // (B - 1 - carry) 2^52 + kept: the implicit bit (2^52, or 2^53 after a
     // carry) lands in the exponent field
     return fpconv::from_bits64((static_cast<uint64_t>(sgn) << 63) +
