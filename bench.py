@@ -50,8 +50,8 @@ TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
     # block row per torus row, complex128 sums by integer operations and
     # streaming loads and stores), one launch, cold L2
-    ("c128", "63463a7da7537292070fa3be1bf53f45f95a5359"): 67132416 + 16863232,
-    ("c64", "63463a7da7537292070fa3be1bf53f45f95a5359"): 33566976 + 268288,
+    ("c128", "28f36ff9b61036ab39926f1b82f91f8f1ef73b72"): 67131648 + 15994880,
+    ("c64", "28f36ff9b61036ab39926f1b82f91f8f1ef73b72"): 33566720 + 324864,
 }
 
 
