@@ -908,17 +908,18 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
 // Grover, any degree: thread per vertex, a pass for the sum and a pass (rows
 // read again, from L2) for the outputs
 template <typename R, int ADDR>
-__global__ void __launch_bounds__(kThreads) k_coined_em_rt(EmArgs a)
+__global__ void __launch_bounds__(kThreads, 4) k_coined_em_rt(EmArgs a)
 {
     using V = typename Cx<R>::T;
     const V *__restrict__ in = static_cast<const V *>(a.in);
     V *__restrict__ out = static_cast<V *>(a.out);
-    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t n = a.n;
+    // row j of vertex v at j n + v < 2|E| < 2^31 (the graph's limit): 32-bit indices
+    const int v = int(blockIdx.x) * int(blockDim.x) + int(threadIdx.x);
+    const int n = int(a.n);
     const int d = a.d;
     pdl_wait();
     if (v < n) {
-        const int mi = find_marked(a.mk, int(v));
+        const int mi = find_marked(a.mk, v);
         if (mi >= 0) {
             if (a.rec_part && a.rec_slot >= 0) {
                 double acc = 0.0;

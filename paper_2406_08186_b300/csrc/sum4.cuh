@@ -173,6 +173,22 @@ HW_HD double sum4_rn_cases(double x0, double x1, double x2, double x3)
     return sum4_seq(x0, x1, x2, x3);
 }
 
+// the per-case form out of line (the rare inputs of sum4_rn_flat)
+#if defined(__CUDACC__)
+static __device__ __noinline__ double sum4_cases_dev(double x0, double x1, double x2, double x3)
+{
+    return sum4_rn_cases(x0, x1, x2, x3);
+}
+#endif
+HW_HD double sum4_cases_call(double x0, double x1, double x2, double x3)
+{
+#if defined(__CUDA_ARCH__)
+    return sum4_cases_dev(x0, x1, x2, x3);
+#else
+    return sum4_rn_cases(x0, x1, x2, x3);
+#endif
+}
+
 HW_HD uint32_t lo32(uint64_t v) { return static_cast<uint32_t>(v); }
 HW_HD uint32_t hi32(uint64_t v) { return static_cast<uint32_t>(v >> 32); }
 
@@ -207,13 +223,19 @@ HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
     }
     const int E01 = e[0] > e[1] ? e[0] : e[1], E23 = e[2] > e[3] ? e[2] : e[3];
     const int E = E01 > E23 ? E01 : E23;
-    bool special = false;
+    // the smallest exponent field among the nonzero addends: infinity or NaN
+    // (E = 0x7ff), a subnormal (0) or a spread of more than 8 binades is special
+    int em[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) em[i] = nz[i] ? e[i] : 0x7ff;
+    const int Em01 = em[0] < em[1] ? em[0] : em[1], Em23 = em[2] < em[3] ? em[2] : em[3];
+    const int Em = Em01 < Em23 ? Em01 : Em23;
+    const bool special = E == 0x7ff || Em == 0 || E - Em > 8;
     uint32_t nneg = 0;
     uint64_t a[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int sft = E - e[i];
-        special = special || e[i] == 0x7ff || (nz[i] && (e[i] == 0 || sft > 8));
         // 53-bit significand (zero for a zero addend) placed at 2^(8 - sft)
         uint32_t mh = (hi[i] & 0xFFFFFu) | (nz[i] ? 0x100000u : 0u), ml = lo[i];
         shl64(mh, ml, (8 - sft) & 31);
@@ -254,7 +276,8 @@ HW_HD double sum4_rn(double x0, double x1, double x2, double x3)
 }
 
 // The same function with every step as a select (no early return for zeros
-// either) up to the fallback to the sequential sum: used where the terms are
+// either) up to one branch to the per-case form (special inputs, a sum that
+// cancelled below 54 bits, a result outside the normal range): used where the terms are
 // general complex amplitudes, summed in a loop of groups, so that the code a
 // group inlines stays short.
 HW_HD double sum4_rn_flat(double x0, double x1, double x2, double x3)
@@ -273,13 +296,17 @@ HW_HD double sum4_rn_flat(double x0, double x1, double x2, double x3)
     }
     const int E01 = e[0] > e[1] ? e[0] : e[1], E23 = e[2] > e[3] ? e[2] : e[3];
     const int E = E01 > E23 ? E01 : E23;
-    bool special = false;
+    int em[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) em[i] = nz[i] ? e[i] : 0x7ff;
+    const int Em01 = em[0] < em[1] ? em[0] : em[1], Em23 = em[2] < em[3] ? em[2] : em[3];
+    const int Em = Em01 < Em23 ? Em01 : Em23;
+    const bool special = E == 0x7ff || Em == 0 || E - Em > 8;
     uint32_t nneg = 0;
     uint64_t a[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int sft = E - e[i];
-        special = special || e[i] == 0x7ff || (nz[i] && (e[i] == 0 || sft > 8));
         uint32_t mh = (hi[i] & 0xFFFFFu) | (nz[i] ? 0x100000u : 0u), ml = lo[i];
         shl64(mh, ml, (8 - sft) & 31);
         const uint32_t neg = hi[i] >> 31, m = 0u - neg;
@@ -292,13 +319,12 @@ HW_HD double sum4_rn_flat(double x0, double x1, double x2, double x3)
     const uint32_t th = hi32(mag), tl = lo32(mag);
     const int lz = th ? clz32(th) : 32 + clz32(tl);
     const int sh = 11 - lz;
-    // sh > 0: round to nearest even; sh <= 0: exact, shifted up
-    const int sr = sh > 0 ? sh : 0, sl = sh > 0 ? 0 : -sh;
-    const uint32_t inc = sr ? ((1u << ((sr - 1) & 31)) - 1u) + ((tl >> sr) & 1u) : 0u;
+    // round to nearest even (sh > 0; a sum that cancelled below 54 bits,
+    // sh <= 0, is exact and goes to the per-case form)
+    const uint32_t inc = ((1u << ((sh - 1) & 31)) - 1u) + ((tl >> (sh & 31)) & 1u);
     const uint64_t r = mag + inc;
     uint32_t kh = hi32(r), kl = lo32(r);
-    shr64(kh, kl, sr);
-    shl64_wide(kh, kl, sl);
+    shr64(kh, kl, sh & 31);
     const uint32_t carry = kh >> 21;
     const int B = E - 8 + sh + static_cast<int>(carry);
     const uint64_t bits = (static_cast<uint64_t>(sgn) << 63) +
@@ -306,8 +332,8 @@ HW_HD double sum4_rn_flat(double x0, double x1, double x2, double x3)
                           join(kh, kl);
     const bool allzero = !(nz[0] || nz[1] || nz[2] || nz[3]);
     const bool cancel = mag == 0;
-    const bool ok = allzero || (!special && (cancel || (B >= 1 && B <= 0x7fe)));
-    if (!ok) return sum4_seq(x0, x1, x2, x3);
+    const bool ok = allzero || (!special && (cancel || (sh > 0 && B >= 1 && B <= 0x7fe)));
+    if (!ok) return sum4_cases_call(x0, x1, x2, x3);
     const uint32_t allneg = (hi[0] & hi[1] & hi[2] & hi[3]) >> 31;
     return fpconv::from_bits64(allzero ? (static_cast<uint64_t>(allneg) << 63) : cancel ? 0ull : bits);
 }
