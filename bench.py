@@ -390,6 +390,7 @@ def run_ours(args):
         # and error figures
         cpu = not args.no_cpu_baseline
         line["cfg1_torus64"] = sub_torus64(hw, reps=max(args.steps, 10), warmup=args.warmup, with_cpu=cpu)
+        line["hypercube20_c128"] = sub_hypercube20(hw, reps=5)
         line["cfg3_hypercube12"] = sub_ctqw_q12(hw, reps=3, warmup=1, with_cpu=cpu)
         line["cfg4_er_batched"] = sub_er_batched(hw, reps=3, warmup=1, with_cpu=cpu)
         line["cfg5_serving"] = sub_serving(hw, args.serving_jobs)
@@ -645,6 +646,53 @@ def er_graph():
     n0 = 1 << 20
     n, eu, ev = synth.erdos_renyi(n0, 8.0 / (n0 - 1), seed=5)
     return n, eu, ev
+
+
+def sub_hypercube20(hw, reps):
+    """The complex128 Grover coin of degree 20 (the 2^20-vertex hypercube,
+    index-free, uniform start, one seeded mark): the two-pass kernel that the
+    serving mix's largest coined jobs run.  Time per walk step = (evolve of 120
+    steps - evolve of 20 steps) / 100, each call after an L2 flush, median of
+    `reps`; bytes per step = the state read and written once."""
+    import torch
+    k = 20
+    n, eu, ev = synth.hypercube(k)
+    row_ptr, col = synth.adjacency_csr(n, eu, ev)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    arcs = G.num_arcs
+    x = torch.full((arcs,), 1 / math.sqrt(arcs), dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    m = synth.seeded_vertex(3, n)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    hw.hw_coined_evolve(G, 0, [m], hw.HW_C128, 1, 20, x, y)
+    torch.cuda.synchronize()
+    times = {}
+    with Clocks(torch.cuda.current_device()) as clk:
+        for steps in (20, 120):
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e = _events(2)
+                e[0].record(stream)
+                hw.hw_coined_evolve(G, 0, [m], hw.HW_C128, 1, steps, x, y)
+                e[1].record(stream)
+                torch.cuda.synchronize()
+                ts.append(e[0].elapsed_time(e[1]) / 1e3)
+            times[steps] = sorted(ts)[len(ts) // 2]
+    per = (times[120] - times[20]) / 100
+    peak, src = measured_peaks()
+    byts = 2 * 16 * arcs
+    norm = float((y.abs() ** 2).sum().item())
+    del flush
+    G.free()
+    return {"workload": "hypercube20_c128_coined", "n": n, "arcs": arcs, "marked": m, "dtype": "f64",
+            "us_per_walk_step": per * 1e6, "value": arcs / per, "unit": "arc-updates/s",
+            "l2": "256 MiB written before every timed call; the 671 MB step exceeds L2",
+            "roofline": {"bound": "hbm", "kernel": "k_coined_em_rt<double,cube>", "achieved": byts / per / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": byts / per / 1e9 / peak, "bytes_per_step": byts,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % src},
+            "norm_after": norm, "clocks": clk.summary()}
 
 
 def sub_er_batched(hw, reps, warmup, with_cpu):
