@@ -623,6 +623,7 @@ def sub_ctqw_q12(hw, reps, warmup, with_cpu):
                           "p_L1": float((p64 - p128).abs().sum().item()),
                           "p_m_record_max_abs": float((rec64 - rec128).abs().max().item())}
     res["c128_sparse_vs_dense_U_max_abs"] = float((U128s - U128d).abs().max().item())
+    res["gamma_critical"] = critical_gamma_variant(hw, G, n, m, stream)
     if with_cpu:
         import oracle
         ar = oracle.Arcs(*g)
@@ -646,6 +647,47 @@ def er_graph():
     n0 = 1 << 20
     n, eu, ev = synth.erdos_renyi(n0, 8.0 / (n0 - 1), seed=5)
     return n, eu, ev
+
+
+def critical_gamma_variant(hw, G, n, m, stream):
+    """Configuration 3 at the critical gamma_c = sum_r C(k, r)/r / (2N) of the
+    hypercube Q_k (1/12 is off-critical at k = 12): one expm and 2000
+    applications per precision, the marked-probability curve's maximum and
+    its time, and the curve's error against the exact Hamming-weight reduction
+    (one mark, uniform start: a (k+1)-dimensional H, diagonalised here)."""
+    import torch
+    k = int(round(math.log2(n)))
+    gamma = sum(math.comb(k, r) / r for r in range(1, k + 1)) / (2 * n)
+    A = np.zeros((k + 1, k + 1))
+    for r in range(k):
+        A[r, r + 1] = A[r + 1, r] = math.sqrt((r + 1) * (k - r))
+    H = -gamma * A
+    H[0, 0] -= 1.0
+    w, V = np.linalg.eigh(H)
+    x0 = np.array([math.sqrt(math.comb(k, r) / n) for r in range(k + 1)])
+    times = 0.1 * np.arange(1, 2001)
+    ref = np.abs((V[0, :][None, :] * np.exp(-1j * np.outer(times, w))) @ (V.T @ x0)) ** 2
+    out = {"gamma": gamma, "exact_p_m_max": float(ref.max()), "exact_t_at_max": float(times[int(np.argmax(ref))])}
+    for dt, name in ((hw.HW_C128, "c128"), (hw.HW_C64, "c64")):
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        U = torch.empty((n, n), dtype=cdt, device="cuda")
+        x = torch.full((n,), 1 / math.sqrt(n), dtype=cdt, device="cuda")
+        y = torch.empty_like(x)
+        rec = torch.empty(2000, dtype=torch.float64, device="cuda")
+        e = _events(4)
+        e[0].record(stream)
+        hw.hw_ctqw_expm(G, gamma, [m], 0.1, dt, U)
+        e[1].record(stream)
+        e[2].record(stream)
+        hw.hw_ctqw_evolve(U, n, dt, 1, 2000, x, y, [m], rec, opts={"u_symmetric": 1})
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        r = rec.cpu().numpy()
+        out[name] = {"expm_ms": e[0].elapsed_time(e[1]), "apply_us": e[2].elapsed_time(e[3]) * 1e3 / 2000,
+                     "p_m_max": float(r.max()), "t_at_max": float(times[int(np.argmax(r))]),
+                     "record_max_abs_vs_exact": float(np.max(np.abs(r - ref)))}
+        del U
+    return out
 
 
 def sub_hypercube20(hw, reps):

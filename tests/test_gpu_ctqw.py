@@ -271,6 +271,56 @@ def test_config3_hypercube12_search_full_size(hw, dt, powers):
     G.free()
 
 
+def _hamming_reduction(k, gamma, m_steps, tstep, m):
+    # one marked vertex, uniform start: the state stays on the Hamming-weight
+    # classes |r> around the mark, A|r> = sqrt(r (k-r+1))|r-1> + sqrt((r+1)(k-r))|r+1>,
+    # and H = -gamma A - |0><0| is (k+1) x (k+1): exact p_m(t) for every step,
+    # and the final probabilities (constant on each class)
+    import math
+    N = 1 << k
+    A = np.zeros((k + 1, k + 1))
+    for r in range(k):
+        A[r, r + 1] = A[r + 1, r] = math.sqrt((r + 1) * (k - r))
+    H = -gamma * A
+    H[0, 0] -= 1.0
+    w, V = np.linalg.eigh(H)
+    x0 = np.array([math.sqrt(math.comb(k, r) / N) for r in range(k + 1)])
+    times = tstep * np.arange(1, m_steps + 1)
+    amp0 = (V[0, :][None, :] * np.exp(-1j * np.outer(times, w))) @ (V.T @ x0)
+    xr = V @ (np.exp(-1j * w * times[-1]) * (V.T @ x0))
+    hd = np.array([bin(v ^ m).count("1") for v in range(N)])
+    prob = np.abs(xr[hd]) ** 2 / np.array([math.comb(k, r) for r in hd])
+    return np.abs(amp0) ** 2, prob
+
+
+@pytest.mark.parametrize("dt", [2, 1])
+def test_config3_critical_gamma_against_hamming_reduction(hw, dt):
+    # configuration 3 at the critical gamma_c = sum_r C(k, r)/r / (2N) of Q_12
+    # (0.09298...; 1/12 is off-critical): the marked probability rises to about
+    # 0.84 near t = 108 instead of peaking at 0.078; the recorded curve of all
+    # 2000 applications against the exact Hamming-weight reduction
+    import math
+    k, tstep, steps = 12, 0.1, 2000
+    N = 1 << k
+    gamma = sum(math.comb(k, r) / r for r in range(1, k + 1)) / (2 * N)
+    g = synth.hypercube(k)
+    m = synth.seeded_vertex(3, N)
+    G, U = gpu_expm(hw, g, gamma, [m], tstep, dt=dt, powers=0)
+    _, rec, prob, norm = gpu_evolve(hw, U, synth.uniform_state(N), steps, [m], dt=dt)
+    ref, prob_ref = _hamming_reduction(k, gamma, steps, tstep, m)
+    if dt == 2:
+        assert np.max(np.abs(rec - ref)) <= TOL128
+        assert np.max(np.abs(prob - prob_ref)) <= TOL128
+    else:
+        # complex64: L1 of the probabilities <= 1e-3 (the stated bound), which
+        # also bounds the error of any one of them, p_m(t) included (here p_m
+        # reaches 0.84, so its absolute error is larger than at gamma = 1/12)
+        assert np.sum(np.abs(prob - prob_ref)) <= 1e-3
+        assert np.max(np.abs(rec - ref)) <= 1e-3
+    assert 0.8 < rec.max() < 0.9 and 100.0 < tstep * (1 + int(np.argmax(rec))) < 115.0
+    G.free()
+
+
 def torch_index(cols):
     import torch
     return torch.from_numpy(np.asarray(cols)).cuda()
