@@ -906,9 +906,11 @@ __global__ void __launch_bounds__(kThreads) k_coined_em(EmArgs a)
 }
 
 // Grover, any degree: thread per vertex, a pass for the sum and a pass (rows
-// read again, from L2) for the outputs
+// read again, from L2) for the outputs; blocks of kRtThreads threads, half an
+// SM's warp slots (64 registers a thread)
+constexpr int kRtThreads = 128;
 template <typename R, int ADDR>
-__global__ void __launch_bounds__(kThreads, 4) k_coined_em_rt(EmArgs a)
+__global__ void __launch_bounds__(kRtThreads, 2048 / kRtThreads / 2) k_coined_em_rt(EmArgs a)
 {
     using V = typename Cx<R>::T;
     const V *__restrict__ in = static_cast<const V *>(a.in);
@@ -1235,9 +1237,11 @@ static void launch_em(int d, int addr, const EmArgs &a, cudaStream_t st)
         else if (cube_regs_kernel<R>(d))
             launch_cube<R, kAddrTable>(d, grid, a, st);
         else if (addr == kAddrCube)
-            launch_pdl(k_coined_em_rt<R, kAddrCube>, grid, dim3(kThreads), 0, st, a);
+            launch_pdl(k_coined_em_rt<R, kAddrCube>, dim3(unsigned((a.n + kRtThreads - 1) / kRtThreads)),
+                       dim3(kRtThreads), 0, st, a);
         else
-            launch_pdl(k_coined_em_rt<R, kAddrTable>, grid, dim3(kThreads), 0, st, a);
+            launch_pdl(k_coined_em_rt<R, kAddrTable>, dim3(unsigned((a.n + kRtThreads - 1) / kRtThreads)),
+                       dim3(kRtThreads), 0, st, a);
         break;
     }
 }
