@@ -244,7 +244,8 @@ __device__ void serve_coined_em_rt(const SJob &Jg, int64_t w, int v0, int v1)
     const V *__restrict__ in = static_cast<const V *>(Jg.X[w & 1]);
     V *__restrict__ out = static_cast<V *>(Jg.X[(w + 1) & 1]);
     const int32_t *__restrict__ revE = Jg.revE;
-    const int64_t n = Jg.n;
+    // row j of vertex v at j n + v < 2|E| < 2^31 (the graph's limit): 32-bit indices
+    const int n = int(Jg.n);
     const int d = Jg.d;
     const bool cube = Jg.fam == HW_GRAPH_HYPERCUBE;   // uniform across the tile
     const int nm = Jg.n_marked;
