@@ -50,8 +50,8 @@ TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
     # block row per torus row, complex128 sums by integer operations and
     # streaming loads and stores), one launch, cold L2
-    ("c128", "28f36ff9b61036ab39926f1b82f91f8f1ef73b72"): 67131648 + 15994880,
-    ("c64", "28f36ff9b61036ab39926f1b82f91f8f1ef73b72"): 33566720 + 324864,
+    ("c128", "c781ebb1d551f72bbb19783a802fdbbaf0b69b27"): 67135488 + 16496640,
+    ("c64", "c781ebb1d551f72bbb19783a802fdbbaf0b69b27"): 33566464 + 281856,
 }
 
 
