@@ -2,8 +2,9 @@
 cluster holding the state in distributed shared memory, Sec. 3.2): against the
 FP64 oracle (complex128 1e-12), bit-identical to the one-launch-per-step path
 (hw_opts.launch_mode = 1), with marks, a strided record, in place, the
-persistent shift, ragged vertex ranges, fewer vertices than CTAs, degrees 2..8
-and the largest size the path takes."""
+persistent shift, ragged vertex ranges, fewer vertices than CTAs, more
+vertices per CTA than thread pairs, degrees 2..8 and the largest size the
+path takes."""
 import numpy as np
 import pytest
 
@@ -21,6 +22,9 @@ CASES = [
     ("reg5", synth.random_regular(600, 5, seed=8)),
     ("reg8", synth.random_regular(2048, 8, seed=6)),    # 16384 arcs: the complex128 size limit
     ("torus64x96", synth.torus_rect(64, 96)),           # 24576 arcs: the complex64 size limit
+    # 24000 arcs (complex64 in one launch): 750 vertices per CTA against 512
+    # thread pairs, so threads take a second vertex in a step
+    ("cycle12000", synth.cycle(12000)),
 ]
 
 
