@@ -1042,6 +1042,7 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     if (m_deg > 40 || sq > 60) return hw_fail(HW_EINVAL, "Taylor degree %d / squarings %d out of range", m_deg, sq);
     const int gmode = opts ? opts->gemm_mode : 0;
     if (gmode < 0 || gmode > 4) return hw_fail(HW_EINVAL, "gemm_mode must be 0..4");
+    if (opts && (opts->gemm_tiles < 0 || opts->gemm_tiles > 2)) return hw_fail(HW_EINVAL, "gemm_tiles must be 0..2");
     const double tau = time / std::ldexp(1.0, sq);
     const int64_t nn = int64_t(n) * n;
     const size_t bytes = sizeof(double) * nn;
@@ -1049,8 +1050,8 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     const int powers = opts ? opts->taylor_powers : 0;
     if (powers < 0 || powers > 2) return hw_fail(HW_EINVAL, "taylor_powers must be 0, 1 or 2");
     // default: the measured faster form on the 4096-vertex hypercube search
-    // (complex128: sparse x dense 6.3 ms against 697 ms of FP64 GEMMs;
-    // complex64: tensor-core GEMMs 1.56 ms against 1.93 ms sparse x dense)
+    // (complex128: sparse x dense 4.9 ms against 697 ms of FP64 GEMMs;
+    // complex64: tensor-core GEMMs on CTA pairs 1.24 ms against 1.60 ms sparse x dense)
     const bool sparse = powers == 2 || (powers == 0 && (dt == HW_C128 || !tc_gemm_available()));
     const bool use_tc = !sparse && (dt == HW_C64) && tc_gemm_available();
     DevBuf Y(st), Q(st), Qn(st), Re(st), Im(st), Qf(st), Qfn(st);

@@ -81,7 +81,7 @@ enum { FMT_BF16 = 0, FMT_F16 = 1 };
 enum { EPI_STORE = 0, EPI_TAYLOR = 1 };
 
 struct TcArgs {
-    const int2 *tiles;       // CTA tiles (P, Q): rows 128 P.., columns 256 Q..
+    const int2 *tiles;       // tiles (P, Q): rows 128 P.. (CTA pairs: 256 P..), columns 256 Q..
     int m, n, k;
     int epi;
     int sym;                 // skip blocks below the diagonal, mirror the others

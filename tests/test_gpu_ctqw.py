@@ -271,6 +271,13 @@ def test_config3_hypercube12_search_full_size(hw, dt, powers):
     G.free()
 
 
+@pytest.mark.parametrize("powers", [1, 2])
+def test_expm_rejects_bad_tile_form(hw, powers):
+    # hw_opts.gemm_tiles is 0..2 whatever form the powers take
+    with pytest.raises(hw.HWError):
+        gpu_expm(hw, synth.hypercube(6), 1 / 6, [5], 0.1, dt=1, powers=powers, opts={"gemm_tiles": 3})
+
+
 def _hamming_reduction(k, gamma, m_steps, tstep, m):
     # one marked vertex, uniform start: the state stays on the Hamming-weight
     # classes |r> around the mark, A|r> = sqrt(r (k-r+1))|r-1> + sqrt((r+1)(k-r))|r+1>,
