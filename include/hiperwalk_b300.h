@@ -88,11 +88,17 @@ typedef struct hw_opts {
                                   S|v,w> = |w,v> (default); 1 = persistent, S|v,w> = |w,u> with
                                   u - w = w - v, the walker keeping its direction (graphs that
                                   hw_graph_structure recognises as a torus only, else HW_EINVAL) */
-    int32_t launch_mode;       /* hw_coined_evolve, batch 1, Grover, regular graph of degree 2..8:
-                                  0 = default: when the walk is small (up to 16384 arcs in
-                                  complex128, 24576 in complex64) every step runs in one
-                                  launch, the state held in the shared memory of one
-                                  thread-block cluster; 1 = one launch per step.  Both give
+    int32_t launch_mode;       /* hw_coined_evolve, batch 1, Grover, regular graph of degree 2..8
+                                  whose arcs fit the shared memory of one thread-block cluster
+                                  (about 60000 arcs in complex128, 110000 in complex64): every
+                                  step can run in one launch, the state held in that shared
+                                  memory.  0 = default: the cheaper of the two paths for the
+                                  call's step count, from their fixed and per-step costs
+                                  measured on the first such call per (graph, dtype, shift),
+                                  which then synchronises the stream once (under stream
+                                  capture: one launch up to 16384 arcs in complex128, 24576 in
+                                  complex64); 1 = one launch per step; 2 = one launch
+                                  (HW_EUNSUPPORTED when the walk does not fit).  All give
                                   bit-identical results. */
     int32_t taylor_powers;     /* hw_ctqw_expm: how the powers Y^k / k! of Y = H time / 2^s are
                                   formed.  1 = dense n^3 products: FP64 GEMMs for HW_C128,

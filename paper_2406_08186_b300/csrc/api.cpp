@@ -188,6 +188,71 @@ hw_status coined_opts(const hw_graph *g, const hw_opts *opts, int *shift, bool *
     *index_free = addressing == 0;
     return HW_OK;
 }
+// Whether a batch-1 walk of `steps` steps that fits one thread-block cluster
+// runs in one launch (hw_opts.launch_mode 0).  The choice rests on the
+// measured fixed and per-step cost of both paths on this graph, dtype and
+// shift: measured once, on the first such call (8 and 40 steps of each from
+// psi_in into scratch, through hw_coined_evolve itself with launch_mode 2 and
+// 1, which synchronises the stream once), then kept on the graph.  Under
+// stream capture nothing can be timed and the size rule decides.
+hw_status choose_one_launch(const hw_graph *g, hw_coin coin, hw_dtype dt, const hw_opts *opts, int shift,
+                            int64_t steps, const void *psi_in, size_t bytes, cudaStream_t st, bool *one)
+{
+    const int key = int(dt) * 4 + shift;
+    std::array<double, 4> c{};
+    bool known = false;
+    {
+        std::lock_guard<std::mutex> lock(g->tune_mu);
+        auto it = g->walk_cost.find(key);
+        if (it != g->walk_cost.end()) { c = it->second; known = true; }
+    }
+    if (!known) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            *one = coined_cluster_by_size(g, dt);
+            return HW_OK;
+        }
+        Scratch out(st);
+        hw_status s = out.get(bytes, "scratch allocation (launch choice)");
+        if (s != HW_OK) return s;
+        hw_opts o;
+        if (opts) o = *opts; else hw_opts_init(&o);
+        o.record_stride = 1;
+        cudaEvent_t ev[5] = {};
+        for (auto &e : ev)
+            if (s == HW_OK) s = hw_cuda(cudaEventCreate(&e), "cudaEventCreate");
+        float ms[4] = {};
+        for (int m = 0; m < 2 && s == HW_OK; ++m) {
+            o.launch_mode = (m == 0) ? 2 : 1;
+            // a warm-up, then 8 and 40 steps between events
+            s = hw_coined_evolve(g, coin, nullptr, 0, dt, 1, 8, psi_in, out.p, nullptr, &o, st);
+            if (s == HW_OK) s = hw_cuda(cudaEventRecord(ev[0], st), "event record");
+            if (s == HW_OK) s = hw_coined_evolve(g, coin, nullptr, 0, dt, 1, 8, psi_in, out.p, nullptr, &o, st);
+            if (s == HW_OK) s = hw_cuda(cudaEventRecord(ev[1], st), "event record");
+            if (s == HW_OK) s = hw_coined_evolve(g, coin, nullptr, 0, dt, 1, 40, psi_in, out.p, nullptr, &o, st);
+            if (s == HW_OK) s = hw_cuda(cudaEventRecord(ev[2], st), "event record");
+            if (s == HW_OK) s = hw_cuda(cudaEventSynchronize(ev[2]), "launch choice");
+            if (s == HW_OK) {
+                cudaEventElapsedTime(&ms[2 * m], ev[0], ev[1]);
+                cudaEventElapsedTime(&ms[2 * m + 1], ev[1], ev[2]);
+            }
+        }
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        if (s != HW_OK) return s;
+        for (int m = 0; m < 2; ++m) {
+            const double per = std::max(0.0, (double(ms[2 * m + 1]) - double(ms[2 * m])) / 32.0);
+            c[2 * m] = std::max(0.0, double(ms[2 * m]) - 8.0 * per);
+            c[2 * m + 1] = per;
+        }
+        std::lock_guard<std::mutex> lock(g->tune_mu);
+        g->walk_cost[key] = c;
+    }
+    *one = c[0] + c[1] * double(steps) <= c[2] + c[3] * double(steps);
+    return HW_OK;
+}
+
 }  // namespace
 
 extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int32_t *marked,
@@ -210,7 +275,7 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
     if (stride < 1) return hw_fail(HW_EINVAL, "record_stride must be >= 1");
     if (opts && (opts->tile < 0 || opts->tile > 14)) return hw_fail(HW_EINVAL, "tile must be 0..14");
     const int launch_mode = opts ? opts->launch_mode : 0;
-    if (launch_mode != 0 && launch_mode != 1) return hw_fail(HW_EINVAL, "launch_mode must be 0 or 1");
+    if (launch_mode < 0 || launch_mode > 2) return hw_fail(HW_EINVAL, "launch_mode must be 0, 1 or 2");
     int shift = kShiftFlipFlop;
     bool index_free = false;
     if (hw_status so = coined_opts(g, opts, &shift, &index_free); so != HW_OK) return so;
@@ -266,7 +331,15 @@ extern "C" hw_status hw_coined_evolve(const hw_graph *g, hw_coin coin, const int
         }
     }
 
-    if (batch == 1 && launch_mode == 0 && coined_cluster_supported(g, coin, dt)) {
+    const bool fits = batch == 1 && launch_mode != 1 && coined_cluster_supported(g, coin, dt);
+    if (launch_mode == 2 && !fits)
+        return hw_fail(HW_EUNSUPPORTED, "launch_mode 2: the walk does not fit one thread-block cluster (batch 1, "
+                                        "Grover, regular of degree 2..8, the arcs in the cluster's shared memory)");
+    bool one_launch = fits && launch_mode == 2;
+    if (fits && launch_mode == 0 &&
+        (s = choose_one_launch(g, coin, dt, opts, shift, steps, psi_in, bytes, st, &one_launch)) != HW_OK)
+        return s;
+    if (one_launch) {
         // small regular graph: every step in one launch, the state held in
         // the shared memory of one thread-block cluster; the kernel records
         // the marked probability after every stride-th step itself

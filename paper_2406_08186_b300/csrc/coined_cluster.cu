@@ -399,15 +399,21 @@ bool coined_cluster_supported(const hw_graph *g, hw_coin coin, hw_dtype dt)
 {
     if (coin != HW_COIN_GROVER || g->min_degree != g->max_degree || g->max_degree < 2 || g->max_degree > 8)
         return false;
-    // the single launch pays off while a step is too small to fill the GPU.
-    // Measured per walk step (one launch per step: 2.4 us whatever the size
-    // below these limits): complex128 2.25 us on 16384 arcs, 4.8 us on 32000;
-    // complex64 0.74 us on 16384, 3.3 us on 32000
-    const int64_t limit = dt == HW_C128 ? 16384 : 24576;
-    if (g->num_arcs > limit) return false;
     int vpc = 0;
-    return cluster_smem(g, dt, kMaxClusterCtas, &vpc) <= size_t(kSmemLimit) &&
-           cluster_ctas(cluster_smem(g, dt, kMaxClusterCtas, &vpc)) > 0;
+    const size_t smem = cluster_smem(g, dt, kMaxClusterCtas, &vpc);
+    return smem <= size_t(kSmemLimit) && cluster_ctas(smem) > 0;
+}
+
+// Whether the single launch pays off without a measurement of this graph:
+// one launch per step costs about 2.4 us whatever the size below these
+// limits, and the single launch (measured on tori, hypercubes, cycles and
+// random regular graphs) costs about 0.35 us plus 0.7 ns (complex128) or
+// 0.15 ns (complex64) per arc of a CTA plus 2 ns per arc it exchanges with
+// another CTA, so it wins on every graph below these sizes but on some random
+// regular graphs close to them
+bool coined_cluster_by_size(const hw_graph *g, hw_dtype dt)
+{
+    return g->num_arcs <= (dt == HW_C128 ? 16384 : 24576);
 }
 
 hw_status launch_coined_cluster(const hw_graph *g, hw_dtype dt, const void *in, void *out, int64_t steps,

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <map>
 #include <utility>
@@ -56,6 +57,10 @@ struct hw_graph {
     // autotuned launch shape of the batched kernel per (batch, dtype)
     mutable std::mutex tune_mu;
     mutable std::map<long long, int> tune_rows;
+    // measured cost of a batch-1 coined walk (hw_coined_evolve, launch_mode 0)
+    // per (dtype, shift): {fixed, per step} of the single launch, then of one
+    // launch per step, in milliseconds
+    mutable std::map<int, std::array<double, 4>> walk_cost;
 };
 
 // ---- errors (api.cpp)
@@ -151,6 +156,7 @@ hw_status launch_coined_step_batched(const hw_graph *g, hw_dtype dt, hw_coin coi
                                      const CoinedStep &s, int tile, cudaStream_t st);
 // whole walks of small regular graphs in one thread-block cluster (coined_cluster.cu)
 bool coined_cluster_supported(const hw_graph *g, hw_coin coin, hw_dtype dt);
+bool coined_cluster_by_size(const hw_graph *g, hw_dtype dt);
 hw_status launch_coined_cluster(const hw_graph *g, hw_dtype dt, const void *in, void *out, int64_t steps,
                                 const MarkedList &mk, double *rec_part, int64_t stride, const int32_t *shift,
                                 cudaStream_t st);

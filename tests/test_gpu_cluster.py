@@ -1,10 +1,10 @@
 """Whole coined walks of small regular graphs in one launch (one thread-block
 cluster holding the state in distributed shared memory, Sec. 3.2): against the
 FP64 oracle (complex128 1e-12), bit-identical to the one-launch-per-step path
-(hw_opts.launch_mode = 1), with marks, a strided record, in place, the
-persistent shift, ragged vertex ranges, fewer vertices than CTAs, more
-vertices per CTA than thread pairs, degrees 2..8 and the largest size the
-path takes."""
+(hw_opts.launch_mode 2 against 1, and the default's measured choice), with
+marks, a strided record, in place, the persistent shift, ragged vertex
+ranges, fewer vertices than CTAs, more vertices per CTA than thread pairs,
+degrees 2..8 and sizes up to 49152 arcs."""
 import numpy as np
 import pytest
 
@@ -20,11 +20,12 @@ CASES = [
     ("Q7", synth.hypercube(7)),                         # degree 7
     ("reg3", synth.random_regular(1002, 3, seed=4)),
     ("reg5", synth.random_regular(600, 5, seed=8)),
-    ("reg8", synth.random_regular(2048, 8, seed=6)),    # 16384 arcs: the complex128 size limit
-    ("torus64x96", synth.torus_rect(64, 96)),           # 24576 arcs: the complex64 size limit
+    ("reg8", synth.random_regular(2048, 8, seed=6)),    # 16384 arcs, almost all exchanged between CTAs
+    ("torus64x96", synth.torus_rect(64, 96)),           # 24576 arcs
     # 24000 arcs (complex64 in one launch): 750 vertices per CTA against 512
     # thread pairs, so threads take a second vertex in a step
     ("cycle12000", synth.cycle(12000)),
+    ("torus96x128", synth.torus_rect(96, 128)),         # 49152 arcs: fits the cluster in both precisions
 ]
 
 
@@ -47,15 +48,17 @@ def test_cluster_walk_matches_oracle_and_per_step_path(hw, name, g, dt):
     x = torch.from_numpy(psi0).to("cuda", cdt)
     slots = steps // stride
     outs, recs = [], []
-    for mode in (0, 1):
+    # one launch, one launch per step, and the default's measured choice
+    for mode in (2, 1, 0):
         y = torch.empty_like(x)
         rec = torch.empty(slots, dtype=torch.float64, device="cuda")
         hw.hw_coined_evolve(G, 0, marked, dt, 1, steps, x, y, rec, opts={"record_stride": stride, "launch_mode": mode})
         outs.append(y)
         recs.append(rec)
     torch.cuda.synchronize()
-    assert torch.equal(outs[0], outs[1])
-    assert torch.equal(recs[0], recs[1])
+    for k in (1, 2):
+        assert torch.equal(outs[0], outs[k])
+        assert torch.equal(recs[0], recs[k])
     ref, rr = oracle.coined_evolve(ar, psi0, steps, marked=marked, record=True)
     got = outs[0].cpu().numpy().astype(np.complex128)
     if dt == 2:
@@ -76,7 +79,7 @@ def test_cluster_walk_in_place_and_persistent_shift(hw):
     psi0 = synth.random_state(ar.num_arcs, seed=3)
     for shift in (0, 1):
         x = torch.from_numpy(psi0).cuda()
-        hw.hw_coined_evolve(G, 0, [17], 2, 1, 21, x, x, opts={"shift": shift})   # in place, odd steps
+        hw.hw_coined_evolve(G, 0, [17], 2, 1, 21, x, x, opts={"shift": shift, "launch_mode": 2})   # in place, odd steps
         ref = oracle.coined_evolve(ar, psi0, 21, marked=[17], persistent_torus=(L1, L2) if shift else None)
         torch.cuda.synchronize()
         assert np.max(np.abs(x.cpu().numpy() - ref)) <= 1e-12
@@ -98,7 +101,7 @@ def test_configuration1_in_one_launch_dihedral_symmetry(hw):
     x = torch.from_numpy(psi0).cuda()
     y = torch.empty_like(x)
     prob = torch.empty(n, dtype=torch.float64, device="cuda")
-    hw.hw_coined_evolve(G, 0, [], 2, 1, 100, x, y)
+    hw.hw_coined_evolve(G, 0, [], 2, 1, 100, x, y, opts={"launch_mode": 2})
     hw.hw_probability(G, n, 2, 1, y, prob)
     ar = oracle.Arcs(n, eu, ev)
     ref = oracle.prob_coined(ar, oracle.coined_evolve(ar, psi0, 100))
@@ -122,13 +125,13 @@ def test_cluster_walk_record_single_mark_and_one_step(hw):
     for steps in (1, 100):
         y = torch.empty_like(x)
         rec = torch.empty(steps, dtype=torch.float64, device="cuda")
-        hw.hw_coined_evolve(G, 0, [2080], 2, 1, steps, x, y, rec)
+        hw.hw_coined_evolve(G, 0, [2080], 2, 1, steps, x, y, rec, opts={"launch_mode": 2})
         ref, rr = oracle.coined_evolve(ar, psi0, steps, marked=[2080], record=True)
         torch.cuda.synchronize()
         assert np.max(np.abs(y.cpu().numpy() - ref)) <= 1e-12
         assert np.max(np.abs(rec.cpu().numpy() - rr)) <= 1e-12
     with pytest.raises(hw.HWError):
-        hw.hw_coined_evolve(G, 0, [], 2, 1, 3, x, x, opts={"launch_mode": 2})
+        hw.hw_coined_evolve(G, 0, [], 2, 1, 3, x, x, opts={"launch_mode": 3})
     G.free()
 
 
@@ -143,7 +146,7 @@ def test_cluster_walk_long_marked_list(hw):
     psi0 = synth.random_state(ar.num_arcs, seed=21)
     x = torch.from_numpy(psi0).cuda()
     outs = []
-    for mode in (0, 1):
+    for mode in (2, 1):
         y = torch.empty_like(x)
         rec = torch.empty(30, dtype=torch.float64, device="cuda")
         hw.hw_coined_evolve(G, 0, marked, 2, 1, 30, x, y, rec, opts={"launch_mode": mode})

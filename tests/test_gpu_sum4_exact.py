@@ -123,7 +123,7 @@ def _sorted_heads(g):
 
 
 CASES = [
-    ("torus64_cluster", synth.torus(64), 0, False, None),
+    ("torus64_cluster", synth.torus(64), 2, False, None),
     ("torus64_per_step", synth.torus(64), 1, False, None),
     ("Q12", synth.hypercube(12), 0, True, None),
     ("Q17", synth.hypercube(17), 0, False, 1500),
