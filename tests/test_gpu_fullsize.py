@@ -5,7 +5,9 @@ compared with the oracle (amplitudes, per-vertex probabilities and the marked
 probability after every step).  Configuration 4 (Erdos-Renyi, n = 2^20, 64
 states drawn on the device as the benchmark draws them, 500 steps): batch
 columns 0, 1, 31 and 63 are compared with the oracle over the whole run
-(amplitudes and per-vertex probabilities), and every column's norm.
+(amplitudes and per-vertex probabilities), and every column's norm.  The
+degree-20 hypercube record (2^20 vertices, complex128): 12 steps of the same
+walk against the oracle.
 """
 import math
 
@@ -103,4 +105,28 @@ def test_config4_batched_full_run_columns(hw):
         assert np.max(np.abs(got - ref)) <= tol, b
         assert np.sum(np.abs(probs[:, b] - oracle.prob_coined(ar, ref))) <= 1e-3, b
     assert np.max(np.abs(norm.cpu().numpy() - 1.0)) <= 1e-4
+    G.free()
+
+
+def test_hypercube20_complex128_against_oracle(hw):
+    # the bench's degree-20 record: the 2^20-vertex hypercube, uniform start,
+    # one seeded mark, complex128 in the two-pass kernel (index-free), here for
+    # 12 steps with the marked probability after every step, against the oracle
+    import torch
+    k, steps = 20, 12
+    g = synth.hypercube(k)
+    n = g[0]
+    m = synth.seeded_vertex(3, n)
+    ar = oracle.Arcs(*g)
+    psi0 = synth.uniform_state(ar.num_arcs)
+    ref, rr = oracle.coined_evolve(ar, psi0, steps, marked=[m], record=True)
+    row_ptr, col = synth.adjacency_csr(*g)
+    G = hw.hw_graph_csr(n, row_ptr, col)
+    x = torch.from_numpy(psi0).cuda()
+    y = torch.empty_like(x)
+    rec = torch.empty(steps, dtype=torch.float64, device="cuda")
+    hw.hw_coined_evolve(G, 0, [m], 2, 1, steps, x, y, rec)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(y.cpu().numpy() - ref)) <= 1e-12
+    assert np.max(np.abs(rec.cpu().numpy() - rr)) <= 1e-12
     G.free()
