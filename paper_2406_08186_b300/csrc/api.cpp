@@ -194,7 +194,8 @@ hw_status coined_opts(const hw_graph *g, const hw_opts *opts, int *shift, bool *
 // shift: measured once, on the first such call (8 and 40 steps of each from
 // psi_in into scratch, through hw_coined_evolve itself with launch_mode 2 and
 // 1, which synchronises the stream once), then kept on the graph.  Under
-// stream capture nothing can be timed and the size rule decides.
+// stream capture nothing can be timed and the size rule decides, as it does
+// when the measurement cannot run (no memory for its scratch state).
 hw_status choose_one_launch(const hw_graph *g, hw_coin coin, hw_dtype dt, const hw_opts *opts, int shift,
                             int64_t steps, const void *psi_in, size_t bytes, cudaStream_t st, bool *one)
 {
@@ -215,7 +216,12 @@ hw_status choose_one_launch(const hw_graph *g, hw_coin coin, hw_dtype dt, const 
         }
         Scratch out(st);
         hw_status s = out.get(bytes, "scratch allocation (launch choice)");
-        if (s != HW_OK) return s;
+        if (s != HW_OK) {
+            hw_clear_error();
+            cudaGetLastError();
+            *one = coined_cluster_by_size(g, dt);
+            return HW_OK;
+        }
         hw_opts o;
         if (opts) o = *opts; else hw_opts_init(&o);
         o.record_stride = 1;
@@ -240,7 +246,14 @@ hw_status choose_one_launch(const hw_graph *g, hw_coin coin, hw_dtype dt, const 
         }
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
-        if (s != HW_OK) return s;
+        if (s != HW_OK) {
+            // no measurement (e.g. no memory for the scratch state): the size
+            // rule decides this call, and the next eligible call measures again
+            hw_clear_error();
+            cudaGetLastError();
+            *one = coined_cluster_by_size(g, dt);
+            return HW_OK;
+        }
         for (int m = 0; m < 2; ++m) {
             const double per = std::max(0.0, (double(ms[2 * m + 1]) - double(ms[2 * m])) / 32.0);
             c[2 * m] = std::max(0.0, double(ms[2 * m]) - 8.0 * per);
