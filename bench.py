@@ -191,6 +191,15 @@ def cpu_baseline(n, eu, ev, m, budget_s=12.0):
             done, psi, oracle.prob_coined(ar, psi))
 
 
+def headline_config(n, arcs, m, world):
+    """The headline workload's `config`, the same on both arms (the reference
+    arm times a bounded sample of it and says so in its cpu_baseline)."""
+    return {"workload": "torus1024_search", "n": n, "arcs": arcs, "walk_steps": WALK_STEPS,
+            "coin": "grover", "marked": m, "state": "complex128", "record": "p_m(t) every step",
+            "l2": "256 MiB written between timed steps; working set 134 MB (two 64 MiB state buffers) > L2",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -212,10 +221,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "torus1024_search", "n": n, "arcs": ar.num_arcs,
-                       "walk_steps_per_step": per, "marked": m, "parallelism": "cpu"},
+            "config": headline_config(n, ar.num_arcs, m, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d walk steps per bench step of the 1024x1024 torus search" % per},
+                             "sample": "%d walk steps per bench step of the 1024x1024 torus search (complex128 "
+                                       "oracle on the host cores, uniform start, the same mark)" % per},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -343,10 +352,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t128 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "torus1024_search", "n": n, "arcs": arcs, "walk_steps": WALK_STEPS,
-                   "coin": "grover", "marked": m, "state": "complex128", "record": "p_m(t) every step",
-                   "l2": "256 MiB written between timed steps; working set 134 MB (two 64 MiB state buffers) > L2",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": headline_config(n, arcs, m, world),
         "roofline": {"bound": "hbm",
                      "kernel": "k_coined_em<double,4,grover,%s>" % ("torus" if index_free else "table"),
                      "achieved": ach128, "peak": peak, "unit": "GB/s", "frac": ach128 / peak,
