@@ -522,11 +522,12 @@ def sub_ctqw_q12(hw, reps, warmup, with_cpu):
     peak, src = measured_peaks()
     tc_peak, tc_src = measured_tensor_peak()
     fp64 = hw.hw_measure_fp64()
+    l2_peak = hw.hw_measure_l2()
     res = {"workload": "hypercube12_ctqw", "n": n, "marked": m, "gamma": 1 / 12, "dt": 0.1,
            "applications": 2000, "reps": reps,
            "l2": "256 MiB written before every timed expm and evolve call (outside the events); inside an "
-                 "evolve call the complex64 upper triangle of U (68 MB) stays in L2 from one application "
-                 "to the next"}
+                 "evolve call the complex64 upper triangle of U, packed once per call into 68 MB of "
+                 "contiguous 64 x 64 blocks, stays in L2 from one application to the next"}
     deg, sq = hw.hw_ctqw_plan(G, 1 / 12, [m], 0.1)
     kept = {}
 
@@ -618,8 +619,10 @@ def sub_ctqw_q12(hw, reps, warmup, with_cpu):
                                                "note": "whole expm (slicing, Taylor sums, finish) over the MMA work"}
                 abytes = n * n // 2 * 8 + n * 8
                 r["apply_roofline"] = {"bound": "l2", "achieved": abytes / (t_ev / 2000) / 1e9, "unit": "GB/s",
+                                       "peak": l2_peak, "frac": abytes / (t_ev / 2000) / 1e9 / l2_peak,
+                                       "peak_source": "hw_measure_l2 (32 MB copy, L2-resident, read + write)",
                                        "bytes_per_apply": abytes,
-                                       "note": "upper triangle of U (68 MB) streamed per application, L2-resident"}
+                                       "note": "packed upper triangle of U (68 MB) streamed per application, L2-resident"}
             res[name] = r
     res["clocks"] = clk.summary()
     U128, U128d, U128s, y128, rec128, p128 = kept["c128"]

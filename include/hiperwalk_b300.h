@@ -69,9 +69,12 @@ typedef struct hw_opts {
     int32_t gemm_mode;         /* hw_ctqw_expm, HW_C64: tensor-core precision mode of the powers,
                                   0 = default (fp16 x 2), else as hw_gemm_tc's mode */
     int32_t u_symmetric;       /* hw_ctqw_evolve: 1 = U is complex symmetric (U^T = U, true for
-                                  U from hw_ctqw_expm): each off-diagonal 64 x 64 block is read
-                                  once and used for both triangles (complex64, batch 1; other
-                                  cases use the dense path) */
+                                  U from hw_ctqw_expm): the 64 x 64 blocks on and above the
+                                  diagonal are copied once per call into device scratch
+                                  (ceil(n/64) (ceil(n/64) + 1) / 2 blocks of 32 KB, contiguous),
+                                  and each application reads every block once for both
+                                  triangles (complex64, batch 1; other cases use the dense
+                                  path) */
     int32_t tile;              /* batched Grover kernel launch shape: 0 = autotuned on the first
                                   call per (graph, dtype, batch), which then synchronises the
                                   stream once; 1..12 = register-row kernel with (rows held

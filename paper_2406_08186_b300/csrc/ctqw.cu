@@ -634,97 +634,62 @@ hw_status launch_apply_3m(const void *U, const double *S, const void *x, const d
 }
 
 // ------------------------------------------------------------ apply a symmetric U
-// U = U^T (complex symmetric): every off-diagonal 64 x 64 block U_IJ (I < J) is
-// read once and gives both y_I += U_IJ x_J and y_J += U_IJ^T x_I, so one
-// application reads n^2/2 elements (for n = 4096 complex64, 68 MB: it stays in
-// L2 from one application to the next).  Pass 1: one CTA per upper block
-// stages it in shared memory, 64 threads form its row sums and 64 its column
-// sums (sequential, fixed order) into per-block partials.  Pass 2: one thread
-// per vertex adds its partials in a fixed order and writes y (and the record).
+// U = U^T (complex symmetric, complex64): every off-diagonal 64 x 64 block U_IJ
+// (I < J) is read once and gives both y_I += U_IJ x_J and y_J += U_IJ^T x_I,
+// so one application reads n^2/2 elements.  Before the first application the
+// blocks on and above the diagonal are packed (k_sym_pack), each a contiguous
+// 32 KB (zero past n), in the order the block pass walks them: packed, the
+// 68 MB of n = 4096 stay in L2 from one application to the next, while read in
+// place from the dense matrix (512-byte row pieces 32 KB apart) the same bytes
+// came from DRAM every time.  Pass 1 (k_apply_sym) forms every block's row and
+// column sums into per-block partials; pass 2 (k_apply_sym_reduce) adds a
+// vertex's partials in a fixed order and writes y (and the record).
 constexpr int kSymB = 64;
+constexpr uint32_t kSymTileBytes = kSymB * kSymB * sizeof(float2);
 
-template <typename R>
-__global__ void __launch_bounds__(128) k_apply_sym_blocks(const void *U_, const void *x_, int n, int nb,
-                                                          void *prow_, void *pcol_)
+// upper block b (row-major over the blocks on and above the diagonal) ->
+// (I, J): I is the last row whose first block S(I) = I nb - I (I - 1) / 2 is
+// at most b, estimated from the root of S(I) = b and then fixed exactly
+__device__ __forceinline__ int64_t sym_row_start(int I, int nb)
 {
-    using V = typename Cx2<R>::T;
-    extern __shared__ __align__(16) unsigned char sym_smem[];
-    V(*sU)[kSymB + 1] = reinterpret_cast<V(*)[kSymB + 1]>(sym_smem);                      // [kSymB][kSymB+1]
-    V(*sx)[kSymB] = reinterpret_cast<V(*)[kSymB]>(sym_smem + sizeof(V) * kSymB * (kSymB + 1));   // [2][kSymB]
-    const V *__restrict__ U = static_cast<const V *>(U_);
-    const V *__restrict__ x = static_cast<const V *>(x_);
-    V *__restrict__ prow = static_cast<V *>(prow_);
-    V *__restrict__ pcol = static_cast<V *>(pcol_);
-    // block index -> (I, J), I <= J, row-major over the upper triangle
-    int b = blockIdx.x, I = 0;
-    while (b >= nb - I) { b -= nb - I; ++I; }
-    const int J = I + b;
-    const int r0 = I * kSymB, c0 = J * kSymB;
-    const int t = threadIdx.x;
-    if (r0 + kSymB <= n && c0 + kSymB <= n && (n & 1) == 0 && sizeof(V) == 8) {
-        // interior block: 16-byte loads, consecutive threads on consecutive pairs of a row
-#pragma unroll
-        for (int i = 0; i < (kSymB * kSymB / 2) / 128; ++i) {
-            const int e2 = t + 128 * i;
-            const int r = e2 / (kSymB / 2), c = 2 * (e2 % (kSymB / 2));
-            const float4 w = *reinterpret_cast<const float4 *>(U + int64_t(r0 + r) * n + c0 + c);
-            sU[r][c].x = w.x;
-            sU[r][c].y = w.y;
-            sU[r][c + 1].x = w.z;
-            sU[r][c + 1].y = w.w;
-        }
-    } else {
-        for (int e = t; e < kSymB * kSymB; e += blockDim.x) {
-            const int r = e / kSymB, c = e % kSymB;
-            V u;
-            if (r0 + r < n && c0 + c < n) u = U[int64_t(r0 + r) * n + c0 + c];
-            else { u.x = 0; u.y = 0; }
-            sU[r][c] = u;
-        }
-    }
-    pdl_wait();   // x is the previous application's output
-    {
-        const int w = t / kSymB, k = t % kSymB;   // 128 threads: sx[0] = x_J (rows), sx[1] = x_I (columns)
-        const int g = (w ? r0 : c0) + k;
-        V v;
-        if (g < n) v = x[g];
-        else { v.x = 0; v.y = 0; }
-        sx[w][k] = v;
-    }
-    __syncthreads();
-    R ax = 0, ay = 0;
-    if (t < kSymB) {               // row t of the block: sum_c U[t][c] x_J[c]
-        for (int c = 0; c < kSymB; ++c) {
-            const V u = sU[t][c], q = sx[0][c];
-            ax = fma(u.x, q.x, fma(-u.y, q.y, ax));
-            ay = fma(u.x, q.y, fma(u.y, q.x, ay));
-        }
-        V o;
-        o.x = ax;
-        o.y = ay;
-        prow[(int64_t(I) * nb + J) * kSymB + t] = o;
-    } else if (I != J) {           // column c of the block: sum_r U[r][c] x_I[r]
-        const int c = t - kSymB;
-        for (int r = 0; r < kSymB; ++r) {
-            const V u = sU[r][c], q = sx[1][r];
-            ax = fma(u.x, q.x, fma(-u.y, q.y, ax));
-            ay = fma(u.x, q.y, fma(u.y, q.x, ay));
-        }
-        V o;
-        o.x = ax;
-        o.y = ay;
-        pcol[(int64_t(J) * nb + I) * kSymB + c] = o;
-    }
-    pdl_trigger();
+    return int64_t(I) * nb - int64_t(I) * (I - 1) / 2;
 }
 
-// The same block pass, complex64, as a persistent kernel fed by TMA: each CTA
-// walks the blocks b = blockIdx.x, + gridDim.x, ... with two 32 KB stages, the
-// next block's 64 x 64 tile arriving (one cp.async.bulk.tensor, zero fill
-// past the matrix edge) while the current one is summed.  Rows are summed
-// starting from column r (row r), so the 64 threads of a row pass touch 64
-// different columns of the dense tile at each step.
+__device__ __forceinline__ void sym_block_ij(int b, int nb, int &I, int &J)
+{
+    const float q = float(2 * nb + 1);
+    int i = int((q - sqrtf(fmaxf(q * q - 8.f * float(b), 0.f))) * 0.5f);
+    i = max(0, min(i, nb - 1));
+    while (i > 0 && sym_row_start(i, nb) > b) --i;
+    while (i + 1 < nb && sym_row_start(i + 1, nb) <= b) ++i;
+    I = i;
+    J = i + int(b - sym_row_start(i, nb));
+}
+
+// one CTA per upper block b (row-major over the upper triangle)
+__global__ void __launch_bounds__(256) k_sym_pack(const float2 *__restrict__ U, int n, int nb,
+                                                  float2 *__restrict__ P)
+{
+    int I, J;
+    sym_block_ij(int(blockIdx.x), nb, I, J);
+    const int r0 = I * kSymB, c0 = J * kSymB;
+    float2 *__restrict__ dst = P + int64_t(blockIdx.x) * kSymB * kSymB;
+    for (int e = threadIdx.x; e < kSymB * kSymB; e += blockDim.x) {
+        const int r = e / kSymB, c = e % kSymB;
+        dst[e] = (r0 + r < n && c0 + c < n) ? U[int64_t(r0 + r) * n + c0 + c] : make_float2(0.f, 0.f);
+    }
+}
+
+// The block pass, a persistent kernel: each CTA walks the packed blocks
+// b = blockIdx.x, + gridDim.x, ... through two 32 KB stages, the next block
+// arriving (one cp.async.bulk) while the current one is summed.  Warp w holds
+// rows 8w..8w+7 of the block and lane l columns 2l and 2l+1: a warp reads 512
+// contiguous bytes of a row at a time, and each element is read from shared
+// memory once and used for both sums, its row's (with x_J) and its column's
+// (with x_I).  Row sums over the 32 lanes: a fixed halving butterfly.  Column
+// sums over the 8 warps: added in warp order through shared memory.
 constexpr int kSymStages = 2;
+constexpr int kSymThreads = 256;
 constexpr uint64_t kSymWaitNs = 2000000000ull;   // bounded stage waits (2 s)
 
 __device__ __forceinline__ uint32_t sym_smem_addr(const void *p)
@@ -753,38 +718,28 @@ __device__ __forceinline__ bool sym_wait(uint32_t bar, uint32_t parity)
     }
 }
 
-__device__ __forceinline__ void sym_block_ij(int b, int nb, int &I, int &J)
+// one thread: packed block b into the stage, completion on bar
+__device__ __forceinline__ void sym_issue(const float2 *P, int b, uint32_t dst, uint32_t bar)
 {
-    I = 0;
-    while (b >= nb - I) { b -= nb - I; ++I; }
-    J = I + b;
-}
-
-// one thread: the tile of upper block b into the stage, completion on bar
-__device__ __forceinline__ void sym_issue(const CUtensorMap *map, int b, int nb, uint32_t dst, uint32_t bar)
-{
-    int I, J;
-    sym_block_ij(b, nb, I, J);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSymB * kSymB * 8)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kSymTileBytes)
                  : "memory");
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-                 ::"r"(dst), "l"(map), "r"(J * kSymB), "r"(I * kSymB), "r"(bar)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(P + int64_t(b) * kSymB * kSymB), "r"(kSymTileBytes), "r"(bar)
                  : "memory");
 }
 
-__global__ void __launch_bounds__(128) k_apply_sym_tma(const __grid_constant__ CUtensorMap mapU, const void *x_,
-                                                       int n, int nb, int nblocks, void *prow_, void *pcol_,
-                                                       int *err)
+__global__ void __launch_bounds__(kSymThreads) k_apply_sym(const float2 *__restrict__ P, const void *x_, int n,
+                                                           int nb, int nblocks, void *prow_, void *pcol_, int *err)
 {
     extern __shared__ __align__(128) unsigned char sym_tma_smem[];
     float2(*tile)[kSymB][kSymB] = reinterpret_cast<float2(*)[kSymB][kSymB]>(sym_tma_smem);   // [stage][row][col]
-    __shared__ float2 sx[2][kSymB];
+    __shared__ float4 cpart[kSymThreads / 32][32];   // [warp][lane]: columns 2l, 2l+1 over the warp's rows
     __shared__ __align__(8) uint64_t bars[kSymStages];
     __shared__ int failed;
     const float2 *__restrict__ x = static_cast<const float2 *>(x_);
-    float2 *__restrict__ prow = static_cast<float2 *>(prow_);
-    float2 *__restrict__ pcol = static_cast<float2 *>(pcol_);
-    const int t = threadIdx.x;
+    float *__restrict__ prow = static_cast<float *>(prow_);   // the complex partials as (re, im) floats
+    float4 *__restrict__ pcol = static_cast<float4 *>(pcol_);  // two complex partials per float4
+    const int t = threadIdx.x, w = t >> 5, l = t & 31;
     if (t == 0) {
         failed = 0;
         for (int k = 0; k < kSymStages; ++k)
@@ -793,66 +748,82 @@ __global__ void __launch_bounds__(128) k_apply_sym_tma(const __grid_constant__ C
         // U does not change between applications: the first tiles load before the wait
         for (int k = 0; k < kSymStages; ++k) {
             const int b = blockIdx.x + k * gridDim.x;
-            if (b < nblocks) sym_issue(&mapU, b, nb, sym_smem_addr(&tile[k][0][0]), sym_smem_addr(&bars[k]));
+            if (b < nblocks) sym_issue(P, b, sym_smem_addr(&tile[k][0][0]), sym_smem_addr(&bars[k]));
         }
     }
     __syncthreads();
     pdl_wait();   // x is the previous application's output; the partials are free again
+    const float2 zero = make_float2(0.f, 0.f);
     int k = 0;
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x, ++k) {
         const int stage = k % kSymStages;
         int I, J;
         sym_block_ij(b, nb, I, J);
-        const int r0 = I * kSymB, c0 = J * kSymB;
-        {
-            const int w = t / kSymB, q = t % kSymB;   // sx[0] = x_J (rows), sx[1] = x_I (columns)
-            const int g = (w ? r0 : c0) + q;
-            sx[w][q] = (g < n) ? x[g] : make_float2(0.f, 0.f);
-        }
+        const int r0 = I * kSymB + 8 * w, c0 = J * kSymB + 2 * l;
+        // x_J at this lane's two columns, x_I at this warp's eight rows (zero
+        // past n, where the packed block is zero)
+        const float2 xa = (c0 < n) ? __ldg(x + c0) : zero;
+        const float2 xb = (c0 + 1 < n) ? __ldg(x + c0 + 1) : zero;
+        float2 xi[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) xi[i] = (r0 + i < n) ? __ldg(x + r0 + i) : zero;
         if (t == 0 && !sym_wait(sym_smem_addr(&bars[stage]), uint32_t((k / kSymStages) & 1))) {
             failed = 1;
             atomicExch(err, 1);
         }
         __syncthreads();
         if (failed) break;   // uniform: the stage never filled
-        float2(*sU)[kSymB] = tile[stage];
-        // four independent chains per thread (entries s*16 + c of the rotated
-        // order), added in a fixed order at the end
-        float ax[4] = {0.f, 0.f, 0.f, 0.f}, ay[4] = {0.f, 0.f, 0.f, 0.f};
-        if (t < kSymB) {               // row t: sum over c of U[t][c] x_J[c], from column t on
+        const float4 *sU = reinterpret_cast<const float4 *>(&tile[stage][0][0]);
+        float rs[16];   // rs[2i], rs[2i+1]: row 8w+i over columns 2l, 2l+1 (re, im)
+        float cax = 0.f, cay = 0.f, cbx = 0.f, cby = 0.f;   // columns 2l, 2l+1 over rows 8w..8w+7
 #pragma unroll
-            for (int c = 0; c < kSymB / 4; ++c) {
-#pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
-                    const int cc = (c + 16 * s4 + t) & (kSymB - 1);
-                    const float2 u = sU[t][cc], q = sx[0][cc];
-                    ax[s4] = fmaf(u.x, q.x, fmaf(-u.y, q.y, ax[s4]));
-                    ay[s4] = fmaf(u.x, q.y, fmaf(u.y, q.x, ay[s4]));
-                }
-            }
-            prow[(int64_t(I) * nb + J) * kSymB + t] =
-                make_float2((ax[0] + ax[1]) + (ax[2] + ax[3]), (ay[0] + ay[1]) + (ay[2] + ay[3]));
-        } else if (I != J) {           // column c: sum over r of U[r][c] x_I[r]
-            const int c = t - kSymB;
-#pragma unroll
-            for (int r = 0; r < kSymB / 4; ++r) {
-#pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
-                    const float2 u = sU[r + 16 * s4][c], q = sx[1][r + 16 * s4];
-                    ax[s4] = fmaf(u.x, q.x, fmaf(-u.y, q.y, ax[s4]));
-                    ay[s4] = fmaf(u.x, q.y, fmaf(u.y, q.x, ay[s4]));
-                }
-            }
-            pcol[(int64_t(J) * nb + I) * kSymB + c] =
-                make_float2((ax[0] + ax[1]) + (ax[2] + ax[3]), (ay[0] + ay[1]) + (ay[2] + ay[3]));
+        for (int i = 0; i < 8; ++i) {
+            const float4 u = sU[(8 * w + i) * (kSymB / 2) + l];   // U[r][2l] = (u.x, u.y), U[r][2l+1] = (u.z, u.w)
+            rs[2 * i] = fmaf(u.x, xa.x, fmaf(-u.y, xa.y, fmaf(u.z, xb.x, -u.w * xb.y)));
+            rs[2 * i + 1] = fmaf(u.x, xa.y, fmaf(u.y, xa.x, fmaf(u.z, xb.y, u.w * xb.x)));
+            cax = fmaf(u.x, xi[i].x, fmaf(-u.y, xi[i].y, cax));
+            cay = fmaf(u.x, xi[i].y, fmaf(u.y, xi[i].x, cay));
+            cbx = fmaf(u.z, xi[i].x, fmaf(-u.w, xi[i].y, cbx));
+            cby = fmaf(u.z, xi[i].y, fmaf(u.w, xi[i].x, cby));
         }
-        __syncthreads();   // the stage and sx are read: refill the stage
+        // halving butterfly: at offset o each lane keeps the half of its values
+        // that its bit o selects and adds the partner's copy of that half; after
+        // offsets 16, 8, 4, 2 lane l holds value l >> 1 summed over 16 lanes, and
+        // offset 1 completes the sum over all 32
+#pragma unroll
+        for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+            const bool up = (l & o) != 0;
+#pragma unroll
+            for (int q = 0; q < h; ++q) {
+                const float keep = up ? rs[q + h] : rs[q];
+                const float send = up ? rs[q] : rs[q + h];
+                rs[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        rs[0] += __shfl_xor_sync(0xffffffffu, rs[0], 1);
+        // value l >> 1 is row 8w + (l >> 2), component (l >> 1) & 1
+        if ((l & 1) == 0) prow[((int64_t(I) * nb + J) * kSymB + 8 * w + (l >> 2)) * 2 + ((l >> 1) & 1)] = rs[0];
+        cpart[w][l] = make_float4(cax, cay, cbx, cby);
+        __syncthreads();   // the stage and cpart are read and written
         if (t == 0) {
             const int bn = b + kSymStages * gridDim.x;
             // order the generic reads of the stage before the async-proxy refill
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (bn < nblocks) sym_issue(&mapU, bn, nb, sym_smem_addr(&tile[stage][0][0]), sym_smem_addr(&bars[stage]));
+            if (bn < nblocks) sym_issue(P, bn, sym_smem_addr(&tile[stage][0][0]), sym_smem_addr(&bars[stage]));
         }
+        if (w == 0 && I != J) {   // column sums of the block, the 8 warps added in order
+            float4 c = cpart[0][l];
+#pragma unroll
+            for (int v = 1; v < kSymThreads / 32; ++v) {
+                const float4 d = cpart[v][l];
+                c.x += d.x;
+                c.y += d.y;
+                c.z += d.z;
+                c.w += d.w;
+            }
+            pcol[((int64_t(J) * nb + I) * kSymB) / 2 + l] = c;
+        }
+        // cpart is written again only after the next tile's barrier, which warp 0 reaches after reading it
     }
     // on a failed wait, wait (bounded) for every stage still in flight, so no
     // bulk copy writes this CTA's shared memory after it exits
@@ -865,39 +836,48 @@ __global__ void __launch_bounds__(128) k_apply_sym_tma(const __grid_constant__ C
     pdl_trigger();
 }
 
-// 8 threads per vertex: thread s adds the partials of blocks s, s+8, ... in
-// order, then a fixed shuffle tree combines the 8 sums
-template <typename R>
+// kSymSub threads per vertex: thread s adds the partials of blocks s,
+// s + kSymSub, ... in order (four loads issued before their adds), then a
+// fixed shuffle tree combines the kSymSub sums
+constexpr int kSymSub = 16;
+
 __global__ void __launch_bounds__(256) k_apply_sym_reduce(const void *prow_, const void *pcol_, int n, int nb,
                                                           void *y_, MarkedList mk, double *rec_part,
                                                           int64_t rec_slot)
 {
-    using V = typename Cx2<R>::T;
-    const V *__restrict__ prow = static_cast<const V *>(prow_);
-    const V *__restrict__ pcol = static_cast<const V *>(pcol_);
-    V *__restrict__ y = static_cast<V *>(y_);
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int sub = threadIdx.x & 7;
+    const float2 *__restrict__ prow = static_cast<const float2 *>(prow_);
+    const float2 *__restrict__ pcol = static_cast<const float2 *>(pcol_);
+    float2 *__restrict__ y = static_cast<float2 *>(y_);
+    const int i = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / kSymSub);
+    const int sub = threadIdx.x % kSymSub;
     pdl_wait();
-    R sx = 0, sy = 0;
+    float sx = 0.f, sy = 0.f;
     if (i < n) {
         const int I = i / kSymB, r = i % kSymB;
-        for (int K = sub; K < nb; K += 8) {
-            // block (I, K) for K >= I, its mirror (K, I) for K < I
-            const V p = (K >= I) ? prow[(int64_t(I) * nb + K) * kSymB + r] : pcol[(int64_t(I) * nb + K) * kSymB + r];
-            sx += p.x;
-            sy += p.y;
+        for (int K0 = sub; K0 < nb; K0 += 4 * kSymSub) {
+            float2 p[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                // block (I, K) for K >= I, its mirror (K, I) for K < I
+                const int K = K0 + u * kSymSub;
+                if (K < nb)
+                    p[u] = (K >= I) ? prow[(int64_t(I) * nb + K) * kSymB + r] : pcol[(int64_t(I) * nb + K) * kSymB + r];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (K0 + u * kSymSub < nb) {
+                    sx += p[u].x;
+                    sy += p[u].y;
+                }
+            }
         }
     }
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < kSymSub; o <<= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
     }
     if (i < n && sub == 0) {
-        V o;
-        o.x = sx;
-        o.y = sy;
-        y[i] = o;
+        y[i] = make_float2(sx, sy);
         if (rec_part && rec_slot >= 0) {
             const int mi = marked_find(mk, int(i));
             if (mi >= 0) rec_part[rec_slot * mk.n + mi] = double(sx) * double(sx) + double(sy) * double(sy);
@@ -906,52 +886,38 @@ __global__ void __launch_bounds__(256) k_apply_sym_reduce(const void *prow_, con
     pdl_trigger();
 }
 
-// complex64 with a tensor map of U (map != NULL): the persistent TMA kernel
-template <typename R>
-hw_status launch_apply_sym(const void *U, const void *x, void *y, int n, void *prow, void *pcol,
-                           const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st,
-                           const CUtensorMap *map = nullptr, int *err = nullptr)
+// the two passes of one application; P from k_sym_pack
+hw_status launch_apply_sym(const float2 *P, const void *x, void *y, int n, void *prow, void *pcol,
+                           const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st, int *err)
 {
-    using V = typename Cx2<R>::T;
     const int nb = (n + kSymB - 1) / kSymB;
     const int blocks = nb * (nb + 1) / 2;
-    if (map && sizeof(V) == 8) {
-        // resident CTAs per device (the shared-memory attribute is set per device too)
-        static std::mutex mu;
-        static std::map<int, int> grids;
-        const size_t tsmem = sizeof(float2) * kSymStages * kSymB * kSymB;
-        int dev = 0, grid = 0;
-        cudaGetDevice(&dev);
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            auto it = grids.find(dev);
-            if (it != grids.end()) {
-                grid = it->second;
-            } else {
-                cudaError_t e =
-                    cudaFuncSetAttribute(k_apply_sym_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tsmem));
-                if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym_tma)");
-                int sms = 0, per = 0;
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_sym_tma, 128, tsmem);
-                if (e != cudaSuccess) return hw_cuda(e, "occupancy (k_apply_sym_tma)");
-                grid = grids[dev] = sms * std::max(per, 1);
-            }
+    // resident CTAs per device (the shared-memory attribute is set per device too)
+    static std::mutex mu;
+    static std::map<int, int> grids;
+    const size_t smem = size_t(kSymTileBytes) * kSymStages;
+    int dev = 0, grid = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = grids.find(dev);
+        if (it != grids.end()) {
+            grid = it->second;
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(k_apply_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym)");
+            int sms = 0, per = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_sym, kSymThreads, smem);
+            if (e != cudaSuccess) return hw_cuda(e, "occupancy (k_apply_sym)");
+            grid = grids[dev] = sms * std::max(per, 1);
         }
-        cudaError_t e = launch_pdl(k_apply_sym_tma, dim3(std::min(grid, blocks)), dim3(128), tsmem, st, *map, x, n, nb,
-                                   blocks, prow, pcol, err);
-        if (e != cudaSuccess) return hw_cuda(e, "k_apply_sym_tma launch");
-        e = launch_pdl(k_apply_sym_reduce<R>, dim3((n * 8 + 255) / 256), dim3(256), 0, st, (const void *)prow,
-                       (const void *)pcol, n, nb, y, mk, rec_part, rec_slot);
-        return hw_cuda(e, "k_apply_sym_reduce launch");
     }
-    const size_t smem = sizeof(V) * (kSymB * (kSymB + 1) + 2 * kSymB);
-    cudaError_t e = cudaFuncSetAttribute(k_apply_sym_blocks<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return hw_cuda(e, "cudaFuncSetAttribute(k_apply_sym_blocks)");
-    e = launch_pdl(k_apply_sym_blocks<R>, dim3(blocks), dim3(128), smem, st, U, x, n, nb, prow, pcol);
-    if (e != cudaSuccess) return hw_cuda(e, "k_apply_sym_blocks launch");
-    e = launch_pdl(k_apply_sym_reduce<R>, dim3((n * 8 + 255) / 256), dim3(256), 0, st, (const void *)prow,
-                   (const void *)pcol, n, nb, y, mk, rec_part, rec_slot);
+    cudaError_t e = launch_pdl(k_apply_sym, dim3(std::min(grid, blocks)), dim3(kSymThreads), smem, st, P, x, n, nb,
+                               blocks, prow, pcol, err);
+    if (e != cudaSuccess) return hw_cuda(e, "k_apply_sym launch");
+    e = launch_pdl(k_apply_sym_reduce, dim3(int((int64_t(n) * kSymSub + 255) / 256)), dim3(256), 0, st,
+                   (const void *)prow, (const void *)pcol, n, nb, y, mk, rec_part, rec_slot);
     return hw_cuda(e, "k_apply_sym_reduce launch");
 }
 
@@ -1278,19 +1244,22 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     // the symmetric path halves the bytes read; complex128 is bound by FP64
     // arithmetic, which both paths share, so it keeps the dense path
     const bool sym = opts && opts->u_symmetric && batch == 1 && dt == HW_C64;
-    // the TMA-fed block pass: a tensor map of U (16-byte aligned, even n)
-    CUtensorMap umap;
-    const bool tma = sym && (uintptr_t(U) % 16) == 0 && n % 2 == 0 && tc_gemm_available() &&
-                     make_map_u64(&umap, U, n, n, n, kSymB, kSymB) == HW_OK;
-    hw_clear_error();
     int *derr = nullptr;
-    if (tma && (s = apply_error_word(&derr)) != HW_OK) return s;
+    if (sym && (s = apply_error_word(&derr)) != HW_OK) return s;
     const int nb = int((n + kSymB - 1) / kSymB);
     const size_t part_bytes = sym ? size_t(nb) * nb * kSymB * esz : 0;   // one array of block partials
     // complex128, one state, dense U: the three-product form with S = Re U + Im U
     const bool three = !sym && dt == HW_C128 && batch == 1;
-    DevBuf tmp(st), recbuf(st), splane(st);
+    DevBuf tmp(st), recbuf(st), splane(st), packed(st);
     if ((s = tmp.get(bytes + 2 * part_bytes + 256, "scratch allocation (state scratch)")) != HW_OK) return s;
+    if (sym) {
+        // the blocks on and above the diagonal, packed once for all applications
+        const int64_t blocks = int64_t(nb) * (nb + 1) / 2;
+        if ((s = packed.get(size_t(blocks) * kSymTileBytes, "scratch allocation (packed blocks of U)")) != HW_OK)
+            return s;
+        k_sym_pack<<<unsigned(blocks), 256, 0, st>>>(static_cast<const float2 *>(U), int(n), nb, packed.as<float2>());
+        if ((s = hw_cuda(cudaGetLastError(), "k_sym_pack launch")) != HW_OK) return s;
+    }
     if (three) {
         // S, then Re x + Im x of the two state buffers
         if ((s = splane.get((size_t(n) * size_t(n) + 2 * size_t(n)) * sizeof(double),
@@ -1330,9 +1299,7 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
         void *dst = ((steps - k) % 2 == 0) ? P : T;
         const int64_t slot = (slots && k % stride == 0) ? k / stride - 1 : -1;
         if (sym)
-            s = (dt == HW_C128) ? launch_apply_sym<double>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st)
-                                : launch_apply_sym<float>(U, src, dst, int(n), prow, pcol, mk, rec_part, slot, st,
-                                                          tma ? &umap : nullptr, derr);
+            s = launch_apply_sym(packed.as<float2>(), src, dst, int(n), prow, pcol, mk, rec_part, slot, st, derr);
         else if (three) {
             s = launch_apply_3m(U, splane.as<double>(), src, xsum, dst, ysum, int(n), mk, rec_part, slot, st);
             std::swap(xsum, ysum);

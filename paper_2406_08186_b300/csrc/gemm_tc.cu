@@ -1251,22 +1251,6 @@ struct TcPower {
     int pend_buf = -1;
 };
 
-hw_status make_map_u64(void *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols,
-                       int box_rows)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
-    if (!enc) return hw_fail(HW_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
-    cuuint64_t strides[1] = {cuuint64_t(ld) * 8};
-    cuuint32_t box[2] = {cuuint32_t(box_cols), cuuint32_t(box_rows)};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(ptr), dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return hw_fail(HW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
-    return HW_OK;
-}
-
 bool tc_gemm_available()
 {
     int dev = 0, major = 0, minor = 0;

@@ -190,11 +190,6 @@ struct SymSparse {
 
 struct TcPower;
 bool tc_gemm_available();
-// 2D TMA tensor map (a CUtensorMap, 128 bytes) over a row-major [rows][cols]
-// matrix of 8-byte elements with row stride ld elements, box box_cols x
-// box_rows, no swizzle, zero fill out of bounds (gemm_tc.cu)
-hw_status make_map_u64(void *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols,
-                       int box_rows);
 hw_status tc_power_begin(const SymSparse &Y, const double *yvals, int nyvals, double theta, int mode, int tiles_mode,
                          cudaStream_t st, TcPower **out);
 hw_status tc_power_step(TcPower *p, int k, double *accU, double sign);

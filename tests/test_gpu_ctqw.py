@@ -366,9 +366,9 @@ def test_symmetric_apply_matches_dense_apply_and_oracle(hw, dt, n_bits, steps):
 
 
 @pytest.mark.parametrize("name,g,gamma,marked", [
-    # even n, not a multiple of the 64-vertex blocks: the TMA-fed pass, zero-filled edge tiles
+    # even n, not a multiple of the 64-vertex blocks: edge blocks packed with zeros past n
     ("reg3_778", synth.random_regular(778, 3, seed=4), 1 / 3, [5, 700]),
-    # odd n: the shared-memory pass without a tensor map
+    # odd n: a lane's two columns straddle n in the last block
     ("er_999", synth.erdos_renyi(1000, 0.006, seed=6), 0.3, [10]),
 ])
 def test_symmetric_apply_ragged_sizes(hw, name, g, gamma, marked):
