@@ -50,8 +50,8 @@ TRAFFIC = {
     # the 1024x1024 torus step (k_coined_em<R,4,grover,torus>, index-free, a
     # block row per torus row, complex128 sums by integer operations and
     # streaming loads and stores), one launch, cold L2
-    ("c128", "f928042c83d924ceedc12177b721f3c2492a271e"): 67130624 + 16286976,
-    ("c64", "f928042c83d924ceedc12177b721f3c2492a271e"): 33566976 + 327168,
+    ("c128", "353bcfad430a774d3180ad7a5bd12c59d60481d2"): 67130624 + 16286976,
+    ("c64", "353bcfad430a774d3180ad7a5bd12c59d60481d2"): 33566976 + 327168,
 }
 
 
