@@ -191,6 +191,26 @@ def cpu_baseline(n, eu, ev, m, budget_s=12.0):
             done, psi, oracle.prob_coined(ar, psi))
 
 
+def l2_copy_per_launch(torch):
+    """Read + write GB/s of a copy between two 32 MB device buffers, one launch per
+    copy (the L2-resident ping-pong of the complex64 step), as a reference rate."""
+    a = torch.ones(8 << 20, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+        a.copy_(b)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(500):
+        b.copy_(a)
+        a.copy_(b)
+    ev[1].record()
+    torch.cuda.synchronize()
+    per_copy = ev[0].elapsed_time(ev[1]) * 1e-3 / 1000
+    return 2.0 * a.numel() * 4 / per_copy / 1e9
+
+
 def headline_config(n, arcs, m, world):
     """The headline workload's `config`, the same on both arms (the reference
     arm times a bounded sample of it and says so in its cpu_baseline)."""
@@ -296,6 +316,7 @@ def run_ours(args):
     peak, peak_src = measured_peaks()
     fp64_peak = hw.hw_measure_fp64()
     l2_peak = hw.hw_measure_l2()
+    l2_launch = l2_copy_per_launch(torch)
     kind, _ = hw.hw_graph_structure(G)
     index_free = kind == hw.HW_GRAPH_TORUS   # the default addressing on a recognised torus
     b128 = make(hw.HW_C128)
@@ -369,6 +390,9 @@ def run_ours(args):
                                    "peak_source": "hw_measure_l2 (32 MB copy, L2-resident, read + write)",
                                    "launch_us": per_launch64 * 1e6,
                                    "traffic": TRAFFIC.get(("c64", src_hash)),
+                                   "copy_per_launch": {"gbs": l2_launch, "frac": ach64 / l2_launch,
+                                                       "how": "one copy kernel per launch between two 32 MB "
+                                                              "buffers (the step's pattern), 500 round trips"},
                                    "note": "the two 32 MB state buffers stay in the 126 MB L2"}},
         "e2e": {"value": work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": arcs * 16,
                 "d2h_bytes_per_step": n * 8 + WALK_STEPS * 8},
