@@ -368,8 +368,14 @@ def test_symmetric_apply_matches_dense_apply_and_oracle(hw, dt, n_bits, steps):
 @pytest.mark.parametrize("name,g,gamma,marked", [
     # even n, not a multiple of the 64-vertex blocks: edge blocks packed with zeros past n
     ("reg3_778", synth.random_regular(778, 3, seed=4), 1 / 3, [5, 700]),
+    # uneven degrees, isolated vertices dropped (n = 998)
+    ("er_998", synth.erdos_renyi(1000, 0.006, seed=6), 0.3, [10]),
     # odd n: a lane's two columns straddle n in the last block
-    ("er_999", synth.erdos_renyi(1000, 0.006, seed=6), 0.3, [10]),
+    ("reg4_999", synth.random_regular(999, 4, seed=5), 0.25, [998]),
+    # one block, smaller than the 64 x 64 block (a single diagonal block)
+    ("cycle_10", synth.cycle(10), 0.5, [3]),
+    # two block rows, the second one vertex high
+    ("cycle_65", synth.cycle(65), 0.5, [64]),
 ])
 def test_symmetric_apply_ragged_sizes(hw, name, g, gamma, marked):
     import torch
