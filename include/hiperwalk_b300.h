@@ -73,8 +73,8 @@ typedef struct hw_opts {
                                   diagonal are copied once per call into device scratch
                                   (ceil(n/64) (ceil(n/64) + 1) / 2 blocks of 32 KB, contiguous),
                                   and each application reads every block once for both
-                                  triangles (complex64, batch 1; other cases use the dense
-                                  path) */
+                                  triangles (complex64, batch 1; other cases, and a call
+                                  that cannot allocate that scratch, use the dense path) */
     int32_t tile;              /* batched Grover kernel launch shape: 0 = autotuned on the first
                                   call per (graph, dtype, batch), which then synchronises the
                                   stream once; 1..12 = register-row kernel with (rows held

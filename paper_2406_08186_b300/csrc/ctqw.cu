@@ -1243,23 +1243,32 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
     const int64_t slots = record ? steps / stride : 0;
     // the symmetric path halves the bytes read; complex128 is bound by FP64
     // arithmetic, which both paths share, so it keeps the dense path
-    const bool sym = opts && opts->u_symmetric && batch == 1 && dt == HW_C64;
+    bool sym = opts && opts->u_symmetric && batch == 1 && dt == HW_C64;
+    const int nb = int((n + kSymB - 1) / kSymB);
+    DevBuf tmp(st), recbuf(st), splane(st), packed(st);
+    if (sym) {
+        // the blocks on and above the diagonal, packed once for all applications;
+        // without room for that copy (n^2 / 2 elements) the dense path runs
+        const int64_t blocks = int64_t(nb) * (nb + 1) / 2;
+        const hw_status ps = packed.get(size_t(blocks) * kSymTileBytes, "scratch allocation (packed blocks of U)");
+        if (ps == HW_ENOMEM) {
+            hw_clear_error();
+            packed.p = nullptr;
+            sym = false;
+        } else if (ps != HW_OK) {
+            return ps;
+        } else {
+            k_sym_pack<<<unsigned(blocks), 256, 0, st>>>(static_cast<const float2 *>(U), int(n), nb,
+                                                          packed.as<float2>());
+            if ((s = hw_cuda(cudaGetLastError(), "k_sym_pack launch")) != HW_OK) return s;
+        }
+    }
     int *derr = nullptr;
     if (sym && (s = apply_error_word(&derr)) != HW_OK) return s;
-    const int nb = int((n + kSymB - 1) / kSymB);
     const size_t part_bytes = sym ? size_t(nb) * nb * kSymB * esz : 0;   // one array of block partials
     // complex128, one state, dense U: the three-product form with S = Re U + Im U
     const bool three = !sym && dt == HW_C128 && batch == 1;
-    DevBuf tmp(st), recbuf(st), splane(st), packed(st);
     if ((s = tmp.get(bytes + 2 * part_bytes + 256, "scratch allocation (state scratch)")) != HW_OK) return s;
-    if (sym) {
-        // the blocks on and above the diagonal, packed once for all applications
-        const int64_t blocks = int64_t(nb) * (nb + 1) / 2;
-        if ((s = packed.get(size_t(blocks) * kSymTileBytes, "scratch allocation (packed blocks of U)")) != HW_OK)
-            return s;
-        k_sym_pack<<<unsigned(blocks), 256, 0, st>>>(static_cast<const float2 *>(U), int(n), nb, packed.as<float2>());
-        if ((s = hw_cuda(cudaGetLastError(), "k_sym_pack launch")) != HW_OK) return s;
-    }
     if (three) {
         // S, then Re x + Im x of the two state buffers
         if ((s = splane.get((size_t(n) * size_t(n) + 2 * size_t(n)) * sizeof(double),
