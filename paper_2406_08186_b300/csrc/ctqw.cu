@@ -886,9 +886,13 @@ __global__ void __launch_bounds__(256) k_apply_sym_reduce(const void *prow_, con
     pdl_trigger();
 }
 
-// the two passes of one application; P from k_sym_pack
+// the two passes of one application; P from k_sym_pack.  The block pass
+// loads its first blocks before its dependency wait, which orders only the
+// launch before it; so the first application after the pack (first = true)
+// is launched without programmatic dependency, after the pack has completed.
 hw_status launch_apply_sym(const float2 *P, const void *x, void *y, int n, void *prow, void *pcol,
-                           const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st, int *err)
+                           const MarkedList &mk, double *rec_part, int64_t rec_slot, cudaStream_t st, int *err,
+                           bool first)
 {
     const int nb = (n + kSymB - 1) / kSymB;
     const int blocks = nb * (nb + 1) / 2;
@@ -913,8 +917,14 @@ hw_status launch_apply_sym(const float2 *P, const void *x, void *y, int n, void 
             grid = grids[dev] = sms * std::max(per, 1);
         }
     }
-    cudaError_t e = launch_pdl(k_apply_sym, dim3(std::min(grid, blocks)), dim3(kSymThreads), smem, st, P, x, n, nb,
-                               blocks, prow, pcol, err);
+    cudaError_t e;
+    if (first) {
+        k_apply_sym<<<std::min(grid, blocks), kSymThreads, smem, st>>>(P, x, n, nb, blocks, prow, pcol, err);
+        e = cudaGetLastError();
+    } else {
+        e = launch_pdl(k_apply_sym, dim3(std::min(grid, blocks)), dim3(kSymThreads), smem, st, P, x, n, nb, blocks,
+                       prow, pcol, err);
+    }
     if (e != cudaSuccess) return hw_cuda(e, "k_apply_sym launch");
     e = launch_pdl(k_apply_sym_reduce, dim3(int((int64_t(n) * kSymSub + 255) / 256)), dim3(256), 0, st,
                    (const void *)prow, (const void *)pcol, n, nb, y, mk, rec_part, rec_slot);
@@ -1308,7 +1318,8 @@ extern "C" hw_status hw_ctqw_evolve(const void *U, int64_t n, hw_dtype dt, int32
         void *dst = ((steps - k) % 2 == 0) ? P : T;
         const int64_t slot = (slots && k % stride == 0) ? k / stride - 1 : -1;
         if (sym)
-            s = launch_apply_sym(packed.as<float2>(), src, dst, int(n), prow, pcol, mk, rec_part, slot, st, derr);
+            s = launch_apply_sym(packed.as<float2>(), src, dst, int(n), prow, pcol, mk, rec_part, slot, st, derr,
+                                 k == 1);
         else if (three) {
             s = launch_apply_3m(U, splane.as<double>(), src, xsum, dst, ysum, int(n), mk, rec_part, slot, st);
             std::swap(xsum, ysum);
