@@ -531,6 +531,19 @@ hw_status hw_measure_fp64(double *ops_per_s, void *stream);
  */
 hw_status hw_measure_l2(double *gbs, void *stream);
 
+/*
+ * hw_check_device_wait -- the failure path of the device-side waits, for
+ * tests.  Launches on `stream` one CTA that takes the bounded mbarrier wait
+ * of the one-launch walks (hw_coined_evolve, launch_mode 2) on a barrier that
+ * no copy completes: after the wait's budget (2 s) it gives up and sets g's
+ * device error word, as a walk whose peer CTA never answers does.  The next
+ * hw_coined_evolve on g then returns HW_ETIMEDOUT and clears the word; the
+ * context stays usable.  The CTA occupies one SM for the budget.  Nothing
+ * faults and nothing waits without a limit.
+ * Errors: HW_EINVAL (NULL graph), HW_ECUDA.
+ */
+hw_status hw_check_device_wait(const hw_graph *g, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

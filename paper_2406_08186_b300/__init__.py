@@ -34,7 +34,7 @@ EXPORTS = ("hw_opts_init", "hw_graph_csr", "hw_graph_arcs_host", "hw_graph_free"
            "hw_server_result", "hw_server_stats", "hw_server_destroy", "hw_trim_scratch", "hw_last_error",
            "hw_version", "hw_coined_sample", "hw_ctqw_sample", "hw_graph_structure",
            "hw_graph_structure_host", "hw_measure_fp64", "hw_measure_l2",
-           "hw_graph_csr_weighted", "hw_success_curve")
+           "hw_graph_csr_weighted", "hw_success_curve", "hw_check_device_wait")
 
 
 class HWError(RuntimeError):
@@ -134,6 +134,8 @@ def lib():
         L.hw_measure_fp64.restype = st
         L.hw_measure_l2.argtypes = [ctypes.POINTER(d), P]
         L.hw_measure_l2.restype = st
+        L.hw_check_device_wait.argtypes = [P, P]
+        L.hw_check_device_wait.restype = st
         L.hw_version.argtypes = []
         L.hw_version.restype = ctypes.c_char_p
         _lib = L
@@ -215,6 +217,12 @@ def hw_measure_l2(stream=None) -> float:
     r = ctypes.c_double()
     _check(lib().hw_measure_l2(ctypes.byref(r), _stream(stream)))
     return r.value
+
+
+def hw_check_device_wait(g: Graph, stream=None):
+    """Run the one-launch walk's bounded device wait on a barrier nothing completes (about 2 s);
+    the next hw_coined_evolve on g reports HW_ETIMEDOUT."""
+    _check(lib().hw_check_device_wait(g, _stream(stream)))
 
 
 def hw_version() -> str:

@@ -282,6 +282,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_coined_cluster(ClusterArgs a
     cluster_barrier();
 }
 
+// The walk's bounded wait on an mbarrier whose expected bytes no copy
+// delivers: the wait gives up after kWaitNs and the kernel sets the error
+// word, exactly as a walk whose peer never answers does (no copy is in
+// flight, so the CTA may exit with the phase open).
+__global__ void k_wait_check(int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        const uint32_t b = smem_addr(&bar);
+        mbar_init(b, 1);
+        mbar_expect(b, 16);
+        if (!mbar_wait(b, 0)) atomicExch(err, 1);
+    }
+}
+
 // the kernel attributes (shared-memory limit kSmemLimit, non-portable
 // cluster size), set once per kernel and device: a walk of 100 steps takes
 // about 90 us, and two driver calls per launch are a visible part of that
@@ -443,4 +458,13 @@ hw_status launch_coined_cluster(const hw_graph *g, hw_dtype dt, const void *in, 
     const cudaError_t e = (dt == HW_C128) ? launch_deg<double>(g->max_degree, a, ctas, threads, smem, st)
                                           : launch_deg<float>(g->max_degree, a, ctas, threads, smem, st);
     return hw_cuda(e, "k_coined_cluster launch");
+}
+
+extern "C" hw_status hw_check_device_wait(const hw_graph *g, void *stream)
+{
+    hw_clear_error();
+    if (!g) return hw_fail(HW_EINVAL, "graph is NULL");
+    if (!g->d_err) return hw_fail(HW_EINVAL, "graph has no device error word");
+    k_wait_check<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(g->d_err);
+    return hw_cuda(cudaGetLastError(), "k_wait_check launch");
 }
