@@ -507,6 +507,17 @@ def sub_torus64(hw, reps, warmup, with_cpu):
         p_ref = oracle.prob_coined(ar, ref)
         res["cpu_baseline"] = {"value": arcs * 100 / el, "unit": UNIT, "cores": _oracle_cores(), "kind": "oracle",
                                "sample": "the whole 100-step run"}
+        # the same run on one host core
+        all_cores = oracle.threads()
+        oracle.threads(1)
+        try:
+            t0 = time.perf_counter()
+            oracle.coined_evolve(ar, psi0_h, 100)
+            el1 = time.perf_counter() - t0
+        finally:
+            oracle.threads(all_cores)
+        res["cpu_baseline_one_core"] = {"value": arcs * 100 / el1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                        "sample": "the whole 100-step run"}
         res["error_vs_oracle"] = {"c128_max_abs_psi": float(np.max(np.abs(out.cpu().numpy() - ref))),
                                   "c128_max_abs_p": float(np.max(np.abs(prob.cpu().numpy() - p_ref)))}
     G.free()
