@@ -41,14 +41,14 @@ def gpu_expm(hw, g, gamma, marked, t, dt=2, opts=None, powers=2):
     return G, U
 
 
-def gpu_evolve(hw, U, psi0, steps, marked, dt=2, batch=1, record=True):
+def gpu_evolve(hw, U, psi0, steps, marked, dt=2, batch=1, record=True, opts=None):
     import torch
     n = U.shape[0]
     cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
     x = torch.from_numpy(np.ascontiguousarray(psi0)).to("cuda", cdt)
     out = torch.empty_like(x)
     rec = torch.empty(steps * batch, dtype=torch.float64, device="cuda") if record else None
-    hw.hw_ctqw_evolve(U, n, dt, batch, steps, x, out, list(marked), rec)
+    hw.hw_ctqw_evolve(U, n, dt, batch, steps, x, out, list(marked), rec, opts=opts)
     prob = torch.empty(n * batch, dtype=torch.float64, device="cuda")
     norm = torch.empty(batch, dtype=torch.float64, device="cuda")
     hw.hw_probability(None, n, dt, batch, out, prob, norm)
@@ -244,10 +244,12 @@ def test_evolve_batched_and_in_place(hw):
     G.free()
 
 
-@pytest.mark.parametrize("powers", POWERS)
+@pytest.mark.parametrize("powers,sym", [(p, 0) for p in POWERS] + [(0, 1)])
 @pytest.mark.parametrize("dt", [2, 1])
-def test_config3_hypercube12_search_full_size(hw, dt, powers):
-    # Q_12, gamma = 1/12, one seeded mark, dt = 0.1, uniform start, 2000 applications.
+def test_config3_hypercube12_search_full_size(hw, dt, powers, sym):
+    # Q_12, gamma = 1/12, one seeded mark, dt = 0.1, uniform start, 2000
+    # applications; sym = 1: the applications read one triangle of U (packed),
+    # as the benchmark's complex64 evolve does (complex128 keeps the dense form)
     k, gamma, tstep, steps = 12, 1 / 12, 0.1, 2000
     g = synth.hypercube(k)
     N = 1 << k
@@ -258,7 +260,7 @@ def test_config3_hypercube12_search_full_size(hw, dt, powers):
     refU = oracle.ctqw_columns(ar, gamma, tstep, cols, marked=[m])
     Uc = U[:, torch_index(cols)].cpu().numpy()
     psi0 = synth.uniform_state(N)
-    psi, rec, prob, norm = gpu_evolve(hw, U, psi0, steps, [m], dt=dt)
+    psi, rec, prob, norm = gpu_evolve(hw, U, psi0, steps, [m], dt=dt, opts={"u_symmetric": sym})
     ref, rec_ref = oracle.ctqw_evolve(ar, gamma, psi0, tstep, steps, marked=[m], record=True)
     if dt == 2:
         assert np.max(np.abs(Uc - refU)) <= TOL128
@@ -300,8 +302,8 @@ def _hamming_reduction(k, gamma, m_steps, tstep, m):
     return np.abs(amp0) ** 2, prob
 
 
-@pytest.mark.parametrize("dt", [2, 1])
-def test_config3_critical_gamma_against_hamming_reduction(hw, dt):
+@pytest.mark.parametrize("dt,sym", [(2, 0), (1, 0), (1, 1)])
+def test_config3_critical_gamma_against_hamming_reduction(hw, dt, sym):
     # configuration 3 at the critical gamma_c = sum_r C(k, r)/r / (2N) of Q_12
     # (0.09298...; 1/12 is off-critical): the marked probability rises to about
     # 0.84 near t = 108 instead of peaking at 0.078; the recorded curve of all
@@ -313,7 +315,7 @@ def test_config3_critical_gamma_against_hamming_reduction(hw, dt):
     g = synth.hypercube(k)
     m = synth.seeded_vertex(3, N)
     G, U = gpu_expm(hw, g, gamma, [m], tstep, dt=dt, powers=0)
-    _, rec, prob, norm = gpu_evolve(hw, U, synth.uniform_state(N), steps, [m], dt=dt)
+    _, rec, prob, norm = gpu_evolve(hw, U, synth.uniform_state(N), steps, [m], dt=dt, opts={"u_symmetric": sym})
     ref, prob_ref = _hamming_reduction(k, gamma, steps, tstep, m)
     if dt == 2:
         assert np.max(np.abs(rec - ref)) <= TOL128
