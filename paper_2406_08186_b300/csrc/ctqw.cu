@@ -762,11 +762,18 @@ __global__ void __launch_bounds__(kSymThreads) k_apply_sym(const float2 *__restr
         const int r0 = I * kSymB + 8 * w, c0 = J * kSymB + 2 * l;
         // x_J at this lane's two columns, x_I at this warp's eight rows (zero
         // past n, where the packed block is zero)
-        const float2 xa = (c0 < n) ? __ldg(x + c0) : zero;
-        const float2 xb = (c0 + 1 < n) ? __ldg(x + c0 + 1) : zero;
-        float2 xi[8];
+        float2 xa, xb, xi[8];
+        if ((J + 1) * kSymB <= n) {   // block inside n (uniform): no guards
+            xa = __ldg(x + c0);
+            xb = __ldg(x + c0 + 1);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) xi[i] = (r0 + i < n) ? __ldg(x + r0 + i) : zero;
+            for (int i = 0; i < 8; ++i) xi[i] = __ldg(x + r0 + i);
+        } else {
+            xa = (c0 < n) ? __ldg(x + c0) : zero;
+            xb = (c0 + 1 < n) ? __ldg(x + c0 + 1) : zero;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) xi[i] = (r0 + i < n) ? __ldg(x + r0 + i) : zero;
+        }
         if (t == 0 && !sym_wait(sym_smem_addr(&bars[stage]), uint32_t((k / kSymStages) & 1))) {
             failed = 1;
             atomicExch(err, 1);
