@@ -666,7 +666,12 @@ __device__ __forceinline__ void sym_block_ij(int b, int nb, int &I, int &J)
     J = i + int(b - sym_row_start(i, nb));
 }
 
-// one CTA per upper block b (row-major over the upper triangle)
+// one CTA per upper block b (row-major over the upper triangle).  Within a
+// packed row, columns 4g and 4g + 1 come first (positions 2g, 2g + 1), then
+// columns 4g + 2 and 4g + 3 (positions 32 + 2g, 32 + 2g + 1): the block pass
+// reads a row's column pairs as 16-byte vectors, 16 lanes side by side
+__device__ __forceinline__ int sym_col_pos(int c) { return ((c & 2) << 4) + ((c >> 2) << 1) + (c & 1); }
+
 __global__ void __launch_bounds__(256) k_sym_pack(const float2 *__restrict__ U, int n, int nb,
                                                   float2 *__restrict__ P)
 {
@@ -676,20 +681,22 @@ __global__ void __launch_bounds__(256) k_sym_pack(const float2 *__restrict__ U, 
     float2 *__restrict__ dst = P + int64_t(blockIdx.x) * kSymB * kSymB;
     for (int e = threadIdx.x; e < kSymB * kSymB; e += blockDim.x) {
         const int r = e / kSymB, c = e % kSymB;
-        dst[e] = (r0 + r < n && c0 + c < n) ? U[int64_t(r0 + r) * n + c0 + c] : make_float2(0.f, 0.f);
+        dst[r * kSymB + sym_col_pos(c)] =
+            (r0 + r < n && c0 + c < n) ? U[int64_t(r0 + r) * n + c0 + c] : make_float2(0.f, 0.f);
     }
 }
 
 // The block pass, a persistent kernel: each CTA walks the packed blocks
 // b = blockIdx.x, + gridDim.x, ... through two 32 KB stages, the next block
-// arriving (one cp.async.bulk) while the current one is summed.  Warp w holds
-// rows 8w..8w+7 of the block and lane l columns 2l and 2l+1: a warp reads 512
-// contiguous bytes of a row at a time, and each element is read from shared
-// memory once and used for both sums, its row's (with x_J) and its column's
-// (with x_I).  Row sums over the 32 lanes: a fixed halving butterfly.  Column
-// sums over the 8 warps: added in warp order through shared memory.
+// arriving (one cp.async.bulk) while the current one is summed.  128 threads
+// per block: half-warp h of warp w holds rows 16w + 8h .. 16w + 8h + 7, lane
+// l of it columns 4l .. 4l + 3 (32 elements a thread, each read from shared
+// memory once, as two 16-byte vectors per row, and used for both sums: its
+// row's with x_J and its column's with x_I).  Row sums over the 16 lanes of a
+// half-warp: a fixed halving butterfly.  Column sums: one halving step across
+// the two half-warps, then the 4 warps added in order through shared memory.
 constexpr int kSymStages = 2;
-constexpr int kSymThreads = 256;
+constexpr int kSymThreads = 128;
 constexpr uint64_t kSymWaitNs = 2000000000ull;   // bounded stage waits (2 s)
 
 __device__ __forceinline__ uint32_t sym_smem_addr(const void *p)
@@ -728,27 +735,37 @@ __device__ __forceinline__ void sym_issue(const float2 *P, int b, uint32_t dst, 
                  : "memory");
 }
 
+// acc += u x (complex, one rounding per fma: re then im)
+__device__ __forceinline__ void cmac(float &re, float &im, float ux, float uy, float2 v)
+{
+    re = fmaf(ux, v.x, fmaf(-uy, v.y, re));
+    im = fmaf(ux, v.y, fmaf(uy, v.x, im));
+}
+
 __global__ void __launch_bounds__(kSymThreads) k_apply_sym(const float2 *__restrict__ P, const void *x_, int n,
                                                            int nb, int nblocks, void *prow_, void *pcol_, int *err)
 {
     extern __shared__ __align__(128) unsigned char sym_tma_smem[];
-    float2(*tile)[kSymB][kSymB] = reinterpret_cast<float2(*)[kSymB][kSymB]>(sym_tma_smem);   // [stage][row][col]
-    __shared__ float4 cpart[kSymThreads / 32][32];   // [warp][lane]: columns 2l, 2l+1 over the warp's rows
+    // [stage][row * 32 + k]: float4 k < 16 holds columns 4k, 4k + 1; 16 + k columns 4k + 2, 4k + 3
+    float4(*tile)[kSymB * kSymB / 2] = reinterpret_cast<float4(*)[kSymB * kSymB / 2]>(sym_tma_smem);
+    __shared__ float4 cpart[kSymThreads / 32][32];   // [warp][lane]: two columns over the warp's 16 rows
     __shared__ __align__(8) uint64_t bars[kSymStages];
     __shared__ int failed;
     const float2 *__restrict__ x = static_cast<const float2 *>(x_);
     float *__restrict__ prow = static_cast<float *>(prow_);   // the complex partials as (re, im) floats
     float4 *__restrict__ pcol = static_cast<float4 *>(pcol_);  // two complex partials per float4
     const int t = threadIdx.x, w = t >> 5, l = t & 31;
+    const int hg = l >> 4, cg = l & 15;      // half-warp (8 rows) and column group (4 columns)
+    const int rbase = 16 * w + 8 * hg;       // this thread's first row in the block
     if (t == 0) {
         failed = 0;
         for (int k = 0; k < kSymStages; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sym_smem_addr(&bars[k])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // U does not change between applications: the first tiles load before the wait
+        // U does not change between applications: the first blocks load before the wait
         for (int k = 0; k < kSymStages; ++k) {
             const int b = blockIdx.x + k * gridDim.x;
-            if (b < nblocks) sym_issue(P, b, sym_smem_addr(&tile[k][0][0]), sym_smem_addr(&bars[k]));
+            if (b < nblocks) sym_issue(P, b, sym_smem_addr(&tile[k][0]), sym_smem_addr(&bars[k]));
         }
     }
     __syncthreads();
@@ -759,18 +776,18 @@ __global__ void __launch_bounds__(kSymThreads) k_apply_sym(const float2 *__restr
         const int stage = k % kSymStages;
         int I, J;
         sym_block_ij(b, nb, I, J);
-        const int r0 = I * kSymB + 8 * w, c0 = J * kSymB + 2 * l;
-        // x_J at this lane's two columns, x_I at this warp's eight rows (zero
-        // past n, where the packed block is zero)
-        float2 xa, xb, xi[8];
+        const int r0 = I * kSymB + rbase, c0 = J * kSymB + 4 * cg;
+        // x_J at this thread's four columns, x_I at its eight rows (zero past
+        // n, where the packed block is zero)
+        float2 xj[4], xi[8];
         if ((J + 1) * kSymB <= n) {   // block inside n (uniform): no guards
-            xa = __ldg(x + c0);
-            xb = __ldg(x + c0 + 1);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xj[j] = __ldg(x + c0 + j);
 #pragma unroll
             for (int i = 0; i < 8; ++i) xi[i] = __ldg(x + r0 + i);
         } else {
-            xa = (c0 < n) ? __ldg(x + c0) : zero;
-            xb = (c0 + 1 < n) ? __ldg(x + c0 + 1) : zero;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xj[j] = (c0 + j < n) ? __ldg(x + c0 + j) : zero;
 #pragma unroll
             for (int i = 0; i < 8; ++i) xi[i] = (r0 + i < n) ? __ldg(x + r0 + i) : zero;
         }
@@ -780,25 +797,31 @@ __global__ void __launch_bounds__(kSymThreads) k_apply_sym(const float2 *__restr
         }
         __syncthreads();
         if (failed) break;   // uniform: the stage never filled
-        const float4 *sU = reinterpret_cast<const float4 *>(&tile[stage][0][0]);
-        float rs[16];   // rs[2i], rs[2i+1]: row 8w+i over columns 2l, 2l+1 (re, im)
-        float cax = 0.f, cay = 0.f, cbx = 0.f, cby = 0.f;   // columns 2l, 2l+1 over rows 8w..8w+7
+        const float4 *sU = tile[stage];
+        float rs[16];                       // rs[2i], rs[2i+1]: row rbase + i over the 4 columns (re, im)
+        float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // column 4cg + j over the 8 rows
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float4 u = sU[(8 * w + i) * (kSymB / 2) + l];   // U[r][2l] = (u.x, u.y), U[r][2l+1] = (u.z, u.w)
-            rs[2 * i] = fmaf(u.x, xa.x, fmaf(-u.y, xa.y, fmaf(u.z, xb.x, -u.w * xb.y)));
-            rs[2 * i + 1] = fmaf(u.x, xa.y, fmaf(u.y, xa.x, fmaf(u.z, xb.y, u.w * xb.x)));
-            cax = fmaf(u.x, xi[i].x, fmaf(-u.y, xi[i].y, cax));
-            cay = fmaf(u.x, xi[i].y, fmaf(u.y, xi[i].x, cay));
-            cbx = fmaf(u.z, xi[i].x, fmaf(-u.w, xi[i].y, cbx));
-            cby = fmaf(u.z, xi[i].y, fmaf(u.w, xi[i].x, cby));
+            const float4 ua = sU[(rbase + i) * 32 + cg];        // columns 4cg, 4cg + 1
+            const float4 ub = sU[(rbase + i) * 32 + 16 + cg];   // columns 4cg + 2, 4cg + 3
+            float re = 0.f, im = 0.f;
+            cmac(re, im, ua.x, ua.y, xj[0]);
+            cmac(re, im, ua.z, ua.w, xj[1]);
+            cmac(re, im, ub.x, ub.y, xj[2]);
+            cmac(re, im, ub.z, ub.w, xj[3]);
+            rs[2 * i] = re;
+            rs[2 * i + 1] = im;
+            cmac(cs[0], cs[1], ua.x, ua.y, xi[i]);
+            cmac(cs[2], cs[3], ua.z, ua.w, xi[i]);
+            cmac(cs[4], cs[5], ub.x, ub.y, xi[i]);
+            cmac(cs[6], cs[7], ub.z, ub.w, xi[i]);
         }
-        // halving butterfly: at offset o each lane keeps the half of its values
-        // that its bit o selects and adds the partner's copy of that half; after
-        // offsets 16, 8, 4, 2 lane l holds value l >> 1 summed over 16 lanes, and
-        // offset 1 completes the sum over all 32
+        // rows: halving butterfly over the half-warp's 16 lanes; at offset o a
+        // lane keeps the half of its values that its bit o selects and adds
+        // the partner's copy of that half, so after offsets 8, 4, 2, 1 lane cg
+        // holds value cg: row rbase + (cg >> 1), component cg & 1
 #pragma unroll
-        for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        for (int h = 8, o = 8; h >= 1; h >>= 1, o >>= 1) {
             const bool up = (l & o) != 0;
 #pragma unroll
             for (int q = 0; q < h; ++q) {
@@ -807,18 +830,24 @@ __global__ void __launch_bounds__(kSymThreads) k_apply_sym(const float2 *__restr
                 rs[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
             }
         }
-        rs[0] += __shfl_xor_sync(0xffffffffu, rs[0], 1);
-        // value l >> 1 is row 8w + (l >> 2), component (l >> 1) & 1
-        if ((l & 1) == 0) prow[((int64_t(I) * nb + J) * kSymB + 8 * w + (l >> 2)) * 2 + ((l >> 1) & 1)] = rs[0];
-        cpart[w][l] = make_float4(cax, cay, cbx, cby);
+        prow[((int64_t(I) * nb + J) * kSymB + rbase + (cg >> 1)) * 2 + (cg & 1)] = rs[0];
+        // columns: the two half-warps, then the warps; half-warp hg keeps
+        // columns 4cg + 2hg and 4cg + 2hg + 1
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float keep = hg ? cs[q + 4] : cs[q];
+            const float send = hg ? cs[q] : cs[q + 4];
+            cs[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+        cpart[w][l] = make_float4(cs[0], cs[1], cs[2], cs[3]);
         __syncthreads();   // the stage and cpart are read and written
         if (t == 0) {
             const int bn = b + kSymStages * gridDim.x;
             // order the generic reads of the stage before the async-proxy refill
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (bn < nblocks) sym_issue(P, bn, sym_smem_addr(&tile[stage][0][0]), sym_smem_addr(&bars[stage]));
+            if (bn < nblocks) sym_issue(P, bn, sym_smem_addr(&tile[stage][0]), sym_smem_addr(&bars[stage]));
         }
-        if (w == 0 && I != J) {   // column sums of the block, the 8 warps added in order
+        if (w == 0 && I != J) {   // column sums of the block, the 4 warps added in order
             float4 c = cpart[0][l];
 #pragma unroll
             for (int v = 1; v < kSymThreads / 32; ++v) {
@@ -828,7 +857,7 @@ __global__ void __launch_bounds__(kSymThreads) k_apply_sym(const float2 *__restr
                 c.z += d.z;
                 c.w += d.w;
             }
-            pcol[((int64_t(J) * nb + I) * kSymB) / 2 + l] = c;
+            pcol[((int64_t(J) * nb + I) * kSymB) / 2 + 2 * cg + hg] = c;
         }
         // cpart is written again only after the next tile's barrier, which warp 0 reaches after reading it
     }
