@@ -273,6 +273,31 @@ def test_config3_hypercube12_search_full_size(hw, dt, powers, sym):
     G.free()
 
 
+@pytest.mark.parametrize("dt,powers", [(2, 0), (2, 1), (1, 0), (1, 2)])
+def test_expm_whole_matrix_probes(hw, dt, powers):
+    # U of configuration 3 (Q_12, gamma = 1/12, one mark, dt = 0.1) checked as
+    # a whole matrix, not column by column: U x for two seeded random states
+    # against the oracle's sparse series applied to x (Freivalds-style
+    # probes), and unitarity on the same probes, U^dagger (U x) = x with
+    # |U x| = |x|; the products are taken on the host in double
+    k, gamma, tstep = 12, 1 / 12, 0.1
+    g = synth.hypercube(k)
+    N = 1 << k
+    m = synth.seeded_vertex(3, N)
+    G, U = gpu_expm(hw, g, gamma, [m], tstep, dt=dt, powers=powers)
+    Uh = U.cpu().numpy().astype(np.complex128)
+    G.free()
+    ar = oracle.Arcs(*g)
+    tol = TOL128 if dt == 2 else 1e-5
+    for seed in (21, 22):
+        x = synth.random_state(N, seed=seed)
+        y = Uh @ x
+        ref = oracle.ctqw_action(ar, gamma, tstep, x, marked=[m])
+        assert np.max(np.abs(y - ref)) <= tol
+        assert np.max(np.abs(Uh.conj().T @ y - x)) <= tol
+        assert abs(np.linalg.norm(y) - np.linalg.norm(x)) <= tol
+
+
 @pytest.mark.parametrize("powers", [1, 2])
 def test_expm_rejects_bad_tile_form(hw, powers):
     # hw_opts.gemm_tiles is 0..2 whatever form the powers take
