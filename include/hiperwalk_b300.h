@@ -151,8 +151,9 @@ hw_status hw_graph_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx
  *            be Hermitian, W[v][u] == conj(W[u][v]) exactly
  * Weights must be finite; a zero weight keeps its arc in the basis.  The
  * structure rules and the arc basis are those of hw_graph_csr.  Weighted
- * graphs serve hw_ctqw_plan, hw_ctqw_expm (real W only: a complex W gives
- * HW_EUNSUPPORTED) and hw_ctqw_evolve_sparse (real or complex W); coined walks
+ * graphs serve hw_ctqw_plan, hw_ctqw_expm and hw_ctqw_evolve_sparse (real or
+ * complex W; hw_ctqw_expm forms the U of a complex W by the sparse series on
+ * the identity's columns); coined walks
  * and served jobs need an unweighted graph (HW_EINVAL / HW_EUNSUPPORTED).
  * Errors: as hw_graph_csr, plus HW_EINVAL for w_re NULL, a non-finite weight
  * or a W that is not symmetric / Hermitian.
@@ -277,6 +278,10 @@ hw_status hw_coined_sample(const hw_graph *g, hw_coin coin, const int32_t *marke
  *            form (dense FP64 GEMMs for HW_C128, sparse x dense products in
  *            float for HW_C64).  Taylor sums and squarings in double; U
  *            rounded to complex64 at the end for HW_C64.
+ *   A graph with complex (Hermitian) weights has complex powers of H: U is
+ *   then e^{-i H time} applied by hw_ctqw_evolve_sparse's series to all the
+ *   columns of the identity at once (batch n), in dt's precision; scratch
+ *   five n x n complex buffers.
  * Scratch: four or five n x n real buffers from the stream-ordered allocator.
  * On the tensor-core path the call synchronises `stream` before returning,
  * to report a device-side pipeline timeout of that kernel as HW_ETIMEDOUT.

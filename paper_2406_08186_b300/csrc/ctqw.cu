@@ -1022,6 +1022,21 @@ extern "C" hw_status hw_ctqw_plan(const hw_graph *g, double gamma, const int32_t
     return HW_OK;
 }
 
+namespace {
+// I[v][v] = 1 in a zeroed n x n complex matrix
+template <typename V>
+__global__ void k_unit_diagonal(V *__restrict__ I, int64_t n)
+{
+    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v < n) {
+        V one;
+        one.x = 1;
+        one.y = 0;
+        I[v * n + v] = one;
+    }
+}
+}  // namespace
+
 extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t *marked,
                                   int32_t n_marked, double time, hw_dtype dt, void *U_out,
                                   const hw_opts *opts, void *stream)
@@ -1034,14 +1049,32 @@ extern "C" hw_status hw_ctqw_expm(const hw_graph *g, double gamma, const int32_t
     if (!std::isfinite(gamma) || !std::isfinite(time)) return hw_fail(HW_EINVAL, "gamma/time not finite");
     if (n_marked < 0 || (n_marked > 0 && !marked)) return hw_fail(HW_EINVAL, "bad marked list");
     if (g->n > 32768) return hw_fail(HW_EUNSUPPORTED, "dense U limited to n <= 32768 (n = %lld)", (long long)g->n);
-    if (g->complex_weights)
-        return hw_fail(HW_EUNSUPPORTED, "the dense U takes a real symmetric W; complex weights run through "
-                                        "hw_ctqw_evolve_sparse");
     int dev = -1;
     hw_status s = hw_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (s != HW_OK) return s;
     if (dev != g->device) return hw_fail(HW_EINVAL, "graph lives on device %d, current is %d", g->device, dev);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (g->complex_weights) {
+        // a complex Hermitian W: the powers of H are complex, so U is
+        // e^{-iH time} applied by the sparse series to every column of the
+        // identity at once (batch n; the [vertex][column] states are U row-major)
+        const int64_t nn = g->n;
+        const size_t bytes = size_t(nn) * size_t(nn) * cplx_bytes(dt);
+        void *eye = nullptr;
+        if ((s = hw_cuda(hw_malloc_async(&eye, bytes, st), "scratch allocation (identity)")) != HW_OK) return s;
+        s = hw_cuda(cudaMemsetAsync(eye, 0, bytes, st), "clear the identity");
+        if (s == HW_OK) {
+            const unsigned grid = unsigned((nn + 255) / 256);
+            if (dt == HW_C128) k_unit_diagonal<double2><<<grid, 256, 0, st>>>(static_cast<double2 *>(eye), nn);
+            else k_unit_diagonal<float2><<<grid, 256, 0, st>>>(static_cast<float2 *>(eye), nn);
+            s = hw_cuda(cudaGetLastError(), "k_unit_diagonal launch");
+        }
+        if (s == HW_OK)
+            s = hw_ctqw_evolve_sparse(g, gamma, marked, n_marked, time, dt, int32_t(nn), 1, eye, U_out, nullptr, opts,
+                                      stream);
+        cudaFreeAsync(eye, st);
+        return s;
+    }
     const int n = int(g->n);
     MarkedList mk;
     if ((s = make_marked(marked, n_marked, g->n, st, &mk)) != HW_OK) return s;

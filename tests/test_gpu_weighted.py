@@ -2,8 +2,9 @@
 H = -gamma W - sum_m |m><m| (Sec. 3.1 with A generalised to a Hermitian W),
 against the FP64 oracle: the sparse-action series (real and complex W, one and
 several columns, records), the dense U (real symmetric W, complex128 and the
-complex64 tensor-core path), the flux ring's closed form, and the calls that
-a weighted graph does not take.
+complex64 tensor-core path; complex W through the sparse series on the
+identity's columns), the flux ring's closed form, and the calls that a
+weighted graph does not take.
 
 Tolerances: complex128 max-abs <= 1e-12; complex64 probability L1 <= 1e-3
 (sparse series) and entry-wise 2e-6 (dense U, as the unweighted tests).
@@ -128,6 +129,39 @@ def test_dense_expm_real_weights(hw, name, g, gamma, marked, t):
     G.free()
 
 
+@pytest.mark.parametrize("name,g,gamma,marked,t", [
+    ("Q6", synth.hypercube(6), 1 / 6, [5], 1.0),
+    ("er300", synth.erdos_renyi(300, 0.03, seed=4), 0.3, [0, 17], 0.5),
+    ("torus37x53", synth.torus_rect(37, 53), 0.25, [100], 0.7),
+])
+def test_dense_expm_complex_weights(hw, name, g, gamma, marked, t):
+    # a complex Hermitian W: the dense U (formed by the sparse series on the
+    # identity's columns) against the oracle's columns, U unitary
+    # (U^dagger U = I), and the dense application of U against the sparse series
+    torch = _torch()
+    n, eu, ev = g
+    we = synth.edge_weights(eu.size, seed=9, complex_phase=True)
+    G = _wgraph(hw, g, we)
+    ar = oracle.Arcs(n, eu, ev)
+    w = ar.weights(eu, ev, we)
+    cols = np.unique(np.array([0, 1, 130, 257, n // 2, n - 2, n - 1]) % n)
+    ref = oracle.ctqw_columns(ar, gamma, t, cols, marked=marked, weights=w)
+    psi0 = synth.random_state(n, seed=4)
+    for dt, tol in ((hw.HW_C128, TOL128), (hw.HW_C64, 2e-6)):
+        cdt = torch.complex128 if dt == hw.HW_C128 else torch.complex64
+        U = torch.empty((n, n), dtype=cdt, device="cuda")
+        hw.hw_ctqw_expm(G, gamma, marked, t, dt, U)
+        Uh = U.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(Uh[:, cols] - ref)) <= tol, dt
+        assert np.max(np.abs(Uh.conj().T @ Uh - np.eye(n))) <= 50 * tol
+        x = torch.from_numpy(psi0).to("cuda", cdt)
+        y = torch.empty_like(x)
+        hw.hw_ctqw_evolve(U, n, dt, 1, 3, x, y, [], None)
+        sp, _ = _sparse(hw, G, gamma, marked, t, dt, 3, psi0)
+        assert np.max(np.abs(y.cpu().numpy().astype(np.complex128) - sp)) <= 10 * tol
+    G.free()
+
+
 def test_plan_uses_the_weights(hw):
     g = synth.erdos_renyi(500, 0.02, seed=3)
     n, eu, ev = g
@@ -151,10 +185,6 @@ def test_weighted_graph_refusals(hw):
     g = synth.torus_rect(5, 6)
     n, eu, ev = g
     G = _wgraph(hw, g, synth.edge_weights(eu.size, seed=1, complex_phase=True))
-    U = torch.empty((n, n), dtype=torch.complex128, device="cuda")
-    with pytest.raises(hw.HWError) as e:
-        hw.hw_ctqw_expm(G, 0.5, [], 0.1, hw.HW_C128, U)
-    assert e.value.status == hw.HW_EUNSUPPORTED
     x = torch.zeros(G.num_arcs, dtype=torch.complex128, device="cuda")
     with pytest.raises(hw.HWError) as e:
         hw.hw_coined_evolve(G, 0, [], hw.HW_C128, 1, 3, x, torch.empty_like(x))
